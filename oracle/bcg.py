@@ -1,0 +1,164 @@
+"""Block CG with adaptive residual re-orthonormalisation, plain FP64 (Ch. 4).
+
+``bcg`` follows Alg. "bcgaro" (BCG-ARO, Ch. 4.3) in the grouping of
+Alg. "2R-CG" (Ch. 8.1), which the thesis states is arithmetically identical.
+M = I throughout (no preconditioner), so Z = R-bar.
+
+Readings (the thesis is silent or ambiguous here):
+  * residual R = B - A X (the algorithms' sign; Ch. 4.1);
+  * convergence: max over columns of ||R_i|| / ||R^0_i|| <= tol (the thesis
+    uses the max-column norm, Ch. 4.1; "relative" is our reading).  Columns
+    with ||R^0_i|| = 0 count as converged;
+  * re-orthonormalisation criterion: see ``blockops.reortho_decision``;
+  * ||R_i|| = ||R-bar sigma_i||: with re-orthonormalisation this is the column
+    norm of sigma (the thesis prints Q^k, meaning R-bar^k); without it,
+    sqrt((sigma^T rho sigma)_ii), which needs no extra pass since M = I;
+  * beta = rho_k^{-1} gamma^T rho_{k+1} as printed in Alg. "bcgro";
+  * alpha and rho are formed as upper triangles and mirrored;
+  * breakdown (Cholesky of alpha or rho fails) stops with the current X.
+
+Test infrastructure only (see the package docstring).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .blockops import (Breakdown, chol_solve, col_norms, gram, kappa_d, normalizer,
+                       project_subalgebra, reortho_decision, spmm)
+
+
+@dataclass
+class BCGResult:
+    X: np.ndarray
+    iters: int
+    reorths: int
+    converged: bool
+    status: str                      # "ok", "not_converged", "breakdown"
+    relres: np.ndarray               # final per-column relative residual (from sigma/rho)
+    history: list = field(default_factory=list)    # max relative residual per iteration
+    decisions: list = field(default_factory=list)  # re-orthonormalised in iteration k?
+    iterates: list = field(default_factory=list)   # X^{k+1} for the first record_iterates steps
+
+
+def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit: int = 1000,
+        eta: float = math.inf, p: int | None = None, forced=None, record_iterates: int = 0,
+        dtype=np.float64, eps: float | None = None, apply_A=None) -> BCGResult:
+    """Alg. "bcgaro" (2R grouping, Alg. "2R-CG") for A X = B, M = I.
+
+    A: CSR (attributes n, row_ptr, col, val) or None when ``apply_A`` is given.
+    p: block size of the *-subalgebra S_BP^p (None or s: block case S_B).
+    forced: optional sequence of booleans replacing the adaptive criterion
+        in iteration k (used to replay another implementation's decisions).
+    dtype: arithmetic of the n x s blocks (float32 for the inner solve of
+        iterative refinement); all s x s quantities stay float64.
+    """
+    B = np.asarray(B)
+    n, s = B.shape
+    if eps is None:
+        eps = float(np.finfo(dtype).eps)
+    op = apply_A if apply_A is not None else (lambda V: spmm(A, V, dtype=dtype))
+    X = np.zeros((n, s), dtype=dtype) if X0 is None else np.array(X0, dtype=dtype, copy=True)
+    B = B.astype(dtype, copy=False)
+
+    R = B - op(X)
+    n0 = col_norms(R)
+    n0_safe = np.where(n0 > 0, n0, 1.0)
+    if eta > 0:
+        Rb, sigma = normalizer(R, p)
+        Rb = Rb.astype(dtype)
+    else:
+        Rb, sigma = R, np.eye(s)
+    P = Rb.copy()
+    rho = gram(Rb, Rb, p)
+    res = _resid_from(sigma, rho, p, reortho=False)
+    relres = np.where(n0 > 0, res / n0_safe, 0.0)
+    out = BCGResult(X, 0, 0, bool(relres.max(initial=0.0) <= tol), "ok", relres)
+    if out.converged:
+        return out
+    for k in range(maxit):
+        Q = op(P)
+        alpha = gram(P, Q, p)
+        try:
+            lam = chol_solve(alpha, rho)
+        except Breakdown:
+            out.status = "breakdown"; out.iters = k; return out
+        lam = project_subalgebra(lam, p)
+        if forced is not None and k < len(forced):
+            reo = bool(forced[k])
+        else:
+            reo = reortho_decision(eta, alpha, eps)
+        # X^{k+1} = X^k + P^k lambda^k sigma^k (uses the old sigma)
+        X += P @ (lam @ sigma).astype(dtype)
+        Rt = Rb - Q @ lam.astype(dtype)
+        if reo:
+            Rb, gamma = normalizer(Rt, p)
+            Rb = Rb.astype(dtype)
+            sigma = gamma @ sigma
+            out.reorths += 1
+        else:
+            Rb, gamma = Rt, np.eye(s)
+        rho_new = gram(Rb, Rb, p)
+        res = _resid_from(sigma, rho_new, p, reortho=reo)
+        relres = np.where(n0 > 0, res / n0_safe, 0.0)
+        out.history.append(float(relres.max(initial=0.0)))
+        out.decisions.append(reo)
+        if k < record_iterates:
+            out.iterates.append(X.copy())
+        out.iters = k + 1
+        out.relres = relres
+        if relres.max(initial=0.0) <= tol:
+            out.converged = True
+            return out
+        try:
+            beta = chol_solve(rho, gamma.T @ rho_new)
+        except Breakdown:
+            out.status = "breakdown"; return out
+        beta = project_subalgebra(beta, p)
+        P = Rb + P @ beta.astype(dtype)
+        rho = rho_new
+    out.status = "not_converged"
+    return out
+
+
+def _resid_from(sigma, rho, p, reortho):
+    """Column norms of the true residual R = R-bar sigma (Ch. 4.3, after Alg. "bcgro")."""
+    if reortho:
+        return col_norms(sigma)
+    M = project_subalgebra(sigma.T @ rho @ sigma, p)
+    return np.sqrt(np.maximum(np.diag(M), 0.0))
+
+
+def scalar_cg(A, b: np.ndarray, x0=None, tol: float = 1e-8, maxit: int = 1000,
+              record_iterates: int = 0, apply_A=None):
+    """Textbook conjugate gradients for one right-hand side (Ch. 2, Hestenes-Stiefel).
+
+    Independent of ``bcg``: scalar step lengths r.r / p.Ap and r'.r' / r.r,
+    stopping on ||r|| / ||r0|| <= tol.  Returns (x, iters, history, iterates).
+    """
+    op = apply_A if apply_A is not None else (lambda v: spmm(A, v[:, None])[:, 0])
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    r = b - op(x)
+    p = r.copy()
+    rr = float(r @ r)
+    r0 = math.sqrt(rr)
+    hist, its = [], []
+    if r0 == 0:
+        return x, 0, hist, its
+    for k in range(maxit):
+        q = op(p)
+        a = rr / float(p @ q)
+        x = x + a * p
+        r = r - a * q
+        rr_new = float(r @ r)
+        hist.append(math.sqrt(rr_new) / r0)
+        if k < record_iterates:
+            its.append(x.copy())
+        if math.sqrt(rr_new) / r0 <= tol:
+            return x, k + 1, hist, its
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return x, maxit, hist, its

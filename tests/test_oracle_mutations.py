@@ -1,0 +1,227 @@
+"""Planted-mistake tests: each mutation of the oracle must fail one of its pins.
+
+A mutation is a one-token edit of the oracle's source (a dropped transpose, a
+flipped sign, swapped operands).  The edited function is compiled in a copy
+of its module's namespace and the relevant pin battery is run on it; the
+test passes only if the battery rejects the mutant.  Nothing here touches a
+GPU; the mistakes are planted in the CPU oracle only.
+"""
+import inspect
+import math
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+
+import oracle  # noqa: F401  (loads the submodules)
+import workloads as W
+
+
+def _mutant(modname, fname, old, new):
+    mod = sys.modules[modname]
+    src = textwrap.dedent(inspect.getsource(getattr(mod, fname)))
+    assert src.count(old) >= 1, f"mutation anchor not found: {old!r}"
+    src = src.replace(old, new, 1)
+    ns = dict(vars(mod))
+    exec(compile(src, f"<mutant {fname}>", "exec"), ns)
+    return ns[fname]
+
+
+def _spd(n, seed, cond=30.0):
+    g = np.random.default_rng(seed)
+    Qm, _ = np.linalg.qr(g.standard_normal((n, n)))
+    return (Qm * np.geomspace(1.0, cond, n)) @ Qm.T
+
+
+class _Dense:
+    def __init__(self, M):
+        n = M.shape[0]
+        self.n = n
+        self.row_ptr = np.arange(0, n * n + 1, n, dtype=np.int32)
+        self.col = np.tile(np.arange(n, dtype=np.int32), n)
+        self.val = M.ravel().copy()
+
+
+def _bcg_battery_passes(bcg_fn):
+    """Dense-solve pin, sigma-residual pin and invariants for a BCG implementation."""
+    try:
+        # eta = 1e-30 normalises R^0 but never again, so sigma != I throughout
+        for eta in (math.inf, 0.0, 1e4, 1e-30):
+            M = _spd(30, 1)
+            B = np.random.default_rng(2).standard_normal((30, 5))
+            r = bcg_fn(_Dense(M), B, tol=1e-12, maxit=60, eta=eta)
+            if not r.converged:
+                return False
+            Xs = np.linalg.solve(M, B)
+            if np.abs(r.X - Xs).max() > 1e-9 * np.abs(Xs).max():
+                return False
+            true = np.linalg.norm(B - M @ r.X, axis=0) / np.linalg.norm(B, axis=0)
+            if np.abs(true - r.relres).max() > 1e-10:
+                return False
+            # mid-run: residual norms from sigma/rho equal the recomputed ones (relative)
+            r3 = bcg_fn(_Dense(M), B, tol=0.0, maxit=3, eta=eta)
+            true3 = np.linalg.norm(B - M @ r3.X, axis=0) / np.linalg.norm(B, axis=0)
+            if np.abs(true3 / r3.relres - 1).max() > 1e-8:
+                return False
+        # s = 1 with eta = 0 is textbook CG, iterate for iterate
+        A = W.lap2d5(9, 8)
+        b = W.normal_block(A.n, 1, 3)
+        r = bcg_fn(A, b, tol=1e-10, maxit=100, eta=0.0, record_iterates=20)
+        _, _, _, xs = sys.modules["oracle.bcg"].scalar_cg(A, b[:, 0], tol=1e-10, maxit=100,
+                                                          record_iterates=20)
+        for k in range(20):
+            if np.abs(r.iterates[k][:, 0] - xs[k]).max() > 1e-12 * np.abs(xs[k]).max():
+                return False
+        return True
+    except Exception:
+        return False
+
+
+BCG_MUTATIONS = [
+    ("oracle.bcg", "bcg", "gamma.T @ rho_new", "rho_new"),                 # dropped gamma^T in beta
+    ("oracle.bcg", "bcg", "gamma.T @ rho_new", "gamma @ rho_new"),         # missing transpose
+    ("oracle.bcg", "bcg", "sigma = gamma @ sigma", "sigma = sigma @ gamma"),  # operand order
+    ("oracle.bcg", "bcg", "Rt = Rb - Q @ lam", "Rt = Rb + Q @ lam"),       # sign
+    ("oracle.bcg", "bcg", "X += P @ (lam @ sigma)", "X += P @ (sigma @ lam)"),
+    ("oracle.bcg", "bcg", "X += P @ (lam @ sigma)", "X += P @ lam"),       # dropped sigma
+    ("oracle.bcg", "bcg", "P = Rb + P @ beta", "P = Rb + P @ beta.T"),
+    ("oracle.bcg", "bcg", "lam = chol_solve(alpha, rho)", "lam = chol_solve(rho, alpha)"),
+    ("oracle.bcg", "_resid_from", "sigma.T @ rho @ sigma", "sigma @ rho @ sigma.T"),
+]
+
+
+def test_unmutated_bcg_passes_battery():
+    assert _bcg_battery_passes(sys.modules["oracle.bcg"].bcg)
+
+
+@pytest.mark.parametrize("mod,fn,old,new", BCG_MUTATIONS)
+def test_bcg_mutation_is_caught(mod, fn, old, new, monkeypatch):
+    m = _mutant(mod, fn, old, new)
+    bmod = sys.modules["oracle.bcg"]
+    if fn == "bcg":
+        assert not _bcg_battery_passes(m)
+    else:
+        monkeypatch.setattr(bmod, fn, m)
+        assert not _bcg_battery_passes(bmod.bcg)
+
+
+def _qr_battery_passes(qr_fn):
+    try:
+        for (n, s) in ((40, 6), (12, 12)):
+            X = np.random.default_rng(n).standard_normal((n, s))
+            Y, R = qr_fn(X)
+            if np.abs(Y.T @ Y - np.eye(s)).max() > 1e-12 or np.abs(Y @ R - X).max() > 1e-12:
+                return False
+            if np.any(np.diag(R) < 0) or not np.allclose(np.tril(R, -1), 0):
+                return False
+        return True
+    except Exception:
+        return False
+
+
+QR_MUTATIONS = [
+    ("tau = (beta - alpha) / beta", "tau = (alpha - beta) / beta"),
+    ("v = x / (alpha - beta)", "v = x / (beta - alpha)"),
+    ("A[j:, j + 1:] -= tau * np.outer(v, w)", "A[j:, j + 1:] += tau * np.outer(v, w)"),
+    ("Y[j:, :] -= taus[j] * np.outer(v, w)", "Y[j:, :] += taus[j] * np.outer(v, w)"),
+    ("for j in range(s - 1, -1, -1):", "for j in range(s):"),
+]
+
+
+def test_unmutated_qr_passes_battery():
+    assert _qr_battery_passes(sys.modules["oracle.blockops"].householder_qr)
+
+
+@pytest.mark.parametrize("old,new", QR_MUTATIONS)
+def test_qr_mutation_is_caught(old, new):
+    assert not _qr_battery_passes(_mutant("oracle.blockops", "householder_qr", old, new))
+
+
+def test_gram_mirror_mutation_is_caught():
+    m = _mutant("oracle.blockops", "gram", "np.triu(G) + np.triu(G, 1).T", "np.triu(G) + np.triu(G, 1)")
+    X = np.random.default_rng(0).integers(-5, 5, (9, 4)).astype(float)
+    G = m(X, X)
+    assert not np.array_equal(G, X.T @ X)
+
+
+def _textbook_bicgstab(M, b, nrec):
+    x = np.zeros_like(b); r = b.copy(); rt = r.copy(); p = r.copy(); rho = rt @ r; xs = []
+    for _ in range(nrec):
+        v = M @ p; a = rho / (rt @ v); s_ = r - a * v; t = M @ s_; w = (t @ s_) / (t @ t)
+        x = x + a * p + w * s_; r = s_ - w * t; xs.append(x.copy())
+        rho_new = rt @ r; p = r + (rho_new / rho) * (a / w) * (p - w * v); rho = rho_new
+    return xs
+
+
+def _bbicg_battery_passes(fn):
+    try:
+        A1 = W.const7(6, 5, 4, W.convdiff3d7_coeffs(5, pe=40.0))
+        b = W.normal_block(A1.n, 1, 0)
+        r = fn(A1, b, tol=1e-14, maxit=8, eta=0.0, record_iterates=8)
+        xs = _textbook_bicgstab(A1.to_dense(), b[:, 0], 8)
+        for k in range(8):
+            if np.abs(r.iterates[k][:, 0] - xs[k]).max() > 1e-11 * np.abs(xs[k]).max():
+                return False
+        A = W.const7(7, 6, 5, W.convdiff3d7_coeffs(6))
+        Ad = A.to_dense()
+        B = W.normal_block(A.n, 3, 0)
+        for eta in (0.0, math.inf, 100.0):
+            r = fn(A, B, tol=1e-10, maxit=300, eta=eta)
+            if not r.converged:
+                return False
+            true = np.linalg.norm(B - Ad @ r.X, axis=0) / np.linalg.norm(B, axis=0)
+            if true.max() > 1e-9 or np.abs(true - r.relres).max() > 1e-9:
+                return False
+        return True
+    except Exception:
+        return False
+
+
+BBICG_MUTATIONS = [
+    ("X += omega * (Th @ sigma_new)", "X += omega * (Th @ sigma)"),      # reading c9 reversed
+    ("X += Ph @ (lam @ sigma)", "X += Ph @ (sigma @ lam)"),
+    ("beta = -lu_solve", "beta = lu_solve"),
+    ("Ph = Rh + (Ph - omega * Qh) @ beta", "Ph = Rh + (Ph + omega * Qh) @ beta"),  # the derivation's "+omega"
+    ("omega = float(np.sum(Uh * Sh)) / uu", "omega = float(np.sum(Uh * Sh)) / uu ** 0.5"),
+]
+
+
+def test_unmutated_bbicgstab_passes_battery():
+    assert _bbicg_battery_passes(sys.modules["oracle.bbicgstab"].bbicgstab)
+
+
+@pytest.mark.parametrize("old,new", BBICG_MUTATIONS)
+def test_bbicgstab_mutation_is_caught(old, new):
+    assert not _bbicg_battery_passes(_mutant("oracle.bbicgstab", "bbicgstab", old, new))
+
+
+def _bgmres_battery_passes(fn):
+    try:
+        A = W.const7(6, 5, 5, W.convdiff3d7_coeffs(6))
+        Ad = A.to_dense()
+        B = W.normal_block(A.n, 3, 1)
+        r = fn(A, B, tol=1e-10, restart=8, maxit=200)
+        if not r.converged:
+            return False
+        true = np.linalg.norm(B - Ad @ r.X, axis=0) / np.linalg.norm(B, axis=0)
+        return true.max() <= 1e-9 and np.abs(true - r.relres).max() <= 1e-9
+    except Exception:
+        return False
+
+
+BGMRES_MUTATIONS = [
+    ("h[j * s:(j + 2) * s] = G[j].T @ blk", "h[j * s:(j + 2) * s] = G[j] @ blk"),
+    ("W = W - V[j] @ hj", "W = W + V[j] @ hj"),
+    ("sig[k * s:(k + 2) * s] = Qk.T @ pair", "sig[k * s:(k + 2) * s] = Qk @ pair"),
+    ("for j in range(l + 1, k_done):", "for j in range(l + 2, k_done):"),
+]
+
+
+def test_unmutated_bgmres_passes_battery():
+    assert _bgmres_battery_passes(sys.modules["oracle.bgmres"].bgmres)
+
+
+@pytest.mark.parametrize("old,new", BGMRES_MUTATIONS)
+def test_bgmres_mutation_is_caught(old, new):
+    assert not _bgmres_battery_passes(_mutant("oracle.bgmres", "bgmres", old, new))
