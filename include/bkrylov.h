@@ -1,0 +1,186 @@
+/*
+ * bkrylov — block Krylov solvers for one NVIDIA GB300 (sm_103a), C ABI.
+ *
+ * Solves the block system  A X = B  with n x s blocks X, B (Dreier 2020,
+ * "Hardware-Oriented Krylov Methods for High-Performance Computing",
+ * Ch. 3, Eq. "blocklinearsystem": s simultaneous systems A x_i = b_i).
+ *
+ * Conventions shared by every entry point
+ *  - Block vectors are n x s ROW-MAJOR arrays (leading dimension s): the s
+ *    right-hand sides of one row are contiguous, as the thesis's SIMD block
+ *    vector (Ch. 3.2).  1 <= s <= 32.
+ *  - s x s results (Gram matrices, R factors) are dense row-major s x s
+ *    arrays of doubles, element (i, j) at [i * s + j].
+ *  - Unless a parameter says "host", pointers are device pointers on the
+ *    handle's device.  The library never frees memory it did not allocate.
+ *  - All GPU work is enqueued on the handle's stream.  Entry points that
+ *    return results to the host (solvers filling bkrylov_info) synchronise
+ *    that stream before returning; the others return right after enqueueing.
+ *  - Every entry point returns a bkrylov_status.  Errors are reported, never
+ *    thrown; on BK_ERR_ARG nothing was enqueued.
+ *  - A handle is not thread-safe; use one handle per host thread.
+ *  - Precision: BK_FP64 blocks are double, BK_FP32 blocks are float.  Gram
+ *    matrices and every s x s computation are always double.
+ */
+#ifndef BKRYLOV_H
+#define BKRYLOV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BKRYLOV_VERSION 100
+#define BKRYLOV_MAX_S 32
+
+typedef struct bkrylov_ctx* bkrylov_handle;   /* owns workspace + stream binding */
+typedef struct bkrylov_op_s* bkrylov_op;      /* operator descriptor             */
+
+typedef enum { BK_FP64 = 0, BK_FP32 = 1, BK_FP32_IR = 2 } bkrylov_prec;
+
+typedef enum {
+  BK_OK = 0,
+  BK_ERR_ARG = 1,          /* invalid argument; nothing enqueued               */
+  BK_ERR_CUDA = 2,         /* a CUDA runtime call failed                       */
+  BK_ERR_ALLOC = 3,        /* device allocation of workspace failed            */
+  BK_NOT_CONVERGED = 4,    /* maxit reached; X holds the last iterate           */
+  BK_BREAKDOWN = 5,        /* an s x s coefficient matrix could not be factored */
+  BK_NONFINITE = 6,        /* NaN/Inf appeared in an s x s quantity             */
+  BK_TIMEOUT = 7,          /* a bounded device-side wait gave up                */
+  BK_ERR_UNSUPPORTED = 8   /* valid request this build does not implement       */
+} bkrylov_status;
+
+/* Matrix-free stencil operators (grid numbered x fastest: i = x + nx*(y + ny*z)). */
+typedef enum {
+  /* 7-point constant coefficients, homogeneous Dirichlet boundary.
+     coeffs: HOST array of 7 doubles (centre, -x, +x, -y, +y, -z, +z), copied.
+     nz = 1 gives the 2D 5-point stencil (the z coefficients are unused). */
+  BK_STENCIL_CONST7 = 0,
+  /* -div(k grad u), cell-centred FV, h = 1, Dirichlet u = 0 in ghost cells:
+     interior face 2 k_i k_j / (k_i + k_j), boundary face 2 k_i.
+     coeffs: DEVICE array of n doubles (k per cell), read once at creation. */
+  BK_STENCIL_VAR7 = 1,
+  /* 2D per-edge diffusion A = sum_e a_e (e_i - e_j)(e_i - e_j)^T plus a_e e_i e_i^T
+     for edges to the Dirichlet ghost.  nz must be 1.  coeffs: DEVICE array of
+     ny*(nx+1) horizontal edges (a_x[y][x] joins cells (x-1,y),(x,y)) followed by
+     (ny+1)*nx vertical edges (a_y[y][x] joins (x,y-1),(x,y)); BORROWED (the caller
+     keeps it alive until bkrylov_op_destroy). */
+  BK_STENCIL_EDGE5 = 2
+} bkrylov_stencil_kind;
+
+/* Solver options (bkrylov_opts_default fills the defaults noted here). */
+typedef struct {
+  double tol;          /* stop when max_i ||R_i|| / ||R0_i|| <= tol           (1e-8)  */
+  int maxit;           /* iteration limit (Arnoldi steps for BGMRes)          (1000)  */
+  double eta;          /* re-orthonormalisation parameter: 0 never, INFINITY always;
+                          otherwise re-orthonormalise when eta*kappa_D > 1/sqrt(eps)
+                          (Ch. 4.3, Eq. "reortho_criterion", read as 1/sqrt(eps))   (INFINITY) */
+  int restart;         /* BGMRes restart length m                              (30)   */
+  int ortho;           /* BGMRes orthogonalisation: 0 = CGS2 (two classical passes),
+                          1 = block MGS                                         (0)    */
+  int prec;            /* bkrylov_prec: FP64, FP32, or FP32 inner + FP64 refinement (FP64) */
+  double ir_inner_tol; /* relative tolerance of each FP32 inner solve          (1e-5)  */
+  int ir_max_outer;    /* refinement steps limit                               (30)    */
+  const uint8_t* forced_reortho; /* HOST, optional: decision of iteration k (k < n_forced)
+                                    replaces the adaptive criterion (replay)    (NULL) */
+  int n_forced;
+  int sync_every;      /* iterations enqueued between host checks of the stop flag;
+                          0 = automatic                                          (0)  */
+} bkrylov_opts;
+
+/* Solver report.  Pointer members are HOST arrays supplied by the caller (or NULL). */
+typedef struct {
+  int iters;           /* iterations performed (SpMMs of the loop; Arnoldi steps)    */
+  int reorths;         /* residual re-orthonormalisations inside the loop            */
+  int converged;       /* 1 if the tolerance was met                                  */
+  int status;          /* bkrylov_status of the solve                                */
+  int outer;           /* refinement steps (FP32_IR), else 0                          */
+  double relres_max;   /* final max_i ||R_i|| / ||R0_i|| as tracked by the method     */
+  double* relres;      /* [s]      final per-column relative residuals, or NULL        */
+  double* history;     /* [maxit]  max relative residual after each iteration, or NULL */
+  uint8_t* decisions;  /* [maxit]  re-orthonormalised in iteration k?, or NULL          */
+  int history_len;     /* capacity of history/decisions (entries written <= this)      */
+  double elapsed_ms;   /* device time of the solve (CUDA events)                      */
+} bkrylov_info;
+
+/* ---- handle ------------------------------------------------------------------ */
+/* Create a handle on `device`, bound to `cuda_stream` (a cudaStream_t; NULL = legacy
+   default stream).  The handle owns a workspace grown on demand and freed by destroy. */
+int bkrylov_create(bkrylov_handle* h, int device, void* cuda_stream);
+int bkrylov_destroy(bkrylov_handle h);
+int bkrylov_set_stream(bkrylov_handle h, void* cuda_stream);
+const char* bkrylov_status_string(int status);
+int bkrylov_version(void);
+void bkrylov_opts_default(bkrylov_opts* o);
+
+/* ---- operators (BOP, Ch. 3.3 Table "kernels") ---------------------------------- */
+/* CSR matrix, n x n, int32 row_ptr[n+1] and col[nnz] (columns sorted within a row),
+   double val[nnz]; all device arrays BORROWED until bkrylov_op_destroy.  A float copy
+   of val is made (owned by the operator) the first time an FP32 product is asked for. */
+int bkrylov_op_csr(bkrylov_handle h, int64_t n, int64_t nnz, const int32_t* row_ptr,
+                   const int32_t* col, const double* val, bkrylov_op* A);
+/* Matrix-free stencil (see bkrylov_stencil_kind).  n = nx*ny*nz.  VAR7 precomputes the
+   3 face coefficients of every cell (owned, 3n doubles); EDGE5 precomputes the diagonal
+   (owned, n doubles). */
+int bkrylov_op_stencil(bkrylov_handle h, int kind, int nx, int ny, int nz,
+                       const double* coeffs, bkrylov_op* A);
+int bkrylov_op_destroy(bkrylov_op A);
+int bkrylov_op_size(bkrylov_op A, int64_t* n, int64_t* nnz);
+
+/* Q = A P (BOP).  P, Q: n x s blocks of precision prec (BK_FP64 or BK_FP32). */
+int bkrylov_spmm(bkrylov_handle h, bkrylov_op A, int s, const void* P, void* Q, int prec);
+/* R = B - A X (the residual of Alg. "bcg", first line). */
+int bkrylov_residual(bkrylov_handle h, bkrylov_op A, int s, const void* B, const void* X,
+                     void* R, int prec);
+
+/* ---- block inner product (BDOT, Ch. 3.1/3.3) ----------------------------------- */
+/* G = X^T Y (s x s, double, device), summed in a fixed order (bitwise reproducible
+   for a given n, s and device).  sym != 0 computes the upper triangle and mirrors it
+   (the thesis's alpha and rho, Eqs. "cg_alpha", "cg_rho"). */
+int bkrylov_bdot(bkrylov_handle h, int64_t n, int s, const void* X, const void* Y,
+                 double* G, int sym, int prec);
+
+/* ---- normalizer = TSQR (Def. "normalizer", Ch. 3.1; TSQR, Ch. 7.3) --------------- */
+/* X = Y sigma with Y^T Y = I, sigma upper triangular s x s (double, device) with
+   diag(sigma) >= 0; defined also for rank-deficient X (Householder at every level).
+   Y may alias X.  n >= s required. */
+int bkrylov_tsqr(bkrylov_handle h, int64_t n, int s, const void* X, void* Y, double* sigma,
+                 int prec);
+
+/* ---- solvers --------------------------------------------------------------------- */
+/* B (read) and X (in: X0, out: solution) are n x s double blocks, either device
+   pointers or HOST pointers (then the library copies them to and from the device
+   inside the call).  opts may be NULL (defaults); info may be NULL.
+   Returns BK_OK, BK_NOT_CONVERGED, BK_BREAKDOWN or BK_NONFINITE (X is the last
+   iterate in the last three cases), or an error code. */
+/* Block CG with adaptive residual re-orthonormalisation, Alg. "bcgaro" (Ch. 4.3)
+   scheduled as Alg. "2R-CG" (Ch. 8.1); prec = BK_FP32_IR runs FP32 inner solves
+   inside FP64 iterative refinement (B - A X in FP64). */
+int bkrylov_solve_bcg(bkrylov_handle h, bkrylov_op A, int s, const double* B, double* X,
+                      const bkrylov_opts* opts, bkrylov_info* info);
+/* Block BiCGStab with adaptive re-orthonormalisation, Alg. "BlockBiCGStab_with_reortho"
+   (Ch. 6.2).  FP64 only. */
+int bkrylov_solve_bbicgstab(bkrylov_handle h, bkrylov_op A, int s, const double* B,
+                            double* X, const bkrylov_opts* opts, bkrylov_info* info);
+/* Restarted block GMRes, Alg. "bgmres" (Ch. 5.1), CGS2 (Ch. 9.1) or MGS Arnoldi and the
+   TSQR normalizer.  FP64 only. */
+int bkrylov_solve_bgmres(bkrylov_handle h, bkrylov_op A, int s, const double* B,
+                         double* X, const bkrylov_opts* opts, bkrylov_info* info);
+
+/* ---- adjoint (reverse-mode derivative of X = A^{-1} B) ----------------------------- */
+/* For a CSR operator: g[e] = -sum_k Lam[i,k] X[j,k] for every stored entry e = (i, j),
+   i.e. dL/dA on the sparsity pattern given Lam = A^{-T} dL/dX.  Lam, X: n x s double. */
+int bkrylov_adjoint_scatter(bkrylov_handle h, bkrylov_op A, int s, const double* Lam,
+                            const double* X, double* g);
+/* For an EDGE5 operator with a_e = exp(theta_e): dL/dtheta_e =
+   -a_e sum_k (Lam_ik - Lam_jk)(X_ik - X_jk) (boundary edges: -a_e sum_k Lam_ik X_ik).
+   gtheta has the layout of the operator's coefficient array. */
+int bkrylov_edge_theta_grad(bkrylov_handle h, bkrylov_op A, int s, const double* Lam,
+                            const double* X, double* gtheta);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BKRYLOV_H */

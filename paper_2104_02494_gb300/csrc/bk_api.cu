@@ -1,0 +1,896 @@
+// C ABI of the bkrylov library: handle, workspace, operators, single-kernel
+// entry points and the device-resident solver drivers.
+//
+// A solver keeps every n x s block and every s x s coefficient on the device.
+// Each iteration is a fixed sequence of kernel launches; data-dependent
+// branches (re-orthonormalise or not, converged, breakdown) are decided on
+// the device and read by the later kernels from the control block, so the
+// host enqueues `sync_every` iterations at a time and only then reads the
+// stop flag.  Kernels of iterations past the stop return immediately.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "bk_common.cuh"
+#include "bk_internal.h"
+
+using namespace bk;
+
+struct bkrylov_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sms = 152;
+  void* ws[2] = {nullptr, nullptr};   // [0] solver internals, [1] refinement / host staging
+  size_t ws_cap[2] = {0, 0};
+  Ctrl* host_ctrl = nullptr;          // pinned staging of the control block
+};
+
+struct bkrylov_op_s {
+  bkrylov_handle h = nullptr;
+  OpDesc d;
+};
+
+namespace {
+
+#define BK_TRY(x)                                   \
+  do {                                              \
+    cudaError_t _e = (x);                           \
+    if (_e != cudaSuccess) return BK_ERR_CUDA;      \
+  } while (0)
+
+struct Bump {
+  char* base;
+  size_t off = 0, cap;
+  Bump(void* b, size_t c) : base((char*)b), cap(c) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = (T*)(base + off);
+    off += sizeof(T) * count;
+    return p;
+  }
+};
+
+int ensure_ws(bkrylov_handle h, int which, size_t bytes) {
+  if (h->ws_cap[which] >= bytes) return BK_OK;
+  if (h->ws[which]) {
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BK_ERR_CUDA;
+    cudaFree(h->ws[which]);
+    h->ws[which] = nullptr;
+    h->ws_cap[which] = 0;
+  }
+  if (cudaMalloc(&h->ws[which], bytes) != cudaSuccess) return BK_ERR_ALLOC;
+  h->ws_cap[which] = bytes;
+  return BK_OK;
+}
+
+Launch launch_of(bkrylov_handle h) {
+  Launch L;
+  L.stream = h->stream;
+  L.sms = h->sms;
+  return L;
+}
+
+bool is_host_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+size_t gpart_count(const Launch& L) {
+  // largest grid of a reducing kernel x largest partial record (two Grams + 2)
+  return (size_t)L.sms * 4 * (kMM + kMM + 8);
+}
+
+void opts_or_default(const bkrylov_opts* o, bkrylov_opts* out) {
+  if (o) *out = *o; else bkrylov_opts_default(out);
+}
+
+// ---- control block upload / download ------------------------------------------
+int ctrl_upload(bkrylov_handle h, Ctrl* dev, int s, const bkrylov_opts& o, double eps) {
+  Ctrl* c = h->host_ctrl;
+  std::memset(c, 0, sizeof(Ctrl));
+  c->s = s;
+  c->maxit = o.maxit;
+  c->tol = o.tol;
+  c->eta = o.eta;
+  c->eps = eps;
+  c->n_forced = (o.forced_reortho && o.n_forced > 0) ? o.n_forced : 0;
+  for (int i = 0; i < s; ++i) c->sigma[i * kMaxS + i] = 1.0;
+  BK_TRY(cudaMemcpyAsync(dev, c, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+  // the pinned staging buffer is reused: wait for the copy before returning
+  BK_TRY(cudaStreamSynchronize(h->stream));
+  return BK_OK;
+}
+
+int ctrl_download(bkrylov_handle h, const Ctrl* dev) {
+  BK_TRY(cudaMemcpyAsync(h->host_ctrl, dev, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+  BK_TRY(cudaStreamSynchronize(h->stream));
+  return BK_OK;
+}
+
+int ctrl_peek(bkrylov_handle h, const Ctrl* dev) {
+  // first 16 bytes: done, status, iter, reorths
+  BK_TRY(cudaMemcpyAsync(h->host_ctrl, dev, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  BK_TRY(cudaStreamSynchronize(h->stream));
+  return BK_OK;
+}
+
+int finish_info(bkrylov_handle h, const Ctrl* dev, int s, const double* hist_dev,
+                const uint8_t* dec_dev, int nrec, bkrylov_info* info, float ms) {
+  int rc = ctrl_download(h, dev);
+  if (rc) return rc;
+  const Ctrl* c = h->host_ctrl;
+  const int status = c->done == kDoneRunning ? BK_NOT_CONVERGED : c->status;
+  if (info) {
+    info->iters = c->iter;
+    info->reorths = c->reorths;
+    info->converged = c->done == kDoneConverged;
+    info->status = status;
+    double mx = 0.0;
+    for (int i = 0; i < s; ++i) mx = std::fmax(mx, c->relres[i]);
+    info->relres_max = mx;
+    if (info->relres) std::memcpy(info->relres, c->relres, sizeof(double) * s);
+    const int nh = c->iter < info->history_len ? c->iter : info->history_len;
+    if (info->history && hist_dev && nh > 0)
+      BK_TRY(cudaMemcpy(info->history, hist_dev, sizeof(double) * nh, cudaMemcpyDeviceToHost));
+    if (info->decisions && dec_dev && nh > 0)
+      BK_TRY(cudaMemcpy(info->decisions, dec_dev, nh, cudaMemcpyDeviceToHost));
+    info->elapsed_ms = ms;
+    (void)nrec;
+  }
+  return status;
+}
+
+// ---------------------------------------------------------------- BCG ----
+template <typename T>
+struct BcgBufs {
+  T *R, *P, *Q;
+  void* tsqr;
+  double* gpart;
+  Ctrl* ctrl;
+  double* hist;
+  uint8_t* dec;
+  uint8_t* forced;
+};
+
+template <typename T, typename Alloc>
+void bcg_layout(Alloc& a, int64_t n, int s, int maxit, const TsqrPlan& tp, const Launch& L,
+                BcgBufs<T>* b) {
+  const size_t ns = (size_t)n * s;
+  auto r = a.template take<T>(ns);
+  auto p = a.template take<T>(ns);
+  auto q = a.template take<T>(ns);
+  auto t = a.template take<char>(tp.bytes);
+  auto g = a.template take<double>(gpart_count(L));
+  auto c = a.template take<Ctrl>(1);
+  auto hs = a.template take<double>((size_t)maxit + 1);
+  auto dc = a.template take<uint8_t>((size_t)maxit + 1);
+  auto fc = a.template take<uint8_t>((size_t)maxit + 1);
+  b->R = r; b->P = p; b->Q = q; b->tsqr = t; b->gpart = g; b->ctrl = c; b->hist = hs;
+  b->dec = dc; b->forced = fc;
+}
+
+// One BCG-ARO iteration (Alg. "2R-CG"): two grid-wide reductions (alpha with
+// the SpMM, rho with the update or after the normaliser).
+template <typename T>
+cudaError_t bcg_iteration(const Launch& L, const OpDesc& A, int s, T* X, const BcgBufs<T>& b,
+                          const TsqrPlan& tp) {
+  Ctrl* c = b.ctrl;
+  cudaError_t e;
+  Epi<T> ep;
+  ep.left = b.P; ep.sym = 1; ep.gram_out = c->alpha; ep.gpart = b.gpart;
+  ep.counter = &c->counters[kCntA]; ep.done = &c->done;
+  if ((e = spmm<T>(L, A, s, b.P, b.Q, nullptr, ep)) != cudaSuccess) return e;
+  if ((e = small_bcg_1(L, c, b.forced)) != cudaSuccess) return e;
+  if ((e = bcg_update<T>(L, A.n, s, b.P, b.Q, X, b.R, c, b.gpart, 1)) != cudaSuccess) return e;
+  if ((e = tsqr<T>(L, tp, b.R, b.R, c->gamma, c->rho_new, b.tsqr, b.gpart, &c->counters[kCntC],
+                   &c->done, &c->reortho_now)) != cudaSuccess) return e;
+  if ((e = small_bcg_2(L, c, b.hist, b.dec)) != cudaSuccess) return e;
+  return bcg_pupdate<T>(L, A.n, s, b.R, b.P, c);
+}
+
+template <typename T>
+int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const bkrylov_opts& o,
+               double eps, bkrylov_info* info) {
+  const Launch L = launch_of(h);
+  const int64_t n = A.n;
+  const TsqrPlan tp = tsqr_plan(n, s);
+  const int maxit = o.maxit > 0 ? o.maxit : 0;
+  BcgBufs<T> b;
+  Bump probe(nullptr, 0);
+  bcg_layout<T>(probe, n, s, maxit, tp, L, &b);
+  int rc = ensure_ws(h, 0, probe.off + 4096);
+  if (rc) return rc;
+  Bump bump(h->ws[0], h->ws_cap[0]);
+  bcg_layout<T>(bump, n, s, maxit, tp, L, &b);
+  if ((rc = ctrl_upload(h, b.ctrl, s, o, eps))) return rc;
+  if (o.forced_reortho && o.n_forced > 0) {
+    const int nf = o.n_forced < maxit + 1 ? o.n_forced : maxit + 1;
+    BK_TRY(cudaMemcpy(b.forced, o.forced_reortho, nf, cudaMemcpyHostToDevice));
+  }
+  cudaEvent_t e0, e1;
+  BK_TRY(cudaEventCreate(&e0));
+  BK_TRY(cudaEventCreate(&e1));
+  BK_TRY(cudaEventRecord(e0, L.stream));
+  Ctrl* c = b.ctrl;
+  // setup: R = B - A X ; n0 ; normalise ; P = R ; rho = R^T R
+  Epi<T> none;
+  BK_TRY(spmm<T>(L, A, s, X, b.R, B, none));
+  Epi<T> g;
+  g.sym = 1; g.gram_out = c->rho_new; g.gpart = b.gpart; g.counter = &c->counters[kCntA];
+  BK_TRY(gram<T>(L, n, s, b.R, b.R, g));
+  BK_TRY(diag_sqrt(L, s, c->rho_new, c->n0));
+  if (o.eta > 0) {
+    BK_TRY(tsqr<T>(L, tp, b.R, b.R, c->sigma, nullptr, b.tsqr, b.gpart, nullptr, nullptr, nullptr));
+  }
+  BK_TRY(cudaMemcpyAsync(b.P, b.R, sizeof(T) * (size_t)n * s, cudaMemcpyDeviceToDevice, L.stream));
+  g.gram_out = c->rho;
+  BK_TRY(gram<T>(L, n, s, b.R, b.R, g));
+  BK_TRY(small_bcg_init(L, c, o.eta > 0));
+  int batch = o.sync_every > 0 ? o.sync_every : (n >= (1 << 20) ? 4 : 16);
+  int enq = 0;
+  while (true) {
+    if ((rc = ctrl_peek(h, c))) return rc;
+    if (h->host_ctrl->done != kDoneRunning || enq >= maxit) break;
+    const int todo = (maxit - enq) < batch ? (maxit - enq) : batch;
+    for (int i = 0; i < todo; ++i) BK_TRY(bcg_iteration<T>(L, A, s, X, b, tp));
+    enq += todo;
+  }
+  BK_TRY(cudaEventRecord(e1, L.stream));
+  BK_TRY(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return finish_info(h, c, s, b.hist, b.dec, maxit, info, ms);
+}
+
+// ------------------------------------------------ iterative refinement ----
+int bcg_ir_device(bkrylov_handle h, bkrylov_op Aop, int s, const double* B, double* X,
+                  const bkrylov_opts& o, bkrylov_info* info, void* outer_ws, size_t outer_off) {
+  const Launch L = launch_of(h);
+  OpDesc& A = Aop->d;
+  BK_TRY(op_make_fp32(L, A));
+  const int64_t n = A.n;
+  const size_t ns = (size_t)n * s;
+  Bump bump((char*)outer_ws + outer_off, h->ws_cap[1] - outer_off);
+  double* R = bump.take<double>(ns);
+  float* R32 = bump.take<float>(ns);
+  float* D32 = bump.take<float>(ns);
+  double* nrm = bump.take<double>(2 * kMaxS);
+  double* gp = bump.take<double>((size_t)L.sms * 4 * kMaxS + 64);
+  unsigned* cnt = bump.take<unsigned>(4);
+  BK_TRY(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned), L.stream));
+  cudaEvent_t e0, e1;
+  BK_TRY(cudaEventCreate(&e0));
+  BK_TRY(cudaEventCreate(&e1));
+  BK_TRY(cudaEventRecord(e0, L.stream));
+  double nb[kMaxS], nr[kMaxS];
+  BK_TRY(ir_colnorms(L, n, s, B, nrm + kMaxS, gp, cnt));
+  BK_TRY(cudaMemcpyAsync(nb, nrm + kMaxS, sizeof(double) * s, cudaMemcpyDeviceToHost, L.stream));
+  BK_TRY(cudaStreamSynchronize(L.stream));
+  for (int i = 0; i < s; ++i) nb[i] = std::sqrt(nb[i]);
+  int outer = 0, inner_total = 0, reorth_total = 0, status = BK_NOT_CONVERGED;
+  double relmax = 0.0, rel[kMaxS];
+  const int max_outer = o.ir_max_outer > 0 ? o.ir_max_outer : 30;
+  std::vector<double> hist;
+  for (;;) {
+    Epi<double> none;
+    BK_TRY(spmm<double>(L, A, s, X, R, B, none));        // R = B - A X in FP64
+    BK_TRY(ir_colnorms(L, n, s, R, nrm, gp, cnt));
+    BK_TRY(cudaMemcpyAsync(nr, nrm, sizeof(double) * s, cudaMemcpyDeviceToHost, L.stream));
+    BK_TRY(cudaStreamSynchronize(L.stream));
+    relmax = 0.0;
+    bool finite = true;
+    for (int i = 0; i < s; ++i) {
+      rel[i] = nb[i] > 0 ? std::sqrt(nr[i]) / nb[i] : 0.0;
+      if (!std::isfinite(rel[i])) finite = false;
+      relmax = std::fmax(relmax, rel[i]);
+    }
+    hist.push_back(relmax);
+    if (!finite) { status = BK_NONFINITE; break; }
+    if (relmax <= o.tol) { status = BK_OK; break; }
+    if (outer >= max_outer) { status = BK_NOT_CONVERGED; break; }
+    BK_TRY(ir_to_fp32(L, n, s, R, nrm, R32));
+    BK_TRY(cudaMemsetAsync(D32, 0, sizeof(float) * ns, L.stream));
+    bkrylov_opts io = o;
+    io.tol = o.ir_inner_tol;
+    io.forced_reortho = nullptr;
+    io.n_forced = 0;
+    bkrylov_info ii;
+    std::memset(&ii, 0, sizeof(ii));
+    const int irc = bcg_device<float>(h, A, s, R32, D32, io, std::ldexp(1.0, -23), &ii);
+    inner_total += ii.iters;
+    reorth_total += ii.reorths;
+    if (irc != BK_OK && irc != BK_NOT_CONVERGED) { status = irc; break; }
+    BK_TRY(ir_accumulate(L, n, s, D32, nrm, X));
+    ++outer;
+  }
+  BK_TRY(cudaEventRecord(e1, L.stream));
+  BK_TRY(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (info) {
+    info->iters = inner_total;
+    info->reorths = reorth_total;
+    info->outer = outer;
+    info->converged = status == BK_OK;
+    info->status = status;
+    info->relres_max = relmax;
+    if (info->relres) std::memcpy(info->relres, rel, sizeof(double) * s);
+    if (info->history)
+      for (int i = 0; i < (int)hist.size() && i < info->history_len; ++i) info->history[i] = hist[i];
+    info->elapsed_ms = ms;
+  }
+  return status;
+}
+
+// ---------------------------------------------------------- BBiCGStab ----
+int bicg_device(bkrylov_handle h, const OpDesc& A, int s, const double* B, double* X,
+                const bkrylov_opts& o, bkrylov_info* info) {
+  const Launch L = launch_of(h);
+  const int64_t n = A.n;
+  const size_t ns = (size_t)n * s;
+  const TsqrPlan tp = tsqr_plan(n, s);
+  const int maxit = o.maxit > 0 ? o.maxit : 0;
+  auto layout = [&](auto& a, double** R, double** P, double** Q, double** U, double** R0,
+                    void** ts, double** gp, Ctrl** c, double** hs, uint8_t** dc, uint8_t** fc) {
+    *R = a.template take<double>(ns); *P = a.template take<double>(ns);
+    *Q = a.template take<double>(ns); *U = a.template take<double>(ns);
+    *R0 = a.template take<double>(ns); *ts = a.template take<char>(tp.bytes);
+    *gp = a.template take<double>(gpart_count(L)); *c = a.template take<Ctrl>(1);
+    *hs = a.template take<double>((size_t)maxit + 1); *dc = a.template take<uint8_t>((size_t)maxit + 1);
+    *fc = a.template take<uint8_t>((size_t)maxit + 1);
+  };
+  double *R, *P, *Q, *U, *R0, *gp, *hs;
+  void* ts;
+  Ctrl* c;
+  uint8_t *dc, *fc;
+  {
+    Bump probe(nullptr, 0);
+    layout(probe, &R, &P, &Q, &U, &R0, &ts, &gp, &c, &hs, &dc, &fc);
+    int rc = ensure_ws(h, 0, probe.off + 4096);
+    if (rc) return rc;
+  }
+  Bump bump(h->ws[0], h->ws_cap[0]);
+  layout(bump, &R, &P, &Q, &U, &R0, &ts, &gp, &c, &hs, &dc, &fc);
+  int rc = ctrl_upload(h, c, s, o, std::ldexp(1.0, -52));
+  if (rc) return rc;
+  if (o.forced_reortho && o.n_forced > 0) {
+    const int nf = o.n_forced < maxit + 1 ? o.n_forced : maxit + 1;
+    BK_TRY(cudaMemcpy(fc, o.forced_reortho, nf, cudaMemcpyHostToDevice));
+  }
+  cudaEvent_t e0, e1;
+  BK_TRY(cudaEventCreate(&e0));
+  BK_TRY(cudaEventCreate(&e1));
+  BK_TRY(cudaEventRecord(e0, L.stream));
+  Epi<double> none;
+  BK_TRY(spmm<double>(L, A, s, X, R, B, none));
+  Epi<double> g;
+  g.sym = 1; g.gram_out = c->rho_new; g.gpart = gp; g.counter = &c->counters[kCntA];
+  BK_TRY(gram<double>(L, n, s, R, R, g));
+  BK_TRY(diag_sqrt(L, s, c->rho_new, c->n0));
+  if (o.eta != 0) BK_TRY(tsqr<double>(L, tp, R, R, c->sigma, nullptr, ts, gp, nullptr, nullptr, nullptr));
+  BK_TRY(cudaMemcpyAsync(P, R, sizeof(double) * ns, cudaMemcpyDeviceToDevice, L.stream));
+  BK_TRY(cudaMemcpyAsync(R0, R, sizeof(double) * ns, cudaMemcpyDeviceToDevice, L.stream));
+  g.gram_out = c->rho;
+  BK_TRY(gram<double>(L, n, s, R, R, g));
+  Epi<double> g2;
+  g2.sym = 0; g2.gram_out = c->g2; g2.gpart = gp; g2.counter = &c->counters[kCntA];
+  BK_TRY(gram<double>(L, n, s, R0, R, g2));
+  if (maxit <= 0) {
+    // nothing to iterate: report the initial state as not converged
+  }
+  const int batch = o.sync_every > 0 ? o.sync_every : (n >= (1 << 20) ? 4 : 16);
+  int enq = 0;
+  while (true) {
+    if ((rc = ctrl_peek(h, c))) return rc;
+    if (h->host_ctrl->done != kDoneRunning || enq >= maxit) break;
+    const int todo = (maxit - enq) < batch ? (maxit - enq) : batch;
+    for (int i = 0; i < todo; ++i) {
+      Epi<double> e1p;
+      e1p.left = R0; e1p.sym = 0; e1p.gram_out = c->alpha; e1p.gpart = gp;
+      e1p.counter = &c->counters[kCntA]; e1p.done = &c->done;
+      BK_TRY(spmm<double>(L, A, s, P, Q, nullptr, e1p));                 // Q = A P, R0^T Q
+      BK_TRY(small_bicg_1(L, c, fc));
+      BK_TRY(bcg_update<double>(L, n, s, P, Q, X, R, c, gp, 0));         // X += P lx ; S = R - Q lam
+      BK_TRY(tsqr<double>(L, tp, R, R, c->gamma, nullptr, ts, gp, nullptr, &c->done, &c->reortho_now));
+      Epi<double> e3;
+      e3.left = R0; e3.sym = 0; e3.gram_out = c->g3; e3.frob = R; e3.frob_out = c->frob;
+      e3.gpart = gp; e3.counter = &c->counters[kCntB]; e3.done = &c->done;
+      BK_TRY(spmm<double>(L, A, s, R, U, nullptr, e3));                  // U = A S, R0^T U, <U,S>, <U,U>
+      BK_TRY(small_bicg_2(L, c));
+      BK_TRY(bicg_final(L, n, s, R, U, X, P, Q, R0, c, gp));
+      BK_TRY(small_bicg_3(L, c, hs, dc));
+    }
+    enq += todo;
+  }
+  BK_TRY(cudaEventRecord(e1, L.stream));
+  BK_TRY(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return finish_info(h, c, s, hs, dc, maxit, info, ms);
+}
+
+// ------------------------------------------------------------- BGMRes ----
+int gmres_device(bkrylov_handle h, const OpDesc& A, int s, const double* B, double* X,
+                 const bkrylov_opts& o, bkrylov_info* info) {
+  const Launch L = launch_of(h);
+  const int64_t n = A.n;
+  const size_t ns = (size_t)n * s;
+  const int m = o.restart > 0 ? o.restart : 30;
+  const int maxit = o.maxit > 0 ? o.maxit : 0;
+  const TsqrPlan tp = tsqr_plan(n, s);
+  const size_t ss = (size_t)s * s;
+  const size_t gmg = (size_t)L.sms * 4 * kMM + (size_t)8 * (m + 1) * kMM;
+  auto layout = [&](auto& a, double** V, double** Hc, double** Ht, double** H, double** Gq,
+                    double** sig, double** zeta, double*** Vp, void** ts, double** gp,
+                    double** gmp, Ctrl** c, double** hs) {
+    *V = a.template take<double>(ns * (m + 1));
+    *Hc = a.template take<double>((size_t)(m + 1) * kMM);
+    *Ht = a.template take<double>((size_t)(m + 1) * kMM);
+    *H = a.template take<double>((size_t)(m + 1) * s * m * s);
+    *Gq = a.template take<double>((size_t)m * (2 * ss + s));
+    *sig = a.template take<double>((size_t)(m + 1) * ss);
+    *zeta = a.template take<double>((size_t)m * kMM);
+    *Vp = a.template take<double*>((size_t)m + 1);
+    *ts = a.template take<char>(tp.bytes);
+    *gp = a.template take<double>(gpart_count(L));
+    *gmp = a.template take<double>(gmg);
+    *c = a.template take<Ctrl>(1);
+    *hs = a.template take<double>((size_t)maxit + 1);
+  };
+  double *V, *Hc, *Ht, *H, *Gq, *sig, *zeta, *gp, *gmp, *hs;
+  double** Vp;
+  void* ts;
+  Ctrl* c;
+  {
+    Bump probe(nullptr, 0);
+    layout(probe, &V, &Hc, &Ht, &H, &Gq, &sig, &zeta, &Vp, &ts, &gp, &gmp, &c, &hs);
+    int rc = ensure_ws(h, 0, probe.off + 4096);
+    if (rc) return rc;
+  }
+  Bump bump(h->ws[0], h->ws_cap[0]);
+  layout(bump, &V, &Hc, &Ht, &H, &Gq, &sig, &zeta, &Vp, &ts, &gp, &gmp, &c, &hs);
+  int rc = ctrl_upload(h, c, s, o, std::ldexp(1.0, -52));
+  if (rc) return rc;
+  std::vector<double*> vp(m + 1);
+  for (int j = 0; j <= m; ++j) vp[j] = V + ns * j;
+  BK_TRY(cudaMemcpyAsync(Vp, vp.data(), sizeof(double*) * (m + 1), cudaMemcpyHostToDevice, L.stream));
+  BK_TRY(cudaStreamSynchronize(L.stream));
+  cudaEvent_t e0, e1;
+  BK_TRY(cudaEventCreate(&e0));
+  BK_TRY(cudaEventCreate(&e1));
+  BK_TRY(cudaEventRecord(e0, L.stream));
+  Epi<double> none;
+  BK_TRY(spmm<double>(L, A, s, X, V, B, none));
+  Epi<double> g;
+  g.sym = 1; g.gram_out = c->rho_new; g.gpart = gp; g.counter = &c->counters[kCntA];
+  BK_TRY(gram<double>(L, n, s, V, V, g));
+  BK_TRY(diag_sqrt(L, s, c->rho_new, c->n0));
+  int total = 0;
+  bool first = true;
+  int status = BK_NOT_CONVERGED;
+  while (total < maxit) {
+    if (!first) BK_TRY(spmm<double>(L, A, s, X, V, B, none));     // restart residual
+    first = false;
+    BK_TRY(tsqr<double>(L, tp, V, V, c->gamma, nullptr, ts, gp, nullptr, nullptr, nullptr));
+    BK_TRY(init_sig(L, s, c->gamma, sig, m + 1));
+    int k_done = 0;
+    bool conv = false;
+    for (int k = 0; k < m && total < maxit; ++k) {
+      double* W = vp[k + 1];
+      BK_TRY(spmm<double>(L, A, s, vp[k], W, nullptr, none));
+      if (o.ortho == 1) {                          // block MGS (Alg. "block-arnoldi")
+        for (int j = 0; j <= k; ++j) {
+          Epi<double> gj;
+          gj.sym = 0; gj.gram_out = Hc + (size_t)j * kMM; gj.gpart = gp; gj.counter = &c->counters[kCntA];
+          BK_TRY(gram<double>(L, n, s, vp[j], W, gj));
+          BK_TRY(block_axpy<double>(L, n, s, vp[j], Hc + (size_t)j * kMM, -1.0, W, 1.0, nullptr));
+        }
+      } else {                                     // CGS2 (Ch. 9.1, #it = 2)
+        BK_TRY(multi_gram(L, n, s, Vp, k + 1, W, Hc, 0, gmp, nullptr, nullptr));
+        BK_TRY(multi_axpy(L, n, s, Vp, k + 1, Hc, W, -1.0, nullptr));
+        BK_TRY(multi_gram(L, n, s, Vp, k + 1, W, Ht, 0, gmp, nullptr, nullptr));
+        BK_TRY(multi_axpy(L, n, s, Vp, k + 1, Ht, W, -1.0, nullptr));
+        BK_TRY(vec_add(L, (int64_t)(k + 1) * kMM, Ht, Hc, nullptr));
+      }
+      BK_TRY(tsqr<double>(L, tp, W, W, c->gamma, nullptr, ts, gp, nullptr, nullptr, nullptr));
+      BK_TRY(small_gmres_step(L, c, Hc, H, Gq, sig, k, m, hs, total));
+      ++total;
+      k_done = k + 1;
+      if ((rc = ctrl_peek(h, c))) return rc;
+      if (h->host_ctrl->done == kDoneConverged) { conv = true; break; }
+      if (h->host_ctrl->done != kDoneRunning) break;
+    }
+    BK_TRY(small_gmres_backsub(L, c, H, sig, zeta, k_done, m));
+    BK_TRY(multi_axpy(L, n, s, Vp, k_done, zeta, X, 1.0, nullptr));
+    if (conv) { status = BK_OK; break; }
+    if (h->host_ctrl->done != kDoneRunning) { status = h->host_ctrl->status; break; }
+  }
+  BK_TRY(cudaEventRecord(e1, L.stream));
+  BK_TRY(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int st = finish_info(h, c, s, hs, nullptr, maxit, info, ms);
+  if (info) info->status = status;
+  (void)st;
+  return status;
+}
+
+// Stage host B/X into device buffers when needed, run, copy X back.
+template <typename F>
+int with_device_blocks(bkrylov_handle h, int64_t n, int s, const double* B, double* X,
+                       size_t extra_outer, F&& run) {
+  const bool hb = is_host_ptr(B), hx = is_host_ptr(X);
+  const size_t ns = (size_t)n * s;
+  size_t need = 256 + extra_outer + (hb ? sizeof(double) * ns + 256 : 0) + (hx ? sizeof(double) * ns + 256 : 0);
+  int rc = ensure_ws(h, 1, need);
+  if (rc) return rc;
+  Bump bump(h->ws[1], h->ws_cap[1]);
+  const double* dB = B;
+  double* dX = X;
+  if (hb) {
+    double* t = bump.take<double>(ns);
+    BK_TRY(cudaMemcpyAsync(t, B, sizeof(double) * ns, cudaMemcpyHostToDevice, h->stream));
+    dB = t;
+  }
+  if (hx) {
+    double* t = bump.take<double>(ns);
+    BK_TRY(cudaMemcpyAsync(t, X, sizeof(double) * ns, cudaMemcpyHostToDevice, h->stream));
+    dX = t;
+  }
+  const size_t off = (bump.off + 255) & ~(size_t)255;
+  const int status = run(dB, dX, off);
+  if (hx) {
+    BK_TRY(cudaMemcpyAsync(X, dX, sizeof(double) * ns, cudaMemcpyDeviceToHost, h->stream));
+    BK_TRY(cudaStreamSynchronize(h->stream));
+  }
+  return status;
+}
+
+bool valid_s(int s) { return s >= 1 && s <= kMaxS; }
+
+// ctrl layout (row stride 32) -> dense row-major s x s
+__global__ void compact_kernel(int s, const double* __restrict__ in, double* __restrict__ out) {
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) out[i] = in[(i / s) * kMaxS + (i % s)];
+}
+
+}  // namespace
+
+// =============================================================== C ABI ====
+extern "C" {
+
+const char* bkrylov_status_string(int st) {
+  switch (st) {
+    case BK_OK: return "ok";
+    case BK_ERR_ARG: return "invalid argument";
+    case BK_ERR_CUDA: return "CUDA error";
+    case BK_ERR_ALLOC: return "device allocation failed";
+    case BK_NOT_CONVERGED: return "not converged";
+    case BK_BREAKDOWN: return "breakdown";
+    case BK_NONFINITE: return "non-finite value";
+    case BK_TIMEOUT: return "timeout";
+    case BK_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+int bkrylov_version(void) { return BKRYLOV_VERSION; }
+
+void bkrylov_opts_default(bkrylov_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-8;
+  o->maxit = 1000;
+  o->eta = INFINITY;
+  o->restart = 30;
+  o->ortho = 0;
+  o->prec = BK_FP64;
+  o->ir_inner_tol = 1e-5;
+  o->ir_max_outer = 30;
+}
+
+int bkrylov_create(bkrylov_handle* out, int device, void* stream) {
+  if (!out) return BK_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return BK_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return BK_ERR_CUDA;
+  bkrylov_ctx* h = new (std::nothrow) bkrylov_ctx();
+  if (!h) return BK_ERR_ALLOC;
+  h->device = device;
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device);
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreate(&h->stream) != cudaSuccess) { delete h; return BK_ERR_CUDA; }
+    h->own_stream = true;
+  }
+  if (cudaMallocHost(&h->host_ctrl, sizeof(Ctrl)) != cudaSuccess) {
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return BK_ERR_ALLOC;
+  }
+  *out = h;
+  return BK_OK;
+}
+
+int bkrylov_destroy(bkrylov_handle h) {
+  if (!h) return BK_ERR_ARG;
+  cudaStreamSynchronize(h->stream);
+  for (int i = 0; i < 2; ++i) if (h->ws[i]) cudaFree(h->ws[i]);
+  if (h->host_ctrl) cudaFreeHost(h->host_ctrl);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return BK_OK;
+}
+
+int bkrylov_set_stream(bkrylov_handle h, void* stream) {
+  if (!h) return BK_ERR_ARG;
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return BK_ERR_CUDA;
+  if (h->own_stream) { cudaStreamDestroy(h->stream); h->own_stream = false; }
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreate(&h->stream) != cudaSuccess) return BK_ERR_CUDA;
+    h->own_stream = true;
+  }
+  return BK_OK;
+}
+
+int bkrylov_op_csr(bkrylov_handle h, int64_t n, int64_t nnz, const int32_t* row_ptr,
+                   const int32_t* col, const double* val, bkrylov_op* A) {
+  if (!h || !A || n <= 0 || nnz < 0 || !row_ptr || (nnz > 0 && (!col || !val))) return BK_ERR_ARG;
+  if (nnz > INT32_MAX) return BK_ERR_ARG;
+  bkrylov_op op = new (std::nothrow) bkrylov_op_s();
+  if (!op) return BK_ERR_ALLOC;
+  op->h = h;
+  op->d.kind = kOpCsr;
+  op->d.n = n;
+  op->d.nnz = nnz;
+  op->d.row_ptr = row_ptr;
+  op->d.col = col;
+  op->d.val = val;
+  *A = op;
+  return BK_OK;
+}
+
+int bkrylov_op_stencil(bkrylov_handle h, int kind, int nx, int ny, int nz, const double* coeffs,
+                       bkrylov_op* A) {
+  if (!h || !A || nx <= 0 || ny <= 0 || nz <= 0 || !coeffs) return BK_ERR_ARG;
+  bkrylov_op op = new (std::nothrow) bkrylov_op_s();
+  if (!op) return BK_ERR_ALLOC;
+  op->h = h;
+  OpDesc& d = op->d;
+  d.nx = nx; d.ny = ny; d.nz = nz;
+  d.n = (int64_t)nx * ny * nz;
+  const Launch L = launch_of(h);
+  if (kind == BK_STENCIL_CONST7) {
+    d.kind = kOpConst7;
+    std::memcpy(d.c7, coeffs, sizeof(double) * 7);
+    const int64_t plane = (int64_t)nx * ny;
+    d.nnz = d.n + 2 * ((int64_t)(nx - 1) * ny * nz + (int64_t)nx * (ny - 1) * nz + plane * (nz - 1));
+  } else if (kind == BK_STENCIL_VAR7) {
+    d.kind = kOpVar7;
+    d.coef_len = 4 * d.n;
+    if (cudaMalloc(&d.coef, sizeof(double) * (size_t)d.coef_len) != cudaSuccess) { delete op; return BK_ERR_ALLOC; }
+    if (op_prepare_stencil(L, d, coeffs) != cudaSuccess) { cudaFree(d.coef); delete op; return BK_ERR_CUDA; }
+    const int64_t plane = (int64_t)nx * ny;
+    d.nnz = d.n + 2 * ((int64_t)(nx - 1) * ny * nz + (int64_t)nx * (ny - 1) * nz + plane * (nz - 1));
+  } else if (kind == BK_STENCIL_EDGE5) {
+    if (nz != 1) { delete op; return BK_ERR_ARG; }
+    d.kind = kOpEdge5;
+    d.edges = coeffs;
+    d.coef_len = d.n;
+    if (cudaMalloc(&d.coef, sizeof(double) * (size_t)d.coef_len) != cudaSuccess) { delete op; return BK_ERR_ALLOC; }
+    if (op_prepare_stencil(L, d, coeffs) != cudaSuccess) { cudaFree(d.coef); delete op; return BK_ERR_CUDA; }
+    d.nnz = d.n + 2 * ((int64_t)(nx - 1) * ny + (int64_t)nx * (ny - 1));
+  } else {
+    delete op;
+    return BK_ERR_ARG;
+  }
+  *A = op;
+  return BK_OK;
+}
+
+int bkrylov_op_destroy(bkrylov_op A) {
+  if (!A) return BK_ERR_ARG;
+  if (A->h) cudaStreamSynchronize(A->h->stream);
+  if (A->d.val32) cudaFree(A->d.val32);
+  if (A->d.coef) cudaFree(A->d.coef);
+  if (A->d.coef32) cudaFree(A->d.coef32);
+  if (A->d.edges32) cudaFree(A->d.edges32);
+  delete A;
+  return BK_OK;
+}
+
+int bkrylov_op_size(bkrylov_op A, int64_t* n, int64_t* nnz) {
+  if (!A) return BK_ERR_ARG;
+  if (n) *n = A->d.n;
+  if (nnz) *nnz = A->d.nnz;
+  return BK_OK;
+}
+
+int bkrylov_spmm(bkrylov_handle h, bkrylov_op A, int s, const void* P, void* Q, int prec) {
+  if (!h || !A || !valid_s(s) || !P || !Q || P == Q) return BK_ERR_ARG;
+  const Launch L = launch_of(h);
+  if (prec == BK_FP64) {
+    Epi<double> none;
+    BK_TRY(spmm<double>(L, A->d, s, (const double*)P, (double*)Q, nullptr, none));
+  } else if (prec == BK_FP32) {
+    BK_TRY(op_make_fp32(L, A->d));
+    Epi<float> none;
+    BK_TRY(spmm<float>(L, A->d, s, (const float*)P, (float*)Q, nullptr, none));
+  } else {
+    return BK_ERR_ARG;
+  }
+  return BK_OK;
+}
+
+int bkrylov_residual(bkrylov_handle h, bkrylov_op A, int s, const void* B, const void* X, void* R,
+                     int prec) {
+  if (!h || !A || !valid_s(s) || !B || !X || !R || X == R) return BK_ERR_ARG;
+  const Launch L = launch_of(h);
+  if (prec == BK_FP64) {
+    Epi<double> none;
+    BK_TRY(spmm<double>(L, A->d, s, (const double*)X, (double*)R, (const double*)B, none));
+  } else if (prec == BK_FP32) {
+    BK_TRY(op_make_fp32(L, A->d));
+    Epi<float> none;
+    BK_TRY(spmm<float>(L, A->d, s, (const float*)X, (float*)R, (const float*)B, none));
+  } else {
+    return BK_ERR_ARG;
+  }
+  return BK_OK;
+}
+
+// Scratch of the single-kernel entry points: grid partials + ticket counter +
+// a ctrl-layout result matrix, in workspace 1.
+static int small_scratch(bkrylov_handle h, double** gp, unsigned** cnt, double** res) {
+  const Launch L = launch_of(h);
+  const size_t gpn = gpart_count(L);
+  int rc = ensure_ws(h, 1, sizeof(double) * (gpn + kMM) + 1024);
+  if (rc) return rc;
+  Bump b(h->ws[1], h->ws_cap[1]);
+  *gp = b.take<double>(gpn);
+  *res = b.take<double>(kMM);
+  *cnt = b.take<unsigned>(8);
+  BK_TRY(cudaMemsetAsync(*cnt, 0, 8 * sizeof(unsigned), h->stream));
+  return BK_OK;
+}
+
+int bkrylov_bdot(bkrylov_handle h, int64_t n, int s, const void* X, const void* Y, double* G, int sym,
+                 int prec) {
+  if (!h || n <= 0 || !valid_s(s) || !X || !Y || !G) return BK_ERR_ARG;
+  double *gp, *res;
+  unsigned* cnt;
+  int rc = small_scratch(h, &gp, &cnt, &res);
+  if (rc) return rc;
+  const Launch L = launch_of(h);
+  if (prec == BK_FP64) {
+    Epi<double> e;
+    e.sym = sym ? 1 : 0; e.gram_out = res; e.gpart = gp; e.counter = cnt;
+    BK_TRY(gram<double>(L, n, s, (const double*)X, (const double*)Y, e));
+  } else if (prec == BK_FP32) {
+    Epi<float> e;
+    e.sym = sym ? 1 : 0; e.gram_out = res; e.gpart = gp; e.counter = cnt;
+    BK_TRY(gram<float>(L, n, s, (const float*)X, (const float*)Y, e));
+  } else {
+    return BK_ERR_ARG;
+  }
+  compact_kernel<<<1, 256, 0, h->stream>>>(s, res, G);
+  BK_TRY(cudaGetLastError());
+  return BK_OK;
+}
+
+int bkrylov_tsqr(bkrylov_handle h, int64_t n, int s, const void* X, void* Y, double* sigma, int prec) {
+  if (!h || !valid_s(s) || n < s || !X || !Y || !sigma) return BK_ERR_ARG;
+  const Launch L = launch_of(h);
+  const TsqrPlan tp = tsqr_plan(n, s);
+  const size_t gpn = gpart_count(L);
+  int rc = ensure_ws(h, 1, tp.bytes + sizeof(double) * (gpn + kMM) + 2048);
+  if (rc) return rc;
+  Bump b(h->ws[1], h->ws_cap[1]);
+  void* sc = b.take<char>(tp.bytes);
+  double* res = b.take<double>(kMM);
+  if (prec == BK_FP64) {
+    BK_TRY(tsqr<double>(L, tp, (const double*)X, (double*)Y, res, nullptr, sc, nullptr, nullptr,
+                        nullptr, nullptr));
+  } else if (prec == BK_FP32) {
+    BK_TRY(tsqr<float>(L, tp, (const float*)X, (float*)Y, res, nullptr, sc, nullptr, nullptr,
+                       nullptr, nullptr));
+  } else {
+    return BK_ERR_ARG;
+  }
+  compact_kernel<<<1, 256, 0, h->stream>>>(s, res, sigma);
+  BK_TRY(cudaGetLastError());
+  return BK_OK;
+}
+
+static int check_solve_args(bkrylov_handle h, bkrylov_op A, int s, const double* B, double* X,
+                            const bkrylov_opts& o) {
+  if (!h || !A || !valid_s(s) || !B || !X || (const void*)B == (const void*)X) return BK_ERR_ARG;
+  if (A->d.n < s) return BK_ERR_ARG;
+  if (!(o.tol >= 0.0) || o.maxit < 0 || !(o.eta >= 0.0)) return BK_ERR_ARG;
+  return BK_OK;
+}
+
+int bkrylov_solve_bcg(bkrylov_handle h, bkrylov_op A, int s, const double* B, double* X,
+                      const bkrylov_opts* opts, bkrylov_info* info) {
+  bkrylov_opts o;
+  opts_or_default(opts, &o);
+  int rc = check_solve_args(h, A, s, B, X, o);
+  if (rc) return rc;
+  const int64_t n = A->d.n;
+  if (o.prec == BK_FP64) {
+    return with_device_blocks(h, n, s, B, X, 0, [&](const double* dB, double* dX, size_t) {
+      return bcg_device<double>(h, A->d, s, dB, dX, o, std::ldexp(1.0, -52), info);
+    });
+  }
+  if (o.prec == BK_FP32_IR) {
+    const size_t ns = (size_t)n * s;
+    const size_t extra = sizeof(double) * ns + 2 * sizeof(float) * ns +
+                         sizeof(double) * ((size_t)h->sms * 4 * kMaxS + 2 * kMaxS + 64) + 4096;
+    return with_device_blocks(h, n, s, B, X, extra, [&](const double* dB, double* dX, size_t off) {
+      return bcg_ir_device(h, A, s, dB, dX, o, info, h->ws[1], off);
+    });
+  }
+  return BK_ERR_ARG;   // plain FP32 solves are reached through refinement only
+}
+
+int bkrylov_solve_bbicgstab(bkrylov_handle h, bkrylov_op A, int s, const double* B, double* X,
+                            const bkrylov_opts* opts, bkrylov_info* info) {
+  bkrylov_opts o;
+  opts_or_default(opts, &o);
+  int rc = check_solve_args(h, A, s, B, X, o);
+  if (rc) return rc;
+  if (o.prec != BK_FP64) return BK_ERR_UNSUPPORTED;
+  return with_device_blocks(h, A->d.n, s, B, X, 0, [&](const double* dB, double* dX, size_t) {
+    return bicg_device(h, A->d, s, dB, dX, o, info);
+  });
+}
+
+int bkrylov_solve_bgmres(bkrylov_handle h, bkrylov_op A, int s, const double* B, double* X,
+                         const bkrylov_opts* opts, bkrylov_info* info) {
+  bkrylov_opts o;
+  opts_or_default(opts, &o);
+  int rc = check_solve_args(h, A, s, B, X, o);
+  if (rc) return rc;
+  if (o.prec != BK_FP64) return BK_ERR_UNSUPPORTED;
+  if (o.restart < 1 || o.restart > 64) return BK_ERR_ARG;
+  return with_device_blocks(h, A->d.n, s, B, X, 0, [&](const double* dB, double* dX, size_t) {
+    return gmres_device(h, A->d, s, dB, dX, o, info);
+  });
+}
+
+int bkrylov_adjoint_scatter(bkrylov_handle h, bkrylov_op A, int s, const double* Lam,
+                            const double* X, double* g) {
+  if (!h || !A || !valid_s(s) || !Lam || !X || !g) return BK_ERR_ARG;
+  if (A->d.kind != kOpCsr) return BK_ERR_ARG;
+  BK_TRY(adjoint_scatter(launch_of(h), A->d, s, Lam, X, g));
+  return BK_OK;
+}
+
+int bkrylov_edge_theta_grad(bkrylov_handle h, bkrylov_op A, int s, const double* Lam,
+                            const double* X, double* g) {
+  if (!h || !A || !valid_s(s) || !Lam || !X || !g) return BK_ERR_ARG;
+  if (A->d.kind != kOpEdge5) return BK_ERR_ARG;
+  BK_TRY(edge_theta_grad(launch_of(h), A->d, s, Lam, X, g));
+  return BK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,173 @@
+// Internal definitions shared by the bkrylov CUDA sources (sm_103a).
+//
+// Thread mapping used by every row-local kernel on an n x s row-major block:
+// a warp is split into 32/SW "sub-warps" of SW = next_pow2(s) lanes; one
+// sub-warp owns one row and lane c < s owns column c.  A warp therefore
+// touches 32/SW consecutive rows = one contiguous span of memory, and the s
+// values of a row can be exchanged with __shfl_sync(width = SW).  Loops over
+// rows advance a whole warp at a time so that every lane of the warp takes
+// part in every shuffle.
+#pragma once
+
+#include <cstdint>
+#include <cstdio>
+#include <cuda_runtime.h>
+
+#include "../../include/bkrylov.h"
+
+namespace bk {
+
+constexpr int kMaxS = BKRYLOV_MAX_S;   // 32
+constexpr int kThreads = 256;          // threads per CTA of the row kernels
+constexpr int kWarps = kThreads / 32;
+
+// ---- per-solve device control block --------------------------------------------
+// s x s matrices are stored with row stride kMaxS: M[i][j] at i * kMaxS + j.
+enum : int { kDoneRunning = 0, kDoneConverged = 1, kDoneStopped = 2 };
+enum : int { kCntA = 0, kCntB = 1, kCntC = 2, kCntD = 3, kNumCounters = 8 };
+constexpr int kMM = kMaxS * kMaxS;
+
+struct Ctrl {
+  int done;          // kDone*
+  int status;        // bkrylov_status
+  int iter;          // completed iterations
+  int reorths;
+  int reortho_now;   // decision of the current iteration
+  int maxit;
+  int s;
+  int n_forced;
+  double tol;
+  double eta;
+  double eps;        // machine epsilon of the working precision
+  double omega;      // BBiCGStab scalar
+  double frob[4];    // Frobenius sums (BBiCGStab: <U,S>, <U,U>)
+  unsigned counters[kNumCounters];
+  double n0[kMaxS];      // ||R0_i||
+  double relres[kMaxS];
+  double alpha[kMM];     // BCG alpha = P^T Q        | BBiCGStab R0s^T Q
+  double rho[kMM];       // BCG rho   = Rb^T Rb      | BBiCGStab R^T R (kappa_D, norms)
+  double rho_new[kMM];
+  double sigma[kMM];
+  double gamma[kMM];     // normalizer R factor of the last TSQR (diag >= 0)
+  double lam[kMM];       // lambda
+  double lx[kMM];        // lambda sigma  (X update)
+  double beta[kMM];
+  double g2[kMM];        // BBiCGStab R0s^T R
+  double g3[kMM];        // BBiCGStab R0s^T U
+  double lu[kMM];        // BBiCGStab LU factors of R0s^T Q
+  double sigma_new[kMM]; // BBiCGStab sigma^{k+1}
+  int piv[kMaxS];
+  double nb[kMaxS];      // refinement: ||B_i||
+};
+
+// ---- small helpers --------------------------------------------------------------
+__host__ __device__ inline int next_pow2_s(int s) {
+  int w = 1;
+  while (w < s) w <<= 1;
+  return w;
+}
+
+template <int SW, typename T>
+__device__ __forceinline__ T sw_bcast(T v, int src) {
+  return __shfl_sync(0xffffffffu, v, src, SW);
+}
+
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
+
+// Upper-triangle packed index of (a, c), a <= c.
+__host__ __device__ inline int ut_index(int a, int c) { return c * (c + 1) / 2 + a; }
+__host__ __device__ inline int ut_count(int s) { return s * (s + 1) / 2; }
+
+// ---- deterministic grid reduction ----------------------------------------------
+// Every CTA stores its `cnt` partial sums (already reduced inside the CTA, in
+// shared memory `part`) to gpart[blockIdx.x * cnt + i].  The last CTA to
+// arrive (atomic ticket) sums the partials of CTA 0, 1, 2, ... in this fixed
+// order, so the result is bitwise reproducible for a given grid.  No thread
+// ever waits for another CTA.  Returns true in the last CTA only; the
+// reduced values are then in `part`.  The ticket counter is reset to 0 by
+// the last CTA for the next use.
+__device__ inline bool grid_reduce_last(double* part, int cnt, double* gpart,
+                                        unsigned* counter) {
+  __shared__ unsigned s_ticket;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) gpart[(size_t)blockIdx.x * cnt + i] = part[i];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_ticket = atomicAdd(counter, 1u);
+  __syncthreads();
+  if (s_ticket != gridDim.x - 1) return false;
+  __threadfence();
+  const int G = gridDim.x;
+  // 8 fixed chunks of CTAs per output when the block has enough threads.
+  const int R = (blockDim.x >= 8 * cnt) ? 8 : 1;
+  if (R == 8) {
+    double acc = 0.0;
+    const int i = threadIdx.x % cnt;
+    const int q = threadIdx.x / cnt;
+    if (q < R) {
+      int b0 = (int)((long long)G * q / R), b1 = (int)((long long)G * (q + 1) / R);
+      for (int b = b0; b < b1; ++b) acc += ldcg(gpart + (size_t)b * cnt + i);
+    }
+    __shared__ double s_acc[kThreads];
+    if (q < R) s_acc[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      double t = 0.0;
+      for (int k = 0; k < R; ++k) t += s_acc[k * cnt + threadIdx.x];
+      part[threadIdx.x] = t;
+    }
+  } else {
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+      double t = 0.0;
+      for (int b = 0; b < G; ++b) t += ldcg(gpart + (size_t)b * cnt + j);
+      part[j] = t;
+    }
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+  __syncthreads();
+  return true;
+}
+
+// Reduce per-lane Gram accumulators of a CTA into shared memory.
+// On entry lane c (< s) of every sub-warp holds acc[a] = partial of G[a][c].
+// `sym`: only a <= c are meaningful; the packed upper triangle is produced.
+// On exit part[0..cnt) holds the CTA's sums (cnt = ut_count(s) or s*s);
+// `scratch` must hold kWarps * cnt doubles.
+template <int SW>
+__device__ inline void cta_reduce_gram(double (&acc)[SW], int s, bool sym, double* scratch,
+                                       double* part) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = lane & (SW - 1);
+#pragma unroll
+  for (int a = 0; a < SW; ++a) {
+#pragma unroll
+    for (int off = SW; off < 32; off <<= 1) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], off);
+  }
+  const int cnt = sym ? ut_count(s) : s * s;
+  if (lane < SW && c < s) {
+#pragma unroll
+    for (int a = 0; a < SW; ++a) {
+      if (a < s && (!sym || a <= c)) scratch[warp * cnt + (sym ? ut_index(a, c) : a * s + c)] = acc[a];
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += scratch[w * cnt + i];
+    part[i] = t;
+  }
+  __syncthreads();
+}
+
+// Unpack a reduced Gram (packed upper or full s x s) into a ctrl-layout matrix.
+__device__ inline void unpack_gram(const double* part, int s, bool sym, double* M) {
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
+    int a = i / s, c = i % s;
+    double v;
+    if (sym) v = (a <= c) ? part[ut_index(a, c)] : part[ut_index(c, a)];
+    else v = part[i];
+    M[a * kMaxS + c] = v;
+  }
+}
+
+}  // namespace bk

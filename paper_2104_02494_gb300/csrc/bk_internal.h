@@ -1,0 +1,144 @@
+// Host-side internal interfaces of the bkrylov library.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/bkrylov.h"
+
+namespace bk {
+
+struct Ctrl;
+
+enum OpKind { kOpCsr = 0, kOpConst7 = 1, kOpVar7 = 2, kOpEdge5 = 3 };
+
+struct OpDesc {
+  int kind = kOpCsr;
+  int64_t n = 0, nnz = 0;
+  // CSR (borrowed) + owned float copy of the values
+  const int32_t* row_ptr = nullptr;
+  const int32_t* col = nullptr;
+  const double* val = nullptr;
+  float* val32 = nullptr;
+  // stencils
+  int nx = 0, ny = 0, nz = 0;
+  double c7[7] = {0, 0, 0, 0, 0, 0, 0};
+  // VAR7: owned diag + faces to the +x/+y/+z neighbour (0 at the boundary), 4 arrays of n.
+  // EDGE5: owned diag (n); borrowed edge coefficients (ny*(nx+1) + (ny+1)*nx).
+  double* coef = nullptr;          // owned double coefficient arrays
+  float* coef32 = nullptr;         // owned float copy (lazy)
+  const double* edges = nullptr;   // EDGE5 borrowed
+  float* edges32 = nullptr;        // EDGE5 owned float copy (lazy)
+  int64_t coef_len = 0;
+};
+
+// Fused epilogue of a row kernel: Gram  left^T out  and Frobenius sums <out, frob>_F, <out,out>_F.
+template <typename T>
+struct Epi {
+  const T* left = nullptr;     // Gram G = left^T out (null: no Gram)
+  int sym = 0;                 // upper triangle only, mirrored
+  const T* frob = nullptr;     // Frobenius partner (null: none)
+  double* gram_out = nullptr;  // s x s result, row stride 32 (device)
+  double* frob_out = nullptr;  // [2]: <out,frob>, <out,out> (device)
+  double* gpart = nullptr;     // grid partials scratch
+  unsigned* counter = nullptr; // ticket counter (0 on entry)
+  const int* done = nullptr;   // optional stop flag: kernel exits when *done != 0
+  const int* only_if = nullptr;  // optional: kernel exits unless *only_if != 0
+};
+
+struct Launch {
+  cudaStream_t stream = nullptr;
+  int sms = 152;
+};
+
+// ---- operator products (bk_spmm.cu) ----
+// out = A in  (or out = sub - A in when sub != null), with optional fused epilogue.
+template <typename T>
+cudaError_t spmm(const Launch& L, const OpDesc& A, int s, const T* in, T* out, const T* sub,
+                 const Epi<T>& ep);
+cudaError_t op_prepare_stencil(const Launch& L, OpDesc& A, const double* coeffs);
+cudaError_t op_make_fp32(const Launch& L, OpDesc& A);
+int spmm_grid(const Launch& L, int64_t n, int s);
+
+// ---- row kernels (bk_rows.cu) ----
+// G = X^T Y reduced deterministically into gram_out (row stride 32).
+template <typename T>
+cudaError_t gram(const Launch& L, int64_t n, int s, const T* X, const T* Y, const Epi<T>& ep);
+// BCG fused update: X += P*lx ; R = R - Q*lam ; if (!reortho) rho_new = R^T R.
+template <typename T>
+cudaError_t bcg_update(const Launch& L, int64_t n, int s, const T* P, const T* Q, T* X, T* R,
+                       Ctrl* ctrl, double* gpart, int use_fp64_x);
+// BCG direction update P = R + P*beta.
+template <typename T>
+cudaError_t bcg_pupdate(const Launch& L, int64_t n, int s, const T* R, T* P, Ctrl* ctrl);
+// Generic Y = alpha*X*M + beta*Y (M s x s row stride 32 on device), optional fused Gram.
+template <typename T>
+cudaError_t block_axpy(const Launch& L, int64_t n, int s, const T* X, const double* M,
+                       double alpha, T* Y, double beta, const int* done);
+cudaError_t adjoint_scatter(const Launch& L, const OpDesc& A, int s, const double* Lam,
+                            const double* X, double* g);
+cudaError_t edge_theta_grad(const Launch& L, const OpDesc& A, int s, const double* Lam,
+                            const double* X, double* g);
+
+// ---- TSQR (bk_tsqr.cu) ----
+struct TsqrPlan {
+  int64_t n = 0;
+  int s = 0;
+  int tile = 256;              // rows per leaf tile
+  int fanin = 8;               // children per tree node
+  int levels = 0;              // number of tree levels above the leaves
+  int64_t nodes[16] = {0};     // nodes per level (level 0 = leaves)
+  size_t bytes = 0;            // scratch bytes
+};
+TsqrPlan tsqr_plan(int64_t n, int s);
+// Y, gamma = Norm(X) (Y may alias X).  gamma -> ctrl-layout s x s (row stride 32).
+// If rho_out != null, also the Gram Y^T Y (row stride 32) is produced.
+// done: optional stop flag (skip when *done); reortho_flag: optional, skip unless *flag.
+template <typename T>
+cudaError_t tsqr(const Launch& L, const TsqrPlan& plan, const T* X, T* Y, double* gamma_out,
+                 double* rho_out, void* scratch, double* gpart, unsigned* counter,
+                 const int* done, const int* reortho_flag);
+
+// ---- small s x s kernels (bk_small.cu) ----
+cudaError_t small_bcg_init(const Launch& L, Ctrl* ctrl, int eta_positive);
+cudaError_t small_bcg_1(const Launch& L, Ctrl* ctrl, const uint8_t* forced);
+cudaError_t small_bcg_2(const Launch& L, Ctrl* ctrl, double* history, uint8_t* decisions);
+cudaError_t small_bicg_1(const Launch& L, Ctrl* ctrl, const uint8_t* forced);
+cudaError_t small_bicg_2(const Launch& L, Ctrl* ctrl);
+cudaError_t small_bicg_3(const Launch& L, Ctrl* ctrl, double* history, uint8_t* decisions);
+cudaError_t small_set_identity(const Launch& L, double* M, int s);
+cudaError_t small_colnorms_from_gram(const Launch& L, Ctrl* ctrl);
+
+// BGMRes small kernels
+cudaError_t small_gmres_step(const Launch& L, Ctrl* ctrl, const double* Hc, double* H, double* Gq,
+                             double* sig, int k, int m, double* history, int hist_index);
+cudaError_t small_gmres_backsub(const Launch& L, Ctrl* ctrl, const double* H, const double* sig,
+                                double* zeta, int k_done, int m);
+
+// multi-block tall-skinny kernels (bk_rows.cu)
+// H_j[a][c] (+)= sum_r V_j[r][a] W[r][c] for j < nb; H_j = H + j*1024, row stride 32
+cudaError_t multi_gram(const Launch& L, int64_t n, int s, const double* const* V, int nb,
+                       const double* W, double* H, int accumulate, double* gpart,
+                       unsigned* counter, const int* done);
+// W[r][c] += sign * sum_j sum_a V_j[r][a] H_j[a][c]   (H_j as above)
+cudaError_t multi_axpy(const Launch& L, int64_t n, int s, const double* const* V, int nb,
+                       const double* H, double* W, double sign, const int* done);
+
+cudaError_t bicg_final(const Launch& L, int64_t n, int s, double* S, const double* U, double* X,
+                       double* P, const double* Q, const double* R0s, Ctrl* ctrl, double* gpart);
+cudaError_t vec_add(const Launch& L, int64_t count, const double* x, double* y, const int* done);
+cudaError_t diag_sqrt(const Launch& L, int s, const double* G, double* out);
+cudaError_t init_sig(const Launch& L, int s, const double* G, double* sig, int nblk);
+int multi_gram_grid(const Launch& L, int64_t n, int s, int nb);
+
+// IR helpers (bk_rows.cu)
+cudaError_t ir_colnorms(const Launch& L, int64_t n, int s, const double* R, double* norms2,
+                        double* gpart, unsigned* counter);
+cudaError_t ir_to_fp32(const Launch& L, int64_t n, int s, const double* R, const double* norms,
+                       float* R32);
+cudaError_t ir_accumulate(const Launch& L, int64_t n, int s, const float* D32,
+                          const double* norms, double* X);
+cudaError_t cast_block(const Launch& L, int64_t count, const double* in, float* out);
+
+}  // namespace bk

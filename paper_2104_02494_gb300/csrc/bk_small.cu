@@ -1,0 +1,673 @@
+// The s x s part of every iteration, on one CTA in FP64 (s <= 32):
+// Cholesky / LU solves for the block coefficients lambda and beta, the
+// diagonally scaled condition number kappa_D of the adaptive
+// re-orthonormalisation test, the residual-transformation sigma, per-column
+// residual norms, the stopping test and the block Givens step of block GMRes.
+// All matrices live in shared memory with row stride 32 (kMaxS).
+#include <math.h>
+
+#include "bk_common.cuh"
+#include "bk_hh.cuh"
+#include "bk_internal.h"
+
+namespace bk {
+
+constexpr int kST = 256;   // threads of the small-solve CTA
+#define IDX(i, j) ((i) * kMaxS + (j))
+
+__device__ void sm_copy(double* dst, const double* src, int s) {
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
+    const int a = i / s, c = i % s;
+    dst[IDX(a, c)] = src[IDX(a, c)];
+  }
+}
+
+__device__ void sm_identity(double* dst, int s) {
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
+    const int a = i / s, c = i % s;
+    dst[IDX(a, c)] = (a == c) ? 1.0 : 0.0;
+  }
+}
+
+// C = op(A) B with op(A) = A or A^T (C must not alias A or B).
+__device__ void sm_matmul(double* C, const double* A, bool transA, const double* B, int s) {
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
+    const int a = i / s, c = i % s;
+    double acc = 0.0;
+    for (int k = 0; k < s; ++k) acc = fma(transA ? A[IDX(k, a)] : A[IDX(a, k)], B[IDX(k, c)], acc);
+    C[IDX(a, c)] = acc;
+  }
+}
+
+__device__ bool sm_all_finite(const double* A, int s, int* flag) {
+  if (threadIdx.x == 0) *flag = 1;
+  __syncthreads();
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x)
+    if (!isfinite(A[IDX(i / s, i % s)])) *flag = 0;
+  __syncthreads();
+  const bool ok = *flag != 0;
+  __syncthreads();
+  return ok;
+}
+
+// In-place Cholesky A = L L^T (lower triangle of A overwritten by L).
+// Fails (returns false) on a non-positive or non-finite pivot, which is the
+// LAPACK potrf criterion.
+__device__ bool sm_cholesky(double* A, int s, int* flag) {
+  if (threadIdx.x == 0) *flag = 1;
+  __syncthreads();
+  for (int k = 0; k < s; ++k) {
+    if (threadIdx.x == 0) {
+      const double d = A[IDX(k, k)];
+      if (!(d > 0.0) || !isfinite(d)) *flag = 0;
+      else A[IDX(k, k)] = sqrt(d);
+    }
+    __syncthreads();
+    if (!*flag) return false;
+    const double lkk = A[IDX(k, k)];
+    for (int i = k + 1 + threadIdx.x; i < s; i += blockDim.x) A[IDX(i, k)] /= lkk;
+    __syncthreads();
+    const int r = s - k - 1;
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+      const int i = k + 1 + e / r, j = k + 1 + e % r;
+      if (j <= i) A[IDX(i, j)] = fma(-A[IDX(i, k)], A[IDX(j, k)], A[IDX(i, j)]);
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// X = (L L^T)^{-1} B, one thread per right-hand-side column (X may alias B).
+__device__ void sm_chol_solve(const double* L, const double* B, double* X, int s) {
+  const int c = threadIdx.x;
+  if (c < s) {
+    for (int i = 0; i < s; ++i) {           // forward: L y = b
+      double v = B[IDX(i, c)];
+      for (int k = 0; k < i; ++k) v = fma(-L[IDX(i, k)], X[IDX(k, c)], v);
+      X[IDX(i, c)] = v / L[IDX(i, i)];
+    }
+    for (int i = s - 1; i >= 0; --i) {      // backward: L^T x = y
+      double v = X[IDX(i, c)];
+      for (int k = i + 1; k < s; ++k) v = fma(-L[IDX(k, i)], X[IDX(k, c)], v);
+      X[IDX(i, c)] = v / L[IDX(i, i)];
+    }
+  }
+  __syncthreads();
+}
+
+// In-place LU with partial pivoting (row interchanges recorded in piv).
+// Fails on an exactly zero or non-finite pivot.
+__device__ bool sm_lu(double* A, int* piv, int s, int* flag) {
+  __shared__ int s_p;
+  if (threadIdx.x == 0) *flag = 1;
+  __syncthreads();
+  for (int k = 0; k < s; ++k) {
+    if (threadIdx.x == 0) {
+      int p = k;
+      double best = fabs(A[IDX(k, k)]);
+      for (int i = k + 1; i < s; ++i) {
+        const double v = fabs(A[IDX(i, k)]);
+        if (v > best) { best = v; p = i; }
+      }
+      piv[k] = p;
+      s_p = p;
+      if (!(best > 0.0) || !isfinite(best)) *flag = 0;
+    }
+    __syncthreads();
+    if (!*flag) return false;
+    const int p = s_p;
+    if (p != k)
+      for (int j = threadIdx.x; j < s; j += blockDim.x) {
+        const double t = A[IDX(k, j)]; A[IDX(k, j)] = A[IDX(p, j)]; A[IDX(p, j)] = t;
+      }
+    __syncthreads();
+    const double pk = A[IDX(k, k)];
+    for (int i = k + 1 + threadIdx.x; i < s; i += blockDim.x) A[IDX(i, k)] /= pk;
+    __syncthreads();
+    const int r = s - k - 1;
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+      const int i = k + 1 + e / r, j = k + 1 + e % r;
+      A[IDX(i, j)] = fma(-A[IDX(i, k)], A[IDX(k, j)], A[IDX(i, j)]);
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// X = A^{-1} B from the LU factors (X may alias B), one thread per column.
+__device__ void sm_lu_solve(const double* LU, const int* piv, const double* B, double* X, int s) {
+  const int c = threadIdx.x;
+  if (c < s) {
+    if (X != B) for (int i = 0; i < s; ++i) X[IDX(i, c)] = B[IDX(i, c)];
+    for (int k = 0; k < s; ++k) {
+      const int p = piv[k];
+      if (p != k) { const double t = X[IDX(k, c)]; X[IDX(k, c)] = X[IDX(p, c)]; X[IDX(p, c)] = t; }
+    }
+    for (int i = 0; i < s; ++i) {
+      double v = X[IDX(i, c)];
+      for (int k = 0; k < i; ++k) v = fma(-LU[IDX(i, k)], X[IDX(k, c)], v);
+      X[IDX(i, c)] = v;
+    }
+    for (int i = s - 1; i >= 0; --i) {
+      double v = X[IDX(i, c)];
+      for (int k = i + 1; k < s; ++k) v = fma(-LU[IDX(i, k)], X[IDX(k, c)], v);
+      X[IDX(i, c)] = v / LU[IDX(i, i)];
+    }
+  }
+  __syncthreads();
+}
+
+// kappa_D(A) = kappa_2(D^-1/2 A D^-1/2), D = diag(A)  (Def. in Ch. 4.3), by
+// cyclic Jacobi with a round-robin ordering (s/2 disjoint rotations per round,
+// applied together).  +inf when a diagonal entry or an eigenvalue is <= 0.
+// M and M2 are shared work matrices.
+__device__ double sm_kappa_d(const double* A, int s, double* M, double* M2, double* rot, int* flag) {
+  __shared__ double s_kappa;
+  if (threadIdx.x == 0) *flag = 1;
+  __syncthreads();
+  for (int i = threadIdx.x; i < s; i += blockDim.x)
+    if (!(A[IDX(i, i)] > 0.0)) *flag = 0;
+  __syncthreads();
+  if (!*flag) return INFINITY;
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
+    const int a = i / s, c = i % s;
+    M[IDX(a, c)] = A[IDX(a, c)] / sqrt(A[IDX(a, a)] * A[IDX(c, c)]);
+  }
+  __syncthreads();
+  const int N = (s % 2) ? s + 1 : s;          // players incl. a dummy for odd s
+  // rot[4*i]: partner index (or -1), rot[4*i+1] c, rot[4*i+2] role sign (+1 for p, -1 for q), rot[4*i+3] sn
+  for (int sweep = 0; sweep < 40 && s > 1; ++sweep) {
+    for (int round = 0; round < N - 1; ++round) {
+      if (threadIdx.x < N / 2) {
+        const int i = threadIdx.x;
+        auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + round) % (N - 1)) + 1; };
+        int p = player(i), q = player(N - 1 - i);
+        if (p > q) { const int t = p; p = q; q = t; }
+        if (q < s) {
+          const double app = M[IDX(p, p)], aqq = M[IDX(q, q)], apq = M[IDX(p, q)];
+          double cs = 1.0, sn = 0.0;
+          if (apq != 0.0) {
+            const double th = (aqq - app) / (2.0 * apq);
+            const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            cs = 1.0 / sqrt(t * t + 1.0);
+            sn = t * cs;
+          }
+          rot[4 * p] = q; rot[4 * p + 1] = cs; rot[4 * p + 2] = 1.0; rot[4 * p + 3] = sn;
+          rot[4 * q] = p; rot[4 * q + 1] = cs; rot[4 * q + 2] = -1.0; rot[4 * q + 3] = sn;
+        } else if (p < s) {
+          rot[4 * p] = -1.0; rot[4 * p + 1] = 1.0; rot[4 * p + 2] = 1.0; rot[4 * p + 3] = 0.0;
+        }
+      }
+      __syncthreads();
+      // M2 = J^T M J; column i of J: (row i: c, row partner: -sn) for a p-role
+      // index, (row partner: sn, row i: c) for a q-role index.
+      for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+        const int i = e / s, j = e % s;
+        const int pi = (int)rot[4 * i], pj = (int)rot[4 * j];
+        const double ci = rot[4 * i + 1], cj = rot[4 * j + 1];
+        const double oi = (pi < 0) ? 0.0 : (rot[4 * i + 2] > 0 ? -rot[4 * i + 3] : rot[4 * i + 3]);
+        const double oj = (pj < 0) ? 0.0 : (rot[4 * j + 2] > 0 ? -rot[4 * j + 3] : rot[4 * j + 3]);
+        double v = ci * cj * M[IDX(i, j)];
+        if (pj >= 0) v = fma(ci * oj, M[IDX(i, pj)], v);
+        if (pi >= 0) v = fma(oi * cj, M[IDX(pi, j)], v);
+        if (pi >= 0 && pj >= 0) v = fma(oi * oj, M[IDX(pi, pj)], v);
+        M2[IDX(i, j)] = v;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+        const int i = e / s, j = e % s;
+        M[IDX(i, j)] = (i == j || (int)rot[4 * i] != j) ? M2[IDX(i, j)] : 0.0;
+      }
+      __syncthreads();
+    }
+    // convergence: every off-diagonal entry negligible relative to its diagonal pair
+    if (threadIdx.x == 0) *flag = 1;
+    __syncthreads();
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+      const int i = e / s, j = e % s;
+      if (i != j && fabs(M[IDX(i, j)]) > 1e-16 * sqrt(fabs(M[IDX(i, i)] * M[IDX(j, j)]))) *flag = 0;
+    }
+    __syncthreads();
+    if (*flag) break;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double lo = M[IDX(0, 0)], hi = lo;
+    for (int i = 1; i < s; ++i) { lo = fmin(lo, M[IDX(i, i)]); hi = fmax(hi, M[IDX(i, i)]); }
+    s_kappa = (lo > 0.0) ? hi / lo : INFINITY;
+  }
+  __syncthreads();
+  return s_kappa;
+}
+
+__device__ inline void stop(Ctrl* c, int status) {
+  if (threadIdx.x == 0) { c->done = kDoneStopped; c->status = status; }
+}
+
+// re-orthonormalisation decision (Eq. "reortho_criterion", read as
+// eta * kappa_D > 1/sqrt(eps); eta = 0 never, eta = inf always)
+__device__ int decide(Ctrl* c, const uint8_t* forced, const double* A, double* M, double* M2,
+                      double* rot, int* flag) {
+  const int k = c->iter;
+  if (forced && k < c->n_forced) return forced[k] ? 1 : 0;
+  if (c->eta == 0.0) return 0;
+  if (isinf(c->eta)) return 1;
+  const double kap = sm_kappa_d(A, c->s, M, M2, rot, flag);
+  return (c->eta * kap > 1.0 / sqrt(c->eps)) ? 1 : 0;
+}
+
+struct SmallSmem {
+  double A[kMM], B[kMM], C[kMM], D[kMM], E[kMM], F[kMM];
+  double rot[4 * (kMaxS + 1)];
+  double red[kST];
+  double w[kMaxS], tau[kMaxS];
+  int flag;
+};
+
+// ---------------------------------------------------------------- BCG ----
+// Initial test: relres_i = sqrt((sigma^T rho sigma)_ii) / ||R0_i||.
+__global__ void __launch_bounds__(kST) small_bcg_init_k(Ctrl* c) {
+  extern __shared__ double smraw[];
+  SmallSmem& S = *reinterpret_cast<SmallSmem*>(smraw);
+  const int s = c->s;
+  sm_copy(S.A, c->rho, s);
+  sm_copy(S.B, c->sigma, s);
+  __syncthreads();
+  sm_matmul(S.C, S.A, false, S.B, s);     // rho sigma
+  __syncthreads();
+  if (threadIdx.x < s) {
+    const int i = threadIdx.x;
+    double v = 0.0;
+    for (int k = 0; k < s; ++k) v = fma(S.B[IDX(k, i)], S.C[IDX(k, i)], v);
+    const double n0 = c->n0[i];
+    c->relres[i] = n0 > 0.0 ? sqrt(fmax(v, 0.0)) / n0 : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < s; ++i) mx = fmax(mx, c->relres[i]);
+    if (!isfinite(mx)) { c->done = kDoneStopped; c->status = BK_NONFINITE; }
+    else if (mx <= c->tol) { c->done = kDoneConverged; c->status = BK_OK; }
+    else if (c->maxit <= 0) { c->done = kDoneStopped; c->status = BK_NOT_CONVERGED; }
+  }
+}
+
+// lambda = alpha^{-1} rho, the re-orthonormalisation decision, lx = lambda sigma.
+__global__ void __launch_bounds__(kST) small_bcg_1_k(Ctrl* c, const uint8_t* forced) {
+  if (c->done) return;
+  extern __shared__ double smraw[];
+  SmallSmem& S = *reinterpret_cast<SmallSmem*>(smraw);
+  const int s = c->s;
+  sm_copy(S.A, c->alpha, s);
+  sm_copy(S.B, c->rho, s);
+  sm_copy(S.E, c->sigma, s);
+  __syncthreads();
+  if (!sm_all_finite(S.A, s, &S.flag)) { stop(c, BK_NONFINITE); return; }
+  sm_copy(S.C, S.A, s);
+  __syncthreads();
+  if (!sm_cholesky(S.C, s, &S.flag)) { stop(c, BK_BREAKDOWN); return; }
+  sm_chol_solve(S.C, S.B, S.D, s);            // D = lambda
+  const int reo = decide(c, forced, S.A, S.B, S.C, S.rot, &S.flag);   // clobbers B, C
+  __syncthreads();
+  sm_matmul(S.B, S.D, false, S.E, s);          // lx = lambda sigma
+  __syncthreads();
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
+    const int a = i / s, b = i % s;
+    c->lam[IDX(a, b)] = S.D[IDX(a, b)];
+    c->lx[IDX(a, b)] = S.B[IDX(a, b)];
+  }
+  if (threadIdx.x == 0) c->reortho_now = reo;
+}
+
+// sigma update, residual norms, stopping test, beta = rho^{-1} gamma^T rho_new.
+__global__ void __launch_bounds__(kST) small_bcg_2_k(Ctrl* c, double* history, uint8_t* decisions) {
+  if (c->done) return;
+  extern __shared__ double smraw[];
+  SmallSmem& S = *reinterpret_cast<SmallSmem*>(smraw);
+  const int s = c->s;
+  const int reo = c->reortho_now;
+  const int k = c->iter;
+  sm_copy(S.A, c->rho_new, s);
+  sm_copy(S.B, c->sigma, s);
+  if (reo) sm_copy(S.C, c->gamma, s); else sm_identity(S.C, s);
+  __syncthreads();
+  if (!sm_all_finite(S.A, s, &S.flag)) { stop(c, BK_NONFINITE); return; }
+  sm_matmul(S.D, S.C, false, S.B, s);          // sigma_new = gamma sigma
+  __syncthreads();
+  if (threadIdx.x < s) {
+    const int i = threadIdx.x;
+    double v = 0.0;
+    if (reo) {
+      for (int r = 0; r < s; ++r) v = fma(S.D[IDX(r, i)], S.D[IDX(r, i)], v);
+    } else {
+      for (int r = 0; r < s; ++r) {
+        double t = 0.0;
+        for (int q = 0; q < s; ++q) t = fma(S.A[IDX(r, q)], S.D[IDX(q, i)], t);
+        v = fma(S.D[IDX(r, i)], t, v);
+      }
+    }
+    const double n0 = c->n0[i];
+    c->relres[i] = n0 > 0.0 ? sqrt(fmax(v, 0.0)) / n0 : 0.0;
+  }
+  __syncthreads();
+  __shared__ int s_conv;
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < s; ++i) mx = fmax(mx, c->relres[i]);
+    if (history) history[k] = mx;
+    if (decisions) decisions[k] = (uint8_t)reo;
+    c->iter = k + 1;
+    c->reorths += reo;
+    s_conv = !isfinite(mx) ? -1 : (mx <= c->tol ? 1 : 0);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) c->sigma[IDX(i / s, i % s)] = S.D[IDX(i / s, i % s)];
+  if (s_conv < 0) { stop(c, BK_NONFINITE); return; }
+  if (s_conv > 0) {
+    if (threadIdx.x == 0) { c->done = kDoneConverged; c->status = BK_OK; }
+    return;
+  }
+  // beta = rho_old^{-1} gamma^T rho_new
+  sm_matmul(S.E, S.C, true, S.A, s);
+  sm_copy(S.D, c->rho, s);
+  __syncthreads();
+  if (!sm_cholesky(S.D, s, &S.flag)) { stop(c, BK_BREAKDOWN); return; }
+  sm_chol_solve(S.D, S.E, S.E, s);
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
+    const int a = i / s, b = i % s;
+    c->beta[IDX(a, b)] = S.E[IDX(a, b)];
+    c->rho[IDX(a, b)] = S.A[IDX(a, b)];
+  }
+  if (threadIdx.x == 0 && c->iter >= c->maxit) { c->done = kDoneStopped; c->status = BK_NOT_CONVERGED; }
+}
+
+static cudaError_t launch_small(void (*k)(Ctrl*), const Launch& L, Ctrl* c) {
+  const size_t sm = sizeof(SmallSmem);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k<<<1, kST, sm, L.stream>>>(c);
+  return cudaGetLastError();
+}
+
+cudaError_t small_bcg_init(const Launch& L, Ctrl* c, int) { return launch_small(small_bcg_init_k, L, c); }
+
+cudaError_t small_bcg_1(const Launch& L, Ctrl* c, const uint8_t* forced) {
+  const size_t sm = sizeof(SmallSmem);
+  cudaError_t e = cudaFuncSetAttribute(small_bcg_1_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  small_bcg_1_k<<<1, kST, sm, L.stream>>>(c, forced);
+  return cudaGetLastError();
+}
+
+cudaError_t small_bcg_2(const Launch& L, Ctrl* c, double* history, uint8_t* decisions) {
+  const size_t sm = sizeof(SmallSmem);
+  cudaError_t e = cudaFuncSetAttribute(small_bcg_2_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  small_bcg_2_k<<<1, kST, sm, L.stream>>>(c, history, decisions);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- BBiCGStab ----
+// (Alg. "BlockBiCGStab_with_reortho", M = I.)  alpha holds R0s^T Q-hat, g2
+// holds R0s^T R-hat, rho holds R-hat^T R-hat.
+// 1: LU of R0s^T Q-hat, lambda-hat = (R0s^T Q-hat)^{-1} R0s^T R-hat, decision
+//    from kappa_D(R-hat^T R-hat), lx = lambda-hat sigma.
+__global__ void __launch_bounds__(kST) small_bicg_1_k(Ctrl* c, const uint8_t* forced) {
+  if (c->done) return;
+  extern __shared__ double smraw[];
+  SmallSmem& S = *reinterpret_cast<SmallSmem*>(smraw);
+  const int s = c->s;
+  sm_copy(S.A, c->alpha, s);
+  sm_copy(S.B, c->g2, s);
+  sm_copy(S.E, c->sigma, s);
+  __syncthreads();
+  if (!sm_all_finite(S.A, s, &S.flag)) { stop(c, BK_NONFINITE); return; }
+  __shared__ int piv[kMaxS];
+  if (!sm_lu(S.A, piv, s, &S.flag)) { stop(c, BK_BREAKDOWN); return; }
+  sm_lu_solve(S.A, piv, S.B, S.D, s);          // D = lambda-hat
+  sm_copy(S.C, c->rho, s);
+  __syncthreads();
+  const int reo = decide(c, forced, S.C, S.B, S.F, S.rot, &S.flag);
+  __syncthreads();
+  sm_matmul(S.B, S.D, false, S.E, s);          // lx = lambda-hat sigma
+  __syncthreads();
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
+    const int a = i / s, b = i % s;
+    c->lu[IDX(a, b)] = S.A[IDX(a, b)];
+    c->lam[IDX(a, b)] = S.D[IDX(a, b)];
+    c->lx[IDX(a, b)] = S.B[IDX(a, b)];
+  }
+  if (threadIdx.x < s) c->piv[threadIdx.x] = piv[threadIdx.x];
+  if (threadIdx.x == 0) c->reortho_now = reo;
+}
+
+// 2: omega-hat = <U,S>_F / <U,U>_F, beta-hat = -(R0s^T Q-hat)^{-1} R0s^T U-hat,
+//    sigma^{k+1} = gamma sigma^k (or sigma^k), lx = omega sigma^{k+1}.
+__global__ void __launch_bounds__(kST) small_bicg_2_k(Ctrl* c) {
+  if (c->done) return;
+  extern __shared__ double smraw[];
+  SmallSmem& S = *reinterpret_cast<SmallSmem*>(smraw);
+  const int s = c->s;
+  const double uu = c->frob[1];
+  if (!(uu > 0.0) || !isfinite(uu) || !isfinite(c->frob[0])) { stop(c, BK_BREAKDOWN); return; }
+  const double omega = c->frob[0] / uu;
+  sm_copy(S.A, c->lu, s);
+  sm_copy(S.B, c->g3, s);
+  sm_copy(S.E, c->sigma, s);
+  if (c->reortho_now) sm_copy(S.C, c->gamma, s); else sm_identity(S.C, s);
+  __shared__ int piv[kMaxS];
+  if (threadIdx.x < s) piv[threadIdx.x] = c->piv[threadIdx.x];
+  __syncthreads();
+  sm_lu_solve(S.A, piv, S.B, S.D, s);          // D = (R0s^T Q)^{-1} R0s^T U
+  sm_matmul(S.B, S.C, false, S.E, s);          // sigma_new
+  __syncthreads();
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
+    const int a = i / s, b = i % s;
+    c->beta[IDX(a, b)] = -S.D[IDX(a, b)];
+    c->sigma_new[IDX(a, b)] = S.B[IDX(a, b)];
+    c->lx[IDX(a, b)] = omega * S.B[IDX(a, b)];
+  }
+  if (threadIdx.x == 0) { c->omega = omega; c->reorths += c->reortho_now; }
+}
+
+// 3: residual norms sqrt(diag(sigma_new^T (R^T R) sigma_new)), stopping test.
+__global__ void __launch_bounds__(kST) small_bicg_3_k(Ctrl* c, double* history, uint8_t* decisions) {
+  if (c->done) return;
+  extern __shared__ double smraw[];
+  SmallSmem& S = *reinterpret_cast<SmallSmem*>(smraw);
+  const int s = c->s;
+  const int k = c->iter;
+  sm_copy(S.A, c->rho, s);
+  sm_copy(S.B, c->sigma_new, s);
+  __syncthreads();
+  if (!sm_all_finite(S.A, s, &S.flag)) { stop(c, BK_NONFINITE); return; }
+  sm_matmul(S.C, S.A, false, S.B, s);
+  __syncthreads();
+  if (threadIdx.x < s) {
+    const int i = threadIdx.x;
+    double v = 0.0;
+    for (int r = 0; r < s; ++r) v = fma(S.B[IDX(r, i)], S.C[IDX(r, i)], v);
+    const double n0 = c->n0[i];
+    c->relres[i] = n0 > 0.0 ? sqrt(fmax(v, 0.0)) / n0 : 0.0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) c->sigma[IDX(i / s, i % s)] = S.B[IDX(i / s, i % s)];
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < s; ++i) mx = fmax(mx, c->relres[i]);
+    if (history) history[k] = mx;
+    if (decisions) decisions[k] = (uint8_t)c->reortho_now;
+    c->iter = k + 1;
+    if (!isfinite(mx)) { c->done = kDoneStopped; c->status = BK_NONFINITE; }
+    else if (mx <= c->tol) { c->done = kDoneConverged; c->status = BK_OK; }
+    else if (c->iter >= c->maxit) { c->done = kDoneStopped; c->status = BK_NOT_CONVERGED; }
+  }
+}
+
+cudaError_t small_bicg_1(const Launch& L, Ctrl* c, const uint8_t* forced) {
+  const size_t sm = sizeof(SmallSmem);
+  cudaError_t e = cudaFuncSetAttribute(small_bicg_1_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  small_bicg_1_k<<<1, kST, sm, L.stream>>>(c, forced);
+  return cudaGetLastError();
+}
+cudaError_t small_bicg_2(const Launch& L, Ctrl* c) { return launch_small(small_bicg_2_k, L, c); }
+cudaError_t small_bicg_3(const Launch& L, Ctrl* c, double* history, uint8_t* decisions) {
+  const size_t sm = sizeof(SmallSmem);
+  cudaError_t e = cudaFuncSetAttribute(small_bicg_3_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  small_bicg_3_k<<<1, kST, sm, L.stream>>>(c, history, decisions);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- helpers ----
+__global__ void set_identity_k(double* M, int s) {
+  for (int i = threadIdx.x; i < kMM; i += blockDim.x) M[i] = ((i / kMaxS) == (i % kMaxS) && (i / kMaxS) < s) ? 1.0 : 0.0;
+}
+cudaError_t small_set_identity(const Launch& L, double* M, int s) {
+  set_identity_k<<<1, 256, 0, L.stream>>>(M, s);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- BGMRes ----
+// One block Givens step of Alg. "bgmres" for Arnoldi step k (Ch. 5.1):
+//   Hc:  the new Hessenberg column, (k+1) blocks h_jk (row stride s) from the
+//        projections, gamma (ctrl->gamma) below it;
+//   rotate it by Q_0^T .. Q_{k-1}^T (their reflectors stored in Gq: 2s x s
+//   reflectors + s taus per step), factor [h_kk; gamma] = Q_k [r; 0] by
+//   Householder, store r and Q_k, update [sigma_k; sigma_k+1] <- Q_k^T [sigma_k; 0]
+//   and test max_i ||sigma_{k+1} e_i|| / ||R0_i|| <= tol.
+// H: (m+1)s x ms, row stride ms: column block k gets the rotated column.
+__global__ void __launch_bounds__(kST)
+small_gmres_step_k(Ctrl* c, const double* __restrict__ Hc, double* __restrict__ H, double* __restrict__ Gq,
+                   double* __restrict__ sig, int k, int m, double* history, int hist_index) {
+  if (c->done) return;
+  extern __shared__ double smraw[];
+  SmallSmem& S = *reinterpret_cast<SmallSmem*>(smraw);
+  const int s = c->s;
+  const int ld = m * s;
+  // stage the 2s x s pair [h_j; h_{j+1}] in A (row stride s) and rotate
+  double* P = S.A;                 // 2s x s  (fits: 2*32*32 = 2 kMM)
+  double* V = S.C;                 // 2s x s reflectors
+  double* tau = S.tau;
+  // working column in global H column block k
+  for (int i = threadIdx.x; i < (k + 1) * s * s; i += blockDim.x) {
+    const int row = i / s, col = i % s;
+    H[(size_t)row * ld + k * s + col] = Hc[(size_t)(row / s) * kMM + (row % s) * kMaxS + col];
+  }
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x)
+    H[(size_t)((k + 1) * s + i / s) * ld + k * s + (i % s)] = c->gamma[IDX(i / s, i % s)];
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    for (int i = threadIdx.x; i < 2 * s * s; i += blockDim.x) {
+      P[i] = H[(size_t)(j * s + i / s) * ld + k * s + (i % s)];
+      V[i] = Gq[(size_t)j * (2 * s * s + s) + i];
+    }
+    if (threadIdx.x < s) tau[threadIdx.x] = Gq[(size_t)j * (2 * s * s + s) + 2 * s * s + threadIdx.x];
+    __syncthreads();
+    cta_apply_qt<double>(V, tau, 2 * s, s, P, s, S.red, S.w);
+    for (int i = threadIdx.x; i < 2 * s * s; i += blockDim.x)
+      H[(size_t)(j * s + i / s) * ld + k * s + (i % s)] = P[i];
+    __syncthreads();
+  }
+  // factor [h_kk; gamma]
+  for (int i = threadIdx.x; i < 2 * s * s; i += blockDim.x) P[i] = H[(size_t)(k * s + i / s) * ld + k * s + (i % s)];
+  __syncthreads();
+  cta_geqr2<double>(P, 2 * s, s, tau, S.red, S.w);
+  for (int i = threadIdx.x; i < 2 * s * s; i += blockDim.x) {
+    const int row = i / s, col = i % s;
+    Gq[(size_t)k * (2 * s * s + s) + i] = P[i];
+    H[(size_t)(k * s + row) * ld + k * s + col] = (row < s && col >= row) ? P[i] : 0.0;
+  }
+  if (threadIdx.x < s) Gq[(size_t)k * (2 * s * s + s) + 2 * s * s + threadIdx.x] = tau[threadIdx.x];
+  __syncthreads();
+  // sigma update: [sigma_k; sigma_{k+1}] <- Q_k^T [sigma_k; 0]
+  for (int i = threadIdx.x; i < 2 * s * s; i += blockDim.x) V[i] = (i < s * s) ? sig[(size_t)k * s * s + i] : 0.0;
+  __syncthreads();
+  cta_apply_qt<double>(P, tau, 2 * s, s, V, s, S.red, S.w);
+  for (int i = threadIdx.x; i < 2 * s * s; i += blockDim.x) sig[(size_t)k * s * s + i] = V[i];
+  __syncthreads();
+  if (threadIdx.x < s) {
+    const int i = threadIdx.x;
+    double v = 0.0;
+    for (int r = 0; r < s; ++r) { const double x = V[(s + r) * s + i]; v = fma(x, x, v); }
+    const double n0 = c->n0[i];
+    c->relres[i] = n0 > 0.0 ? sqrt(v) / n0 : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < s; ++i) mx = fmax(mx, c->relres[i]);
+    if (history) history[hist_index] = mx;
+    c->iter = c->iter + 1;
+    if (!isfinite(mx)) { c->done = kDoneStopped; c->status = BK_NONFINITE; }
+    else if (mx <= c->tol) { c->done = kDoneConverged; c->status = BK_OK; }
+  }
+}
+
+cudaError_t small_gmres_step(const Launch& L, Ctrl* c, const double* Hc, double* H, double* Gq,
+                              double* sig, int k, int m, double* history, int hist_index) {
+  const size_t sm = sizeof(SmallSmem);
+  cudaError_t e = cudaFuncSetAttribute(small_gmres_step_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  small_gmres_step_k<<<1, kST, sm, L.stream>>>(c, Hc, H, Gq, sig, k, m, history, hist_index);
+  return cudaGetLastError();
+}
+
+// Block back-substitution R zeta = sigma over k_done steps (Alg. "bgmres"):
+// zeta_l = r_ll^{-1} (sigma_l - sum_{j>l} r_lj zeta_j).  zeta: k_done blocks of
+// 32 x 32 doubles (row stride 32).  Runs even when the solve has stopped (it is
+// the final update).
+__global__ void __launch_bounds__(kST)
+small_gmres_backsub_k(Ctrl* c, const double* __restrict__ H, const double* __restrict__ sig,
+                      double* __restrict__ zeta, int k_done, int m) {
+  extern __shared__ double smraw[];
+  SmallSmem& S = *reinterpret_cast<SmallSmem*>(smraw);
+  const int s = c->s;
+  const int ld = m * s;
+  for (int l = k_done - 1; l >= 0; --l) {
+    for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
+      const int a = i / s, b = i % s;
+      double v = sig[(size_t)l * s * s + i];
+      for (int j = l + 1; j < k_done; ++j)
+        for (int q = 0; q < s; ++q)
+          v = fma(-H[(size_t)(l * s + a) * ld + j * s + q], zeta[(size_t)j * kMM + q * kMaxS + b], v);
+      S.B[IDX(a, b)] = v;
+      S.A[IDX(a, b)] = H[(size_t)(l * s + a) * ld + l * s + b];
+    }
+    __syncthreads();
+    if (threadIdx.x < s) {                     // upper-triangular solve, column threadIdx.x
+      const int b = threadIdx.x;
+      for (int a = s - 1; a >= 0; --a) {
+        double v = S.B[IDX(a, b)];
+        for (int q = a + 1; q < s; ++q) v = fma(-S.A[IDX(a, q)], S.B[IDX(q, b)], v);
+        const double d = S.A[IDX(a, a)];
+        S.B[IDX(a, b)] = (d != 0.0) ? v / d : 0.0;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < s * s; i += blockDim.x)
+      zeta[(size_t)l * kMM + (i / s) * kMaxS + (i % s)] = S.B[IDX(i / s, i % s)];
+    __syncthreads();
+  }
+}
+
+cudaError_t small_gmres_backsub(const Launch& L, Ctrl* c, const double* H, const double* sig,
+                                double* zeta, int k_done, int m) {
+  const size_t sm = sizeof(SmallSmem);
+  cudaError_t e = cudaFuncSetAttribute(small_gmres_backsub_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  small_gmres_backsub_k<<<1, kST, sm, L.stream>>>(c, H, sig, zeta, k_done, m);
+  return cudaGetLastError();
+}
+
+// ||R0_i|| from squared column norms (ctrl->n0 holds squares on entry).
+__global__ void sqrt_n0_k(Ctrl* c) {
+  if (threadIdx.x < c->s) c->n0[threadIdx.x] = sqrt(c->n0[threadIdx.x]);
+}
+cudaError_t small_colnorms_from_gram(const Launch& L, Ctrl* c) {
+  sqrt_n0_k<<<1, 32, 0, L.stream>>>(c);
+  return cudaGetLastError();
+}
+
+}  // namespace bk

@@ -1,0 +1,400 @@
+// BOP: operator applied to an n x s row-major block (Ch. 3.3, Table "kernels"),
+// for an assembled CSR matrix and three matrix-free stencils, with an optional
+// fused epilogue that accumulates a block inner product left^T Q (the alpha of
+// Alg. "bcg", Eq. "cg_alpha") and Frobenius sums in the same pass.
+//
+// Mapping: one sub-warp of SW = next_pow2(s) lanes per row, lane c computes
+// Q[r][c].  CSR: the lanes of a row read the same val/col entries (broadcast)
+// and the s contiguous values P[col][0..s) (one coalesced segment).  Stencils:
+// the neighbour rows r +- 1, r +- nx, r +- nx*ny are contiguous s-value
+// segments; their reuse across rows is served by L1/L2 (a 128^2 plane of a
+// 32-column FP64 block is 4 MB, far below the 129 MB L2).
+#include "bk_common.cuh"
+#include "bk_internal.h"
+
+namespace bk {
+
+// ---------------------------------------------------------------- operators ----
+template <typename T>
+struct CsrRow {
+  const int32_t* __restrict__ row_ptr;
+  const int32_t* __restrict__ col;
+  const T* __restrict__ val;
+  __device__ __forceinline__ T operator()(int64_t r, int c, int s, const T* __restrict__ P) const {
+    const int b = row_ptr[r], e = row_ptr[r + 1];
+    T q = T(0);
+    for (int j = b; j < e; ++j) q = fma(val[j], P[(int64_t)col[j] * s + c], q);
+    return q;
+  }
+};
+
+// 7-point constant coefficients; terms summed in ascending column order
+// (-z, -y, -x, centre, +x, +y, +z), the order of a column-sorted CSR row.
+template <typename T>
+struct Const7Row {
+  int nx, ny, nz;
+  T c0, cxm, cxp, cym, cyp, czm, czp;
+  __device__ __forceinline__ T operator()(int64_t r, int c, int s, const T* __restrict__ P) const {
+    const int64_t plane = (int64_t)nx * ny;
+    const int x = (int)(r % nx);
+    const int y = (int)((r / nx) % ny);
+    const int z = (int)(r / plane);
+    const T* p = P + r * s + c;
+    T q = T(0);
+    if (z > 0) q = fma(czm, p[-plane * s], q);
+    if (y > 0) q = fma(cym, p[-(int64_t)nx * s], q);
+    if (x > 0) q = fma(cxm, p[-s], q);
+    q = fma(c0, p[0], q);
+    if (x < nx - 1) q = fma(cxp, p[s], q);
+    if (y < ny - 1) q = fma(cyp, p[(int64_t)nx * s], q);
+    if (z < nz - 1) q = fma(czp, p[plane * s], q);
+    return q;
+  }
+};
+
+// Variable-coefficient 7-point FV operator with precomputed coefficients:
+// diag[r], fx[r] (face to r+1), fy[r] (face to r+nx), fz[r] (face to r+nx*ny).
+template <typename T>
+struct Var7Row {
+  int nx, ny, nz;
+  const T* __restrict__ diag;
+  const T* __restrict__ fx;
+  const T* __restrict__ fy;
+  const T* __restrict__ fz;
+  __device__ __forceinline__ T operator()(int64_t r, int c, int s, const T* __restrict__ P) const {
+    const int64_t plane = (int64_t)nx * ny;
+    const int x = (int)(r % nx);
+    const int y = (int)((r / nx) % ny);
+    const int z = (int)(r / plane);
+    const T* p = P + r * s + c;
+    T q = T(0);
+    if (z > 0) q = fma(-fz[r - plane], p[-plane * s], q);
+    if (y > 0) q = fma(-fy[r - nx], p[-(int64_t)nx * s], q);
+    if (x > 0) q = fma(-fx[r - 1], p[-s], q);
+    q = fma(diag[r], p[0], q);
+    if (x < nx - 1) q = fma(-fx[r], p[s], q);
+    if (y < ny - 1) q = fma(-fy[r], p[(int64_t)nx * s], q);
+    if (z < nz - 1) q = fma(-fz[r], p[plane * s], q);
+    return q;
+  }
+};
+
+// 2D per-edge diffusion: ax[y][x] (ny x (nx+1)) joins (x-1,y),(x,y); ay[y][x]
+// ((ny+1) x nx) joins (x,y-1),(x,y); diag precomputed.
+template <typename T>
+struct Edge5Row {
+  int nx, ny;
+  const T* __restrict__ diag;
+  const T* __restrict__ ax;
+  const T* __restrict__ ay;
+  __device__ __forceinline__ T operator()(int64_t r, int c, int s, const T* __restrict__ P) const {
+    const int x = (int)(r % nx);
+    const int y = (int)(r / nx);
+    const T* p = P + r * s + c;
+    T q = T(0);
+    if (y > 0) q = fma(-ay[(int64_t)y * nx + x], p[-(int64_t)nx * s], q);
+    if (x > 0) q = fma(-ax[(int64_t)y * (nx + 1) + x], p[-s], q);
+    q = fma(diag[r], p[0], q);
+    if (x < nx - 1) q = fma(-ax[(int64_t)y * (nx + 1) + x + 1], p[s], q);
+    if (y < ny - 1) q = fma(-ay[(int64_t)(y + 1) * nx + x], p[(int64_t)nx * s], q);
+    return q;
+  }
+};
+
+// Identity "operator": the row kernel then just streams Y, which turns the
+// fused epilogue into a stand-alone block inner product X^T Y (BDOT).
+template <typename T>
+struct IdRow {
+  __device__ __forceinline__ T operator()(int64_t r, int c, int s, const T* __restrict__ P) const {
+    return P[r * s + c];
+  }
+};
+
+// ------------------------------------------------------------------- kernel ----
+// FP32 blocks: Gram products are accumulated in float over kFlush row groups
+// and then added into double accumulators, so the double-precision work is
+// 1/kFlush of the product count while every Gram partial sum beyond one flush
+// window is carried in double.
+constexpr int kFlush = 16;
+
+template <typename T, int SW, class RowOp>
+__global__ void __launch_bounds__(kThreads)
+spmm_kernel(RowOp op, int64_t n, int s, const T* __restrict__ P, T* __restrict__ Q,
+            const T* __restrict__ sub, Epi<T> ep) {
+  if (ep.done && *ep.done) return;
+  if (ep.only_if && !*ep.only_if) return;
+  extern __shared__ double smem[];
+  constexpr int RPW = 32 / SW;
+  const int lane = threadIdx.x & 31;
+  const int c = lane & (SW - 1);
+  const int rs = lane / SW;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t nw = (int64_t)gridDim.x * kWarps;
+  const bool has_gram = ep.left != nullptr;
+  const bool has_frob = ep.frob != nullptr;
+  double acc[SW];
+#pragma unroll
+  for (int a = 0; a < SW; ++a) acc[a] = 0.0;
+  T acc_t[SW];
+#pragma unroll
+  for (int a = 0; a < SW; ++a) acc_t[a] = T(0);
+  int since_flush = 0;
+  double f_qf = 0.0, f_qq = 0.0;
+
+  for (int64_t base = gw * RPW; base < n; base += nw * RPW) {
+    const int64_t r = base + rs;
+    const bool ok = (r < n) && (c < s);
+    T q = T(0);
+    if (ok) {
+      q = op(r, c, s, P);
+      if (sub) q = sub[r * s + c] - q;
+      if (Q) Q[r * s + c] = q;
+    }
+    if (has_gram) {
+      const T l = ok ? ep.left[r * s + c] : T(0);
+      if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int a = 0; a < SW; ++a) {
+          const T la = sw_bcast<SW>(l, a);
+          if (!ep.sym || a <= c) acc[a] = fma((double)la, (double)q, acc[a]);
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < SW; ++a) {
+          const T la = sw_bcast<SW>(l, a);
+          if (!ep.sym || a <= c) acc_t[a] = fma(la, q, acc_t[a]);
+        }
+        if (++since_flush == kFlush) {
+#pragma unroll
+          for (int a = 0; a < SW; ++a) { acc[a] += (double)acc_t[a]; acc_t[a] = T(0); }
+          since_flush = 0;
+        }
+      }
+    }
+    if (has_frob && ok) {
+      const double f = (double)ep.frob[r * s + c];
+      f_qf = fma((double)q, f, f_qf);
+      f_qq = fma((double)q, (double)q, f_qq);
+    }
+  }
+  if (!has_gram && !has_frob) return;
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int a = 0; a < SW; ++a) acc[a] += (double)acc_t[a];
+  }
+  // ---- CTA reduction of the epilogue sums into part[0..cnt) ----
+  const int gcnt = has_gram ? (ep.sym ? ut_count(s) : s * s) : 0;
+  const int cnt = gcnt + (has_frob ? 2 : 0);
+  double* part = smem;                    // cnt
+  double* scratch = smem + ((cnt + 1) & ~1); // kWarps * max(gcnt, 2)
+  if (has_gram) cta_reduce_gram<SW>(acc, s, ep.sym != 0, scratch, part);
+  if (has_frob) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      f_qf += __shfl_xor_sync(0xffffffffu, f_qf, off);
+      f_qq += __shfl_xor_sync(0xffffffffu, f_qq, off);
+    }
+    if (lane == 0) { scratch[2 * (threadIdx.x >> 5)] = f_qf; scratch[2 * (threadIdx.x >> 5) + 1] = f_qq; }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      double t = 0.0;
+      for (int w = 0; w < kWarps; ++w) t += scratch[2 * w + threadIdx.x];
+      part[gcnt + threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+  if (!grid_reduce_last(part, cnt, ep.gpart, ep.counter)) return;
+  if (has_gram) unpack_gram(part, s, ep.sym != 0, ep.gram_out);
+  if (has_frob && threadIdx.x < 2) ep.frob_out[threadIdx.x] = part[gcnt + threadIdx.x];
+}
+
+int spmm_grid(const Launch& L, int64_t n, int s) {
+  const int rpw = 32 / next_pow2_s(s);
+  const int64_t rows_per_cta = (int64_t)rpw * kWarps;
+  int64_t need = (n + rows_per_cta - 1) / rows_per_cta;
+  const int64_t cap = (int64_t)L.sms * 4;
+  if (need > cap) need = cap;
+  if (need < 1) need = 1;
+  return (int)need;
+}
+
+static size_t epi_smem(int s, bool gram, bool sym, bool frob) {
+  const int gcnt = gram ? (sym ? ut_count(s) : s * s) : 0;
+  const int cnt = gcnt + (frob ? 2 : 0);
+  const int sc = gcnt > 2 ? gcnt : 2;
+  return sizeof(double) * (size_t)(((cnt + 1) & ~1) + kWarps * sc);
+}
+
+template <typename T, int SW, class RowOp>
+static cudaError_t launch_sw(const Launch& L, const RowOp& op, int64_t n, int s, const T* in,
+                             T* out, const T* sub, const Epi<T>& ep) {
+  const bool g = ep.left != nullptr, f = ep.frob != nullptr;
+  int grid = spmm_grid(L, n, s);
+  size_t sm = (g || f) ? epi_smem(s, g, ep.sym != 0, f) : 0;
+  auto kern = spmm_kernel<T, SW, RowOp>;
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<grid, kThreads, sm, L.stream>>>(op, n, s, in, out, sub, ep);
+  return cudaGetLastError();
+}
+
+template <typename T, class RowOp>
+static cudaError_t launch_op(const Launch& L, const RowOp& op, int64_t n, int s, const T* in,
+                             T* out, const T* sub, const Epi<T>& ep) {
+  switch (next_pow2_s(s)) {
+    case 1: return launch_sw<T, 1>(L, op, n, s, in, out, sub, ep);
+    case 2: return launch_sw<T, 2>(L, op, n, s, in, out, sub, ep);
+    case 4: return launch_sw<T, 4>(L, op, n, s, in, out, sub, ep);
+    case 8: return launch_sw<T, 8>(L, op, n, s, in, out, sub, ep);
+    case 16: return launch_sw<T, 16>(L, op, n, s, in, out, sub, ep);
+    case 32: return launch_sw<T, 32>(L, op, n, s, in, out, sub, ep);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T> static const T* pick(const double* d, const float* f);
+template <> const double* pick<double>(const double* d, const float*) { return d; }
+template <> const float* pick<float>(const double*, const float* f) { return f; }
+
+template <typename T>
+cudaError_t spmm(const Launch& L, const OpDesc& A, int s, const T* in, T* out, const T* sub,
+                 const Epi<T>& ep) {
+  const int64_t n = A.n;
+  switch (A.kind) {
+    case kOpCsr: {
+      CsrRow<T> op{A.row_ptr, A.col, pick<T>(A.val, A.val32)};
+      if (!op.val) return cudaErrorInvalidValue;
+      return launch_op<T>(L, op, n, s, in, out, sub, ep);
+    }
+    case kOpConst7: {
+      Const7Row<T> op{A.nx, A.ny, A.nz, (T)A.c7[0], (T)A.c7[1], (T)A.c7[2], (T)A.c7[3],
+                      (T)A.c7[4], (T)A.c7[5], (T)A.c7[6]};
+      return launch_op<T>(L, op, n, s, in, out, sub, ep);
+    }
+    case kOpVar7: {
+      const T* base = pick<T>(A.coef, A.coef32);
+      if (!base) return cudaErrorInvalidValue;
+      Var7Row<T> op{A.nx, A.ny, A.nz, base, base + n, base + 2 * n, base + 3 * n};
+      return launch_op<T>(L, op, n, s, in, out, sub, ep);
+    }
+    case kOpEdge5: {
+      const T* dg = pick<T>(A.coef, A.coef32);
+      const T* e = pick<T>(A.edges, A.edges32);
+      if (!dg || !e) return cudaErrorInvalidValue;
+      Edge5Row<T> op{A.nx, A.ny, dg, e, e + (int64_t)A.ny * (A.nx + 1)};
+      return launch_op<T>(L, op, n, s, in, out, sub, ep);
+    }
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t gram(const Launch& L, int64_t n, int s, const T* X, const T* Y, const Epi<T>& ep) {
+  Epi<T> e = ep;
+  e.left = X;
+  return launch_op<T>(L, IdRow<T>{}, n, s, Y, (T*)nullptr, (const T*)nullptr, e);
+}
+template cudaError_t gram<double>(const Launch&, int64_t, int, const double*, const double*,
+                                  const Epi<double>&);
+template cudaError_t gram<float>(const Launch&, int64_t, int, const float*, const float*,
+                                 const Epi<float>&);
+
+template cudaError_t spmm<double>(const Launch&, const OpDesc&, int, const double*, double*,
+                                  const double*, const Epi<double>&);
+template cudaError_t spmm<float>(const Launch&, const OpDesc&, int, const float*, float*,
+                                 const float*, const Epi<float>&);
+
+// ------------------------------------------------- operator preparation ----
+// VAR7: diag and +x/+y/+z face coefficients from the cell field k (h = 1).
+// Interior face 2 k_i k_j / (k_i + k_j); boundary face 2 k_i; the diagonal is
+// the sum of the six faces taken in the order -x, +x, -y, +y, -z, +z.
+__global__ void var7_prepare(int nx, int ny, int nz, const double* __restrict__ k,
+                             double* __restrict__ out) {
+  const int64_t n = (int64_t)nx * ny * nz;
+  const int64_t plane = (int64_t)nx * ny;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(r % nx), y = (int)((r / nx) % ny), z = (int)(r / plane);
+    const double ki = k[r];
+    auto face = [&](bool in, int64_t j) {
+      if (!in) return 2.0 * ki;
+      const double kj = k[j];
+      return 2.0 * ki * kj / (ki + kj);
+    };
+    const double fxm = face(x > 0, r - 1), fxp = face(x < nx - 1, r + 1);
+    const double fym = face(y > 0, r - nx), fyp = face(y < ny - 1, r + nx);
+    const double fzm = face(z > 0, r - plane), fzp = face(z < nz - 1, r + plane);
+    double d = 0.0;
+    d += fxm; d += fxp; d += fym; d += fyp; d += fzm; d += fzp;
+    out[r] = d;
+    out[n + r] = (x < nx - 1) ? fxp : 0.0;
+    out[2 * n + r] = (y < ny - 1) ? fyp : 0.0;
+    out[3 * n + r] = (z < nz - 1) ? fzp : 0.0;
+  }
+}
+
+// EDGE5: diag[y][x] = ax[y][x] + ax[y][x+1] + ay[y][x] + ay[y+1][x].
+__global__ void edge5_prepare(int nx, int ny, const double* __restrict__ e, double* __restrict__ diag) {
+  const int64_t n = (int64_t)nx * ny;
+  const double* ax = e;
+  const double* ay = e + (int64_t)ny * (nx + 1);
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(r % nx), y = (int)(r / nx);
+    diag[r] = ax[(int64_t)y * (nx + 1) + x] + ax[(int64_t)y * (nx + 1) + x + 1] +
+              ay[(int64_t)y * nx + x] + ay[(int64_t)(y + 1) * nx + x];
+  }
+}
+
+__global__ void cast_kernel(int64_t count, const double* __restrict__ in, float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+static int elem_grid(const Launch& L, int64_t count) {
+  int64_t g = (count + 255) / 256;
+  const int64_t cap = (int64_t)L.sms * 8;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+cudaError_t cast_block(const Launch& L, int64_t count, const double* in, float* out) {
+  if (count <= 0) return cudaSuccess;
+  cast_kernel<<<elem_grid(L, count), 256, 0, L.stream>>>(count, in, out);
+  return cudaGetLastError();
+}
+
+cudaError_t op_prepare_stencil(const Launch& L, OpDesc& A, const double* coeffs) {
+  if (A.kind == kOpVar7) {
+    var7_prepare<<<elem_grid(L, A.n), 256, 0, L.stream>>>(A.nx, A.ny, A.nz, coeffs, A.coef);
+    return cudaGetLastError();
+  }
+  if (A.kind == kOpEdge5) {
+    edge5_prepare<<<elem_grid(L, A.n), 256, 0, L.stream>>>(A.nx, A.ny, coeffs, A.coef);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
+}
+
+cudaError_t op_make_fp32(const Launch& L, OpDesc& A) {
+  cudaError_t e = cudaSuccess;
+  if (A.kind == kOpCsr && !A.val32) {
+    if ((e = cudaMalloc(&A.val32, sizeof(float) * (size_t)(A.nnz > 0 ? A.nnz : 1))) != cudaSuccess) return e;
+    return cast_block(L, A.nnz, A.val, A.val32);
+  }
+  if ((A.kind == kOpVar7 || A.kind == kOpEdge5) && !A.coef32) {
+    if ((e = cudaMalloc(&A.coef32, sizeof(float) * (size_t)A.coef_len)) != cudaSuccess) return e;
+    if ((e = cast_block(L, A.coef_len, A.coef, A.coef32)) != cudaSuccess) return e;
+  }
+  if (A.kind == kOpEdge5 && !A.edges32) {
+    const int64_t ne = (int64_t)A.ny * (A.nx + 1) + (int64_t)(A.ny + 1) * A.nx;
+    if ((e = cudaMalloc(&A.edges32, sizeof(float) * (size_t)ne)) != cudaSuccess) return e;
+    return cast_block(L, ne, A.edges, A.edges32);
+  }
+  return cudaSuccess;
+}
+
+}  // namespace bk

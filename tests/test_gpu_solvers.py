@@ -1,0 +1,216 @@
+"""GPU solver parity against the oracle: BCG-ARO, BBiCGStab-ARO, BGMRes(m), FP32+IR, error paths.
+
+Iterate parity (FP64): X^k of the GPU and of the oracle agree to 1e-12
+relative (max-norm) for k <= 50, with the re-orthonormalisation schedule
+fixed (eta = 0 or inf, or the oracle's decisions replayed); beyond that,
+floating-point divergence of CG makes iterate comparisons meaningless, and
+only the final residuals (<= tol on both sides) and iteration counts (+-2)
+are compared.  X^k of the GPU is obtained by running the solver with
+maxit = k and tol = 0.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h():
+    from paper_2104_02494_gb300 import build
+    from paper_2104_02494_gb300.api import Handle
+    build()
+    with Handle(0) as hh:
+        yield hh
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _op(h, prob, use):
+    from paper_2104_02494_gb300.api import operator_from_problem
+    return operator_from_problem(h, prob, use)
+
+
+def _gpu_iterate(h, method, op, B, k, **kw):
+    X, info = h.solve(method, op, _dev(B), tol=0.0, maxit=k, **kw)
+    return X.cpu().numpy(), info
+
+
+@pytest.mark.parametrize("eta", [math.inf, 0.0])
+@pytest.mark.parametrize("use", ["csr", "stencil"])
+def test_bcg_poisson2d_iterates_and_final(h, eta, use):
+    prob = W.problem("poisson2d")                       # 64^2, s = 4
+    op = _op(h, prob, use)
+    ref = oracle.bcg(prob.A, prob.B, tol=1e-8, maxit=1000, eta=eta, record_iterates=50)
+    for k in (1, 2, 5, 10, 20, 50):
+        Xk, info = _gpu_iterate(h, "bcg", op, prob.B, k, eta=eta)
+        assert info.iters == k
+        assert _rel(Xk, ref.iterates[k - 1]) <= 1e-12, (k, _rel(Xk, ref.iterates[k - 1]))
+    X, info = h.solve("bcg", op, _dev(prob.B), tol=1e-8, maxit=1000, eta=eta)
+    assert info.converged and ref.converged
+    assert abs(info.iters - ref.iters) <= 2
+    assert info.relres_max <= 1e-8
+    true = oracle.col_norms(prob.B - oracle.spmm(prob.A, X.cpu().numpy())) / oracle.col_norms(prob.B)
+    assert true.max() <= 1.5e-8
+    if math.isinf(eta):
+        assert info.reorths == info.iters and all(info.decisions)
+    op.close()
+
+
+@pytest.mark.parametrize("s", [1, 3, 8, 32])
+def test_bcg_laplace_small_grid(h, s):
+    prob = W.problem("laplace3d", s=s, grid=14)
+    op = _op(h, prob, "stencil")
+    ref = oracle.bcg(prob.A, prob.B, tol=1e-8, maxit=500, eta=math.inf, record_iterates=30)
+    for k in (3, 30):
+        Xk, _ = _gpu_iterate(h, "bcg", op, prob.B, k, eta=math.inf)
+        assert _rel(Xk, ref.iterates[k - 1]) <= 1e-12
+    X, info = h.solve("bcg", op, _dev(prob.B), tol=1e-8, maxit=500, eta=math.inf)
+    assert info.converged and abs(info.iters - ref.iters) <= 2
+    op.close()
+
+
+def test_bcg_adaptive_eta_with_replay(h):
+    prob = W.problem("laplace3d", s=8, grid=16)
+    op = _op(h, prob, "csr")
+    ref = oracle.bcg(prob.A, prob.B, tol=1e-8, maxit=500, eta=1e4, record_iterates=50)
+    X, info = h.solve("bcg", op, _dev(prob.B), tol=1e-8, maxit=500, eta=1e4)
+    assert info.converged
+    # the decisions agree except possibly where kappa_D sits at the threshold
+    K = min(len(info.decisions), len(ref.decisions))
+    mism = sum(a != b for a, b in zip(info.decisions[:K], ref.decisions[:K]))
+    assert mism <= 2
+    # replaying the oracle's schedule gives iterate parity
+    for k in (5, 25, 50):
+        Xk, _ = _gpu_iterate(h, "bcg", op, prob.B, k, eta=1e4, forced_reortho=ref.decisions)
+        assert _rel(Xk, ref.iterates[k - 1]) <= 1e-12
+    op.close()
+
+
+def test_bcg_s1_equals_scalar_cg(h):
+    prob = W.problem("laplace3d", s=1, grid=12)
+    op = _op(h, prob, "stencil")
+    x, its, hist, xs = oracle.scalar_cg(prob.A, prob.B[:, 0], tol=1e-10, maxit=500, record_iterates=40)
+    for k in (1, 10, 40):
+        Xk, _ = _gpu_iterate(h, "bcg", op, prob.B, k, eta=0.0)
+        assert _rel(Xk[:, 0], xs[k - 1]) <= 1e-12
+    X, info = h.solve("bcg", op, _dev(prob.B), tol=1e-10, maxit=500, eta=0.0)
+    assert abs(info.iters - its) <= 1
+    op.close()
+
+
+def test_bcg_full_size_laplace_first_iterates(h):
+    """128^3 Laplacian, s = 8, eta = inf (QR stabilisation): first iterates vs the oracle."""
+    prob = W.problem("laplace3d", s=8)
+    op = _op(h, prob, "stencil")
+    ref = oracle.bcg(prob.A, prob.B, tol=0.0, maxit=3, eta=math.inf, record_iterates=3)
+    Xk, info = _gpu_iterate(h, "bcg", op, prob.B, 3, eta=math.inf)
+    assert info.iters == 3
+    assert _rel(Xk, ref.iterates[2]) <= 1e-12
+    assert np.abs(info.relres - ref.relres).max() <= 1e-12
+    op.close()
+
+
+def test_bcg_host_buffers_equal_device(h):
+    prob = W.problem("poisson2d", s=4, grid=40)
+    op = _op(h, prob, "csr")
+    Xd, i1 = h.solve("bcg", op, _dev(prob.B), tol=1e-9, maxit=300)
+    Xh = np.zeros_like(prob.B)
+    Xh, i2 = h.solve("bcg", op, prob.B.copy(), Xh, tol=1e-9, maxit=300)
+    assert i1.iters == i2.iters
+    assert np.array_equal(Xd.cpu().numpy(), Xh)
+    op.close()
+
+
+def test_bcg_error_paths(h):
+    from paper_2104_02494_gb300.api import BkError
+    prob = W.problem("poisson2d", s=4, grid=16)
+    op = _op(h, prob, "csr")
+    # zero right-hand side: converged before the first iteration
+    X, info = h.solve("bcg", op, _dev(np.zeros_like(prob.B)), tol=1e-8, maxit=10)
+    assert info.converged and info.iters == 0 and info.status == 0
+    # maxit reached: NOT_CONVERGED with the last iterate
+    ref = oracle.bcg(prob.A, prob.B, tol=0.0, maxit=3, eta=math.inf, record_iterates=3)
+    X, info = h.solve("bcg", op, _dev(prob.B), tol=1e-30, maxit=3)
+    assert info.status == 4 and info.iters == 3
+    assert _rel(X.cpu().numpy(), ref.iterates[2]) <= 1e-12
+    # negative definite operator: alpha is not SPD -> BREAKDOWN, X unchanged
+    neg = W.csr_from_triples(prob.A.n, np.arange(prob.A.n), np.arange(prob.A.n), -np.ones(prob.A.n))
+    opn = h.op_csr(_dev(neg.row_ptr), _dev(neg.col), _dev(neg.val))
+    X, info = h.solve("bcg", opn, _dev(prob.B), tol=1e-8, maxit=10, eta=0.0)
+    assert info.status == 5 and info.iters == 0
+    assert np.all(X.cpu().numpy() == 0)
+    # invalid block sizes are rejected before any work
+    with pytest.raises(BkError):
+        h.solve("bcg", op, _dev(np.zeros((prob.A.n, 33))), maxit=1)
+    with pytest.raises(BkError):
+        h.bdot(_dev(np.zeros((10, 0))), _dev(np.zeros((10, 0))))
+    # NaN in the right-hand side: NONFINITE
+    Bn = prob.B.copy(); Bn[5, 1] = np.nan
+    X, info = h.solve("bcg", op, _dev(Bn), tol=1e-8, maxit=10)
+    assert info.status == 6
+    op.close(); opn.close()
+
+
+@pytest.mark.parametrize("eta", [0.0, math.inf, 100.0])
+def test_bbicgstab_convdiff(h, eta):
+    prob = W.problem("convdiff3d", s=8, grid=12)
+    op = _op(h, prob, "stencil")
+    ref = oracle.bbicgstab(prob.A, prob.B, tol=1e-8, maxit=500, eta=eta, record_iterates=20)
+    forced = ref.decisions if 0 < eta < math.inf else None
+    for k in (1, 5, 20):
+        if k > ref.iters:
+            break
+        Xk, _ = _gpu_iterate(h, "bbicgstab", op, prob.B, k, eta=eta, forced_reortho=forced)
+        assert _rel(Xk, ref.iterates[k - 1]) <= 1e-11, (k, _rel(Xk, ref.iterates[k - 1]))
+    X, info = h.solve("bbicgstab", op, _dev(prob.B), tol=1e-8, maxit=500, eta=eta)
+    assert info.converged and ref.converged
+    assert abs(info.iters - ref.iters) <= 2
+    true = oracle.col_norms(prob.B - oracle.spmm(prob.A, X.cpu().numpy())) / oracle.col_norms(prob.B)
+    assert true.max() <= 1.5e-8
+    op.close()
+
+
+@pytest.mark.parametrize("ortho", ["cgs2", "mgs"])
+def test_bgmres_convdiff(h, ortho):
+    prob = W.problem("convdiff3d", s=4, grid=10)
+    op = _op(h, prob, "stencil")
+    ref = oracle.bgmres(prob.A, prob.B, tol=1e-8, restart=10, maxit=300, ortho=ortho)
+    for k in (1, 4, 10, 13):
+        Xk, info = _gpu_iterate(h, "bgmres", op, prob.B, k, restart=10, ortho=ortho)
+        rk = oracle.bgmres(prob.A, prob.B, tol=0.0, restart=10, maxit=k, ortho=ortho)
+        assert _rel(Xk, rk.X) <= 1e-11, (k, _rel(Xk, rk.X))
+    X, info = h.solve("bgmres", op, _dev(prob.B), tol=1e-8, maxit=300, restart=10, ortho=ortho)
+    assert info.converged and ref.converged and abs(info.iters - ref.iters) <= 1
+    true = oracle.col_norms(prob.B - oracle.spmm(prob.A, X.cpu().numpy())) / oracle.col_norms(prob.B)
+    assert true.max() <= 1.5e-8
+    # per-column residual tracked by sigma equals the recomputed one
+    assert abs(true.max() - info.relres_max) <= 1e-10
+    op.close()
+
+
+def test_bcg_ir_reaches_1e10(h):
+    prob = W.problem("vardiff3d", s=4, grid=14)
+    op = _op(h, prob, "stencil")
+    X, info = h.solve("bcg", op, _dev(prob.B), tol=1e-10, maxit=5000, prec="fp32_ir")
+    assert info.converged and info.outer >= 2
+    Xn = X.cpu().numpy()
+    true = oracle.col_norms(prob.B - oracle.spmm(prob.A, Xn)) / oracle.col_norms(prob.B)
+    assert true.max() <= 1e-10
+    ref = oracle.bcg_ir(prob.A, prob.B, tol=1e-10, inner_tol=1e-5)
+    assert ref.converged
+    Xs = np.linalg.solve(prob.A.to_dense(), prob.B)
+    assert _rel(Xn, Xs) <= 1e-8
+    assert abs(info.outer - ref.outer) <= 1
+    op.close()
