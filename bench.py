@@ -1,0 +1,296 @@
+"""Benchmark: block-CG RHS*iterations/s on the 128^3 7-point Laplacian (FP64).
+
+Workload (the configuration the headline metric is quoted on): 3D 7-point
+Laplacian on a 128^3 grid (n = 2,097,152), matrix-free stencil, FP64,
+s = 8 right-hand sides drawn N(0,1) (seed 0), block CG with residual-block
+QR stabilisation in every iteration (eta = inf, Alg. "bcgaro" scheduled as
+Alg. "2R-CG").  One step = one BCG iteration: SpMM with the fused alpha Gram,
+s x s solve, fused X/R update, TSQR normaliser (leaf factor, tree, leaf apply,
+rho Gram), s x s step, direction update.
+
+  value      RHS*iterations/s = s * K / (device time of K steady-state iterations);
+             the K iterations are timed as the difference of two solves with
+             maxit = W + K and maxit = W (setup cancels), each bracketed by
+             CUDA events on the library's stream;
+  e2e        the same metric through the C ABI with HOST buffers (B and X0 copied
+             in, X copied out inside the call), host wall clock around the call;
+  roofline   the dominant kernel phase, timed live with CUDA events (profiled
+             solve), against the FP64 FMA rate of this GPU (the path is bound by
+             FP64 arithmetic at s = 8);
+  cpu_baseline  the FP64 oracle (numpy/scipy) on the host cores, a bounded
+             number of iterations of the same workload.
+
+Every n x s block is 134 MB > 129 MB L2, so no L2 flush is needed between
+timed iterations ("inputs larger than L2").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "block-CG RHS*iter/s (128^3 Laplacian, FP64, QR-stabilised BCG)"
+UNIT = "RHS*iter/s"
+FP64_PEAK_TFLOPS = 1.196   # measured FP64 FMA throughput of this GB300
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--s", type=int, default=8)
+    p.add_argument("--grid", type=int, default=128)
+    p.add_argument("--op", default="stencil", choices=["stencil", "csr"])
+    p.add_argument("--sweep", action="store_true", help="also time s in {1,4,8,16,32}, stencil and CSR")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_init(args):
+    if args.gpus <= 1 or "RANK" not in os.environ:
+        return 0, 1, None
+    import torch.distributed as dist
+    dist.init_process_group("gloo")
+    return dist.get_rank(), dist.get_world_size(), dist
+
+
+def iteration_flops(n, s, tp_levels=None):
+    """Algorithmic FP64 flops of one BCG iteration (stencil, eta = inf); FMA = 2 flops.
+
+    SpMM 7-point 14ns, alpha Gram (upper) n s(s+1), X and R updates 4ns^2,
+    Householder leaf factor 2ns^2, leaf apply 4ns^2, rho Gram n s(s+1),
+    P update 2ns^2 (the s x s work and the tree are O(n s^2 / 256) and ignored).
+    """
+    return 14 * n * s + 2 * n * s * (s + 1) + 12 * n * s * s
+
+
+PHASE_FLOPS = {
+    # algorithmic flops per launch of each phase, as functions of (n, s)
+    "spmm_alpha": lambda n, s: 14 * n * s + n * s * (s + 1),
+    "update_rho": lambda n, s: 4 * n * s * s,
+    "tsqr_leaf_factor": lambda n, s: 2 * n * s * s,
+    "tsqr_leaf_apply": lambda n, s: 4 * n * s * s,
+    "tsqr_rho_gram": lambda n, s: n * s * (s + 1),
+    "p_update": lambda n, s: 2 * n * s * s,
+}
+PHASE_BYTES = {
+    # algorithmic bytes per launch (FP64): blocks read + written
+    "spmm_alpha": lambda n, s: 2 * 8 * n * s,
+    "update_rho": lambda n, s: 6 * 8 * n * s,
+    "tsqr_leaf_factor": lambda n, s: 2 * 8 * n * s,
+    "tsqr_leaf_apply": lambda n, s: 2 * 8 * n * s,
+    "tsqr_rho_gram": lambda n, s: 8 * n * s,
+    "p_update": lambda n, s: 3 * 8 * n * s,
+}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev=0):
+        self.dev = dev
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        if not self.p or not self.out:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(prob, s, iters=3):
+    """The FP64 oracle on the host cores: `iters` BCG-ARO iterations of the same workload."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.bcg(prob.A, prob.B, tol=0.0, maxit=iters, eta=math.inf)
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0))
+    return {"value": s * iters / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{iters} BCG iterations (setup included) of the full {prob.A.n}-row, s={s} "
+                      f"workload, CSR operator, numpy/scipy FP64 ({cores} host cores visible; "
+                      f"BLAS calls threaded, sparse product single-threaded)",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import workloads as W
+    prob = W.problem("laplace3d", s=args.s, grid=args.grid)
+    iters = max(1, min(args.steps, 3))
+    res = cpu_baseline(prob, args.s, iters)
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": iters, "warmup": 0,
+            "ms_per_step": 1000.0 * res["seconds"] / iters, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"laplace3d {args.grid}^3 s={args.s} BCG eta=inf (oracle, CSR)"},
+            "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def time_iters(h, op, Bd, s, W, K, torch):
+    """Device ms of K steady-state iterations: solve(W+K) - solve(W), best of 2."""
+    best = math.inf
+    for _ in range(2):
+        X1 = torch.zeros_like(Bd)
+        _, i1 = h.solve("bcg", op, Bd, X1, tol=0.0, maxit=W + K, eta=math.inf, sync_every=W + K,
+                        record=False)
+        X0 = torch.zeros_like(Bd)
+        _, i0 = h.solve("bcg", op, Bd, X0, tol=0.0, maxit=W, eta=math.inf, sync_every=max(W, 1),
+                        record=False)
+        assert i1.iters == W + K and i0.iters == W
+        best = min(best, i1.elapsed_ms - i0.elapsed_ms)
+    return best
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, dist = dist_init(args)
+    import torch
+    import workloads as W
+    from paper_2104_02494_gb300 import build
+    from paper_2104_02494_gb300.api import Handle, operator_from_problem
+    from paper_2104_02494_gb300 import _lib
+
+    build()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    s, Wm, K = args.s, max(3, args.warmup), max(1, args.steps)
+    prob = W.problem("laplace3d", s=s, grid=args.grid, with_csr=(args.op == "csr" or rank == 0))
+    n = prob.B.shape[0]
+    h = Handle(dev)
+    op = operator_from_problem(h, prob, args.op)
+    Bd = torch.from_numpy(prob.B).cuda()
+    torch.cuda.synchronize()
+
+    # warm up the library (workspace, module load)
+    h.solve("bcg", op, Bd, tol=0.0, maxit=Wm, eta=math.inf, record=False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    with Clocks(dev) as clk:
+        ms = time_iters(h, op, Bd, s, Wm, K, torch)
+    torch.cuda.synchronize()
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = world * s * K / (ms / 1000.0)
+
+    # per-phase device times (profiled solve, events around every phase)
+    h.profile_reset()
+    h.solve("bcg", op, Bd, tol=0.0, maxit=K, eta=math.inf, record=False, profile=True)
+    prof = [(nm, t, nl) for nm, t, nl in h.profile() if nl > 0]
+    tot = sum(t for _, t, _ in prof)
+    phases = {nm: {"ms_per_launch": t / max(nl, 1) * (1 if nm != "tsqr_tree" else 1), "share": t / tot,
+                   "launches": nl} for nm, t, nl in prof}
+    dom = max((p for p in prof if p[0] in PHASE_FLOPS), key=lambda p: p[1])
+    dom_ms = dom[1] / max(dom[2], 1)
+    flops = PHASE_FLOPS[dom[0]](n, s)
+    achieved = flops / (dom_ms / 1000.0) / 1e12
+    roofline = {"bound": "alu", "kernel": dom[0], "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "measured FP64 FMA throughput (probe, DESIGN.md)",
+                "hbm_achieved_gbs": PHASE_BYTES[dom[0]](n, s) / (dom_ms / 1000.0) / 1e9}
+
+    # end to end through the C ABI with host buffers
+    Bh = np.ascontiguousarray(prob.B)
+    Xh = np.zeros_like(Bh)
+    t0 = time.perf_counter()
+    _, ie = h.solve("bcg", op, Bh, Xh, tol=0.0, maxit=K, eta=math.inf, record=False)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": s * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * Bh.nbytes / K,
+           "d2h_bytes_per_step": Xh.nbytes / K, "note": "setup (residual, first QR) included"}
+
+    sweep = None
+    if args.sweep and rank == 0:
+        sweep = {}
+        for use in ("stencil", "csr"):
+            for ss in (1, 4, 8, 16, 32):
+                pr = W.problem("laplace3d", s=ss, grid=args.grid, with_csr=(use == "csr"))
+                o2 = operator_from_problem(h, pr, use)
+                B2 = torch.from_numpy(pr.B).cuda()
+                kk = max(3, min(K, 10))
+                m2 = time_iters(h, o2, B2, ss, 3, kk, torch)
+                sweep[f"{use}_s{ss}"] = {"rhs_iter_per_s": ss * kk / (m2 / 1000.0), "ms_per_iter": m2 / kk,
+                                         "fp64_tflops": iteration_flops(pr.B.shape[0], ss) / (m2 / kk / 1000.0) / 1e12}
+                o2.close()
+                del B2
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(prob, s, iters=3)
+        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    launches = _lib.load().bkrylov_bcg_launches_per_iteration(n, s) * K
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+                "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"laplace3d {args.grid}^3 7-point, {args.op}, s={s}, BCG eta=inf",
+                           "n": n, "s": s, "l2": "inputs larger than L2 (each n x s block 134 MB)",
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "fp64_tflops_per_iter": iteration_flops(n, s) / (ms / K / 1000.0) / 1e12},
+                "roofline": roofline, "phases": phases, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk.summary(), "gpu_launches": launches}
+        if sweep:
+            line["sweep"] = sweep
+        print(json.dumps(line))
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

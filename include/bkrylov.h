@@ -88,6 +88,10 @@ typedef struct {
   int n_forced;
   int sync_every;      /* iterations enqueued between host checks of the stop flag;
                           0 = automatic                                          (0)  */
+  int profile;         /* BCG only: time every kernel phase of every iteration with
+                          CUDA events on the handle's stream (adds one stream
+                          synchronisation per iteration); read with
+                          bkrylov_profile_get                                      (0)  */
 } bkrylov_opts;
 
 /* Solver report.  Pointer members are HOST arrays supplied by the caller (or NULL). */
@@ -168,6 +172,18 @@ int bkrylov_solve_bbicgstab(bkrylov_handle h, bkrylov_op A, int s, const double*
    TSQR normalizer.  FP64 only. */
 int bkrylov_solve_bgmres(bkrylov_handle h, bkrylov_op A, int s, const double* B,
                          double* X, const bkrylov_opts* opts, bkrylov_info* info);
+
+/* ---- measurement ----------------------------------------------------------------- */
+/* Number of timed phases of a BCG iteration (spmm_alpha, small_1, update_rho,
+   tsqr_leaf_factor, tsqr_tree, tsqr_leaf_apply, tsqr_rho_gram, small_2, p_update). */
+int bkrylov_profile_count(void);
+/* Accumulated device time (ms) and kernel launches of phase i over all profiled
+   iterations since the last reset; *name is a static string. */
+int bkrylov_profile_get(bkrylov_handle h, int i, const char** name, double* total_ms,
+                        long long* launches);
+int bkrylov_profile_reset(bkrylov_handle h);
+/* Kernel launches of one BCG iteration for an n x s block (host-only, no GPU). */
+int bkrylov_bcg_launches_per_iteration(int64_t n, int s);
 
 /* ---- adjoint (reverse-mode derivative of X = A^{-1} B) ----------------------------- */
 /* For a CSR operator: g[e] = -sum_k Lam[i,k] X[j,k] for every stored entry e = (i, j),

@@ -25,7 +25,7 @@ class bkrylov_opts(C.Structure):
         ("tol", C.c_double), ("maxit", C.c_int), ("eta", C.c_double), ("restart", C.c_int),
         ("ortho", C.c_int), ("prec", C.c_int), ("ir_inner_tol", C.c_double),
         ("ir_max_outer", C.c_int), ("forced_reortho", C.POINTER(C.c_uint8)), ("n_forced", C.c_int),
-        ("sync_every", C.c_int),
+        ("sync_every", C.c_int), ("profile", C.c_int),
     ]
 
 
@@ -65,6 +65,11 @@ SIGNATURES = [
                                           C.POINTER(bkrylov_opts), C.POINTER(bkrylov_info)]),
     ("bkrylov_solve_bgmres", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                        C.POINTER(bkrylov_opts), C.POINTER(bkrylov_info)]),
+    ("bkrylov_profile_count", C.c_int, []),
+    ("bkrylov_profile_get", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_longlong)]),
+    ("bkrylov_profile_reset", C.c_int, [C.c_void_p]),
+    ("bkrylov_bcg_launches_per_iteration", C.c_int, [C.c_int64, C.c_int]),
     ("bkrylov_adjoint_scatter", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                           C.c_void_p]),
     ("bkrylov_edge_theta_grad", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,

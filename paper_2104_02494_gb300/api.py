@@ -153,10 +153,24 @@ class Handle:
                "bkrylov_edge_theta_grad")
         return g
 
+    # ---- measurement ----
+    def profile(self):
+        """[(phase, total_ms, launches)] accumulated by solves run with profile=True."""
+        out = []
+        for i in range(self.lib.bkrylov_profile_count()):
+            name, ms, nl = C.c_char_p(), C.c_double(), C.c_longlong()
+            _check(self.lib.bkrylov_profile_get(self.h, i, C.byref(name), C.byref(ms), C.byref(nl)),
+                   "bkrylov_profile_get")
+            out.append((name.value.decode(), ms.value, nl.value))
+        return out
+
+    def profile_reset(self):
+        _check(self.lib.bkrylov_profile_reset(self.h), "bkrylov_profile_reset")
+
     # ---- solvers ----
     def solve(self, method: str, A: "Operator", B, X=None, *, tol=1e-8, maxit=1000, eta=math.inf,
               prec="fp64", restart=30, ortho="cgs2", ir_inner_tol=1e-5, ir_max_outer=30,
-              forced_reortho=None, sync_every=0, record=True):
+              forced_reortho=None, sync_every=0, record=True, profile=False):
         """Run bkrylov_solve_{bcg,bbicgstab,bgmres}; returns (X, SolveInfo).
 
         B, X: float64 n x s blocks, on the device (torch CUDA tensors) or on
@@ -171,6 +185,7 @@ class Handle:
         o.ortho = {"cgs2": 0, "mgs": 1}[ortho]
         o.prec = _PREC[prec]
         o.ir_inner_tol, o.ir_max_outer, o.sync_every = float(ir_inner_tol), int(ir_max_outer), int(sync_every)
+        o.profile = 1 if profile else 0
         forced_arr = None
         if forced_reortho is not None:
             forced_arr = (C.c_uint8 * max(1, len(forced_reortho)))(*[1 if f else 0 for f in forced_reortho])

@@ -26,7 +26,12 @@ struct bkrylov_ctx {
   void* ws[2] = {nullptr, nullptr};   // [0] solver internals, [1] refinement / host staging
   size_t ws_cap[2] = {0, 0};
   Ctrl* host_ctrl = nullptr;          // pinned staging of the control block
+  Prof prof;                          // per-phase timing of profiled solves
 };
+
+const char* const bk::kPhaseNames[kNumPhases] = {
+    "spmm_alpha", "small_1", "update_rho", "tsqr_leaf_factor", "tsqr_tree", "tsqr_leaf_apply",
+    "tsqr_rho_gram", "small_2", "p_update"};
 
 struct bkrylov_op_s {
   bkrylov_handle h = nullptr;
@@ -187,14 +192,28 @@ cudaError_t bcg_iteration(const Launch& L, const OpDesc& A, int s, T* X, const B
   Epi<T> ep;
   ep.left = b.P; ep.sym = 1; ep.gram_out = c->alpha; ep.gpart = b.gpart;
   ep.counter = &c->counters[kCntA]; ep.done = &c->done;
+  prof_begin(L, kPhSpmm);
   if ((e = spmm<T>(L, A, s, b.P, b.Q, nullptr, ep)) != cudaSuccess) return e;
+  prof_end(L, kPhSpmm, 1);
+  prof_begin(L, kPhSmall1);
   if ((e = small_bcg_1(L, c, b.forced)) != cudaSuccess) return e;
+  prof_end(L, kPhSmall1, 1);
+  prof_begin(L, kPhUpdate);
   if ((e = bcg_update<T>(L, A.n, s, b.P, b.Q, X, b.R, c, b.gpart, 1)) != cudaSuccess) return e;
+  prof_end(L, kPhUpdate, 1);
   if ((e = tsqr<T>(L, tp, b.R, b.R, c->gamma, c->rho_new, b.tsqr, b.gpart, &c->counters[kCntC],
                    &c->done, &c->reortho_now)) != cudaSuccess) return e;
+  prof_begin(L, kPhSmall2);
   if ((e = small_bcg_2(L, c, b.hist, b.dec)) != cudaSuccess) return e;
-  return bcg_pupdate<T>(L, A.n, s, b.R, b.P, c);
+  prof_end(L, kPhSmall2, 1);
+  prof_begin(L, kPhPupdate);
+  e = bcg_pupdate<T>(L, A.n, s, b.R, b.P, c);
+  prof_end(L, kPhPupdate, 1);
+  return e;
 }
+
+// launches of one iteration (the TSQR tree has 2 * levels + 1 launches)
+int bcg_launches_per_iter(const TsqrPlan& tp) { return 8 + 2 * tp.levels + 1; }
 
 template <typename T>
 int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const bkrylov_opts& o,
@@ -234,13 +253,18 @@ int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const
   g.gram_out = c->rho;
   BK_TRY(gram<T>(L, n, s, b.R, b.R, g));
   BK_TRY(small_bcg_init(L, c, o.eta > 0));
+  Launch Lp = L;
+  if (o.profile) Lp.prof = &h->prof;
   int batch = o.sync_every > 0 ? o.sync_every : (n >= (1 << 20) ? 4 : 16);
   int enq = 0;
   while (true) {
     if ((rc = ctrl_peek(h, c))) return rc;
     if (h->host_ctrl->done != kDoneRunning || enq >= maxit) break;
     const int todo = (maxit - enq) < batch ? (maxit - enq) : batch;
-    for (int i = 0; i < todo; ++i) BK_TRY(bcg_iteration<T>(L, A, s, X, b, tp));
+    for (int i = 0; i < todo; ++i) {
+      BK_TRY(bcg_iteration<T>(Lp, A, s, X, b, tp));
+      prof_collect(Lp.prof);
+    }
     enq += todo;
   }
   BK_TRY(cudaEventRecord(e1, L.stream));
@@ -620,6 +644,10 @@ int bkrylov_create(bkrylov_handle* out, int device, void* stream) {
     if (cudaStreamCreate(&h->stream) != cudaSuccess) { delete h; return BK_ERR_CUDA; }
     h->own_stream = true;
   }
+  for (int i = 0; i < Prof::kMax; ++i) {
+    cudaEventCreate(&h->prof.b[i]);
+    cudaEventCreate(&h->prof.e[i]);
+  }
   if (cudaMallocHost(&h->host_ctrl, sizeof(Ctrl)) != cudaSuccess) {
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -634,6 +662,10 @@ int bkrylov_destroy(bkrylov_handle h) {
   cudaStreamSynchronize(h->stream);
   for (int i = 0; i < 2; ++i) if (h->ws[i]) cudaFree(h->ws[i]);
   if (h->host_ctrl) cudaFreeHost(h->host_ctrl);
+  for (int i = 0; i < Prof::kMax; ++i) {
+    if (h->prof.b[i]) cudaEventDestroy(h->prof.b[i]);
+    if (h->prof.e[i]) cudaEventDestroy(h->prof.e[i]);
+  }
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
   return BK_OK;
@@ -875,6 +907,28 @@ int bkrylov_solve_bgmres(bkrylov_handle h, bkrylov_op A, int s, const double* B,
   return with_device_blocks(h, A->d.n, s, B, X, 0, [&](const double* dB, double* dX, size_t) {
     return gmres_device(h, A->d, s, dB, dX, o, info);
   });
+}
+
+int bkrylov_profile_count(void) { return kNumPhases; }
+
+int bkrylov_profile_get(bkrylov_handle h, int i, const char** name, double* total_ms,
+                        long long* launches) {
+  if (!h || i < 0 || i >= kNumPhases) return BK_ERR_ARG;
+  if (name) *name = kPhaseNames[i];
+  if (total_ms) *total_ms = h->prof.ms[i];
+  if (launches) *launches = h->prof.launches[i];
+  return BK_OK;
+}
+
+int bkrylov_profile_reset(bkrylov_handle h) {
+  if (!h) return BK_ERR_ARG;
+  for (int i = 0; i < Prof::kMax; ++i) { h->prof.ms[i] = 0.0; h->prof.launches[i] = 0; }
+  return BK_OK;
+}
+
+int bkrylov_bcg_launches_per_iteration(int64_t n, int s) {
+  if (n < 1 || s < 1 || s > kMaxS) return -1;
+  return bcg_launches_per_iter(tsqr_plan(n, s));
 }
 
 int bkrylov_adjoint_scatter(bkrylov_handle h, bkrylov_op A, int s, const double* Lam,

@@ -47,10 +47,50 @@ struct Epi {
   const int* only_if = nullptr;  // optional: kernel exits unless *only_if != 0
 };
 
+// Optional per-phase device timing (CUDA events on the launching stream).
+enum Phase : int {
+  kPhSpmm = 0, kPhSmall1, kPhUpdate, kPhTsqrLeaf, kPhTsqrTree, kPhTsqrApply, kPhTsqrGram,
+  kPhSmall2, kPhPupdate, kNumPhases
+};
+struct Prof {
+  static constexpr int kMax = 16;
+  cudaEvent_t b[kMax] = {}, e[kMax] = {};
+  bool used[kMax] = {};
+  int nl[kMax] = {};          // launches in the pending phase
+  double ms[kMax] = {};
+  long long launches[kMax] = {};
+};
+extern const char* const kPhaseNames[kNumPhases];
+
 struct Launch {
   cudaStream_t stream = nullptr;
   int sms = 152;
+  Prof* prof = nullptr;
 };
+
+inline void prof_begin(const Launch& L, int id) {
+  if (L.prof) cudaEventRecord(L.prof->b[id], L.stream);
+}
+inline void prof_end(const Launch& L, int id, int nlaunch) {
+  if (L.prof) {
+    cudaEventRecord(L.prof->e[id], L.stream);
+    L.prof->used[id] = true;
+    L.prof->nl[id] = nlaunch;
+  }
+}
+// Wait for the recorded phases and add their durations (device time).
+inline void prof_collect(Prof* p) {
+  if (!p) return;
+  for (int i = 0; i < Prof::kMax; ++i) {
+    if (!p->used[i]) continue;
+    float ms = 0.f;
+    cudaEventSynchronize(p->e[i]);
+    cudaEventElapsedTime(&ms, p->b[i], p->e[i]);
+    p->ms[i] += ms;
+    p->launches[i] += p->nl[i];
+    p->used[i] = false;
+  }
+}
 
 // ---- operator products (bk_spmm.cu) ----
 // out = A in  (or out = sub - A in when sub != null), with optional fused epilogue.

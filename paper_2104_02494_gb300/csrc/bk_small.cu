@@ -240,6 +240,9 @@ __device__ double sm_kappa_d(const double* A, int s, double* M, double* M2, doub
   return s_kappa;
 }
 
+// max that propagates NaN (fmax would drop it)
+__device__ inline double nanmax(double a, double b) { return (isnan(b) || b > a) ? b : a; }
+
 __device__ inline void stop(Ctrl* c, int status) {
   if (threadIdx.x == 0) { c->done = kDoneStopped; c->status = status; }
 }
@@ -280,12 +283,12 @@ __global__ void __launch_bounds__(kST) small_bcg_init_k(Ctrl* c) {
     double v = 0.0;
     for (int k = 0; k < s; ++k) v = fma(S.B[IDX(k, i)], S.C[IDX(k, i)], v);
     const double n0 = c->n0[i];
-    c->relres[i] = n0 > 0.0 ? sqrt(fmax(v, 0.0)) / n0 : 0.0;
+    c->relres[i] = !isfinite(n0) ? NAN : (n0 > 0.0 ? sqrt(fmax(v, 0.0)) / n0 : 0.0);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double mx = 0.0;
-    for (int i = 0; i < s; ++i) mx = fmax(mx, c->relres[i]);
+    for (int i = 0; i < s; ++i) mx = nanmax(mx, c->relres[i]);
     if (!isfinite(mx)) { c->done = kDoneStopped; c->status = BK_NONFINITE; }
     else if (mx <= c->tol) { c->done = kDoneConverged; c->status = BK_OK; }
     else if (c->maxit <= 0) { c->done = kDoneStopped; c->status = BK_NOT_CONVERGED; }
@@ -347,13 +350,13 @@ __global__ void __launch_bounds__(kST) small_bcg_2_k(Ctrl* c, double* history, u
       }
     }
     const double n0 = c->n0[i];
-    c->relres[i] = n0 > 0.0 ? sqrt(fmax(v, 0.0)) / n0 : 0.0;
+    c->relres[i] = (!isfinite(n0) || isnan(v)) ? NAN : (n0 > 0.0 ? sqrt(fmax(v, 0.0)) / n0 : 0.0);
   }
   __syncthreads();
   __shared__ int s_conv;
   if (threadIdx.x == 0) {
     double mx = 0.0;
-    for (int i = 0; i < s; ++i) mx = fmax(mx, c->relres[i]);
+    for (int i = 0; i < s; ++i) mx = nanmax(mx, c->relres[i]);
     if (history) history[k] = mx;
     if (decisions) decisions[k] = (uint8_t)reo;
     c->iter = k + 1;
@@ -488,13 +491,13 @@ __global__ void __launch_bounds__(kST) small_bicg_3_k(Ctrl* c, double* history, 
     double v = 0.0;
     for (int r = 0; r < s; ++r) v = fma(S.B[IDX(r, i)], S.C[IDX(r, i)], v);
     const double n0 = c->n0[i];
-    c->relres[i] = n0 > 0.0 ? sqrt(fmax(v, 0.0)) / n0 : 0.0;
+    c->relres[i] = (!isfinite(n0) || isnan(v)) ? NAN : (n0 > 0.0 ? sqrt(fmax(v, 0.0)) / n0 : 0.0);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < s * s; i += blockDim.x) c->sigma[IDX(i / s, i % s)] = S.B[IDX(i / s, i % s)];
   if (threadIdx.x == 0) {
     double mx = 0.0;
-    for (int i = 0; i < s; ++i) mx = fmax(mx, c->relres[i]);
+    for (int i = 0; i < s; ++i) mx = nanmax(mx, c->relres[i]);
     if (history) history[k] = mx;
     if (decisions) decisions[k] = (uint8_t)c->reortho_now;
     c->iter = k + 1;
@@ -592,12 +595,12 @@ small_gmres_step_k(Ctrl* c, const double* __restrict__ Hc, double* __restrict__ 
     double v = 0.0;
     for (int r = 0; r < s; ++r) { const double x = V[(s + r) * s + i]; v = fma(x, x, v); }
     const double n0 = c->n0[i];
-    c->relres[i] = n0 > 0.0 ? sqrt(v) / n0 : 0.0;
+    c->relres[i] = (!isfinite(n0) || isnan(v)) ? NAN : (n0 > 0.0 ? sqrt(v) / n0 : 0.0);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double mx = 0.0;
-    for (int i = 0; i < s; ++i) mx = fmax(mx, c->relres[i]);
+    for (int i = 0; i < s; ++i) mx = nanmax(mx, c->relres[i]);
     if (history) history[hist_index] = mx;
     c->iter = c->iter + 1;
     if (!isfinite(mx)) { c->done = kDoneStopped; c->status = BK_NONFINITE; }

@@ -212,6 +212,7 @@ cudaError_t tsqr(const Launch& L, const TsqrPlan& p, const T* X, T* Y, double* g
   TsqrPtrs q = tsqr_ptrs(p, scratch);
   cudaError_t e;
   // 1. leaves
+  prof_begin(L, kPhTsqrLeaf);
   {
     const size_t sm = sizeof(T) * ((size_t)kTile * s + kTT + 2 * kMaxS) + 64;
     auto k = leaf_factor<T>;
@@ -219,7 +220,9 @@ cudaError_t tsqr(const Launch& L, const TsqrPlan& p, const T* X, T* Y, double* g
     k<<<(unsigned)p.nodes[0], kTT, sm, L.stream>>>(n, s, X, Y, q.R[0], q.tau[0], done, flag);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  prof_end(L, kPhTsqrLeaf, 1);
   // 2. tree up
+  prof_begin(L, kPhTsqrTree);
   const int F = p.fanin;
   const size_t smf = sizeof(double) * ((size_t)F * s * s + kTT + 2 * kMaxS) + 64;
   if ((e = set_smem(tree_factor, smf)) != cudaSuccess) return e;
@@ -239,7 +242,9 @@ cudaError_t tsqr(const Launch& L, const TsqrPlan& p, const T* X, T* Y, double* g
                                                               q.R[l], q.R[l - 1], done, flag);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  prof_end(L, kPhTsqrTree, 2 * p.levels + 1);
   // 5. leaves
+  prof_begin(L, kPhTsqrApply);
   {
     const size_t sm = sizeof(T) * (2 * (size_t)kTile * s + kTT + 2 * kMaxS) + 64;
     auto k = leaf_apply<T>;
@@ -247,6 +252,7 @@ cudaError_t tsqr(const Launch& L, const TsqrPlan& p, const T* X, T* Y, double* g
     k<<<(unsigned)p.nodes[0], kTT, sm, L.stream>>>(n, s, Y, q.R[0], q.tau[0], done, flag);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  prof_end(L, kPhTsqrApply, 1);
   if (rho_out) {
     Epi<T> ep;
     ep.sym = 1;
@@ -255,7 +261,10 @@ cudaError_t tsqr(const Launch& L, const TsqrPlan& p, const T* X, T* Y, double* g
     ep.counter = counter;
     ep.done = done;
     ep.only_if = flag;          // a skipped normalisation also skips its Gram
-    return gram<T>(L, n, s, Y, Y, ep);
+    prof_begin(L, kPhTsqrGram);
+    e = gram<T>(L, n, s, Y, Y, ep);
+    prof_end(L, kPhTsqrGram, 1);
+    return e;
   }
   return cudaSuccess;
 }
