@@ -146,6 +146,25 @@ int bkrylov_residual(bkrylov_handle h, bkrylov_op A, int s, const void* B, const
 int bkrylov_bdot(bkrylov_handle h, int64_t n, int s, const void* X, const void* Y,
                  double* G, int sym, int prec);
 
+/* G = X^T Y as bkrylov_bdot, for callers that cannot allocate device memory (a program
+   that runs under a fixed device-memory budget, e.g. a host framework that reserved all
+   device memory up front, or a loop where an allocation could block or fail).  The thesis
+   has no counterpart: this is a deployment variant of the block inner product above.
+   No handle: the call allocates nothing (no cudaMalloc/cudaFree, no allocating library
+   routine).  Its scratch (per-CTA partial sums, the reduced matrix, the ticket counter)
+   is one file-scope device array of 4.2 MB that every GPU loading the library keeps
+   until the process exits; the reduction grid is limited to 512 CTAs (any n works).
+   X, Y: n x s device blocks (prec BK_FP64 or BK_FP32); G: s x s device doubles.
+   Work is enqueued on cuda_stream (NULL = legacy default stream).
+   Errors: BK_ERR_ARG for n < 1, s outside 1..32, null pointers or another prec, before
+   any work; BK_ERR_CUDA if a CUDA call fails.
+   The first call on a device looks up the array's device address (cudaGetSymbolAddress
+   on the current device); make that first call before any stream capture.
+   All calls share the one array: calls that overlap on the GPU (other streams, other
+   host threads) race and must be serialised by the caller. */
+int bkrylov_bdot_noalloc(int64_t n, int s, const void* X, const void* Y, double* G, int sym,
+                         int prec, void* cuda_stream);
+
 /* ---- normalizer = TSQR (Def. "normalizer", Ch. 3.1; TSQR, Ch. 7.3) --------------- */
 /* X = Y sigma with Y^T Y = I, sigma upper triangular s x s (double, device) with
    diag(sigma) >= 0; defined also for rank-deficient X (Householder at every level).

@@ -57,6 +57,8 @@ SIGNATURES = [
                                    C.c_int]),
     ("bkrylov_bdot", C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_int, C.c_int]),
+    ("bkrylov_bdot_noalloc", C.c_int, [C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_int, C.c_int, C.c_void_p]),
     ("bkrylov_tsqr", C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_int]),
     ("bkrylov_solve_bcg", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
