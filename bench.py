@@ -69,11 +69,12 @@ def dist_init(args):
 def iteration_flops(n, s, tp_levels=None):
     """Algorithmic FP64 flops of one BCG iteration (stencil, eta = inf); FMA = 2 flops.
 
-    SpMM 7-point 14ns, alpha Gram (upper) n s(s+1), X and R updates 4ns^2,
-    Householder leaf factor 2ns^2, leaf apply 4ns^2, rho Gram n s(s+1),
-    P update 2ns^2 (the s x s work and the tree are O(n s^2 / 256) and ignored).
+    SpMM 7-point 14ns; the Grams alpha and rho (upper triangles) 2 n s(s+1);
+    the block updates X += P lx, R -= Q lam, P = R + P beta: 6ns^2; the
+    normaliser, Householder factor 2ns^2 and Q [sigma~; 0] 2ns^2.  The s x s
+    work, the WY factors and the TSQR tree are O(n s^2 / tile) and not counted.
     """
-    return 14 * n * s + 2 * n * s * (s + 1) + 12 * n * s * s
+    return 14 * n * s + 2 * n * s * (s + 1) + 10 * n * s * s
 
 
 PHASE_FLOPS = {
@@ -81,8 +82,7 @@ PHASE_FLOPS = {
     "spmm_alpha": lambda n, s: 14 * n * s + n * s * (s + 1),
     "update_rho": lambda n, s: 4 * n * s * s,
     "tsqr_leaf_factor": lambda n, s: 2 * n * s * s,
-    "tsqr_leaf_apply": lambda n, s: 4 * n * s * s,
-    "tsqr_rho_gram": lambda n, s: n * s * (s + 1),
+    "tsqr_leaf_apply": lambda n, s: 2 * n * s * s + n * s * (s + 1),
     "p_update": lambda n, s: 2 * n * s * s,
 }
 PHASE_BYTES = {
@@ -91,7 +91,6 @@ PHASE_BYTES = {
     "update_rho": lambda n, s: 6 * 8 * n * s,
     "tsqr_leaf_factor": lambda n, s: 2 * 8 * n * s,
     "tsqr_leaf_apply": lambda n, s: 2 * 8 * n * s,
-    "tsqr_rho_gram": lambda n, s: 8 * n * s,
     "p_update": lambda n, s: 3 * 8 * n * s,
 }
 

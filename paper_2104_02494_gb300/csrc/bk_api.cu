@@ -88,9 +88,12 @@ bool is_host_ptr(const void* p) {
   return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
 }
 
-size_t gpart_count(const Launch& L) {
-  // largest grid of a reducing kernel x largest partial record (two Grams + 2)
-  return (size_t)L.sms * 4 * (kMM + kMM + 8);
+size_t gpart_count(const Launch& L, const TsqrPlan& tp) {
+  // largest grid of a reducing row kernel x largest partial record (two Grams + 2),
+  // or one record per TSQR leaf tile, whichever is larger
+  const size_t rows = (size_t)L.sms * 4 * (kMM + kMM + 8);
+  const size_t tiles = tsqr_gpart_count(tp);
+  return rows > tiles ? rows : tiles;
 }
 
 void opts_or_default(const bkrylov_opts* o, bkrylov_opts* out) {
@@ -173,7 +176,7 @@ void bcg_layout(Alloc& a, int64_t n, int s, int maxit, const TsqrPlan& tp, const
   auto p = a.template take<T>(ns);
   auto q = a.template take<T>(ns);
   auto t = a.template take<char>(tp.bytes);
-  auto g = a.template take<double>(gpart_count(L));
+  auto g = a.template take<double>(gpart_count(L, tp));
   auto c = a.template take<Ctrl>(1);
   auto hs = a.template take<double>((size_t)maxit + 1);
   auto dc = a.template take<uint8_t>((size_t)maxit + 1);
@@ -213,7 +216,7 @@ cudaError_t bcg_iteration(const Launch& L, const OpDesc& A, int s, T* X, const B
 }
 
 // launches of one iteration (the TSQR tree has 2 * levels + 1 launches)
-int bcg_launches_per_iter(const TsqrPlan& tp) { return 8 + 2 * tp.levels + 1; }
+int bcg_launches_per_iter(const TsqrPlan& tp) { return 5 + tsqr_launches(tp); }
 
 template <typename T>
 int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const bkrylov_opts& o,
@@ -371,7 +374,7 @@ int bicg_device(bkrylov_handle h, const OpDesc& A, int s, const double* B, doubl
     *R = a.template take<double>(ns); *P = a.template take<double>(ns);
     *Q = a.template take<double>(ns); *U = a.template take<double>(ns);
     *R0 = a.template take<double>(ns); *ts = a.template take<char>(tp.bytes);
-    *gp = a.template take<double>(gpart_count(L)); *c = a.template take<Ctrl>(1);
+    *gp = a.template take<double>(gpart_count(L, tp)); *c = a.template take<Ctrl>(1);
     *hs = a.template take<double>((size_t)maxit + 1); *dc = a.template take<uint8_t>((size_t)maxit + 1);
     *fc = a.template take<uint8_t>((size_t)maxit + 1);
   };
@@ -470,7 +473,7 @@ int gmres_device(bkrylov_handle h, const OpDesc& A, int s, const double* B, doub
     *zeta = a.template take<double>((size_t)m * kMM);
     *Vp = a.template take<double*>((size_t)m + 1);
     *ts = a.template take<char>(tp.bytes);
-    *gp = a.template take<double>(gpart_count(L));
+    *gp = a.template take<double>(gpart_count(L, tp));
     *gmp = a.template take<double>(gmg);
     *c = a.template take<Ctrl>(1);
     *hs = a.template take<double>((size_t)maxit + 1);
@@ -794,7 +797,7 @@ int bkrylov_residual(bkrylov_handle h, bkrylov_op A, int s, const void* B, const
 // a ctrl-layout result matrix, in workspace 1.
 static int small_scratch(bkrylov_handle h, double** gp, unsigned** cnt, double** res) {
   const Launch L = launch_of(h);
-  const size_t gpn = gpart_count(L);
+  const size_t gpn = (size_t)L.sms * 4 * (kMM + kMM + 8);
   int rc = ensure_ws(h, 1, sizeof(double) * (gpn + kMM) + 1024);
   if (rc) return rc;
   Bump b(h->ws[1], h->ws_cap[1]);
@@ -833,7 +836,7 @@ int bkrylov_tsqr(bkrylov_handle h, int64_t n, int s, const void* X, void* Y, dou
   if (!h || !valid_s(s) || n < s || !X || !Y || !sigma) return BK_ERR_ARG;
   const Launch L = launch_of(h);
   const TsqrPlan tp = tsqr_plan(n, s);
-  const size_t gpn = gpart_count(L);
+  const size_t gpn = gpart_count(L, tp);
   int rc = ensure_ws(h, 1, tp.bytes + sizeof(double) * (gpn + kMM) + 2048);
   if (rc) return rc;
   Bump b(h->ws[1], h->ws_cap[1]);

@@ -98,9 +98,11 @@ __device__ inline bool grid_reduce_last(double* part, int cnt, double* gpart,
   if (s_ticket != gridDim.x - 1) return false;
   __threadfence();
   const int G = gridDim.x;
-  // 8 fixed chunks of CTAs per output when the block has enough threads.
-  const int R = (blockDim.x >= 8 * cnt) ? 8 : 1;
-  if (R == 8) {
+  // R fixed chunks of CTAs per output (R = blockDim / cnt, at most 8); the
+  // chunk sums are then added in chunk order.
+  int R = (int)blockDim.x / cnt;
+  if (R > 8) R = 8;
+  if (R >= 2) {
     double acc = 0.0;
     const int i = threadIdx.x % cnt;
     const int q = threadIdx.x / cnt;

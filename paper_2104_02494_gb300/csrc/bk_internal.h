@@ -128,10 +128,16 @@ struct TsqrPlan {
   int tile = 256;              // rows per leaf tile
   int fanin = 8;               // children per tree node
   int levels = 0;              // number of tree levels above the leaves
-  int64_t nodes[16] = {0};     // nodes per level (level 0 = leaves)
+  int64_t nodes[16] = {0};     // tiles per level (level 0 = the block's row tiles)
+  int64_t rows[16] = {0};      // rows per level (level l + 1 = stacked R factors of level l)
   size_t bytes = 0;            // scratch bytes
 };
+int tsqr_launches(const TsqrPlan& p);
 TsqrPlan tsqr_plan(int64_t n, int s);
+// doubles of grid partials the fused Gram of the leaf apply needs (one record per tile)
+inline size_t tsqr_gpart_count(const TsqrPlan& p) {
+  return (size_t)p.nodes[0] * (size_t)(p.s * (p.s + 1) / 2) + 64;
+}
 // Y, gamma = Norm(X) (Y may alias X).  gamma -> ctrl-layout s x s (row stride 32).
 // If rho_out != null, also the Gram Y^T Y (row stride 32) is produced.
 // done: optional stop flag (skip when *done); reortho_flag: optional, skip unless *flag.

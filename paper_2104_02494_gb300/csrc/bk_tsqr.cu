@@ -4,53 +4,55 @@
 //
 // The thesis splits the rows over MPI processes; here the "processes" are
 // row tiles of one GPU:
-//   1. leaf factor   one CTA per tile of 256 rows: Householder QR of the
-//                    tile in shared memory; the reflectors overwrite the tile
-//                    in Y, the tile's R factor goes to scratch;
+//   1. leaf factor   one CTA per tile of 8192/next_pow2(s) rows, held in shared
+//                    memory: Householder QR of the tile; the reflectors overwrite
+//                    the tile in Y; the tile's R factor and the triangular factor
+//                    T of its compact WY form  H_0 ... H_{s-1} = I - V T V^T
+//                    go to scratch;
 //   2. tree factor   one CTA per tree node: Householder QR of the stacked R
 //                    factors of its F = max(2, 256/s) children (FP64);
 //   3. root          sign fix: gamma = D R_root with D = sign(diag R_root);
 //   4. tree apply    top-down, each node turns its scatter factor sigma~ into
 //                    those of its children: Q_node [sigma~; 0];
-//   5. leaf apply    Y_tile = Q_tile [sigma~_tile; 0].
-// Every sum inside a CTA runs in a fixed order, so the result is bitwise
-// reproducible for a given n, s and device.
+//   5. leaf apply    Y_tile = Q_tile [sigma~; 0] = [sigma~; 0] - V (T V_1^T sigma~)
+//                    (V_1 = the tile's top s x s reflector block): one
+//                    n x s by s x s product, with the Gram Y^T Y fused.
+// Every sum runs in a fixed order, so the result is bitwise reproducible for
+// a given n, s and device.
 #include "bk_common.cuh"
 #include "bk_internal.h"
 #include "bk_hh.cuh"
 
 namespace bk {
 
-constexpr int kTile = 256;       // rows per leaf tile (>= s)
-constexpr int kTT = 256;         // threads per TSQR CTA
+constexpr int kTT = 256;                 // threads per TSQR CTA
+
+// Rows per leaf tile: 256 threads x (32 / next_pow2(s)) rows per thread, so the
+// tile (row stride s|1) stays below ~100 KB of shared memory (2 CTAs per SM).
+__host__ __device__ inline int leaf_tile_rows(int s) { return 8192 / next_pow2_s(s); }
 
 TsqrPlan tsqr_plan(int64_t n, int s) {
   TsqrPlan p;
-  p.n = n; p.s = s; p.tile = kTile;
-  p.fanin = (kTile / s) < 2 ? 2 : kTile / s;
-  if (p.fanin * s > kTile) p.fanin = kTile / s;
-  p.nodes[0] = (n + kTile - 1) / kTile;
+  p.n = n; p.s = s; p.tile = leaf_tile_rows(s);
+  p.fanin = p.tile / s;
+  p.rows[0] = n;
   int l = 0;
-  while (p.nodes[l] > 1 && l < 15) {
-    p.nodes[l + 1] = (p.nodes[l] + p.fanin - 1) / p.fanin;
+  for (;;) {
+    p.nodes[l] = (p.rows[l] + p.tile - 1) / p.tile;
+    if (p.nodes[l] <= 1 || l == 15) break;
+    p.rows[l + 1] = p.nodes[l] * s;       // the stacked R factors of level l
     ++l;
   }
   p.levels = l;
-  // scratch: per level l: R/sigma~ slots nodes_l*s*s, taus nodes_l*s; reflectors for l >= 1.
   size_t b = 0;
-  for (int i = 0; i <= p.levels; ++i) {
-    b += sizeof(double) * (size_t)p.nodes[i] * s * s;           // R / sigma~
-    b += sizeof(double) * (size_t)p.nodes[i] * s;               // taus
-    if (i >= 1) b += sizeof(double) * (size_t)p.nodes[i] * p.fanin * s * s;  // reflectors
-  }
+  for (int i = 0; i <= p.levels; ++i) b += 2 * sizeof(double) * (size_t)p.nodes[i] * s * s + 512;
   p.bytes = b + 256;
   return p;
 }
 
 struct TsqrPtrs {
-  double* R[16];
-  double* tau[16];
-  double* V[16];
+  double* R[16];       // stacked R factors of level l (later: the scatter factors sigma~)
+  double* Tf[16];      // WY factors T of the tiles of level l
 };
 
 static TsqrPtrs tsqr_ptrs(const TsqrPlan& p, void* scratch) {
@@ -58,9 +60,8 @@ static TsqrPtrs tsqr_ptrs(const TsqrPlan& p, void* scratch) {
   char* c = (char*)scratch;
   const int s = p.s;
   for (int i = 0; i <= p.levels; ++i) {
-    q.R[i] = (double*)c; c += sizeof(double) * (size_t)p.nodes[i] * s * s;
-    q.tau[i] = (double*)c; c += sizeof(double) * (size_t)p.nodes[i] * s;
-    if (i >= 1) { q.V[i] = (double*)c; c += sizeof(double) * (size_t)p.nodes[i] * p.fanin * s * s; }
+    q.R[i] = (double*)c; c += (sizeof(double) * (size_t)p.nodes[i] * s * s + 255) & ~(size_t)255;
+    q.Tf[i] = (double*)c; c += (sizeof(double) * (size_t)p.nodes[i] * s * s + 255) & ~(size_t)255;
   }
   return q;
 }
@@ -69,61 +70,153 @@ __device__ __forceinline__ bool tsqr_skip(const int* done, const int* flag) {
   return (done && *done) || (flag && !*flag);
 }
 
-// ---- 1. leaf factor -------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kTT)
-leaf_factor(int64_t n, int s, const T* __restrict__ X, T* __restrict__ Y, double* __restrict__ R0,
-            double* __restrict__ tau0, const int* done, const int* flag) {
-  if (tsqr_skip(done, flag)) return;
-  extern __shared__ double smem_d[];
-  T* M = reinterpret_cast<T*>(smem_d);
-  T* red = M + kTile * s;
-  T* w = red + kTT;
-  T* tau = w + kMaxS;
-  const int64_t r0 = (int64_t)blockIdx.x * kTile;
-  const int m = (int)((n - r0) < kTile ? (n - r0) : kTile);
-  for (int i = threadIdx.x; i < kTile * s; i += blockDim.x) {
-    const int t = i / s;
-    M[i] = (t < m) ? X[(r0 + t) * s + (i % s)] : T(0);
+// Sum the V-vector v over the 32 lanes of a warp by recursive halving: after
+// log2(V) exchange steps every lane holds one component, whose index it
+// returns; the remaining steps add that component over the lanes that share
+// it.  V (a power of two <= 32) shuffles instead of 5 V.
+template <int V, typename A>
+__device__ __forceinline__ int warp_reduce_scatter(A (&v)[V]) {
+  const int lane = threadIdx.x & 31;
+  int comp = 0;
+  int len = V;
+#pragma unroll
+  for (int o = 16, step = 0; (1 << step) < V; o >>= 1, ++step) {
+    const int half = V >> (step + 1);
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const A send = upper ? v[i] : v[i + half];
+      const A recv = __shfl_xor_sync(0xffffffffu, send, o);
+      v[i] = (upper ? v[i + half] : v[i]) + recv;
+    }
+    if (upper) comp += half;
+    len = half;
   }
-  __syncthreads();
-  const int mm = m > s ? m : s;       // a short tile is padded with zero rows up to s
-  cta_geqr2<T>(M, mm, s, tau, red, w);
-  for (int i = threadIdx.x; i < m * s; i += blockDim.x) Y[r0 * s + i] = M[i];
-  double* Rb = R0 + (size_t)blockIdx.x * s * s;
-  for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
-    const int a = i / s, c = i % s;
-    Rb[i] = (c >= a && a < mm) ? (double)M[a * s + c] : 0.0;
-  }
-  if (threadIdx.x < s) tau0[(size_t)blockIdx.x * s + threadIdx.x] = (double)tau[threadIdx.x];
+  (void)len;
+#pragma unroll
+  for (int o = 16 / V; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+  return comp;
 }
 
-// ---- 2. tree factor -------------------------------------------------------------
+// ---- 1. leaf factor -------------------------------------------------------------
+// Thread t owns tile rows t, t + 256, ... in registers (32 / next_pow2(s) rows
+// of next_pow2(s) values); the column loop is unrolled so every register index
+// is a compile-time constant.  Column j of the Householder QR:
+//   tail = sum_{g > j} M[g][j]^2 (CTA sum), beta = -sign(alpha) sqrt(alpha^2 + tail),
+//   tau = (beta - alpha) / beta, v_g = M[g][j] / (alpha - beta) for g > j, v_j = 1,
+//   v_g = 0 for g < j;
+//   p[c] = sum_g v_g M[g][c] for every c != j (one CTA vector sum):
+//     c > j gives w_c for the trailing update M[g][c] -= tau w_c v_g,
+//     c < j gives y_c = V[:, c]^T v_j for column j of the WY factor:
+//     T[0:j, j] = -tau T[0:j, 0:j] y,  T[j][j] = tau.
+template <typename T, int SW>
 __global__ void __launch_bounds__(kTT)
-tree_factor(int64_t nchild, int F, int s, const double* __restrict__ Rc, double* __restrict__ Rn,
-            double* __restrict__ Vn, double* __restrict__ taun, const int* done, const int* flag) {
+leaf_factor(int64_t n, int s, const T* __restrict__ X, T* __restrict__ Y, double* __restrict__ R0,
+            double* __restrict__ T0, const int* done, const int* flag) {
   if (tsqr_skip(done, flag)) return;
-  extern __shared__ double smem_d[];
-  const int m = F * s;
-  double* M = smem_d;
-  double* red = M + m * s;
-  double* w = red + kTT;
-  double* tau = w + kMaxS;
-  const int64_t c0 = (int64_t)blockIdx.x * F;
-  for (int i = threadIdx.x; i < m * s; i += blockDim.x) {
-    const int g = i / (s * s);
-    M[i] = (c0 + g < nchild) ? Rc[(size_t)(c0 + g) * s * s + (i % (s * s))] : 0.0;
+  constexpr int RPT = 32 / SW;
+  constexpr int tile = kTT * RPT;
+  __shared__ double Tm[SW * SW];
+  __shared__ T red_t[2][kWarps + 1];
+  __shared__ T red_w[2][kWarps][SW];
+  __shared__ T wy[2][SW];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t r0 = (int64_t)blockIdx.x * tile;
+  const int m = (int)((n - r0) < tile ? (n - r0) : tile);
+  T row[RPT][SW];
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const int g = tid + k * kTT;
+#pragma unroll
+    for (int c = 0; c < SW; ++c) row[k][c] = (g < m && c < s) ? X[(r0 + g) * s + c] : T(0);
+  }
+  for (int i = tid; i < SW * SW; i += kTT) Tm[i] = 0.0;
+#pragma unroll
+  for (int j = 0; j < SW; ++j) {
+    if (j >= s) break;
+    const int par = j & 1;
+    T part = T(0);
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      const int g = tid + k * kTT;
+      if (g > j) part = fma(row[k][j], row[k][j], part);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) red_t[par][warp] = part;
+    if (tid == j) red_t[par][kWarps] = row[0][j];
+    __syncthreads();
+    T tail = T(0);
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) tail += red_t[par][w];
+    const T alpha = red_t[par][kWarps];
+    T beta, tj, scale;
+    if (tail == T(0)) { tj = T(0); beta = alpha; scale = T(0); }
+    else {
+      const T nrm = sqrt(alpha * alpha + tail);
+      beta = alpha >= T(0) ? -nrm : nrm;
+      tj = (beta - alpha) / beta;
+      scale = T(1) / (alpha - beta);
+    }
+    if (tj != T(0)) {
+      T v[RPT];
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) {
+        const int g = tid + k * kTT;
+        if (g > j) { row[k][j] *= scale; v[k] = row[k][j]; }
+        else v[k] = (g == j) ? T(1) : T(0);
+      }
+      T p[SW];
+#pragma unroll
+      for (int c = 0; c < SW; ++c) {
+        p[c] = T(0);
+        if (c != j) {
+#pragma unroll
+          for (int k = 0; k < RPT; ++k) p[c] = fma(v[k], row[k][c], p[c]);
+        }
+      }
+      const int comp = warp_reduce_scatter<SW, T>(p);
+      if ((lane & (32 / SW - 1)) == 0) red_w[par][warp][comp] = p[0];
+      __syncthreads();
+      if (tid < SW) {
+        T acc = T(0);
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) acc += red_w[par][w][tid];
+        wy[par][tid] = acc;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int c = j + 1; c < SW; ++c) {
+        const T tw = -tj * wy[par][c];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) row[k][c] = fma(tw, v[k], row[k][c]);
+      }
+      if (tid < j) {
+        double acc = 0.0;
+        for (int b = tid; b < j; ++b) acc = fma(Tm[tid * SW + b], (double)wy[par][b], acc);
+        Tm[tid * SW + j] = -(double)tj * acc;
+      } else if (tid == j) {
+        Tm[j * SW + j] = (double)tj;
+      }
+    }
+    if (tid == j) row[0][j] = beta;
+  }
+#pragma unroll
+  for (int k = 0; k < RPT; ++k) {
+    const int g = tid + k * kTT;
+    if (g < m) {
+#pragma unroll
+      for (int c = 0; c < SW; ++c) if (c < s) Y[(r0 + g) * s + c] = row[k][c];
+    }
+  }
+  double* Rb = R0 + (size_t)blockIdx.x * s * s;
+  if (tid < s) {
+#pragma unroll
+    for (int c = 0; c < SW; ++c) if (c < s) Rb[tid * s + c] = (c >= tid) ? (double)row[0][c] : 0.0;
   }
   __syncthreads();
-  cta_geqr2<double>(M, m, s, tau, red, w);
-  double* V = Vn + (size_t)blockIdx.x * m * s;
-  for (int i = threadIdx.x; i < m * s; i += blockDim.x) V[i] = M[i];
-  double* Rb = Rn + (size_t)blockIdx.x * s * s;
-  for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
-    const int a = i / s, c = i % s;
-    Rb[i] = (c >= a) ? M[a * s + c] : 0.0;
-  }
-  if (threadIdx.x < s) taun[(size_t)blockIdx.x * s + threadIdx.x] = tau[threadIdx.x];
+  double* Tb = T0 + (size_t)blockIdx.x * s * s;
+  for (int i = tid; i < s * s; i += kTT) Tb[i] = Tm[(i / s) * SW + (i % s)];
 }
 
 // ---- 3. root: gamma = D R, sigma~_root = D ------------------------------------------
@@ -144,57 +237,106 @@ __global__ void root_fix(int s, double* __restrict__ Rroot, double* __restrict__
   }
 }
 
-// ---- 4. tree apply --------------------------------------------------------------
-__global__ void __launch_bounds__(kTT)
-tree_apply(int64_t nchild, int F, int s, const double* __restrict__ Vn, const double* __restrict__ taun,
-           const double* __restrict__ Sn, double* __restrict__ Sc, const int* done, const int* flag) {
-  if (tsqr_skip(done, flag)) return;
-  extern __shared__ double smem_d[];
-  const int m = F * s;
-  double* V = smem_d;
-  double* C = V + m * s;
-  double* red = C + m * s;
-  double* w = red + kTT;
-  double* tau = w + kMaxS;
-  const double* Vb = Vn + (size_t)blockIdx.x * m * s;
-  for (int i = threadIdx.x; i < m * s; i += blockDim.x) {
-    V[i] = Vb[i];
-    C[i] = (i < s * s) ? Sn[(size_t)blockIdx.x * s * s + i] : 0.0;
-  }
-  if (threadIdx.x < s) tau[threadIdx.x] = taun[(size_t)blockIdx.x * s + threadIdx.x];
-  __syncthreads();
-  cta_apply_q<double>(V, tau, m, s, C, red, w);
-  const int64_t c0 = (int64_t)blockIdx.x * F;
-  for (int i = threadIdx.x; i < m * s; i += blockDim.x) {
-    const int g = i / (s * s);
-    if (c0 + g < nchild) Sc[(size_t)(c0 + g) * s * s + (i % (s * s))] = C[i];
-  }
-}
-
 // ---- 5. leaf apply ----------------------------------------------------------------
-template <typename T>
+// Y_tile = [sigma~; 0] - V W with W = T (V_1^T sigma~), V the tile's unit lower
+// trapezoidal reflector block (stored below the diagonal in Y, implicit unit
+// diagonal, zero above).  One sub-warp per row, lane c computes Y[g][c]; the
+// Gram Y^T Y (upper, mirrored) is accumulated in the same pass when rho_out
+// is given and reduced over the tiles by the last CTA.
+template <typename T, int SW>
 __global__ void __launch_bounds__(kTT)
 leaf_apply(int64_t n, int s, T* __restrict__ Y, const double* __restrict__ S0,
-           const double* __restrict__ tau0, const int* done, const int* flag) {
+           const double* __restrict__ T0, double* rho_out, double* gpart, unsigned* counter,
+           const int* done, const int* flag) {
   if (tsqr_skip(done, flag)) return;
   extern __shared__ double smem_d[];
-  T* V = reinterpret_cast<T*>(smem_d);
-  T* C = V + kTile * s;
-  T* red = C + kTile * s;
-  T* w = red + kTT;
-  T* tau = w + kMaxS;
-  const int64_t r0 = (int64_t)blockIdx.x * kTile;
-  const int m = (int)((n - r0) < kTile ? (n - r0) : kTile);
-  const int mm = m > s ? m : s;
-  for (int i = threadIdx.x; i < mm * s; i += blockDim.x) {
-    const int t = i / s;
-    V[i] = (t < m) ? Y[(r0 + t) * s + (i % s)] : T(0);
-    C[i] = (i < s * s) ? (T)S0[(size_t)blockIdx.x * s * s + i] : T(0);
+  constexpr int RPW = 32 / SW;
+  constexpr int tile = kTT * (32 / SW);
+  double* Sg = smem_d;              // sigma~ (s x s, row stride 32)
+  double* Tt = Sg + kMM;            // T
+  double* Zm = Tt + kMM;            // V_1^T sigma~, then scratch
+  double* V1 = Zm + kMM;            // top s x s reflector block
+  T* Wt = reinterpret_cast<T*>(V1 + kMM);   // W (s x s, row stride s) in the working precision
+  double* red = V1 + kMM + kMM;     // reduction scratch (after W, which needs <= kMM doubles)
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t r0 = (int64_t)blockIdx.x * tile;
+  const int m = (int)((n - r0) < tile ? (n - r0) : tile);
+  for (int i = tid; i < s * s; i += kTT) {
+    const int a = i / s, c = i - a * s;
+    Sg[a * kMaxS + c] = S0[(size_t)blockIdx.x * s * s + i];
+    Tt[a * kMaxS + c] = T0[(size_t)blockIdx.x * s * s + i];
+    // V_1[a][c]: 1 on the diagonal, stored reflector entries below, 0 above
+    V1[a * kMaxS + c] = (c == a) ? 1.0 : ((c < a && a < m) ? (double)Y[(r0 + a) * s + c] : 0.0);
   }
-  if (threadIdx.x < s) tau[threadIdx.x] = (T)tau0[(size_t)blockIdx.x * s + threadIdx.x];
   __syncthreads();
-  cta_apply_q<T>(V, tau, mm, s, C, red, w);
-  for (int i = threadIdx.x; i < m * s; i += blockDim.x) Y[r0 * s + i] = C[i];
+  for (int i = tid; i < s * s; i += kTT) {          // Z = V_1^T sigma~
+    const int a = i / s, c = i - a * s;
+    double acc = 0.0;
+    for (int g = a; g < s; ++g) acc = fma(V1[g * kMaxS + a], Sg[g * kMaxS + c], acc);
+    Zm[a * kMaxS + c] = acc;
+  }
+  __syncthreads();
+  for (int i = tid; i < s * s; i += kTT) {          // W = T Z (T upper triangular)
+    const int a = i / s, c = i - a * s;
+    double acc = 0.0;
+    for (int b = a; b < s; ++b) acc = fma(Tt[a * kMaxS + b], Zm[b * kMaxS + c], acc);
+    Wt[a * s + c] = (T)acc;
+  }
+  __syncthreads();
+  const int c = lane & (SW - 1), rs = lane / SW, warp = tid >> 5;
+  const bool want_rho = rho_out != nullptr;
+  double acc[SW];
+#pragma unroll
+  for (int a = 0; a < SW; ++a) acc[a] = 0.0;
+  T acc_t[SW];
+#pragma unroll
+  for (int a = 0; a < SW; ++a) acc_t[a] = T(0);
+  int since = 0;
+  for (int base = warp * RPW; base < m; base += kWarps * RPW) {
+    const int g = base + rs;
+    const bool ok = (g < m) && (c < s);
+    T v = T(0);
+    if (ok) v = (g < s) ? (c == g ? T(1) : (c < g ? Y[(r0 + g) * s + c] : T(0))) : Y[(r0 + g) * s + c];
+    T y = (ok && g < s) ? (T)Sg[g * kMaxS + c] : T(0);
+#pragma unroll
+    for (int a = 0; a < SW; ++a) {
+      const T va = sw_bcast<SW>(v, a);
+      if (a < s && c < s) y = fma(-va, Wt[a * s + c], y);
+    }
+    if (ok) Y[(r0 + g) * s + c] = y;
+    if (want_rho) {
+      const T yv = ok ? y : T(0);
+      if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int a = 0; a < SW; ++a) {
+          const T ya = sw_bcast<SW>(yv, a);
+          if (a <= c) acc[a] = fma((double)ya, (double)yv, acc[a]);
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < SW; ++a) {
+          const T ya = sw_bcast<SW>(yv, a);
+          if (a <= c) acc_t[a] = fma(ya, yv, acc_t[a]);
+        }
+        if (++since == 16) {
+#pragma unroll
+          for (int a = 0; a < SW; ++a) { acc[a] += (double)acc_t[a]; acc_t[a] = T(0); }
+          since = 0;
+        }
+      }
+    }
+  }
+  if (!want_rho) return;
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int a = 0; a < SW; ++a) acc[a] += (double)acc_t[a];
+  }
+  const int cnt = ut_count(s);
+  double* part = red;
+  double* scratch = red + cnt + 1;
+  cta_reduce_gram<SW>(acc, s, true, scratch, part);
+  if (!grid_reduce_last(part, cnt, gpart, counter)) return;
+  unpack_gram(part, s, true, rho_out);
 }
 
 template <typename K>
@@ -203,70 +345,73 @@ static cudaError_t set_smem(K kern, size_t bytes) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+template <typename T, int SW>
+static cudaError_t launch_leaves(const Launch& L, int64_t rows, int s, int64_t tiles, const T* X, T* Y,
+                                 double* Rst, double* Tf, double* rho_out, double* gpart,
+                                 unsigned* counter, const int* done, const int* flag, bool factor) {
+  if (factor) {
+    leaf_factor<T, SW><<<(unsigned)tiles, kTT, 0, L.stream>>>(rows, s, X, Y, Rst, Tf, done, flag);
+    return cudaGetLastError();
+  }
+  const size_t sm = sizeof(double) * (6 * kMM + ut_count(s) + 2 + kWarps * ut_count(s)) + 64;
+  auto k = leaf_apply<T, SW>;
+  cudaError_t e = set_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  k<<<(unsigned)tiles, kTT, sm, L.stream>>>(rows, s, Y, Rst, Tf, rho_out, gpart, counter, done, flag);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t leaves(const Launch& L, int64_t rows, int s, int64_t tiles, const T* X, T* Y,
+                          double* Rst, double* Tf, double* rho_out, double* gpart, unsigned* counter,
+                          const int* done, const int* flag, bool factor) {
+#define BK_LEAVES(SWV) \
+  return launch_leaves<T, SWV>(L, rows, s, tiles, X, Y, Rst, Tf, rho_out, gpart, counter, done, flag, factor)
+  switch (next_pow2_s(s)) {
+    case 1: BK_LEAVES(1);
+    case 2: BK_LEAVES(2);
+    case 4: BK_LEAVES(4);
+    case 8: BK_LEAVES(8);
+    case 16: BK_LEAVES(16);
+    case 32: BK_LEAVES(32);
+    default: return cudaErrorInvalidValue;
+  }
+#undef BK_LEAVES
+}
+
+int tsqr_launches(const TsqrPlan& p) { return 2 * (p.levels + 1) + 1; }
+
+// X = Y gamma (Y may alias X).  Level 0 tiles the n x s block; level l + 1
+// tiles the stacked R factors of level l (FP64) until one tile remains, whose
+// R is the root.  The scatter factors then travel down: the apply of level l
+// turns the sigma~ of its tiles into the stacked sigma~ of level l - 1.
 template <typename T>
 cudaError_t tsqr(const Launch& L, const TsqrPlan& p, const T* X, T* Y, double* gamma_out,
                  double* rho_out, void* scratch, double* gpart, unsigned* counter, const int* done,
                  const int* flag) {
   const int s = p.s;
-  const int64_t n = p.n;
   TsqrPtrs q = tsqr_ptrs(p, scratch);
   cudaError_t e;
-  // 1. leaves
+  if (rho_out && !counter) return cudaErrorInvalidValue;
   prof_begin(L, kPhTsqrLeaf);
-  {
-    const size_t sm = sizeof(T) * ((size_t)kTile * s + kTT + 2 * kMaxS) + 64;
-    auto k = leaf_factor<T>;
-    if ((e = set_smem(k, sm)) != cudaSuccess) return e;
-    k<<<(unsigned)p.nodes[0], kTT, sm, L.stream>>>(n, s, X, Y, q.R[0], q.tau[0], done, flag);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
+  if ((e = leaves<T>(L, p.n, s, p.nodes[0], X, Y, q.R[0], q.Tf[0], nullptr, nullptr, nullptr, done,
+                     flag, true)) != cudaSuccess) return e;
   prof_end(L, kPhTsqrLeaf, 1);
-  // 2. tree up
   prof_begin(L, kPhTsqrTree);
-  const int F = p.fanin;
-  const size_t smf = sizeof(double) * ((size_t)F * s * s + kTT + 2 * kMaxS) + 64;
-  if ((e = set_smem(tree_factor, smf)) != cudaSuccess) return e;
-  for (int l = 1; l <= p.levels; ++l) {
-    tree_factor<<<(unsigned)p.nodes[l], kTT, smf, L.stream>>>(p.nodes[l - 1], F, s, q.R[l - 1], q.R[l],
-                                                               q.V[l], q.tau[l], done, flag);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  // 3. root
+  for (int l = 1; l <= p.levels; ++l)
+    if ((e = leaves<double>(L, p.rows[l], s, p.nodes[l], q.R[l - 1], q.R[l - 1], q.R[l], q.Tf[l],
+                            nullptr, nullptr, nullptr, done, flag, true)) != cudaSuccess) return e;
   root_fix<<<1, 256, 0, L.stream>>>(s, q.R[p.levels], gamma_out, done, flag);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // 4. tree down
-  const size_t sma = sizeof(double) * (2 * (size_t)F * s * s + kTT + 2 * kMaxS) + 64;
-  if ((e = set_smem(tree_apply, sma)) != cudaSuccess) return e;
-  for (int l = p.levels; l >= 1; --l) {
-    tree_apply<<<(unsigned)p.nodes[l], kTT, sma, L.stream>>>(p.nodes[l - 1], F, s, q.V[l], q.tau[l],
-                                                              q.R[l], q.R[l - 1], done, flag);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
+  for (int l = p.levels; l >= 1; --l)
+    if ((e = leaves<double>(L, p.rows[l], s, p.nodes[l], nullptr, q.R[l - 1], q.R[l], q.Tf[l],
+                            nullptr, nullptr, nullptr, done, flag, false)) != cudaSuccess) return e;
   prof_end(L, kPhTsqrTree, 2 * p.levels + 1);
-  // 5. leaves
   prof_begin(L, kPhTsqrApply);
-  {
-    const size_t sm = sizeof(T) * (2 * (size_t)kTile * s + kTT + 2 * kMaxS) + 64;
-    auto k = leaf_apply<T>;
-    if ((e = set_smem(k, sm)) != cudaSuccess) return e;
-    k<<<(unsigned)p.nodes[0], kTT, sm, L.stream>>>(n, s, Y, q.R[0], q.tau[0], done, flag);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
+  e = leaves<T>(L, p.n, s, p.nodes[0], nullptr, Y, q.R[0], q.Tf[0], rho_out, gpart, counter, done, flag,
+                false);
   prof_end(L, kPhTsqrApply, 1);
-  if (rho_out) {
-    Epi<T> ep;
-    ep.sym = 1;
-    ep.gram_out = rho_out;
-    ep.gpart = gpart;
-    ep.counter = counter;
-    ep.done = done;
-    ep.only_if = flag;          // a skipped normalisation also skips its Gram
-    prof_begin(L, kPhTsqrGram);
-    e = gram<T>(L, n, s, Y, Y, ep);
-    prof_end(L, kPhTsqrGram, 1);
-    return e;
-  }
-  return cudaSuccess;
+  return e;
 }
 
 template cudaError_t tsqr<double>(const Launch&, const TsqrPlan&, const double*, double*, double*,
