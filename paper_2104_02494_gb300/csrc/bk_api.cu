@@ -91,7 +91,7 @@ bool is_host_ptr(const void* p) {
 size_t gpart_count(const Launch& L, const TsqrPlan& tp) {
   // largest grid of a reducing row kernel x largest partial record (two Grams + 2),
   // or one record per TSQR leaf tile, whichever is larger
-  const size_t rows = (size_t)L.sms * 4 * (kMM + kMM + 8);
+  const size_t rows = (size_t)L.sms * kCtasPerSm * (kMM + kMM + 8);
   const size_t tiles = tsqr_gpart_count(tp);
   return rows > tiles ? rows : tiles;
 }
@@ -797,7 +797,7 @@ int bkrylov_residual(bkrylov_handle h, bkrylov_op A, int s, const void* B, const
 // a ctrl-layout result matrix, in workspace 1.
 static int small_scratch(bkrylov_handle h, double** gp, unsigned** cnt, double** res) {
   const Launch L = launch_of(h);
-  const size_t gpn = (size_t)L.sms * 4 * (kMM + kMM + 8);
+  const size_t gpn = (size_t)L.sms * kCtasPerSm * (kMM + kMM + 8);
   int rc = ensure_ws(h, 1, sizeof(double) * (gpn + kMM) + 1024);
   if (rc) return rc;
   Bump b(h->ws[1], h->ws_cap[1]);

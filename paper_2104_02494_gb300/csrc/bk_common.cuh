@@ -20,6 +20,9 @@ namespace bk {
 constexpr int kMaxS = BKRYLOV_MAX_S;   // 32
 constexpr int kThreads = 256;          // threads per CTA of the row kernels
 constexpr int kWarps = kThreads / 32;
+// CTAs per SM launched by the row kernels (8 x 256 threads = full residency),
+// so that enough loads are in flight to cover HBM latency.
+constexpr int kCtasPerSm = 8;
 
 // ---- per-solve device control block --------------------------------------------
 // s x s matrices are stored with row stride kMaxS: M[i][j] at i * kMaxS + j.
@@ -160,6 +163,71 @@ __device__ inline void cta_reduce_gram(double (&acc)[SW], int s, bool sym, doubl
   }
   __syncthreads();
 }
+
+// Symmetric Gram  l^T q  (upper triangle) of TWO rows per sub-warp, FP64,
+// without idle lanes.  Lane c of a sub-warp (SW >= 2 lanes) holds column c
+// of row A (la, qa) and of row B (lb, qb).  A row's upper triangle has
+// SW(SW+1)/2 entries; lane cc = c mod SW/2 takes the column pair (cc, SW-1-cc),
+// i.e. the entries (a, cc), a <= cc, and (a, SW-1-cc), a <= SW-1-cc: SW + 1
+// entries, the same count for every lane.  Lanes c < SW/2 do this for row A,
+// lanes c >= SW/2 for row B.  acc[t] is entry (t, cc) for t <= cc and
+// (t - cc - 1, SW-1-cc) otherwise.  Columns >= s hold zeros in la/qa/lb/qb,
+// so their entries vanish.
+template <int SW>
+struct SymGramPair {
+  double acc[SW + 1];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int t = 0; t <= SW; ++t) acc[t] = 0.0;
+  }
+  __device__ __forceinline__ void add(double la, double qa, double lb, double qb) {
+    const int c = threadIdx.x & (SW - 1);
+    const bool hi = c >= SW / 2;
+    const int cc = hi ? c - SW / 2 : c;
+    const int c2 = SW - 1 - cc;
+    const double q1a = __shfl_sync(0xffffffffu, qa, cc, SW), q1b = __shfl_sync(0xffffffffu, qb, cc, SW);
+    const double q2a = __shfl_sync(0xffffffffu, qa, c2, SW), q2b = __shfl_sync(0xffffffffu, qb, c2, SW);
+    const double q1 = hi ? q1b : q1a, q2 = hi ? q2b : q2a;
+#pragma unroll
+    for (int t = 0; t <= SW; ++t) {
+      const bool first = t <= cc;
+      const int a = first ? t : t - cc - 1;
+      const double va = __shfl_sync(0xffffffffu, la, a, SW);
+      const double vb = __shfl_sync(0xffffffffu, lb, a, SW);
+      acc[t] = fma(hi ? vb : va, first ? q1 : q2, acc[t]);
+    }
+  }
+  // CTA sum into the packed upper triangle part[0..s(s+1)/2); scratch holds
+  // kWarps * s(s+1)/2 doubles.  Every entry with column < s is written by
+  // exactly one lane of every warp.
+  __device__ void cta_reduce(int s, double* scratch, double* part) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int t = 0; t <= SW; ++t) {
+      acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], SW / 2);
+#pragma unroll
+      for (int off = SW; off < 32; off <<= 1) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], off);
+    }
+    const int cnt = ut_count(s);
+    if (lane < SW / 2) {
+      const int cc = lane, c2 = SW - 1 - lane;
+#pragma unroll
+      for (int t = 0; t <= SW; ++t) {
+        const bool first = t <= cc;
+        const int a = first ? t : t - cc - 1;
+        const int col = first ? cc : c2;
+        if (col < s) scratch[warp * cnt + ut_index(a, col)] = acc[t];
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      double t = 0.0;
+      for (int w = 0; w < kWarps; ++w) t += scratch[w * cnt + i];
+      part[i] = t;
+    }
+    __syncthreads();
+  }
+};
 
 // Unpack a reduced Gram (packed upper or full s x s) into a ctrl-layout matrix.
 __device__ inline void unpack_gram(const double* part, int s, bool sym, double* M) {

@@ -63,7 +63,7 @@ extern "C" int bkrylov_bdot_noalloc(int64_t n, int s, const void* X, const void*
   if (rc != BK_OK) return rc;
   Launch L;
   L.stream = static_cast<cudaStream_t>(cuda_stream);
-  L.sms = kNaMaxCtas / 4;            // the row kernels launch at most 4 * sms CTAs
+  L.sms = kNaMaxCtas / kCtasPerSm;   // the row kernels launch at most kCtasPerSm * sms CTAs
   unsigned* counter = reinterpret_cast<unsigned*>(scratch + kNaCounter);
   // the ticket counter must start at zero; the previous call's last CTA reset
   // it, but a call that failed mid-way might not have

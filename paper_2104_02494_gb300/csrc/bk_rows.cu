@@ -11,7 +11,7 @@
 
 namespace bk {
 
-static int row_grid(const Launch& L, int64_t n, int s, int per_sm = 4) {
+static int row_grid(const Launch& L, int64_t n, int s, int per_sm = kCtasPerSm) {
   const int rpw = 32 / next_pow2_s(s);
   const int64_t rows_per_cta = (int64_t)rpw * kWarps;
   int64_t need = (n + rows_per_cta - 1) / rows_per_cta;
@@ -47,15 +47,17 @@ bcg_update_kernel(int64_t n, int s, const T* __restrict__ P, const T* __restrict
   const int lane = threadIdx.x & 31, c = lane & (SW - 1), rs = lane / SW;
   const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const int64_t nw = (int64_t)gridDim.x * kWarps;
+  constexpr bool kPair = (sizeof(T) == 8) && (SW >= 2);
   double acc[SW];
 #pragma unroll
   for (int a = 0; a < SW; ++a) acc[a] = 0.0;
   T acc_t[SW];
 #pragma unroll
   for (int a = 0; a < SW; ++a) acc_t[a] = T(0);
+  SymGramPair<kPair ? SW : 2> pg;
+  pg.zero();
   int since = 0;
-  for (int64_t base = gw * RPW; base < n; base += nw * RPW) {
-    const int64_t r = base + rs;
+  auto do_row = [&](int64_t r) -> T {
     const bool ok = (r < n) && (c < s);
     const T p = ok ? P[r * s + c] : T(0);
     const T q = ok ? Q[r * s + c] : T(0);
@@ -75,25 +77,34 @@ bcg_update_kernel(int64_t n, int s, const T* __restrict__ P, const T* __restrict
       rt = R[r * s + c] - rq;
       R[r * s + c] = rt;
     }
-    if (want_rho) {
-      if constexpr (sizeof(T) == 8) {
+    return rt;
+  };
+  auto accum_row = [&](T rt) {
+    if constexpr (sizeof(T) == 8) {
 #pragma unroll
-        for (int a = 0; a < SW; ++a) {
-          const T ra = sw_bcast<SW>(rt, a);
-          if (a <= c) acc[a] = fma((double)ra, (double)rt, acc[a]);
-        }
-      } else {
-#pragma unroll
-        for (int a = 0; a < SW; ++a) {
-          const T ra = sw_bcast<SW>(rt, a);
-          if (a <= c) acc_t[a] = fma(ra, rt, acc_t[a]);
-        }
-        if (++since == 16) {
-#pragma unroll
-          for (int a = 0; a < SW; ++a) { acc[a] += (double)acc_t[a]; acc_t[a] = T(0); }
-          since = 0;
-        }
+      for (int a = 0; a < SW; ++a) {
+        const T ra = sw_bcast<SW>(rt, a);
+        if (a <= c) acc[a] = fma((double)ra, (double)rt, acc[a]);
       }
+    } else {
+#pragma unroll
+      for (int a = 0; a < SW; ++a) {
+        const T ra = sw_bcast<SW>(rt, a);
+        if (a <= c) acc_t[a] = fma(ra, rt, acc_t[a]);
+      }
+      if (++since == 16) {
+#pragma unroll
+        for (int a = 0; a < SW; ++a) { acc[a] += (double)acc_t[a]; acc_t[a] = T(0); }
+        since = 0;
+      }
+    }
+  };
+  for (int64_t base = gw * RPW; base < n; base += 2 * nw * RPW) {
+    const T rA = do_row(base + rs);
+    const T rB = do_row(base + nw * RPW + rs);
+    if (want_rho) {
+      if constexpr (kPair) pg.add((double)rA, (double)rA, (double)rB, (double)rB);
+      else { accum_row(rA); accum_row(rB); }
     }
   }
   if (!want_rho) return;
@@ -104,7 +115,8 @@ bcg_update_kernel(int64_t n, int s, const T* __restrict__ P, const T* __restrict
   const int cnt = ut_count(s);
   double* part = red;
   double* scratch = red + cnt + 1;
-  cta_reduce_gram<SW>(acc, s, true, scratch, part);
+  if constexpr (kPair) pg.cta_reduce(s, scratch, part);
+  else cta_reduce_gram<SW>(acc, s, true, scratch, part);
   if (!grid_reduce_last(part, cnt, gpart, &ctrl->counters[kCntB])) return;
   unpack_gram(part, s, true, ctrl->rho_new);
 }
@@ -121,17 +133,27 @@ bcg_pupdate_kernel(int64_t n, int s, const T* __restrict__ R, T* __restrict__ P,
   const int lane = threadIdx.x & 31, c = lane & (SW - 1), rs = lane / SW;
   const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const int64_t nw = (int64_t)gridDim.x * kWarps;
-  for (int64_t base = gw * RPW; base < n; base += nw * RPW) {
-    const int64_t r = base + rs;
-    const bool ok = (r < n) && (c < s);
-    const T p = ok ? P[r * s + c] : T(0);
-    T acc = T(0);
+  // two row groups per trip: both rows' loads are issued before the shuffles
+  for (int64_t base = gw * RPW; base < n; base += 2 * nw * RPW) {
+    const int64_t rA = base + rs, rB = base + nw * RPW + rs;
+    const bool okA = (rA < n) && (c < s), okB = (rB < n) && (c < s);
+    const T pA = okA ? P[rA * s + c] : T(0);
+    const T pB = okB ? P[rB * s + c] : T(0);
+    const T xA = okA ? R[rA * s + c] : T(0);
+    const T xB = okB ? R[rB * s + c] : T(0);
+    T accA = T(0), accB = T(0);
 #pragma unroll
     for (int a = 0; a < SW; ++a) {
-      const T pa = sw_bcast<SW>(p, a);
-      if (a < s && c < s) acc = fma(pa, beta[a * s + c], acc);
+      const T paA = sw_bcast<SW>(pA, a);
+      const T paB = sw_bcast<SW>(pB, a);
+      if (a < s && c < s) {
+        const T b = beta[a * s + c];
+        accA = fma(paA, b, accA);
+        accB = fma(paB, b, accB);
+      }
     }
-    if (ok) P[r * s + c] = R[r * s + c] + acc;
+    if (okA) P[rA * s + c] = xA + accA;
+    if (okB) P[rB * s + c] = xB + accB;
   }
 }
 

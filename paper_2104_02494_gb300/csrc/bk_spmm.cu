@@ -132,49 +132,79 @@ spmm_kernel(RowOp op, int64_t n, int s, const T* __restrict__ P, T* __restrict__
   const int64_t nw = (int64_t)gridDim.x * kWarps;
   const bool has_gram = ep.left != nullptr;
   const bool has_frob = ep.frob != nullptr;
+  // FP64 symmetric Grams use the idle-lane-free pairing of two rows per
+  // sub-warp; FP32 and non-symmetric Grams accumulate per row.
+  constexpr bool kPair = (sizeof(T) == 8) && (SW >= 2);
+  const bool use_pair = kPair && has_gram && ep.sym;
   double acc[SW];
 #pragma unroll
   for (int a = 0; a < SW; ++a) acc[a] = 0.0;
   T acc_t[SW];
 #pragma unroll
   for (int a = 0; a < SW; ++a) acc_t[a] = T(0);
+  SymGramPair<kPair ? SW : 2> pg;
+  pg.zero();
   int since_flush = 0;
   double f_qf = 0.0, f_qq = 0.0;
 
-  for (int64_t base = gw * RPW; base < n; base += nw * RPW) {
-    const int64_t r = base + rs;
-    const bool ok = (r < n) && (c < s);
-    T q = T(0);
-    if (ok) {
-      q = op(r, c, s, P);
-      if (sub) q = sub[r * s + c] - q;
-      if (Q) Q[r * s + c] = q;
-    }
-    if (has_gram) {
-      const T l = ok ? ep.left[r * s + c] : T(0);
-      if constexpr (sizeof(T) == 8) {
+  auto accum_row = [&](T l, T q) {
+    if constexpr (sizeof(T) == 8) {
 #pragma unroll
-        for (int a = 0; a < SW; ++a) {
-          const T la = sw_bcast<SW>(l, a);
-          if (!ep.sym || a <= c) acc[a] = fma((double)la, (double)q, acc[a]);
-        }
-      } else {
+      for (int a = 0; a < SW; ++a) {
+        const T la = sw_bcast<SW>(l, a);
+        if (!ep.sym || a <= c) acc[a] = fma((double)la, (double)q, acc[a]);
+      }
+    } else {
 #pragma unroll
-        for (int a = 0; a < SW; ++a) {
-          const T la = sw_bcast<SW>(l, a);
-          if (!ep.sym || a <= c) acc_t[a] = fma(la, q, acc_t[a]);
-        }
-        if (++since_flush == kFlush) {
+      for (int a = 0; a < SW; ++a) {
+        const T la = sw_bcast<SW>(l, a);
+        if (!ep.sym || a <= c) acc_t[a] = fma(la, q, acc_t[a]);
+      }
+      if (++since_flush == kFlush) {
 #pragma unroll
-          for (int a = 0; a < SW; ++a) { acc[a] += (double)acc_t[a]; acc_t[a] = T(0); }
-          since_flush = 0;
-        }
+        for (int a = 0; a < SW; ++a) { acc[a] += (double)acc_t[a]; acc_t[a] = T(0); }
+        since_flush = 0;
       }
     }
-    if (has_frob && ok) {
-      const double f = (double)ep.frob[r * s + c];
-      f_qf = fma((double)q, f, f_qf);
-      f_qq = fma((double)q, (double)q, f_qq);
+  };
+
+  // two row groups per trip (rows A and B of every sub-warp)
+  for (int64_t base = gw * RPW; base < n; base += 2 * nw * RPW) {
+    const int64_t rA = base + rs, rB = base + nw * RPW + rs;
+    const bool okA = (rA < n) && (c < s), okB = (rB < n) && (c < s);
+    T qA = T(0), qB = T(0);
+    if (okA) {
+      qA = op(rA, c, s, P);
+      if (sub) qA = sub[rA * s + c] - qA;
+      if (Q) Q[rA * s + c] = qA;
+    }
+    if (okB) {
+      qB = op(rB, c, s, P);
+      if (sub) qB = sub[rB * s + c] - qB;
+      if (Q) Q[rB * s + c] = qB;
+    }
+    if (has_gram) {
+      const T lA = okA ? ep.left[rA * s + c] : T(0);
+      const T lB = okB ? ep.left[rB * s + c] : T(0);
+      if constexpr (kPair) {
+        if (use_pair) pg.add((double)lA, (double)qA, (double)lB, (double)qB);
+        else { accum_row(lA, qA); accum_row(lB, qB); }
+      } else {
+        accum_row(lA, qA);
+        accum_row(lB, qB);
+      }
+    }
+    if (has_frob) {
+      if (okA) {
+        const double f = (double)ep.frob[rA * s + c];
+        f_qf = fma((double)qA, f, f_qf);
+        f_qq = fma((double)qA, (double)qA, f_qq);
+      }
+      if (okB) {
+        const double f = (double)ep.frob[rB * s + c];
+        f_qf = fma((double)qB, f, f_qf);
+        f_qq = fma((double)qB, (double)qB, f_qq);
+      }
     }
   }
   if (!has_gram && !has_frob) return;
@@ -187,7 +217,10 @@ spmm_kernel(RowOp op, int64_t n, int s, const T* __restrict__ P, T* __restrict__
   const int cnt = gcnt + (has_frob ? 2 : 0);
   double* part = smem;                    // cnt
   double* scratch = smem + ((cnt + 1) & ~1); // kWarps * max(gcnt, 2)
-  if (has_gram) cta_reduce_gram<SW>(acc, s, ep.sym != 0, scratch, part);
+  if (has_gram) {
+    if (use_pair) pg.cta_reduce(s, scratch, part);
+    else cta_reduce_gram<SW>(acc, s, ep.sym != 0, scratch, part);
+  }
   if (has_frob) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -212,7 +245,7 @@ int spmm_grid(const Launch& L, int64_t n, int s) {
   const int rpw = 32 / next_pow2_s(s);
   const int64_t rows_per_cta = (int64_t)rpw * kWarps;
   int64_t need = (n + rows_per_cta - 1) / rows_per_cta;
-  const int64_t cap = (int64_t)L.sms * 4;
+  const int64_t cap = (int64_t)L.sms * kCtasPerSm;
   if (need > cap) need = cap;
   if (need < 1) need = 1;
   return (int)need;

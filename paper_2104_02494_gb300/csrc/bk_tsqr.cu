@@ -38,7 +38,8 @@ TsqrPlan tsqr_plan(int64_t n, int s) {
   p.rows[0] = n;
   int l = 0;
   for (;;) {
-    p.nodes[l] = (p.rows[l] + p.tile - 1) / p.tile;
+    const int tl = (l == 0) ? p.tile : kTT;     // tree levels: one row per thread
+    p.nodes[l] = (p.rows[l] + tl - 1) / tl;
     if (p.nodes[l] <= 1 || l == 15) break;
     p.rows[l + 1] = p.nodes[l] * s;       // the stacked R factors of level l
     ++l;
@@ -99,27 +100,29 @@ __device__ __forceinline__ int warp_reduce_scatter(A (&v)[V]) {
 }
 
 // ---- 1. leaf factor -------------------------------------------------------------
-// Thread t owns tile rows t, t + 256, ... in registers (32 / next_pow2(s) rows
-// of next_pow2(s) values); the column loop is unrolled so every register index
-// is a compile-time constant.  Column j of the Householder QR:
-//   tail = sum_{g > j} M[g][j]^2 (CTA sum), beta = -sign(alpha) sqrt(alpha^2 + tail),
-//   tau = (beta - alpha) / beta, v_g = M[g][j] / (alpha - beta) for g > j, v_j = 1,
-//   v_g = 0 for g < j;
-//   p[c] = sum_g v_g M[g][c] for every c != j (one CTA vector sum):
-//     c > j gives w_c for the trailing update M[g][c] -= tau w_c v_g,
-//     c < j gives y_c = V[:, c]^T v_j for column j of the WY factor:
-//     T[0:j, j] = -tau T[0:j, 0:j] y,  T[j][j] = tau.
-template <typename T, int SW>
+// Thread t owns tile rows t, t + 256, ... in registers (RPT rows of
+// next_pow2(s) values); the column loop is unrolled so every register index is
+// a compile-time constant.  Column j of the Householder QR needs one CTA vector
+// sum: q[c] = sum_{g > j} M[g][j] M[g][c] for every c (q[j] is the squared
+// norm below the diagonal).  With alpha = M[j][j]:
+//   beta = -sign(alpha) sqrt(alpha^2 + q[j]),  tau = (beta - alpha) / beta,
+//   scale = 1 / (alpha - beta),  v_g = scale M[g][j] (g > j), v_j = 1;
+//   v^T M[:, c] = scale q[c] + M[j][c]:
+//     c > j: w_c = tau (scale q[c] + M[j][c]), trailing update M[g][c] -= w_c v_g;
+//     c < j: y_c = scale q[c] + M[j][c] = V[:, c]^T v_j, column j of the WY factor
+//            T[0:j, j] = -tau T[0:j, 0:j] y,  T[j][j] = tau.
+// The scalars are computed once, by warp 0, and published in shared memory.
+template <typename T, int SW, int RPT>
 __global__ void __launch_bounds__(kTT)
 leaf_factor(int64_t n, int s, const T* __restrict__ X, T* __restrict__ Y, double* __restrict__ R0,
             double* __restrict__ T0, const int* done, const int* flag) {
   if (tsqr_skip(done, flag)) return;
-  constexpr int RPT = 32 / SW;
   constexpr int tile = kTT * RPT;
   __shared__ double Tm[SW * SW];
-  __shared__ T red_t[2][kWarps + 1];
   __shared__ T red_w[2][kWarps][SW];
+  __shared__ T rowj[2][SW];
   __shared__ T wy[2][SW];
+  __shared__ T sc[2][4];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t r0 = (int64_t)blockIdx.x * tile;
   const int m = (int)((n - r0) < tile ? (n - r0) : tile);
@@ -135,30 +138,59 @@ leaf_factor(int64_t n, int s, const T* __restrict__ X, T* __restrict__ Y, double
   for (int j = 0; j < SW; ++j) {
     if (j >= s) break;
     const int par = j & 1;
-    T part = T(0);
+    T q[SW];
 #pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-      const int g = tid + k * kTT;
-      if (g > j) part = fma(row[k][j], row[k][j], part);
+    for (int c = 0; c < SW; ++c) {
+      q[c] = T(0);
+#pragma unroll
+      for (int k = 0; k < RPT; ++k) {
+        const int g = tid + k * kTT;
+        if (g > j) q[c] = fma(row[k][j], row[k][c], q[c]);
+      }
     }
+    if (tid == j) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if (lane == 0) red_t[par][warp] = part;
-    if (tid == j) red_t[par][kWarps] = row[0][j];
+      for (int c = 0; c < SW; ++c) rowj[par][c] = row[0][c];
+    }
+    const int comp = warp_reduce_scatter<SW, T>(q);
+    if ((lane & (32 / SW - 1)) == 0) red_w[par][warp][comp] = q[0];
     __syncthreads();
-    T tail = T(0);
+    if (warp == 0) {
+      T qc = T(0);
+      if (lane < SW) {
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) tail += red_t[par][w];
-    const T alpha = red_t[par][kWarps];
-    T beta, tj, scale;
-    if (tail == T(0)) { tj = T(0); beta = alpha; scale = T(0); }
-    else {
-      const T nrm = sqrt(alpha * alpha + tail);
-      beta = alpha >= T(0) ? -nrm : nrm;
-      tj = (beta - alpha) / beta;
-      scale = T(1) / (alpha - beta);
+        for (int w = 0; w < kWarps; ++w) qc += red_w[par][w][lane];
+      }
+      const T tail = __shfl_sync(0xffffffffu, qc, j);
+      const T alpha = rowj[par][j];
+      T beta, tj, scale;
+      if (tail == T(0)) { tj = T(0); beta = alpha; scale = T(0); }
+      else {
+        const T nrm = sqrt(alpha * alpha + tail);
+        beta = alpha >= T(0) ? -nrm : nrm;
+        tj = (beta - alpha) / beta;
+        scale = T(1) / (alpha - beta);
+      }
+      if (lane < SW) {
+        const T vc = fma(scale, qc, rowj[par][lane]);       // v^T M[:, lane]
+        wy[par][lane] = (lane > j) ? tj * vc : vc;
+      }
+      if (lane == 0) { sc[par][0] = beta; sc[par][1] = tj; sc[par][2] = scale; }
+      __syncwarp();
+      if (tj != T(0)) {
+        if (lane < j) {
+          double acc = 0.0;
+          for (int b = lane; b < j; ++b) acc = fma(Tm[lane * SW + b], (double)wy[par][b], acc);
+          Tm[lane * SW + j] = -(double)tj * acc;
+        } else if (lane == j) {
+          Tm[j * SW + j] = (double)tj;
+        }
+      }
     }
+    __syncthreads();
+    const T tj = sc[par][1];
     if (tj != T(0)) {
+      const T scale = sc[par][2];
       T v[RPT];
 #pragma unroll
       for (int k = 0; k < RPT; ++k) {
@@ -166,40 +198,14 @@ leaf_factor(int64_t n, int s, const T* __restrict__ X, T* __restrict__ Y, double
         if (g > j) { row[k][j] *= scale; v[k] = row[k][j]; }
         else v[k] = (g == j) ? T(1) : T(0);
       }
-      T p[SW];
-#pragma unroll
-      for (int c = 0; c < SW; ++c) {
-        p[c] = T(0);
-        if (c != j) {
-#pragma unroll
-          for (int k = 0; k < RPT; ++k) p[c] = fma(v[k], row[k][c], p[c]);
-        }
-      }
-      const int comp = warp_reduce_scatter<SW, T>(p);
-      if ((lane & (32 / SW - 1)) == 0) red_w[par][warp][comp] = p[0];
-      __syncthreads();
-      if (tid < SW) {
-        T acc = T(0);
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) acc += red_w[par][w][tid];
-        wy[par][tid] = acc;
-      }
-      __syncthreads();
 #pragma unroll
       for (int c = j + 1; c < SW; ++c) {
-        const T tw = -tj * wy[par][c];
+        const T w = wy[par][c];
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) row[k][c] = fma(tw, v[k], row[k][c]);
-      }
-      if (tid < j) {
-        double acc = 0.0;
-        for (int b = tid; b < j; ++b) acc = fma(Tm[tid * SW + b], (double)wy[par][b], acc);
-        Tm[tid * SW + j] = -(double)tj * acc;
-      } else if (tid == j) {
-        Tm[j * SW + j] = (double)tj;
+        for (int k = 0; k < RPT; ++k) row[k][c] = fma(-w, v[k], row[k][c]);
       }
     }
-    if (tid == j) row[0][j] = beta;
+    if (tid == j) row[0][j] = sc[par][0];
   }
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
@@ -243,7 +249,7 @@ __global__ void root_fix(int s, double* __restrict__ Rroot, double* __restrict__
 // diagonal, zero above).  One sub-warp per row, lane c computes Y[g][c]; the
 // Gram Y^T Y (upper, mirrored) is accumulated in the same pass when rho_out
 // is given and reduced over the tiles by the last CTA.
-template <typename T, int SW>
+template <typename T, int SW, int RPT>
 __global__ void __launch_bounds__(kTT)
 leaf_apply(int64_t n, int s, T* __restrict__ Y, const double* __restrict__ S0,
            const double* __restrict__ T0, double* rho_out, double* gpart, unsigned* counter,
@@ -251,7 +257,7 @@ leaf_apply(int64_t n, int s, T* __restrict__ Y, const double* __restrict__ S0,
   if (tsqr_skip(done, flag)) return;
   extern __shared__ double smem_d[];
   constexpr int RPW = 32 / SW;
-  constexpr int tile = kTT * (32 / SW);
+  constexpr int tile = kTT * RPT;
   double* Sg = smem_d;              // sigma~ (s x s, row stride 32)
   double* Tt = Sg + kMM;            // T
   double* Zm = Tt + kMM;            // V_1^T sigma~, then scratch
@@ -285,15 +291,17 @@ leaf_apply(int64_t n, int s, T* __restrict__ Y, const double* __restrict__ S0,
   __syncthreads();
   const int c = lane & (SW - 1), rs = lane / SW, warp = tid >> 5;
   const bool want_rho = rho_out != nullptr;
+  constexpr bool kPair = (sizeof(T) == 8) && (SW >= 2);
   double acc[SW];
 #pragma unroll
   for (int a = 0; a < SW; ++a) acc[a] = 0.0;
   T acc_t[SW];
 #pragma unroll
   for (int a = 0; a < SW; ++a) acc_t[a] = T(0);
+  SymGramPair<kPair ? SW : 2> pg;
+  pg.zero();
   int since = 0;
-  for (int base = warp * RPW; base < m; base += kWarps * RPW) {
-    const int g = base + rs;
+  auto do_row = [&](int g) -> T {
     const bool ok = (g < m) && (c < s);
     T v = T(0);
     if (ok) v = (g < s) ? (c == g ? T(1) : (c < g ? Y[(r0 + g) * s + c] : T(0))) : Y[(r0 + g) * s + c];
@@ -304,26 +312,34 @@ leaf_apply(int64_t n, int s, T* __restrict__ Y, const double* __restrict__ S0,
       if (a < s && c < s) y = fma(-va, Wt[a * s + c], y);
     }
     if (ok) Y[(r0 + g) * s + c] = y;
-    if (want_rho) {
-      const T yv = ok ? y : T(0);
-      if constexpr (sizeof(T) == 8) {
+    return ok ? y : T(0);
+  };
+  auto accum_row = [&](T yv) {
+    if constexpr (sizeof(T) == 8) {
 #pragma unroll
-        for (int a = 0; a < SW; ++a) {
-          const T ya = sw_bcast<SW>(yv, a);
-          if (a <= c) acc[a] = fma((double)ya, (double)yv, acc[a]);
-        }
-      } else {
-#pragma unroll
-        for (int a = 0; a < SW; ++a) {
-          const T ya = sw_bcast<SW>(yv, a);
-          if (a <= c) acc_t[a] = fma(ya, yv, acc_t[a]);
-        }
-        if (++since == 16) {
-#pragma unroll
-          for (int a = 0; a < SW; ++a) { acc[a] += (double)acc_t[a]; acc_t[a] = T(0); }
-          since = 0;
-        }
+      for (int a = 0; a < SW; ++a) {
+        const T ya = sw_bcast<SW>(yv, a);
+        if (a <= c) acc[a] = fma((double)ya, (double)yv, acc[a]);
       }
+    } else {
+#pragma unroll
+      for (int a = 0; a < SW; ++a) {
+        const T ya = sw_bcast<SW>(yv, a);
+        if (a <= c) acc_t[a] = fma(ya, yv, acc_t[a]);
+      }
+      if (++since == 16) {
+#pragma unroll
+        for (int a = 0; a < SW; ++a) { acc[a] += (double)acc_t[a]; acc_t[a] = T(0); }
+        since = 0;
+      }
+    }
+  };
+  for (int base = warp * RPW; base < m; base += 2 * kWarps * RPW) {
+    const T yA = do_row(base + rs);
+    const T yB = do_row(base + kWarps * RPW + rs);
+    if (want_rho) {
+      if constexpr (kPair) pg.add((double)yA, (double)yA, (double)yB, (double)yB);
+      else { accum_row(yA); accum_row(yB); }
     }
   }
   if (!want_rho) return;
@@ -334,7 +350,8 @@ leaf_apply(int64_t n, int s, T* __restrict__ Y, const double* __restrict__ S0,
   const int cnt = ut_count(s);
   double* part = red;
   double* scratch = red + cnt + 1;
-  cta_reduce_gram<SW>(acc, s, true, scratch, part);
+  if constexpr (kPair) pg.cta_reduce(s, scratch, part);
+  else cta_reduce_gram<SW>(acc, s, true, scratch, part);
   if (!grid_reduce_last(part, cnt, gpart, counter)) return;
   unpack_gram(part, s, true, rho_out);
 }
@@ -345,28 +362,34 @@ static cudaError_t set_smem(K kern, size_t bytes) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <typename T, int SW>
+template <typename T, int SW, int RPT>
 static cudaError_t launch_leaves(const Launch& L, int64_t rows, int s, int64_t tiles, const T* X, T* Y,
                                  double* Rst, double* Tf, double* rho_out, double* gpart,
                                  unsigned* counter, const int* done, const int* flag, bool factor) {
   if (factor) {
-    leaf_factor<T, SW><<<(unsigned)tiles, kTT, 0, L.stream>>>(rows, s, X, Y, Rst, Tf, done, flag);
+    leaf_factor<T, SW, RPT><<<(unsigned)tiles, kTT, 0, L.stream>>>(rows, s, X, Y, Rst, Tf, done, flag);
     return cudaGetLastError();
   }
   const size_t sm = sizeof(double) * (6 * kMM + ut_count(s) + 2 + kWarps * ut_count(s)) + 64;
-  auto k = leaf_apply<T, SW>;
+  auto k = leaf_apply<T, SW, RPT>;
   cudaError_t e = set_smem(k, sm);
   if (e != cudaSuccess) return e;
   k<<<(unsigned)tiles, kTT, sm, L.stream>>>(rows, s, Y, Rst, Tf, rho_out, gpart, counter, done, flag);
   return cudaGetLastError();
 }
 
+// Level 0 tiles hold 32 / next_pow2(s) rows per thread; the tree levels
+// (stacked R factors, few rows) use one row per thread so that more CTAs share
+// the work.
 template <typename T>
 static cudaError_t leaves(const Launch& L, int64_t rows, int s, int64_t tiles, const T* X, T* Y,
                           double* Rst, double* Tf, double* rho_out, double* gpart, unsigned* counter,
-                          const int* done, const int* flag, bool factor) {
-#define BK_LEAVES(SWV) \
-  return launch_leaves<T, SWV>(L, rows, s, tiles, X, Y, Rst, Tf, rho_out, gpart, counter, done, flag, factor)
+                          const int* done, const int* flag, bool factor, bool bottom) {
+#define BK_LEAVES(SWV)                                                                               \
+  return bottom ? launch_leaves<T, SWV, 32 / SWV>(L, rows, s, tiles, X, Y, Rst, Tf, rho_out, gpart,  \
+                                                  counter, done, flag, factor)                       \
+                : launch_leaves<T, SWV, 1>(L, rows, s, tiles, X, Y, Rst, Tf, rho_out, gpart, counter, \
+                                           done, flag, factor)
   switch (next_pow2_s(s)) {
     case 1: BK_LEAVES(1);
     case 2: BK_LEAVES(2);
@@ -395,21 +418,21 @@ cudaError_t tsqr(const Launch& L, const TsqrPlan& p, const T* X, T* Y, double* g
   if (rho_out && !counter) return cudaErrorInvalidValue;
   prof_begin(L, kPhTsqrLeaf);
   if ((e = leaves<T>(L, p.n, s, p.nodes[0], X, Y, q.R[0], q.Tf[0], nullptr, nullptr, nullptr, done,
-                     flag, true)) != cudaSuccess) return e;
+                     flag, true, true)) != cudaSuccess) return e;
   prof_end(L, kPhTsqrLeaf, 1);
   prof_begin(L, kPhTsqrTree);
   for (int l = 1; l <= p.levels; ++l)
     if ((e = leaves<double>(L, p.rows[l], s, p.nodes[l], q.R[l - 1], q.R[l - 1], q.R[l], q.Tf[l],
-                            nullptr, nullptr, nullptr, done, flag, true)) != cudaSuccess) return e;
+                            nullptr, nullptr, nullptr, done, flag, true, false)) != cudaSuccess) return e;
   root_fix<<<1, 256, 0, L.stream>>>(s, q.R[p.levels], gamma_out, done, flag);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int l = p.levels; l >= 1; --l)
     if ((e = leaves<double>(L, p.rows[l], s, p.nodes[l], nullptr, q.R[l - 1], q.R[l], q.Tf[l],
-                            nullptr, nullptr, nullptr, done, flag, false)) != cudaSuccess) return e;
+                            nullptr, nullptr, nullptr, done, flag, false, false)) != cudaSuccess) return e;
   prof_end(L, kPhTsqrTree, 2 * p.levels + 1);
   prof_begin(L, kPhTsqrApply);
   e = leaves<T>(L, p.n, s, p.nodes[0], nullptr, Y, q.R[0], q.Tf[0], rho_out, gpart, counter, done, flag,
-                false);
+                false, true);
   prof_end(L, kPhTsqrApply, 1);
   return e;
 }
