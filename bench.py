@@ -103,6 +103,22 @@ def dist_init(args):
     return dist.get_rank(), dist.get_world_size(), dist
 
 
+def aggregate(ms: float, units_per_rank: float, dist=None):
+    """Whole-job throughput of independent replicas: every rank's units over the slowest rank's time.
+
+    Returns (max_ms, value) with value = world * units_per_rank / (max_ms / 1000).  The only
+    cross-rank operation of the bench is this max (a host-side gloo all-reduce of one float).
+    """
+    world = 1
+    if dist is not None:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        world = dist.get_world_size()
+    return ms, world * units_per_rank / (ms / 1000.0)
+
+
 def iteration_flops(n, s, tp_levels=None):
     """Algorithmic FP64 flops of one BCG iteration (stencil, eta = inf); FMA = 2 flops.
 
@@ -259,12 +275,9 @@ def main():
     with Clocks(dev) as clk:
         ms = time_iters(h, op, Bd, s, Wm, K, torch)
     torch.cuda.synchronize()
+    ms, value = aggregate(ms, s * K, dist)
     if dist:
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    value = world * s * K / (ms / 1000.0)
 
     # per-phase device times (profiled solve, events around every phase)
     h.profile_reset()

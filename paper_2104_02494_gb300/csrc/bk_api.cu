@@ -203,7 +203,7 @@ cudaError_t bcg_iteration(const Launch& L, const OpDesc& A, int s, T* X, const B
   prof_end(L, kPhSmall1, 1);
   prof_begin(L, kPhUpdate);
   if ((e = bcg_update<T>(L, A.n, s, b.P, b.Q, X, b.R, c, b.gpart, 1)) != cudaSuccess) return e;
-  prof_end(L, kPhUpdate, 1);
+  prof_end(L, kPhUpdate, 2);
   if ((e = tsqr<T>(L, tp, b.R, b.R, c->gamma, c->rho_new, b.tsqr, b.gpart, &c->counters[kCntC],
                    &c->done, &c->reortho_now)) != cudaSuccess) return e;
   prof_begin(L, kPhSmall2);
@@ -216,7 +216,7 @@ cudaError_t bcg_iteration(const Launch& L, const OpDesc& A, int s, T* X, const B
 }
 
 // launches of one iteration (the TSQR tree has 2 * levels + 1 launches)
-int bcg_launches_per_iter(const TsqrPlan& tp) { return 5 + tsqr_launches(tp); }
+int bcg_launches_per_iter(const TsqrPlan& tp) { return 6 + tsqr_launches(tp); }
 
 template <typename T>
 int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const bkrylov_opts& o,
@@ -707,6 +707,7 @@ int bkrylov_op_csr(bkrylov_handle h, int64_t n, int64_t nnz, const int32_t* row_
 int bkrylov_op_stencil(bkrylov_handle h, int kind, int nx, int ny, int nz, const double* coeffs,
                        bkrylov_op* A) {
   if (!h || !A || nx <= 0 || ny <= 0 || nz <= 0 || !coeffs) return BK_ERR_ARG;
+  if ((int64_t)nx * ny * nz > (int64_t)UINT32_MAX) return BK_ERR_ARG;   // 32-bit grid indexing
   bkrylov_op op = new (std::nothrow) bkrylov_op_s();
   if (!op) return BK_ERR_ALLOC;
   op->h = h;

@@ -63,6 +63,28 @@ struct Ctrl {
   double nb[kMaxS];      // refinement: ||B_i||
 };
 
+// ---- division by a loop-invariant integer ---------------------------------------
+// Unsigned 32-bit division by an invariant divisor d >= 1 with one high
+// multiply (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, Fig. 4.1): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1,  q = (t + ((x - t) >> sh1)) >> sh2,
+// t = mulhi(m, x), sh1 = min(l, 1), sh2 = max(l - 1, 0); exact for all 32-bit x.
+struct FastDiv {
+  uint32_t d = 1, m = 1, sh1 = 0, sh2 = 0;
+  FastDiv() = default;
+  __host__ explicit FastDiv(uint32_t div) : d(div) {
+    uint32_t l = 0;
+    while ((1ull << l) < div) ++l;
+    m = (uint32_t)((((1ull << 32) * ((1ull << l) - div)) / div) + 1);
+    sh1 = l < 1 ? l : 1;
+    sh2 = l > 0 ? l - 1 : 0;
+  }
+  __device__ __forceinline__ uint32_t div(uint32_t x) const {
+    const uint32_t t = __umulhi(m, x);
+    return (t + ((x - t) >> sh1)) >> sh2;
+  }
+};
+
 // ---- small helpers --------------------------------------------------------------
 __host__ __device__ inline int next_pow2_s(int s) {
   int w = 1;
@@ -228,6 +250,43 @@ struct SymGramPair {
     __syncthreads();
   }
 };
+
+// FP32 Gram partials: every lane accumulates its column's products in float
+// registers over a window of rows and then adds them into its own FP64 slots
+// in shared memory, lacc[tid * lacc_stride(SW) + a] (no two lanes share a
+// slot).  This keeps the FP64 work at 1/window of the products and the
+// registers at SW floats per lane.
+__host__ __device__ constexpr int lacc_stride(int SW) { return SW == 1 ? 1 : SW + 1; }
+
+template <int SW>
+__device__ __forceinline__ void lacc_flush(double* lacc, float (&acc_t)[SW]) {
+  double* mine = lacc + threadIdx.x * lacc_stride(SW);
+#pragma unroll
+  for (int a = 0; a < SW; ++a) { mine[a] += (double)acc_t[a]; acc_t[a] = 0.f; }
+}
+
+// CTA sum of the lacc slots into part[] (packed upper triangle when sym, else
+// s x s row-major), in the fixed order warp 0..7, sub-warp 0..32/SW-1.
+template <int SW>
+__device__ void lacc_reduce(const double* lacc, int s, bool sym, double* part) {
+  const int cnt = sym ? ut_count(s) : s * s;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    int a, c;
+    if (sym) {
+      c = 0;
+      while ((c + 1) * (c + 2) / 2 <= i) ++c;
+      a = i - c * (c + 1) / 2;
+    } else {
+      a = i / s;
+      c = i - a * s;
+    }
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w)
+      for (int rs = 0; rs < 32 / SW; ++rs) t += lacc[(w * 32 + rs * SW + c) * lacc_stride(SW) + a];
+    part[i] = t;
+  }
+  __syncthreads();
+}
 
 // Unpack a reduced Gram (packed upper or full s x s) into a ctrl-layout matrix.
 __device__ inline void unpack_gram(const double* part, int s, bool sym, double* M) {

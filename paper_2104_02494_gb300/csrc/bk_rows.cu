@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(kThreads)
 bcg_update_kernel(int64_t n, int s, const T* __restrict__ P, const T* __restrict__ Q,
                   T* __restrict__ X, T* __restrict__ R, Ctrl* ctrl, double* gpart, int rho_mode) {
   if (ctrl->done) return;
+  if (ctrl->reortho_now) return;        // then the lean kernel updates, TSQR gives rho
   extern __shared__ double smem[];
   T* lx = reinterpret_cast<T*>(smem);
   T* lam = lx + kMM;
@@ -121,9 +122,50 @@ bcg_update_kernel(int64_t n, int s, const T* __restrict__ P, const T* __restrict
   unpack_gram(part, s, true, ctrl->rho_new);
 }
 
+// The same update without a Gram (iterations that re-orthonormalise, where the
+// normaliser produces rho, and BBiCGStab's S = R - Q lambda):  X <- X + P lx,
+// R <- R - Q lam.  Few registers, both rows' loads issued before the shuffles.
+template <typename T, int SW>
+__global__ void __launch_bounds__(kThreads, 4)
+bcg_update_lean_kernel(int64_t n, int s, const T* __restrict__ P, const T* __restrict__ Q,
+                       T* __restrict__ X, T* __restrict__ R, Ctrl* ctrl, int only_if_reortho) {
+  if (ctrl->done) return;
+  if (only_if_reortho && !ctrl->reortho_now) return;
+  __shared__ T lx[kMM];
+  __shared__ T lam[kMM];
+  stage_matrix(lx, ctrl->lx, s);
+  stage_matrix(lam, ctrl->lam, s);
+  __syncthreads();
+  constexpr int RPW = 32 / SW;
+  const int lane = threadIdx.x & 31, c = lane & (SW - 1), rs = lane / SW;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t nw = (int64_t)gridDim.x * kWarps;
+  for (int64_t base = gw * RPW; base < n; base += 2 * nw * RPW) {
+    const int64_t rA = base + rs, rB = base + nw * RPW + rs;
+    const bool okA = (rA < n) && (c < s), okB = (rB < n) && (c < s);
+    const T pA = okA ? P[rA * s + c] : T(0), pB = okB ? P[rB * s + c] : T(0);
+    const T qA = okA ? Q[rA * s + c] : T(0), qB = okB ? Q[rB * s + c] : T(0);
+    const T xA = okA ? X[rA * s + c] : T(0), xB = okB ? X[rB * s + c] : T(0);
+    const T zA = okA ? R[rA * s + c] : T(0), zB = okB ? R[rB * s + c] : T(0);
+    T dxA = T(0), dxB = T(0), rqA = T(0), rqB = T(0);
+#pragma unroll
+    for (int a = 0; a < SW; ++a) {
+      const T paA = sw_bcast<SW>(pA, a), paB = sw_bcast<SW>(pB, a);
+      const T qaA = sw_bcast<SW>(qA, a), qaB = sw_bcast<SW>(qB, a);
+      if (a < s && c < s) {
+        const T l1 = lx[a * s + c], l2 = lam[a * s + c];
+        dxA = fma(paA, l1, dxA); dxB = fma(paB, l1, dxB);
+        rqA = fma(qaA, l2, rqA); rqB = fma(qaB, l2, rqB);
+      }
+    }
+    if (okA) { X[rA * s + c] = xA + dxA; R[rA * s + c] = zA - rqA; }
+    if (okB) { X[rB * s + c] = xB + dxB; R[rB * s + c] = zB - rqB; }
+  }
+}
+
 // BCG direction update (Eq. "cg_update_p" with M = I):  P <- R + P * beta.
 template <typename T, int SW>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 bcg_pupdate_kernel(int64_t n, int s, const T* __restrict__ R, T* __restrict__ P, Ctrl* ctrl) {
   if (ctrl->done) return;
   __shared__ T beta[kMM];
@@ -182,10 +224,19 @@ static cudaError_t launch_update(const Launch& L, int64_t n, int s, const T* P, 
     default: return cudaErrorInvalidValue;             \
   }
 
+// rho_mode 1 (BCG): the lean kernel runs when the iteration re-orthonormalises,
+// the Gram-carrying kernel otherwise (the device flag picks; the other returns).
+// rho_mode 0 (BBiCGStab): the lean kernel always.
 template <typename T>
 cudaError_t bcg_update(const Launch& L, int64_t n, int s, const T* P, const T* Q, T* X, T* R,
                        Ctrl* ctrl, double* gpart, int rho_mode) {
-  BK_SW_DISPATCH(s, return (launch_update<T, SW>(L, n, s, P, Q, X, R, ctrl, gpart, rho_mode)));
+  const int grid = row_grid(L, n, s);
+  BK_SW_DISPATCH(s, {
+    bcg_update_lean_kernel<T, SW><<<grid, kThreads, 0, L.stream>>>(n, s, P, Q, X, R, ctrl, rho_mode);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || rho_mode == 0) return e;
+    return launch_update<T, SW>(L, n, s, P, Q, X, R, ctrl, gpart, rho_mode);
+  });
 }
 
 template <typename T>

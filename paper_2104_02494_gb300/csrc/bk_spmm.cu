@@ -30,15 +30,26 @@ struct CsrRow {
 
 // 7-point constant coefficients; terms summed in ascending column order
 // (-z, -y, -x, centre, +x, +y, +z), the order of a column-sorted CSR row.
+// Grid coordinates of row r (x fastest) with two divisions by invariants.
+__device__ __forceinline__ void grid_xyz(int64_t r, const FastDiv& dx, const FastDiv& dy, int& x, int& y,
+                                         int& z) {
+  const uint32_t u = (uint32_t)r;
+  const uint32_t q1 = dx.div(u);
+  x = (int)(u - q1 * dx.d);
+  const uint32_t q2 = dy.div(q1);
+  y = (int)(q1 - q2 * dy.d);
+  z = (int)q2;
+}
+
 template <typename T>
 struct Const7Row {
   int nx, ny, nz;
+  FastDiv dx, dy;
   T c0, cxm, cxp, cym, cyp, czm, czp;
   __device__ __forceinline__ T operator()(int64_t r, int c, int s, const T* __restrict__ P) const {
     const int64_t plane = (int64_t)nx * ny;
-    const int x = (int)(r % nx);
-    const int y = (int)((r / nx) % ny);
-    const int z = (int)(r / plane);
+    int x, y, z;
+    grid_xyz(r, dx, dy, x, y, z);
     const T* p = P + r * s + c;
     T q = T(0);
     if (z > 0) q = fma(czm, p[-plane * s], q);
@@ -57,15 +68,15 @@ struct Const7Row {
 template <typename T>
 struct Var7Row {
   int nx, ny, nz;
+  FastDiv dx, dy;
   const T* __restrict__ diag;
   const T* __restrict__ fx;
   const T* __restrict__ fy;
   const T* __restrict__ fz;
   __device__ __forceinline__ T operator()(int64_t r, int c, int s, const T* __restrict__ P) const {
     const int64_t plane = (int64_t)nx * ny;
-    const int x = (int)(r % nx);
-    const int y = (int)((r / nx) % ny);
-    const int z = (int)(r / plane);
+    int x, y, z;
+    grid_xyz(r, dx, dy, x, y, z);
     const T* p = P + r * s + c;
     T q = T(0);
     if (z > 0) q = fma(-fz[r - plane], p[-plane * s], q);
@@ -84,12 +95,15 @@ struct Var7Row {
 template <typename T>
 struct Edge5Row {
   int nx, ny;
+  FastDiv dx;
   const T* __restrict__ diag;
   const T* __restrict__ ax;
   const T* __restrict__ ay;
   __device__ __forceinline__ T operator()(int64_t r, int c, int s, const T* __restrict__ P) const {
-    const int x = (int)(r % nx);
-    const int y = (int)(r / nx);
+    const uint32_t u = (uint32_t)r;
+    const uint32_t q1 = dx.div(u);
+    const int x = (int)(u - q1 * dx.d);
+    const int y = (int)q1;
     const T* p = P + r * s + c;
     T q = T(0);
     if (y > 0) q = fma(-ay[(int64_t)y * nx + x], p[-(int64_t)nx * s], q);
@@ -146,6 +160,16 @@ spmm_kernel(RowOp op, int64_t n, int s, const T* __restrict__ P, T* __restrict__
   pg.zero();
   int since_flush = 0;
   double f_qf = 0.0, f_qq = 0.0;
+  // shared-memory layout of the epilogue: part | scratch | FP32 lane slots
+  const int gcnt = has_gram ? (ep.sym ? ut_count(s) : s * s) : 0;
+  const int cnt = gcnt + (has_frob ? 2 : 0);
+  double* part = smem;
+  double* scratch = smem + ((cnt + 1) & ~1);
+  double* lacc = scratch + kWarps * (gcnt > 2 ? gcnt : 2);
+  if constexpr (sizeof(T) == 4) {
+    if (has_gram)
+      for (int a = 0; a < lacc_stride(SW); ++a) lacc[threadIdx.x * lacc_stride(SW) + a] = 0.0;
+  }
 
   auto accum_row = [&](T l, T q) {
     if constexpr (sizeof(T) == 8) {
@@ -161,8 +185,7 @@ spmm_kernel(RowOp op, int64_t n, int s, const T* __restrict__ P, T* __restrict__
         if (!ep.sym || a <= c) acc_t[a] = fma(la, q, acc_t[a]);
       }
       if (++since_flush == kFlush) {
-#pragma unroll
-        for (int a = 0; a < SW; ++a) { acc[a] += (double)acc_t[a]; acc_t[a] = T(0); }
+        lacc_flush<SW>(lacc, acc_t);
         since_flush = 0;
       }
     }
@@ -208,18 +231,16 @@ spmm_kernel(RowOp op, int64_t n, int s, const T* __restrict__ P, T* __restrict__
     }
   }
   if (!has_gram && !has_frob) return;
-  if constexpr (sizeof(T) == 4) {
-#pragma unroll
-    for (int a = 0; a < SW; ++a) acc[a] += (double)acc_t[a];
-  }
   // ---- CTA reduction of the epilogue sums into part[0..cnt) ----
-  const int gcnt = has_gram ? (ep.sym ? ut_count(s) : s * s) : 0;
-  const int cnt = gcnt + (has_frob ? 2 : 0);
-  double* part = smem;                    // cnt
-  double* scratch = smem + ((cnt + 1) & ~1); // kWarps * max(gcnt, 2)
   if (has_gram) {
-    if (use_pair) pg.cta_reduce(s, scratch, part);
-    else cta_reduce_gram<SW>(acc, s, ep.sym != 0, scratch, part);
+    if constexpr (sizeof(T) == 4) {
+      lacc_flush<SW>(lacc, acc_t);
+      __syncthreads();
+      lacc_reduce<SW>(lacc, s, ep.sym != 0, part);
+    } else {
+      if (use_pair) pg.cta_reduce(s, scratch, part);
+      else cta_reduce_gram<SW>(acc, s, ep.sym != 0, scratch, part);
+    }
   }
   if (has_frob) {
 #pragma unroll
@@ -251,11 +272,12 @@ int spmm_grid(const Launch& L, int64_t n, int s) {
   return (int)need;
 }
 
-static size_t epi_smem(int s, bool gram, bool sym, bool frob) {
+static size_t epi_smem(int s, bool gram, bool sym, bool frob, bool f32) {
   const int gcnt = gram ? (sym ? ut_count(s) : s * s) : 0;
   const int cnt = gcnt + (frob ? 2 : 0);
   const int sc = gcnt > 2 ? gcnt : 2;
-  return sizeof(double) * (size_t)(((cnt + 1) & ~1) + kWarps * sc);
+  const size_t lanes = (f32 && gram) ? (size_t)kThreads * lacc_stride(next_pow2_s(s)) : 0;
+  return sizeof(double) * ((size_t)(((cnt + 1) & ~1) + kWarps * sc) + lanes);
 }
 
 template <typename T, int SW, class RowOp>
@@ -263,7 +285,7 @@ static cudaError_t launch_sw(const Launch& L, const RowOp& op, int64_t n, int s,
                              T* out, const T* sub, const Epi<T>& ep) {
   const bool g = ep.left != nullptr, f = ep.frob != nullptr;
   int grid = spmm_grid(L, n, s);
-  size_t sm = (g || f) ? epi_smem(s, g, ep.sym != 0, f) : 0;
+  size_t sm = (g || f) ? epi_smem(s, g, ep.sym != 0, f, sizeof(T) == 4) : 0;
   auto kern = spmm_kernel<T, SW, RowOp>;
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -302,21 +324,22 @@ cudaError_t spmm(const Launch& L, const OpDesc& A, int s, const T* in, T* out, c
       return launch_op<T>(L, op, n, s, in, out, sub, ep);
     }
     case kOpConst7: {
-      Const7Row<T> op{A.nx, A.ny, A.nz, (T)A.c7[0], (T)A.c7[1], (T)A.c7[2], (T)A.c7[3],
-                      (T)A.c7[4], (T)A.c7[5], (T)A.c7[6]};
+      Const7Row<T> op{A.nx, A.ny, A.nz, FastDiv((uint32_t)A.nx), FastDiv((uint32_t)A.ny), (T)A.c7[0],
+                      (T)A.c7[1], (T)A.c7[2], (T)A.c7[3], (T)A.c7[4], (T)A.c7[5], (T)A.c7[6]};
       return launch_op<T>(L, op, n, s, in, out, sub, ep);
     }
     case kOpVar7: {
       const T* base = pick<T>(A.coef, A.coef32);
       if (!base) return cudaErrorInvalidValue;
-      Var7Row<T> op{A.nx, A.ny, A.nz, base, base + n, base + 2 * n, base + 3 * n};
+      Var7Row<T> op{A.nx, A.ny, A.nz, FastDiv((uint32_t)A.nx), FastDiv((uint32_t)A.ny), base, base + n,
+                    base + 2 * n, base + 3 * n};
       return launch_op<T>(L, op, n, s, in, out, sub, ep);
     }
     case kOpEdge5: {
       const T* dg = pick<T>(A.coef, A.coef32);
       const T* e = pick<T>(A.edges, A.edges32);
       if (!dg || !e) return cudaErrorInvalidValue;
-      Edge5Row<T> op{A.nx, A.ny, dg, e, e + (int64_t)A.ny * (A.nx + 1)};
+      Edge5Row<T> op{A.nx, A.ny, FastDiv((uint32_t)A.nx), dg, e, e + (int64_t)A.ny * (A.nx + 1)};
       return launch_op<T>(L, op, n, s, in, out, sub, ep);
     }
     default: return cudaErrorInvalidValue;

@@ -244,34 +244,24 @@ __global__ void root_fix(int s, double* __restrict__ Rroot, double* __restrict__
 }
 
 // ---- 5. leaf apply ----------------------------------------------------------------
-// Y_tile = [sigma~; 0] - V W with W = T (V_1^T sigma~), V the tile's unit lower
-// trapezoidal reflector block (stored below the diagonal in Y, implicit unit
-// diagonal, zero above).  One sub-warp per row, lane c computes Y[g][c]; the
-// Gram Y^T Y (upper, mirrored) is accumulated in the same pass when rho_out
-// is given and reduced over the tiles by the last CTA.
-template <typename T, int SW, int RPT>
+// Y_tile = [sigma~; 0] - V W with W = T (V_1^T sigma~): V is the tile's unit
+// lower trapezoidal reflector block (stored below the diagonal in Y, implicit
+// unit diagonal, zero above), V_1 its top s x s block.
+//
+// (a) tile_w: one CTA per tile forms W (s x s, FP64) and stores it over T.
+template <typename T>
 __global__ void __launch_bounds__(kTT)
-leaf_apply(int64_t n, int s, T* __restrict__ Y, const double* __restrict__ S0,
-           const double* __restrict__ T0, double* rho_out, double* gpart, unsigned* counter,
-           const int* done, const int* flag) {
+tile_w(int64_t n, int s, int tile, const T* __restrict__ Y, const double* __restrict__ S0,
+       double* __restrict__ TW, const int* done, const int* flag) {
   if (tsqr_skip(done, flag)) return;
-  extern __shared__ double smem_d[];
-  constexpr int RPW = 32 / SW;
-  constexpr int tile = kTT * RPT;
-  double* Sg = smem_d;              // sigma~ (s x s, row stride 32)
-  double* Tt = Sg + kMM;            // T
-  double* Zm = Tt + kMM;            // V_1^T sigma~, then scratch
-  double* V1 = Zm + kMM;            // top s x s reflector block
-  T* Wt = reinterpret_cast<T*>(V1 + kMM);   // W (s x s, row stride s) in the working precision
-  double* red = V1 + kMM + kMM;     // reduction scratch (after W, which needs <= kMM doubles)
-  const int tid = threadIdx.x, lane = tid & 31;
+  __shared__ double Sg[kMM], Tt[kMM], Zm[kMM], V1[kMM];
+  const int tid = threadIdx.x;
   const int64_t r0 = (int64_t)blockIdx.x * tile;
   const int m = (int)((n - r0) < tile ? (n - r0) : tile);
   for (int i = tid; i < s * s; i += kTT) {
     const int a = i / s, c = i - a * s;
     Sg[a * kMaxS + c] = S0[(size_t)blockIdx.x * s * s + i];
-    Tt[a * kMaxS + c] = T0[(size_t)blockIdx.x * s * s + i];
-    // V_1[a][c]: 1 on the diagonal, stored reflector entries below, 0 above
+    Tt[a * kMaxS + c] = TW[(size_t)blockIdx.x * s * s + i];
     V1[a * kMaxS + c] = (c == a) ? 1.0 : ((c < a && a < m) ? (double)Y[(r0 + a) * s + c] : 0.0);
   }
   __syncthreads();
@@ -286,12 +276,30 @@ leaf_apply(int64_t n, int s, T* __restrict__ Y, const double* __restrict__ S0,
     const int a = i / s, c = i - a * s;
     double acc = 0.0;
     for (int b = a; b < s; ++b) acc = fma(Tt[a * kMaxS + b], Zm[b * kMaxS + c], acc);
-    Wt[a * s + c] = (T)acc;
+    TW[(size_t)blockIdx.x * s * s + i] = acc;
   }
-  __syncthreads();
-  const int c = lane & (SW - 1), rs = lane / SW, warp = tid >> 5;
+}
+
+// (b) apply_rows: every warp takes a contiguous chunk of rows (two row groups
+// per trip), so consecutive trips stay inside one tile and lane c keeps
+// column c of that tile's W in registers.  Lane c computes Y[r][c]; the Gram
+// Y^T Y (upper, mirrored) is accumulated in the same pass when rho_out is given.
+template <typename T, int SW>
+__global__ void __launch_bounds__(kThreads)
+apply_rows(int64_t n, int s, int tile_shift, T* __restrict__ Y, const double* __restrict__ S0,
+           const double* __restrict__ W, double* rho_out, double* gpart, unsigned* counter,
+           const int* done, const int* flag) {
+  if (tsqr_skip(done, flag)) return;
+  extern __shared__ double smem_d[];
+  constexpr int RPW = 32 / SW;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c = lane & (SW - 1), rs = lane / SW;
   const bool want_rho = rho_out != nullptr;
   constexpr bool kPair = (sizeof(T) == 8) && (SW >= 2);
+  const int cnt = ut_count(s);
+  double* part = smem_d;
+  double* scratch = smem_d + cnt + 1;
+  double* lacc = scratch + kWarps * (cnt > 2 ? cnt : 2);
   double acc[SW];
 #pragma unroll
   for (int a = 0; a < SW; ++a) acc[a] = 0.0;
@@ -301,17 +309,38 @@ leaf_apply(int64_t n, int s, T* __restrict__ Y, const double* __restrict__ S0,
   SymGramPair<kPair ? SW : 2> pg;
   pg.zero();
   int since = 0;
-  auto do_row = [&](int g) -> T {
-    const bool ok = (g < m) && (c < s);
-    T v = T(0);
-    if (ok) v = (g < s) ? (c == g ? T(1) : (c < g ? Y[(r0 + g) * s + c] : T(0))) : Y[(r0 + g) * s + c];
-    T y = (ok && g < s) ? (T)Sg[g * kMaxS + c] : T(0);
+  if constexpr (sizeof(T) == 4) {
+    if (want_rho)
+      for (int a = 0; a < lacc_stride(SW); ++a) lacc[tid * lacc_stride(SW) + a] = 0.0;
+  }
+  // contiguous chunk of this warp, a multiple of 2 * RPW rows
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  const int64_t gwarp = (int64_t)blockIdx.x * kWarps + warp;
+  int64_t chunk = (n + nwarps - 1) / nwarps;
+  chunk = (chunk + 2 * RPW - 1) / (2 * RPW) * (2 * RPW);
+  const int64_t lo = gwarp * chunk;
+  const int64_t hi = (lo + chunk < n) ? lo + chunk : n;
+  const int64_t tmask = ((int64_t)1 << tile_shift) - 1;
+  int64_t cur_tile = -1;
+  T wcol[SW];
+#pragma unroll
+  for (int a = 0; a < SW; ++a) wcol[a] = T(0);
+  // a trip (2 * RPW rows starting at a multiple of 2 * RPW) never straddles a
+  // tile (tiles are powers of two >= 256 rows), so the tile is warp-uniform
+  auto do_row = [&](int64_t r, int64_t tl) -> T {
+    const int g = (int)(r & tmask);
+    const bool ok = (r < hi) && (c < s);
+    T v = T(0), y = T(0);
+    if (ok) {
+      v = (g < s) ? (c == g ? T(1) : (c < g ? Y[r * s + c] : T(0))) : Y[r * s + c];
+      if (g < s) y = (T)S0[(size_t)tl * s * s + g * s + c];
+    }
 #pragma unroll
     for (int a = 0; a < SW; ++a) {
       const T va = sw_bcast<SW>(v, a);
-      if (a < s && c < s) y = fma(-va, Wt[a * s + c], y);
+      y = fma(-va, wcol[a], y);
     }
-    if (ok) Y[(r0 + g) * s + c] = y;
+    if (ok) Y[r * s + c] = y;
     return ok ? y : T(0);
   };
   auto accum_row = [&](T yv) {
@@ -328,15 +357,21 @@ leaf_apply(int64_t n, int s, T* __restrict__ Y, const double* __restrict__ S0,
         if (a <= c) acc_t[a] = fma(ya, yv, acc_t[a]);
       }
       if (++since == 16) {
-#pragma unroll
-        for (int a = 0; a < SW; ++a) { acc[a] += (double)acc_t[a]; acc_t[a] = T(0); }
+        lacc_flush<SW>(lacc, acc_t);
         since = 0;
       }
     }
   };
-  for (int base = warp * RPW; base < m; base += 2 * kWarps * RPW) {
-    const T yA = do_row(base + rs);
-    const T yB = do_row(base + kWarps * RPW + rs);
+  for (int64_t base = lo; base < hi; base += 2 * RPW) {
+    const int64_t tl = base >> tile_shift;
+    if (tl != cur_tile) {
+      cur_tile = tl;
+#pragma unroll
+      for (int a = 0; a < SW; ++a)
+        wcol[a] = (a < s && c < s) ? (T)W[(size_t)tl * s * s + a * s + c] : T(0);
+    }
+    const T yA = do_row(base + rs, tl);
+    const T yB = do_row(base + RPW + rs, tl);
     if (want_rho) {
       if constexpr (kPair) pg.add((double)yA, (double)yA, (double)yB, (double)yB);
       else { accum_row(yA); accum_row(yB); }
@@ -344,14 +379,14 @@ leaf_apply(int64_t n, int s, T* __restrict__ Y, const double* __restrict__ S0,
   }
   if (!want_rho) return;
   if constexpr (sizeof(T) == 4) {
-#pragma unroll
-    for (int a = 0; a < SW; ++a) acc[a] += (double)acc_t[a];
+    lacc_flush<SW>(lacc, acc_t);
+    __syncthreads();
+    lacc_reduce<SW>(lacc, s, true, part);
+  } else if constexpr (kPair) {
+    pg.cta_reduce(s, scratch, part);
+  } else {
+    cta_reduce_gram<SW>(acc, s, true, scratch, part);
   }
-  const int cnt = ut_count(s);
-  double* part = red;
-  double* scratch = red + cnt + 1;
-  if constexpr (kPair) pg.cta_reduce(s, scratch, part);
-  else cta_reduce_gram<SW>(acc, s, true, scratch, part);
   if (!grid_reduce_last(part, cnt, gpart, counter)) return;
   unpack_gram(part, s, true, rho_out);
 }
@@ -370,11 +405,23 @@ static cudaError_t launch_leaves(const Launch& L, int64_t rows, int s, int64_t t
     leaf_factor<T, SW, RPT><<<(unsigned)tiles, kTT, 0, L.stream>>>(rows, s, X, Y, Rst, Tf, done, flag);
     return cudaGetLastError();
   }
-  const size_t sm = sizeof(double) * (6 * kMM + ut_count(s) + 2 + kWarps * ut_count(s)) + 64;
-  auto k = leaf_apply<T, SW, RPT>;
-  cudaError_t e = set_smem(k, sm);
+  const int tile = kTT * RPT;
+  tile_w<T><<<(unsigned)tiles, kTT, 0, L.stream>>>(rows, s, tile, Y, Rst, Tf, done, flag);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k<<<(unsigned)tiles, kTT, sm, L.stream>>>(rows, s, Y, Rst, Tf, rho_out, gpart, counter, done, flag);
+  int shift = 0;
+  while ((1 << shift) < tile) ++shift;
+  const int cnt = ut_count(s);
+  const size_t lanes = (sizeof(T) == 4) ? (size_t)kThreads * lacc_stride(SW) : 0;
+  const size_t sm = sizeof(double) * (cnt + 1 + kWarps * (cnt > 2 ? cnt : 2) + lanes) + 64;
+  auto k = apply_rows<T, SW>;
+  if ((e = set_smem(k, sm)) != cudaSuccess) return e;
+  int64_t grid = (rows + 2 * kWarps - 1) / (2 * kWarps);
+  const int64_t cap = (int64_t)L.sms * kCtasPerSm;
+  if (grid > cap) grid = cap;
+  if (grid < 1) grid = 1;
+  k<<<(unsigned)grid, kThreads, sm, L.stream>>>(rows, s, shift, Y, Rst, Tf, rho_out, gpart, counter,
+                                                 done, flag);
   return cudaGetLastError();
 }
 
