@@ -257,6 +257,12 @@ struct SymGramPair {
 // slot).  This keeps the FP64 work at 1/window of the products and the
 // registers at SW floats per lane.
 __host__ __device__ constexpr int lacc_stride(int SW) { return SW == 1 ? 1 : SW + 1; }
+// rows per FP32 accumulation window: the float partial of one window carries a
+// relative error of at most kF32Window * 2^-24; beyond it the sums are FP64.
+constexpr int kF32Window = 64;
+// CTAs per SM the row kernels are compiled for: FP32 instantiations are capped
+// at 64 registers (4 CTAs of 256 threads) so that enough loads are in flight.
+template <typename T> constexpr int min_ctas() { return sizeof(T) == 4 ? 4 : 1; }
 
 template <int SW>
 __device__ __forceinline__ void lacc_flush(double* lacc, float (&acc_t)[SW]) {

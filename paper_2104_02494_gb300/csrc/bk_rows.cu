@@ -31,7 +31,7 @@ __device__ inline void stage_matrix(T* dst, const double* src, int s) {
 //   R      <- R - Q * lambda        (R-tilde)
 //   rho_new = R^T R  (upper, mirrored) when no re-orthonormalisation follows.
 template <typename T, int SW>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, min_ctas<T>())
 bcg_update_kernel(int64_t n, int s, const T* __restrict__ P, const T* __restrict__ Q,
                   T* __restrict__ X, T* __restrict__ R, Ctrl* ctrl, double* gpart, int rho_mode) {
   if (ctrl->done) return;
@@ -93,7 +93,7 @@ bcg_update_kernel(int64_t n, int s, const T* __restrict__ P, const T* __restrict
         const T ra = sw_bcast<SW>(rt, a);
         if (a <= c) acc_t[a] = fma(ra, rt, acc_t[a]);
       }
-      if (++since == 16) {
+      if (++since == kF32Window) {
 #pragma unroll
         for (int a = 0; a < SW; ++a) { acc[a] += (double)acc_t[a]; acc_t[a] = T(0); }
         since = 0;

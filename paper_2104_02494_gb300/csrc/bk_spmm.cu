@@ -129,10 +129,15 @@ struct IdRow {
 // and then added into double accumulators, so the double-precision work is
 // 1/kFlush of the product count while every Gram partial sum beyond one flush
 // window is carried in double.
-constexpr int kFlush = 16;
+constexpr int kFlush = kF32Window;
 
-template <typename T, int SW, class RowOp>
-__global__ void __launch_bounds__(kThreads)
+// Epilogue kinds (compile time, so that each instantiation carries only its
+// own accumulators): none; symmetric Gram left^T Q; full Gram left^T Q and/or
+// the Frobenius sums <Q, frob>_F, <Q, Q>_F.
+enum : int { kEpiNone = 0, kEpiSym = 1, kEpiFull = 2 };
+
+template <typename T, int SW, class RowOp, int kEpi>
+__global__ void __launch_bounds__(kThreads, min_ctas<T>())
 spmm_kernel(RowOp op, int64_t n, int s, const T* __restrict__ P, T* __restrict__ Q,
             const T* __restrict__ sub, Epi<T> ep) {
   if (ep.done && *ep.done) return;
@@ -144,49 +149,56 @@ spmm_kernel(RowOp op, int64_t n, int s, const T* __restrict__ P, T* __restrict__
   const int rs = lane / SW;
   const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const int64_t nw = (int64_t)gridDim.x * kWarps;
-  const bool has_gram = ep.left != nullptr;
-  const bool has_frob = ep.frob != nullptr;
+  const bool has_gram = (kEpi != kEpiNone) && ep.left != nullptr;
+  const bool has_frob = (kEpi == kEpiFull) && ep.frob != nullptr;
+  constexpr bool kSym = kEpi == kEpiSym;
   // FP64 symmetric Grams use the idle-lane-free pairing of two rows per
-  // sub-warp; FP32 and non-symmetric Grams accumulate per row.
-  constexpr bool kPair = (sizeof(T) == 8) && (SW >= 2);
-  const bool use_pair = kPair && has_gram && ep.sym;
-  double acc[SW];
+  // sub-warp; FP32 Grams accumulate in float and flush to shared memory.
+  constexpr bool kPair = kSym && (sizeof(T) == 8) && (SW >= 2);
+  constexpr bool kRegAcc = (kEpi != kEpiNone) && (sizeof(T) == 8) && !kPair;
+  constexpr int NACC = kRegAcc ? SW : 1;
+  constexpr int NACCT = (kEpi != kEpiNone && sizeof(T) == 4) ? SW : 1;
+  double acc[NACC];
 #pragma unroll
-  for (int a = 0; a < SW; ++a) acc[a] = 0.0;
-  T acc_t[SW];
+  for (int a = 0; a < NACC; ++a) acc[a] = 0.0;
+  T acc_t[NACCT];
 #pragma unroll
-  for (int a = 0; a < SW; ++a) acc_t[a] = T(0);
+  for (int a = 0; a < NACCT; ++a) acc_t[a] = T(0);
   SymGramPair<kPair ? SW : 2> pg;
-  pg.zero();
+  if constexpr (kPair) pg.zero();
   int since_flush = 0;
   double f_qf = 0.0, f_qq = 0.0;
   // shared-memory layout of the epilogue: part | scratch | FP32 lane slots
-  const int gcnt = has_gram ? (ep.sym ? ut_count(s) : s * s) : 0;
+  const int gcnt = has_gram ? (kSym ? ut_count(s) : s * s) : 0;
   const int cnt = gcnt + (has_frob ? 2 : 0);
   double* part = smem;
   double* scratch = smem + ((cnt + 1) & ~1);
   double* lacc = scratch + kWarps * (gcnt > 2 ? gcnt : 2);
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 4 && kEpi != kEpiNone) {
     if (has_gram)
       for (int a = 0; a < lacc_stride(SW); ++a) lacc[threadIdx.x * lacc_stride(SW) + a] = 0.0;
   }
 
   auto accum_row = [&](T l, T q) {
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (kEpi != kEpiNone) {
+      if constexpr (sizeof(T) == 8) {
+        if constexpr (kRegAcc) {
 #pragma unroll
-      for (int a = 0; a < SW; ++a) {
-        const T la = sw_bcast<SW>(l, a);
-        if (!ep.sym || a <= c) acc[a] = fma((double)la, (double)q, acc[a]);
-      }
-    } else {
+          for (int a = 0; a < SW; ++a) {
+            const T la = sw_bcast<SW>(l, a);
+            if (!kSym || a <= c) acc[a] = fma((double)la, (double)q, acc[a]);
+          }
+        }
+      } else {
 #pragma unroll
-      for (int a = 0; a < SW; ++a) {
-        const T la = sw_bcast<SW>(l, a);
-        if (!ep.sym || a <= c) acc_t[a] = fma(la, q, acc_t[a]);
-      }
-      if (++since_flush == kFlush) {
-        lacc_flush<SW>(lacc, acc_t);
-        since_flush = 0;
+        for (int a = 0; a < SW; ++a) {
+          const T la = sw_bcast<SW>(l, a);
+          if (!kSym || a <= c) acc_t[a] = fma(la, q, acc_t[a]);
+        }
+        if (++since_flush == kFlush) {
+          lacc_flush<SW>(lacc, acc_t);
+          since_flush = 0;
+        }
       }
     }
   };
@@ -206,60 +218,66 @@ spmm_kernel(RowOp op, int64_t n, int s, const T* __restrict__ P, T* __restrict__
       if (sub) qB = sub[rB * s + c] - qB;
       if (Q) Q[rB * s + c] = qB;
     }
+    if constexpr (kEpi != kEpiNone) {
+      if (has_gram) {
+        const T lA = okA ? ep.left[rA * s + c] : T(0);
+        const T lB = okB ? ep.left[rB * s + c] : T(0);
+        if constexpr (kPair) {
+          pg.add((double)lA, (double)qA, (double)lB, (double)qB);
+        } else {
+          accum_row(lA, qA);
+          accum_row(lB, qB);
+        }
+      }
+      if (has_frob) {
+        if (okA) {
+          const double f = (double)ep.frob[rA * s + c];
+          f_qf = fma((double)qA, f, f_qf);
+          f_qq = fma((double)qA, (double)qA, f_qq);
+        }
+        if (okB) {
+          const double f = (double)ep.frob[rB * s + c];
+          f_qf = fma((double)qB, f, f_qf);
+          f_qq = fma((double)qB, (double)qB, f_qq);
+        }
+      }
+    }
+  }
+  if constexpr (kEpi == kEpiNone) {
+    return;
+  } else {
+    if (!has_gram && !has_frob) return;
+    // ---- CTA reduction of the epilogue sums into part[0..cnt) ----
     if (has_gram) {
-      const T lA = okA ? ep.left[rA * s + c] : T(0);
-      const T lB = okB ? ep.left[rB * s + c] : T(0);
-      if constexpr (kPair) {
-        if (use_pair) pg.add((double)lA, (double)qA, (double)lB, (double)qB);
-        else { accum_row(lA, qA); accum_row(lB, qB); }
+      if constexpr (sizeof(T) == 4) {
+        lacc_flush<SW>(lacc, acc_t);
+        __syncthreads();
+        lacc_reduce<SW>(lacc, s, kSym, part);
+      } else if constexpr (kPair) {
+        pg.cta_reduce(s, scratch, part);
       } else {
-        accum_row(lA, qA);
-        accum_row(lB, qB);
+        cta_reduce_gram<SW>(acc, s, kSym, scratch, part);
       }
     }
     if (has_frob) {
-      if (okA) {
-        const double f = (double)ep.frob[rA * s + c];
-        f_qf = fma((double)qA, f, f_qf);
-        f_qq = fma((double)qA, (double)qA, f_qq);
-      }
-      if (okB) {
-        const double f = (double)ep.frob[rB * s + c];
-        f_qf = fma((double)qB, f, f_qf);
-        f_qq = fma((double)qB, (double)qB, f_qq);
-      }
-    }
-  }
-  if (!has_gram && !has_frob) return;
-  // ---- CTA reduction of the epilogue sums into part[0..cnt) ----
-  if (has_gram) {
-    if constexpr (sizeof(T) == 4) {
-      lacc_flush<SW>(lacc, acc_t);
-      __syncthreads();
-      lacc_reduce<SW>(lacc, s, ep.sym != 0, part);
-    } else {
-      if (use_pair) pg.cta_reduce(s, scratch, part);
-      else cta_reduce_gram<SW>(acc, s, ep.sym != 0, scratch, part);
-    }
-  }
-  if (has_frob) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      f_qf += __shfl_xor_sync(0xffffffffu, f_qf, off);
-      f_qq += __shfl_xor_sync(0xffffffffu, f_qq, off);
+      for (int off = 16; off > 0; off >>= 1) {
+        f_qf += __shfl_xor_sync(0xffffffffu, f_qf, off);
+        f_qq += __shfl_xor_sync(0xffffffffu, f_qq, off);
+      }
+      if (lane == 0) { scratch[2 * (threadIdx.x >> 5)] = f_qf; scratch[2 * (threadIdx.x >> 5) + 1] = f_qq; }
+      __syncthreads();
+      if (threadIdx.x < 2) {
+        double t = 0.0;
+        for (int w = 0; w < kWarps; ++w) t += scratch[2 * w + threadIdx.x];
+        part[gcnt + threadIdx.x] = t;
+      }
+      __syncthreads();
     }
-    if (lane == 0) { scratch[2 * (threadIdx.x >> 5)] = f_qf; scratch[2 * (threadIdx.x >> 5) + 1] = f_qq; }
-    __syncthreads();
-    if (threadIdx.x < 2) {
-      double t = 0.0;
-      for (int w = 0; w < kWarps; ++w) t += scratch[2 * w + threadIdx.x];
-      part[gcnt + threadIdx.x] = t;
-    }
-    __syncthreads();
+    if (!grid_reduce_last(part, cnt, ep.gpart, ep.counter)) return;
+    if (has_gram) unpack_gram(part, s, kSym, ep.gram_out);
+    if (has_frob && threadIdx.x < 2) ep.frob_out[threadIdx.x] = part[gcnt + threadIdx.x];
   }
-  if (!grid_reduce_last(part, cnt, ep.gpart, ep.counter)) return;
-  if (has_gram) unpack_gram(part, s, ep.sym != 0, ep.gram_out);
-  if (has_frob && threadIdx.x < 2) ep.frob_out[threadIdx.x] = part[gcnt + threadIdx.x];
 }
 
 int spmm_grid(const Launch& L, int64_t n, int s) {
@@ -286,13 +304,17 @@ static cudaError_t launch_sw(const Launch& L, const RowOp& op, int64_t n, int s,
   const bool g = ep.left != nullptr, f = ep.frob != nullptr;
   int grid = spmm_grid(L, n, s);
   size_t sm = (g || f) ? epi_smem(s, g, ep.sym != 0, f, sizeof(T) == 4) : 0;
-  auto kern = spmm_kernel<T, SW, RowOp>;
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-  }
-  kern<<<grid, kThreads, sm, L.stream>>>(op, n, s, in, out, sub, ep);
-  return cudaGetLastError();
+  auto launch = [&](auto kern) -> cudaError_t {
+    if (sm > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, kThreads, sm, L.stream>>>(op, n, s, in, out, sub, ep);
+    return cudaGetLastError();
+  };
+  if (!g && !f) return launch(spmm_kernel<T, SW, RowOp, kEpiNone>);
+  if (g && !f && ep.sym) return launch(spmm_kernel<T, SW, RowOp, kEpiSym>);
+  return launch(spmm_kernel<T, SW, RowOp, kEpiFull>);
 }
 
 template <typename T, class RowOp>

@@ -285,7 +285,7 @@ tile_w(int64_t n, int s, int tile, const T* __restrict__ Y, const double* __rest
 // column c of that tile's W in registers.  Lane c computes Y[r][c]; the Gram
 // Y^T Y (upper, mirrored) is accumulated in the same pass when rho_out is given.
 template <typename T, int SW>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, min_ctas<T>())
 apply_rows(int64_t n, int s, int tile_shift, T* __restrict__ Y, const double* __restrict__ S0,
            const double* __restrict__ W, double* rho_out, double* gpart, unsigned* counter,
            const int* done, const int* flag) {
@@ -356,7 +356,7 @@ apply_rows(int64_t n, int s, int tile_shift, T* __restrict__ Y, const double* __
         const T ya = sw_bcast<SW>(yv, a);
         if (a <= c) acc_t[a] = fma(ya, yv, acc_t[a]);
       }
-      if (++since == 16) {
+      if (++since == kF32Window) {
         lacc_flush<SW>(lacc, acc_t);
         since = 0;
       }
