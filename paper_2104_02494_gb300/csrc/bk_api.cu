@@ -223,7 +223,7 @@ int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const
                double eps, bkrylov_info* info) {
   const Launch L = launch_of(h);
   const int64_t n = A.n;
-  const TsqrPlan tp = tsqr_plan(n, s);
+  const TsqrPlan tp = tsqr_plan(n, s, (int)sizeof(T));
   const int maxit = o.maxit > 0 ? o.maxit : 0;
   BcgBufs<T> b;
   Bump probe(nullptr, 0);
@@ -836,7 +836,7 @@ int bkrylov_bdot(bkrylov_handle h, int64_t n, int s, const void* X, const void* 
 int bkrylov_tsqr(bkrylov_handle h, int64_t n, int s, const void* X, void* Y, double* sigma, int prec) {
   if (!h || !valid_s(s) || n < s || !X || !Y || !sigma) return BK_ERR_ARG;
   const Launch L = launch_of(h);
-  const TsqrPlan tp = tsqr_plan(n, s);
+  const TsqrPlan tp = tsqr_plan(n, s, prec == BK_FP32 ? 4 : 8);
   const size_t gpn = gpart_count(L, tp);
   int rc = ensure_ws(h, 1, tp.bytes + sizeof(double) * (gpn + kMM) + 2048);
   if (rc) return rc;

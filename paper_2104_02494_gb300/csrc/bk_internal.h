@@ -112,6 +112,10 @@ cudaError_t bcg_update(const Launch& L, int64_t n, int s, const T* P, const T* Q
 // BCG direction update P = R + P*beta.
 template <typename T>
 cudaError_t bcg_pupdate(const Launch& L, int64_t n, int s, const T* R, T* P, Ctrl* ctrl);
+// The same two updates for FP32 blocks in the quad layout (s % 4 == 0), bk_quad.cu.
+cudaError_t bcg_update4(const Launch& L, int64_t n, int s, const float* P, const float* Q, float* X,
+                        float* R, Ctrl* ctrl, double* gpart, int rho_mode);
+cudaError_t bcg_pupdate4(const Launch& L, int64_t n, int s, const float* R, float* P, Ctrl* ctrl);
 // Generic Y = alpha*X*M + beta*Y (M s x s row stride 32 on device), optional fused Gram.
 template <typename T>
 cudaError_t block_axpy(const Launch& L, int64_t n, int s, const T* X, const double* M,
@@ -133,7 +137,8 @@ struct TsqrPlan {
   size_t bytes = 0;            // scratch bytes
 };
 int tsqr_launches(const TsqrPlan& p);
-TsqrPlan tsqr_plan(int64_t n, int s);
+// elem_bytes: 8 for FP64 blocks, 4 for FP32 ones (larger leaf tiles)
+TsqrPlan tsqr_plan(int64_t n, int s, int elem_bytes = 8);
 // doubles of grid partials the fused Gram of the leaf apply needs (one record per tile)
 inline size_t tsqr_gpart_count(const TsqrPlan& p) {
   return (size_t)p.nodes[0] * (size_t)(p.s * (p.s + 1) / 2) + 64;

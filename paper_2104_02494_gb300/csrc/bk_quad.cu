@@ -1,0 +1,291 @@
+// FP32 row kernels in the quad layout (one float4 per lane, s a multiple of
+// 4): the operator product with its fused Gram (BOP + BDOT, Ch. 3.3), the
+// BCG block updates with the fused rho Gram (Alg. "2R-CG") and the direction
+// update P = R + P beta (Eq. "cg_update_p", M = I).  They compute the same
+// sums as the scalar-layout kernels, term for term in the same order for the
+// row outputs; only the Gram summation order differs.
+#include "bk_internal.h"
+#include "bk_quad.cuh"
+
+namespace bk {
+
+enum : int { kQEpiNone = 0, kQEpiSym = 1, kQEpiFull = 2 };
+
+// ------------------------------------------------------------------ BOP ----
+// Q = A P (or Q = sub - A P), optional fused Gram left^T Q (upper triangle or
+// full), reduced deterministically over the grid into ep.gram_out.
+template <int SW, class RowOp, int kEpi>
+__global__ void __launch_bounds__(kThreads, quad_min_ctas<SW>())
+spmm4_kernel(RowOp op, int64_t n, int s, const float* __restrict__ P, float* __restrict__ Q,
+             const float* __restrict__ sub, Epi<float> ep) {
+  if (ep.done && *ep.done) return;
+  if (ep.only_if && !*ep.only_if) return;
+  using S = QuadShape<SW>;
+  extern __shared__ double smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int qi = lane % S::LPR, rho = lane / S::LPR;
+  const bool qok = 4 * qi < s;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
+  const int64_t nw = (int64_t)gridDim.x * kWarps;
+  constexpr bool kGram = kEpi != kQEpiNone;
+  const int cnt = kGram ? (kEpi == kQEpiSym ? ut_count(s) : s * s) : 0;
+  double* part = smem;
+  float* stage = reinterpret_cast<float*>(smem + ((cnt + 1) & ~1));
+  float* l2 = stage + kWarps * 2 * S::STAGE;
+  float* stl = stage + warp * 2 * S::STAGE;
+  float* stq = stl + S::STAGE;
+  QuadGram<SW> g;
+  if constexpr (kGram) g.init(l2);
+  for (int64_t base = gw * S::RW; base < n; base += nw * S::RW) {
+    const int64_t r = base + rho;
+    const bool ok = (r < n) && qok;
+    float4 q = zero4(), l = zero4();
+    if (ok) {
+      q = op.quad(r, qi, s, P);
+      if (sub) q = sub4(ld4(sub + r * s + 4 * qi), q);
+      if (Q) st4(Q + r * s + 4 * qi, q);
+      if constexpr (kGram) l = ld4(ep.left + r * s + 4 * qi);
+    }
+    if constexpr (kGram) {
+      st4(stl + rho * SW + 4 * qi, l);
+      st4(stq + rho * SW + 4 * qi, q);
+      __syncwarp();
+      g.trip(stl, stq);
+      __syncwarp();
+    }
+  }
+  if constexpr (kGram) {
+    g.cta_reduce(s, kEpi == kQEpiSym, l2, part);
+    if (!grid_reduce_last(part, cnt, ep.gpart, ep.counter)) return;
+    unpack_gram(part, s, kEpi == kQEpiSym, ep.gram_out);
+  }
+}
+
+template <int SW>
+static size_t spmm4_smem(int s, int epi) {
+  if (epi == kQEpiNone) return 0;
+  const int cnt = epi == kQEpiSym ? ut_count(s) : s * s;
+  return sizeof(double) * (size_t)((cnt + 1) & ~1) + sizeof(float) * quad_gram_floats<SW>();
+}
+
+template <int SW, class RowOp, int kEpi>
+static cudaError_t spmm4_launch(const Launch& L, const RowOp& op, int64_t n, int s, const float* in,
+                                float* out, const float* sub, const Epi<float>& ep) {
+  auto k = spmm4_kernel<SW, RowOp, kEpi>;
+  const size_t sm = spmm4_smem<SW>(s, kEpi);
+  cudaError_t err = cudaSuccess;
+  const int occ = quad_occupancy(k, sm, &err);
+  if (!occ) return err;
+  k<<<quad_grid(L, occ, n, QuadShape<SW>::RW), kThreads, sm, L.stream>>>(op, n, s, in, out, sub, ep);
+  return cudaGetLastError();
+}
+
+template <int SW, class RowOp>
+static cudaError_t spmm4_sw(const Launch& L, const RowOp& op, int64_t n, int s, const float* in,
+                            float* out, const float* sub, const Epi<float>& ep) {
+  if (!ep.left) return spmm4_launch<SW, RowOp, kQEpiNone>(L, op, n, s, in, out, sub, ep);
+  if (ep.sym) return spmm4_launch<SW, RowOp, kQEpiSym>(L, op, n, s, in, out, sub, ep);
+  return spmm4_launch<SW, RowOp, kQEpiFull>(L, op, n, s, in, out, sub, ep);
+}
+
+template <class RowOp>
+cudaError_t spmm4(const Launch& L, const RowOp& op, int64_t n, int s, const float* in, float* out,
+                  const float* sub, const Epi<float>& ep) {
+  if (s % 4 != 0 || ep.frob) return cudaErrorInvalidValue;
+  switch (next_pow2_s(s)) {
+    case 4: return spmm4_sw<4>(L, op, n, s, in, out, sub, ep);
+    case 8: return spmm4_sw<8>(L, op, n, s, in, out, sub, ep);
+    case 16: return spmm4_sw<16>(L, op, n, s, in, out, sub, ep);
+    case 32: return spmm4_sw<32>(L, op, n, s, in, out, sub, ep);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t spmm4<CsrRow<float>>(const Launch&, const CsrRow<float>&, int64_t, int,
+                                          const float*, float*, const float*, const Epi<float>&);
+template cudaError_t spmm4<Const7Row<float>>(const Launch&, const Const7Row<float>&, int64_t, int,
+                                             const float*, float*, const float*, const Epi<float>&);
+template cudaError_t spmm4<Var7Row<float>>(const Launch&, const Var7Row<float>&, int64_t, int,
+                                           const float*, float*, const float*, const Epi<float>&);
+template cudaError_t spmm4<Edge5Row<float>>(const Launch&, const Edge5Row<float>&, int64_t, int,
+                                            const float*, float*, const float*, const Epi<float>&);
+template cudaError_t spmm4<IdRow<float>>(const Launch&, const IdRow<float>&, int64_t, int,
+                                         const float*, float*, const float*, const Epi<float>&);
+
+// -------------------------------------------------------- BCG updates ----
+// X <- X + P lx, R <- R - Q lam (lx = lambda sigma); with kRho also
+// rho_new = R^T R (upper, mirrored).  kRho runs in iterations that do not
+// re-orthonormalise; the lean form in those that do (or always, when
+// only_if_reortho == 0).
+template <int SW, bool kRho>
+__global__ void __launch_bounds__(kThreads, quad_min_ctas<SW>())
+update4_kernel(int64_t n, int s, const float* __restrict__ P, const float* __restrict__ Q,
+               float* __restrict__ X, float* __restrict__ R, Ctrl* ctrl, double* gpart,
+               int only_if_reortho) {
+  if (ctrl->done) return;
+  if constexpr (kRho) {
+    if (ctrl->reortho_now) return;
+  } else {
+    if (only_if_reortho && !ctrl->reortho_now) return;
+  }
+  using S = QuadShape<SW>;
+  extern __shared__ double smem[];
+  const int cnt = kRho ? ut_count(s) : 0;
+  double* part = smem;
+  float* lx = reinterpret_cast<float*>(smem + ((cnt + 1) & ~1));
+  float* lam = lx + SW * SW;
+  float* stage = lam + SW * SW;
+  float* l2 = stage + kWarps * 2 * S::STAGE;
+  stage_quad_matrix<SW>(lx, ctrl->lx, s);
+  stage_quad_matrix<SW>(lam, ctrl->lam, s);
+  QuadGram<SW> g;
+  if constexpr (kRho) g.init(l2);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int qi = lane % S::LPR, rho = lane / S::LPR;
+  const bool qok = 4 * qi < s;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
+  const int64_t nw = (int64_t)gridDim.x * kWarps;
+  float* stp = stage + warp * 2 * S::STAGE;
+  float* stq = stp + S::STAGE;
+  for (int64_t base = gw * S::RW; base < n; base += nw * S::RW) {
+    const int64_t r = base + rho;
+    const bool ok = (r < n) && qok;
+    float4 p4 = zero4(), q4 = zero4(), x4 = zero4(), z4 = zero4();
+    if (ok) {
+      p4 = ld4(P + r * s + 4 * qi);
+      q4 = ld4(Q + r * s + 4 * qi);
+      x4 = ld4(X + r * s + 4 * qi);
+      z4 = ld4(R + r * s + 4 * qi);
+    }
+    st4(stp + rho * SW + 4 * qi, p4);
+    st4(stq + rho * SW + 4 * qi, q4);
+    __syncwarp();
+    float4 dx = zero4(), rq = zero4();
+#pragma unroll 4
+    for (int k = 0; k < S::NQ; ++k) {
+      const float4 pk = ld4(stp + rho * SW + 4 * k);
+      const float4 qk = ld4(stq + rho * SW + 4 * k);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int a = 4 * k + t;
+        dx = fma4(comp4(pk, t), ld4(lx + a * SW + 4 * qi), dx);
+        rq = fma4(comp4(qk, t), ld4(lam + a * SW + 4 * qi), rq);
+      }
+    }
+    x4 = add4(x4, dx);
+    z4 = sub4(z4, rq);
+    if (ok) {
+      st4(X + r * s + 4 * qi, x4);
+      st4(R + r * s + 4 * qi, z4);
+    }
+    __syncwarp();
+    if constexpr (kRho) {
+      st4(stp + rho * SW + 4 * qi, ok ? z4 : zero4());
+      __syncwarp();
+      g.trip(stp, stp);
+      __syncwarp();
+    }
+  }
+  if constexpr (kRho) {
+    g.cta_reduce(s, true, l2, part);
+    if (!grid_reduce_last(part, cnt, gpart, &ctrl->counters[kCntB])) return;
+    unpack_gram(part, s, true, ctrl->rho_new);
+  }
+}
+
+// P <- R + P beta.  The warp stages its rows of P before any lane writes P.
+template <int SW>
+__global__ void __launch_bounds__(kThreads, quad_min_ctas<SW>())
+pupdate4_kernel(int64_t n, int s, const float* __restrict__ R, float* __restrict__ P, Ctrl* ctrl) {
+  if (ctrl->done) return;
+  using S = QuadShape<SW>;
+  __shared__ __align__(16) float beta[SW * SW];
+  __shared__ __align__(16) float stage[kWarps * S::STAGE];
+  stage_quad_matrix<SW>(beta, ctrl->beta, s);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int qi = lane % S::LPR, rho = lane / S::LPR;
+  const bool qok = 4 * qi < s;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
+  const int64_t nw = (int64_t)gridDim.x * kWarps;
+  float* stp = stage + warp * S::STAGE;
+  for (int64_t base = gw * S::RW; base < n; base += nw * S::RW) {
+    const int64_t r = base + rho;
+    const bool ok = (r < n) && qok;
+    float4 p4 = zero4(), z4 = zero4();
+    if (ok) {
+      p4 = ld4(P + r * s + 4 * qi);
+      z4 = ld4(R + r * s + 4 * qi);
+    }
+    st4(stp + rho * SW + 4 * qi, p4);
+    __syncwarp();
+    float4 acc = zero4();
+#pragma unroll 4
+    for (int k = 0; k < S::NQ; ++k) {
+      const float4 pk = ld4(stp + rho * SW + 4 * k);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) acc = fma4(comp4(pk, t), ld4(beta + (4 * k + t) * SW + 4 * qi), acc);
+    }
+    __syncwarp();
+    if (ok) st4(P + r * s + 4 * qi, add4(z4, acc));
+  }
+}
+
+template <int SW>
+static cudaError_t update4_sw(const Launch& L, int64_t n, int s, const float* P, const float* Q,
+                              float* X, float* R, Ctrl* ctrl, double* gpart, int rho_mode) {
+  using S = QuadShape<SW>;
+  cudaError_t err = cudaSuccess;
+  {
+    auto k = update4_kernel<SW, false>;
+    const size_t sm = sizeof(double) * 2 + sizeof(float) * (2 * SW * SW + (size_t)kWarps * 2 * S::STAGE);
+    const int occ = quad_occupancy(k, sm, &err);
+    if (!occ) return err;
+    k<<<quad_grid(L, occ, n, S::RW), kThreads, sm, L.stream>>>(n, s, P, Q, X, R, ctrl, gpart, rho_mode);
+    if ((err = cudaGetLastError()) != cudaSuccess || rho_mode == 0) return err;
+  }
+  auto k = update4_kernel<SW, true>;
+  const int cnt = ut_count(s);
+  const size_t sm = sizeof(double) * (size_t)((cnt + 1) & ~1) +
+                    sizeof(float) * (2 * SW * SW + quad_gram_floats<SW>());
+  const int occ = quad_occupancy(k, sm, &err);
+  if (!occ) return err;
+  k<<<quad_grid(L, occ, n, S::RW), kThreads, sm, L.stream>>>(n, s, P, Q, X, R, ctrl, gpart, rho_mode);
+  return cudaGetLastError();
+}
+
+cudaError_t bcg_update4(const Launch& L, int64_t n, int s, const float* P, const float* Q, float* X,
+                        float* R, Ctrl* ctrl, double* gpart, int rho_mode) {
+  if (s % 4 != 0) return cudaErrorInvalidValue;
+  switch (next_pow2_s(s)) {
+    case 4: return update4_sw<4>(L, n, s, P, Q, X, R, ctrl, gpart, rho_mode);
+    case 8: return update4_sw<8>(L, n, s, P, Q, X, R, ctrl, gpart, rho_mode);
+    case 16: return update4_sw<16>(L, n, s, P, Q, X, R, ctrl, gpart, rho_mode);
+    case 32: return update4_sw<32>(L, n, s, P, Q, X, R, ctrl, gpart, rho_mode);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int SW>
+static cudaError_t pupdate4_sw(const Launch& L, int64_t n, int s, const float* R, float* P, Ctrl* ctrl) {
+  auto k = pupdate4_kernel<SW>;
+  cudaError_t err = cudaSuccess;
+  const int occ = quad_occupancy(k, 0, &err);
+  if (!occ) return err;
+  k<<<quad_grid(L, occ, n, QuadShape<SW>::RW), kThreads, 0, L.stream>>>(n, s, R, P, ctrl);
+  return cudaGetLastError();
+}
+
+cudaError_t bcg_pupdate4(const Launch& L, int64_t n, int s, const float* R, float* P, Ctrl* ctrl) {
+  if (s % 4 != 0) return cudaErrorInvalidValue;
+  switch (next_pow2_s(s)) {
+    case 4: return pupdate4_sw<4>(L, n, s, R, P, ctrl);
+    case 8: return pupdate4_sw<8>(L, n, s, R, P, ctrl);
+    case 16: return pupdate4_sw<16>(L, n, s, R, P, ctrl);
+    case 32: return pupdate4_sw<32>(L, n, s, R, P, ctrl);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace bk

@@ -205,7 +205,7 @@ static cudaError_t launch_update(const Launch& L, int64_t n, int s, const T* P, 
   const int grid = row_grid(L, n, s);
   const size_t sm = 2 * kMM * sizeof(T) + sizeof(double) * (ut_count(s) + 2 + kWarps * ut_count(s));
   auto k = bcg_update_kernel<T, SW>;
-  if (sm > 48 * 1024) {
+  if (sm > 44 * 1024) {   // 48 KB default includes the static reduction buffers
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
@@ -230,6 +230,9 @@ static cudaError_t launch_update(const Launch& L, int64_t n, int s, const T* P, 
 template <typename T>
 cudaError_t bcg_update(const Launch& L, int64_t n, int s, const T* P, const T* Q, T* X, T* R,
                        Ctrl* ctrl, double* gpart, int rho_mode) {
+  if constexpr (sizeof(T) == 4) {
+    if (s % 4 == 0) return bcg_update4(L, n, s, P, Q, X, R, ctrl, gpart, rho_mode);
+  }
   const int grid = row_grid(L, n, s);
   BK_SW_DISPATCH(s, {
     bcg_update_lean_kernel<T, SW><<<grid, kThreads, 0, L.stream>>>(n, s, P, Q, X, R, ctrl, rho_mode);
@@ -241,6 +244,9 @@ cudaError_t bcg_update(const Launch& L, int64_t n, int s, const T* P, const T* Q
 
 template <typename T>
 cudaError_t bcg_pupdate(const Launch& L, int64_t n, int s, const T* R, T* P, Ctrl* ctrl) {
+  if constexpr (sizeof(T) == 4) {
+    if (s % 4 == 0) return bcg_pupdate4(L, n, s, R, P, ctrl);
+  }
   const int grid = row_grid(L, n, s);
   BK_SW_DISPATCH(s, bcg_pupdate_kernel<T, SW><<<grid, kThreads, 0, L.stream>>>(n, s, R, P, ctrl);
                  return cudaGetLastError());

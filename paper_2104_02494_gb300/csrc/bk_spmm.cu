@@ -11,118 +11,10 @@
 // 32-column FP64 block is 4 MB, far below the 129 MB L2).
 #include "bk_common.cuh"
 #include "bk_internal.h"
+#include "bk_ops.cuh"
+#include "bk_quad.cuh"
 
 namespace bk {
-
-// ---------------------------------------------------------------- operators ----
-template <typename T>
-struct CsrRow {
-  const int32_t* __restrict__ row_ptr;
-  const int32_t* __restrict__ col;
-  const T* __restrict__ val;
-  __device__ __forceinline__ T operator()(int64_t r, int c, int s, const T* __restrict__ P) const {
-    const int b = row_ptr[r], e = row_ptr[r + 1];
-    T q = T(0);
-    for (int j = b; j < e; ++j) q = fma(val[j], P[(int64_t)col[j] * s + c], q);
-    return q;
-  }
-};
-
-// 7-point constant coefficients; terms summed in ascending column order
-// (-z, -y, -x, centre, +x, +y, +z), the order of a column-sorted CSR row.
-// Grid coordinates of row r (x fastest) with two divisions by invariants.
-__device__ __forceinline__ void grid_xyz(int64_t r, const FastDiv& dx, const FastDiv& dy, int& x, int& y,
-                                         int& z) {
-  const uint32_t u = (uint32_t)r;
-  const uint32_t q1 = dx.div(u);
-  x = (int)(u - q1 * dx.d);
-  const uint32_t q2 = dy.div(q1);
-  y = (int)(q1 - q2 * dy.d);
-  z = (int)q2;
-}
-
-template <typename T>
-struct Const7Row {
-  int nx, ny, nz;
-  FastDiv dx, dy;
-  T c0, cxm, cxp, cym, cyp, czm, czp;
-  __device__ __forceinline__ T operator()(int64_t r, int c, int s, const T* __restrict__ P) const {
-    const int64_t plane = (int64_t)nx * ny;
-    int x, y, z;
-    grid_xyz(r, dx, dy, x, y, z);
-    const T* p = P + r * s + c;
-    T q = T(0);
-    if (z > 0) q = fma(czm, p[-plane * s], q);
-    if (y > 0) q = fma(cym, p[-(int64_t)nx * s], q);
-    if (x > 0) q = fma(cxm, p[-s], q);
-    q = fma(c0, p[0], q);
-    if (x < nx - 1) q = fma(cxp, p[s], q);
-    if (y < ny - 1) q = fma(cyp, p[(int64_t)nx * s], q);
-    if (z < nz - 1) q = fma(czp, p[plane * s], q);
-    return q;
-  }
-};
-
-// Variable-coefficient 7-point FV operator with precomputed coefficients:
-// diag[r], fx[r] (face to r+1), fy[r] (face to r+nx), fz[r] (face to r+nx*ny).
-template <typename T>
-struct Var7Row {
-  int nx, ny, nz;
-  FastDiv dx, dy;
-  const T* __restrict__ diag;
-  const T* __restrict__ fx;
-  const T* __restrict__ fy;
-  const T* __restrict__ fz;
-  __device__ __forceinline__ T operator()(int64_t r, int c, int s, const T* __restrict__ P) const {
-    const int64_t plane = (int64_t)nx * ny;
-    int x, y, z;
-    grid_xyz(r, dx, dy, x, y, z);
-    const T* p = P + r * s + c;
-    T q = T(0);
-    if (z > 0) q = fma(-fz[r - plane], p[-plane * s], q);
-    if (y > 0) q = fma(-fy[r - nx], p[-(int64_t)nx * s], q);
-    if (x > 0) q = fma(-fx[r - 1], p[-s], q);
-    q = fma(diag[r], p[0], q);
-    if (x < nx - 1) q = fma(-fx[r], p[s], q);
-    if (y < ny - 1) q = fma(-fy[r], p[(int64_t)nx * s], q);
-    if (z < nz - 1) q = fma(-fz[r], p[plane * s], q);
-    return q;
-  }
-};
-
-// 2D per-edge diffusion: ax[y][x] (ny x (nx+1)) joins (x-1,y),(x,y); ay[y][x]
-// ((ny+1) x nx) joins (x,y-1),(x,y); diag precomputed.
-template <typename T>
-struct Edge5Row {
-  int nx, ny;
-  FastDiv dx;
-  const T* __restrict__ diag;
-  const T* __restrict__ ax;
-  const T* __restrict__ ay;
-  __device__ __forceinline__ T operator()(int64_t r, int c, int s, const T* __restrict__ P) const {
-    const uint32_t u = (uint32_t)r;
-    const uint32_t q1 = dx.div(u);
-    const int x = (int)(u - q1 * dx.d);
-    const int y = (int)q1;
-    const T* p = P + r * s + c;
-    T q = T(0);
-    if (y > 0) q = fma(-ay[(int64_t)y * nx + x], p[-(int64_t)nx * s], q);
-    if (x > 0) q = fma(-ax[(int64_t)y * (nx + 1) + x], p[-s], q);
-    q = fma(diag[r], p[0], q);
-    if (x < nx - 1) q = fma(-ax[(int64_t)y * (nx + 1) + x + 1], p[s], q);
-    if (y < ny - 1) q = fma(-ay[(int64_t)(y + 1) * nx + x], p[(int64_t)nx * s], q);
-    return q;
-  }
-};
-
-// Identity "operator": the row kernel then just streams Y, which turns the
-// fused epilogue into a stand-alone block inner product X^T Y (BDOT).
-template <typename T>
-struct IdRow {
-  __device__ __forceinline__ T operator()(int64_t r, int c, int s, const T* __restrict__ P) const {
-    return P[r * s + c];
-  }
-};
 
 // ------------------------------------------------------------------- kernel ----
 // FP32 blocks: Gram products are accumulated in float over kFlush row groups
@@ -305,7 +197,7 @@ static cudaError_t launch_sw(const Launch& L, const RowOp& op, int64_t n, int s,
   int grid = spmm_grid(L, n, s);
   size_t sm = (g || f) ? epi_smem(s, g, ep.sym != 0, f, sizeof(T) == 4) : 0;
   auto launch = [&](auto kern) -> cudaError_t {
-    if (sm > 48 * 1024) {
+    if (sm > 44 * 1024) {   // 48 KB default includes the static reduction buffers
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return e;
     }
@@ -320,6 +212,10 @@ static cudaError_t launch_sw(const Launch& L, const RowOp& op, int64_t n, int s,
 template <typename T, class RowOp>
 static cudaError_t launch_op(const Launch& L, const RowOp& op, int64_t n, int s, const T* in,
                              T* out, const T* sub, const Epi<T>& ep) {
+  // FP32 blocks of width 4, 8, 12, ... use the vectorised quad layout
+  if constexpr (sizeof(T) == 4) {
+    if (s % 4 == 0 && !ep.frob) return spmm4<RowOp>(L, op, n, s, in, out, sub, ep);
+  }
   switch (next_pow2_s(s)) {
     case 1: return launch_sw<T, 1>(L, op, n, s, in, out, sub, ep);
     case 2: return launch_sw<T, 2>(L, op, n, s, in, out, sub, ep);

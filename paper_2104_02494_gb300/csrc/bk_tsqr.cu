@@ -22,18 +22,21 @@
 #include "bk_common.cuh"
 #include "bk_internal.h"
 #include "bk_hh.cuh"
+#include "bk_quad.cuh"
 
 namespace bk {
 
 constexpr int kTT = 256;                 // threads per TSQR CTA
 
-// Rows per leaf tile: 256 threads x (32 / next_pow2(s)) rows per thread, so the
-// tile (row stride s|1) stays below ~100 KB of shared memory (2 CTAs per SM).
-__host__ __device__ inline int leaf_tile_rows(int s) { return 8192 / next_pow2_s(s); }
+// Rows per leaf tile: 256 threads x RPT rows each, RPT = 64 / next_pow2(s)
+// for FP32 blocks and 32 / next_pow2(s) for FP64 ones, i.e. 64 registers of
+// row data per thread.  Larger FP32 tiles also shrink the FP64 tree.
+constexpr int leaf_rpt(int sw, int elem_bytes) { return (elem_bytes == 4 ? 64 : 32) / sw; }
+inline int leaf_tile_rows(int s, int elem_bytes) { return kTT * leaf_rpt(next_pow2_s(s), elem_bytes); }
 
-TsqrPlan tsqr_plan(int64_t n, int s) {
+TsqrPlan tsqr_plan(int64_t n, int s, int elem_bytes) {
   TsqrPlan p;
-  p.n = n; p.s = s; p.tile = leaf_tile_rows(s);
+  p.n = n; p.s = s; p.tile = leaf_tile_rows(s, elem_bytes);
   p.fanin = p.tile / s;
   p.rows[0] = n;
   int l = 0;
@@ -109,9 +112,13 @@ __device__ __forceinline__ int warp_reduce_scatter(A (&v)[V]) {
 //   scale = 1 / (alpha - beta),  v_g = scale M[g][j] (g > j), v_j = 1;
 //   v^T M[:, c] = scale q[c] + M[j][c]:
 //     c > j: w_c = tau (scale q[c] + M[j][c]), trailing update M[g][c] -= w_c v_g;
-//     c < j: y_c = scale q[c] + M[j][c] = V[:, c]^T v_j, column j of the WY factor
-//            T[0:j, j] = -tau T[0:j, 0:j] y,  T[j][j] = tau.
-// The scalars are computed once, by warp 0, and published in shared memory.
+//     c < j: y_c = scale q[c] + M[j][c] = V[:, c]^T v_j.
+// The compact WY form H_0 ... H_{s-1} = I - V T V^T has T upper triangular
+// with T^{-1} = diag(1 / tau) + strict_upper(V^T V), so the tile stores
+// F = strict_upper(V^T V) + diag(tau) (entry (c, j) = y_c, (j, j) = tau_j)
+// and never forms T: the apply solves with T^{-1} instead (tile_w).  This
+// keeps the column loop free of the serial T recursion.  The scalars are
+// computed once per column, by warp 0, and published in shared memory.
 template <typename T, int SW, int RPT>
 __global__ void __launch_bounds__(kTT)
 leaf_factor(int64_t n, int s, const T* __restrict__ X, T* __restrict__ Y, double* __restrict__ R0,
@@ -173,19 +180,11 @@ leaf_factor(int64_t n, int s, const T* __restrict__ X, T* __restrict__ Y, double
       }
       if (lane < SW) {
         const T vc = fma(scale, qc, rowj[par][lane]);       // v^T M[:, lane]
-        wy[par][lane] = (lane > j) ? tj * vc : vc;
+        wy[par][lane] = tj * vc;                            // read for lane > j only
+        if (lane < j) Tm[lane * SW + j] = (double)vc;       // V_lane^T v_j
+        else if (lane == j) Tm[j * SW + j] = (double)tj;    // tau_j
       }
       if (lane == 0) { sc[par][0] = beta; sc[par][1] = tj; sc[par][2] = scale; }
-      __syncwarp();
-      if (tj != T(0)) {
-        if (lane < j) {
-          double acc = 0.0;
-          for (int b = lane; b < j; ++b) acc = fma(Tm[lane * SW + b], (double)wy[par][b], acc);
-          Tm[lane * SW + j] = -(double)tj * acc;
-        } else if (lane == j) {
-          Tm[j * SW + j] = (double)tj;
-        }
-      }
     }
     __syncthreads();
     const T tj = sc[par][1];
@@ -248,7 +247,8 @@ __global__ void root_fix(int s, double* __restrict__ Rroot, double* __restrict__
 // lower trapezoidal reflector block (stored below the diagonal in Y, implicit
 // unit diagonal, zero above), V_1 its top s x s block.
 //
-// (a) tile_w: one CTA per tile forms W (s x s, FP64) and stores it over T.
+// (a) tile_w: one CTA per tile forms W (s x s, FP64) and stores it over the
+// tile's factor F.
 template <typename T>
 __global__ void __launch_bounds__(kTT)
 tile_w(int64_t n, int s, int tile, const T* __restrict__ Y, const double* __restrict__ S0,
@@ -272,12 +272,20 @@ tile_w(int64_t n, int s, int tile, const T* __restrict__ Y, const double* __rest
     Zm[a * kMaxS + c] = acc;
   }
   __syncthreads();
-  for (int i = tid; i < s * s; i += kTT) {          // W = T Z (T upper triangular)
-    const int a = i / s, c = i - a * s;
-    double acc = 0.0;
-    for (int b = a; b < s; ++b) acc = fma(Tt[a * kMaxS + b], Zm[b * kMaxS + c], acc);
-    TW[(size_t)blockIdx.x * s * s + i] = acc;
+  // W = T Z, i.e. T^{-1} W = Z with T^{-1} = diag(1 / tau) + strict_upper(V^T V):
+  // back substitution W[a] = tau_a (Z[a] - sum_{b > a} (V^T V)[a][b] W[b]),
+  // exact also for tau_a = 0 (then row a and column a of T vanish)
+  double* Wm = Sg;                                   // sigma~ is no longer needed
+  __syncthreads();
+  for (int c = tid; c < s; c += kTT) {
+    for (int a = s - 1; a >= 0; --a) {
+      double acc = Zm[a * kMaxS + c];
+      for (int b = a + 1; b < s; ++b) acc = fma(-Tt[a * kMaxS + b], Wm[b * kMaxS + c], acc);
+      Wm[a * kMaxS + c] = Tt[a * kMaxS + a] * acc;
+    }
   }
+  __syncthreads();
+  for (int i = tid; i < s * s; i += kTT) TW[(size_t)blockIdx.x * s * s + i] = Wm[(i / s) * kMaxS + (i % s)];
 }
 
 // (b) apply_rows: every warp takes a contiguous chunk of rows (two row groups
@@ -391,9 +399,112 @@ apply_rows(int64_t n, int s, int tile_shift, T* __restrict__ Y, const double* __
   unpack_gram(part, s, true, rho_out);
 }
 
+// (b') the same apply for FP32 blocks with s % 4 == 0 in the quad layout:
+// lane (row, quad i) forms Y[r][4i .. 4i + 3]; the warp stages its rows of V
+// and keeps the current tile's W (float, row stride SW) in shared memory; the
+// Gram Y^T Y accumulates in 4 x 4 register blocks.  Same terms, same order
+// as apply_rows for every output.
+template <int SW>
+__global__ void __launch_bounds__(kThreads, quad_min_ctas<SW>())
+apply4(int64_t n, int s, int tile_shift, float* __restrict__ Y, const double* __restrict__ S0,
+       const double* __restrict__ W, double* rho_out, double* gpart, unsigned* counter,
+       const int* done, const int* flag) {
+  if (tsqr_skip(done, flag)) return;
+  using S = QuadShape<SW>;
+  extern __shared__ double smem_d[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int qi = lane % S::LPR, rho = lane / S::LPR;
+  const bool qok = 4 * qi < s;
+  const bool want_rho = rho_out != nullptr;
+  const int cnt = ut_count(s);
+  double* part = smem_d;
+  float* wt = reinterpret_cast<float*>(smem_d + ((cnt + 1) & ~1));
+  float* stage = wt + kWarps * SW * SW;
+  float* l2 = stage + kWarps * 2 * S::STAGE;
+  float* ws = wt + warp * SW * SW;
+  float* stv = stage + warp * 2 * S::STAGE;
+  QuadGram<SW> g;
+  if (want_rho) g.init(l2);
+  // contiguous chunk of this warp, a multiple of RW rows; a trip never
+  // straddles a tile (tiles are powers of two >= 256 rows)
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  const int64_t gwarp = (int64_t)blockIdx.x * kWarps + warp;
+  int64_t chunk = (n + nwarps - 1) / nwarps;
+  chunk = (chunk + S::RW - 1) / S::RW * S::RW;
+  const int64_t lo = gwarp * chunk;
+  const int64_t hi = (lo + chunk < n) ? lo + chunk : n;
+  const int64_t tmask = ((int64_t)1 << tile_shift) - 1;
+  int64_t cur_tile = -1;
+  for (int64_t base = lo; base < hi; base += S::RW) {
+    const int64_t tl = base >> tile_shift;
+    if (tl != cur_tile) {
+      cur_tile = tl;
+      __syncwarp();
+      for (int i = lane; i < SW * SW; i += 32) {
+        const int a = i / SW, c = i % SW;
+        ws[i] = (a < s && c < s) ? (float)W[(size_t)tl * s * s + a * s + c] : 0.f;
+      }
+      __syncwarp();
+    }
+    const int64_t r = base + rho;
+    const int gr = (int)(r & tmask);
+    const bool ok = (r < hi) && qok;
+    float4 v = ok ? ld4(Y + r * s + 4 * qi) : zero4();
+    float4 y = zero4();
+    if (ok && gr < s) {
+      // top rows of the tile: V = unit lower triangle there; [sigma~; 0] term
+      const double* sg = S0 + (size_t)tl * s * s + (size_t)gr * s + 4 * qi;
+      float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int a = 4 * qi + t;
+        vv[t] = (a == gr) ? 1.f : (a < gr ? vv[t] : 0.f);
+      }
+      v = make_float4(vv[0], vv[1], vv[2], vv[3]);
+      y = make_float4((float)sg[0], (float)sg[1], (float)sg[2], (float)sg[3]);
+    }
+    st4(stv + rho * SW + 4 * qi, v);
+    __syncwarp();
+#pragma unroll 4
+    for (int k = 0; k < S::NQ; ++k) {
+      const float4 vk = ld4(stv + rho * SW + 4 * k);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) y = fma4(-comp4(vk, t), ld4(ws + (4 * k + t) * SW + 4 * qi), y);
+    }
+    if (ok) st4(Y + r * s + 4 * qi, y);
+    __syncwarp();
+    if (want_rho) {
+      st4(stv + rho * SW + 4 * qi, ok ? y : zero4());
+      __syncwarp();
+      g.trip(stv, stv);
+      __syncwarp();
+    }
+  }
+  if (!want_rho) return;
+  g.cta_reduce(s, true, l2, part);
+  if (!grid_reduce_last(part, cnt, gpart, counter)) return;
+  unpack_gram(part, s, true, rho_out);
+}
+
+template <int SW>
+static cudaError_t launch_apply4(const Launch& L, int64_t rows, int s, int shift, float* Y,
+                                 const double* Rst, const double* Tf, double* rho_out, double* gpart,
+                                 unsigned* counter, const int* done, const int* flag) {
+  auto k = apply4<SW>;
+  const int cnt = ut_count(s);
+  const size_t sm = sizeof(double) * (size_t)((cnt + 1) & ~1) +
+                    sizeof(float) * ((size_t)kWarps * SW * SW + quad_gram_floats<SW>());
+  cudaError_t err = cudaSuccess;
+  const int occ = quad_occupancy(k, sm, &err);
+  if (!occ) return err;
+  k<<<quad_grid(L, occ, rows, QuadShape<SW>::RW), kThreads, sm, L.stream>>>(
+      rows, s, shift, Y, Rst, Tf, rho_out, gpart, counter, done, flag);
+  return cudaGetLastError();
+}
+
 template <typename K>
 static cudaError_t set_smem(K kern, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  if (bytes <= 44 * 1024) return cudaSuccess;   // 48 KB default includes static buffers
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
@@ -411,6 +522,10 @@ static cudaError_t launch_leaves(const Launch& L, int64_t rows, int s, int64_t t
   if (e != cudaSuccess) return e;
   int shift = 0;
   while ((1 << shift) < tile) ++shift;
+  if constexpr (sizeof(T) == 4 && SW >= 4) {
+    if (s % 4 == 0)
+      return launch_apply4<SW>(L, rows, s, shift, Y, Rst, Tf, rho_out, gpart, counter, done, flag);
+  }
   const int cnt = ut_count(s);
   const size_t lanes = (sizeof(T) == 4) ? (size_t)kThreads * lacc_stride(SW) : 0;
   const size_t sm = sizeof(double) * (cnt + 1 + kWarps * (cnt > 2 ? cnt : 2) + lanes) + 64;
@@ -425,15 +540,15 @@ static cudaError_t launch_leaves(const Launch& L, int64_t rows, int s, int64_t t
   return cudaGetLastError();
 }
 
-// Level 0 tiles hold 32 / next_pow2(s) rows per thread; the tree levels
-// (stacked R factors, few rows) use one row per thread so that more CTAs share
-// the work.
+// Level 0 tiles hold leaf_rpt rows per thread; the tree levels (stacked R
+// factors, few rows) use one row per thread so that more CTAs share the work.
 template <typename T>
 static cudaError_t leaves(const Launch& L, int64_t rows, int s, int64_t tiles, const T* X, T* Y,
                           double* Rst, double* Tf, double* rho_out, double* gpart, unsigned* counter,
                           const int* done, const int* flag, bool factor, bool bottom) {
 #define BK_LEAVES(SWV)                                                                               \
-  return bottom ? launch_leaves<T, SWV, 32 / SWV>(L, rows, s, tiles, X, Y, Rst, Tf, rho_out, gpart,  \
+  return bottom ? launch_leaves<T, SWV, leaf_rpt(SWV, sizeof(T))>(L, rows, s, tiles, X, Y, Rst, Tf,   \
+                                                                 rho_out, gpart,                     \
                                                   counter, done, flag, factor)                       \
                 : launch_leaves<T, SWV, 1>(L, rows, s, tiles, X, Y, Rst, Tf, rho_out, gpart, counter, \
                                            done, flag, factor)

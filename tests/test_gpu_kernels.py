@@ -127,13 +127,32 @@ def test_bdot_integer_bit_exact_and_deterministic(h):
     assert np.array_equal(a, b)
 
 
-def test_bdot_fp32(h):
-    g = np.random.default_rng(4)
-    X = g.standard_normal((40000, 8)).astype(np.float32); Y = g.standard_normal((40000, 8)).astype(np.float32)
-    G = h.bdot(_dev(X), _dev(Y)).cpu().numpy()
+@pytest.mark.parametrize("n", [1, 37, 40000, 300007])
+@pytest.mark.parametrize("s", [3, 4, 8, 12, 16, 32])
+def test_bdot_fp32(h, n, s):
+    # s % 4 == 0 runs the vectorised (float4) layout, other widths the scalar one
+    g = np.random.default_rng(4 + n + s)
+    X = g.standard_normal((n, s)).astype(np.float32); Y = g.standard_normal((n, s)).astype(np.float32)
     ref = X.astype(np.float64).T @ Y.astype(np.float64)
     bound = np.abs(X.astype(np.float64)).T @ np.abs(Y.astype(np.float64))
-    assert np.all(np.abs(G - ref) <= 2e-6 * bound)
+    for sym in (False, True):
+        G = h.bdot(_dev(X), _dev(Y), sym=sym).cpu().numpy()
+        if sym:
+            iu = np.triu_indices(s)
+            assert np.all(np.abs(G[iu] - ref[iu]) <= 2e-6 * bound[iu]), (n, s)
+            assert np.array_equal(G, G.T)
+        else:
+            assert np.all(np.abs(G - ref) <= 2e-6 * bound), (n, s)
+
+
+def test_bdot_fp32_integer_bit_exact(h):
+    # small integers: every float product and partial sum is exact
+    g = np.random.default_rng(8)
+    for s in (4, 16, 32, 5):
+        X = g.integers(-8, 8, (70001, s)).astype(np.float32)
+        Y = g.integers(-8, 8, (70001, s)).astype(np.float32)
+        G = h.bdot(_dev(X), _dev(Y)).cpu().numpy()
+        assert np.array_equal(G, X.astype(np.float64).T @ Y.astype(np.float64)), s
 
 
 @pytest.mark.parametrize("n,s", [(8, 8), (100, 3), (515, 8), (5157, 4), (5157, 32), (70001, 32),
@@ -163,13 +182,18 @@ def test_tsqr_in_place_and_rank_deficient(h):
     assert abs(sig[5, 5]) <= 1e-13 and abs(sig[3, 3]) <= 1e-12
 
 
-def test_tsqr_fp32(h):
-    X = np.random.default_rng(5).standard_normal((20000, 8)).astype(np.float32)
+@pytest.mark.parametrize("n,s", [(20000, 8), (100, 3), (1000, 1), (5157, 4), (40000, 12),
+                                 (300007, 16), (70001, 32)])
+def test_tsqr_fp32(h, n, s):
+    # FP32 leaves (quad-layout apply for s % 4 == 0), FP64 tree
+    X = np.random.default_rng(5 + n + s).standard_normal((n, s)).astype(np.float32)
     Y, sig = h.tsqr(_dev(X))
     Y = Y.cpu().numpy().astype(np.float64); sig = sig.cpu().numpy()
     _, Rr = oracle.householder_qr(X.astype(np.float64))
-    assert np.abs(sig - Rr).max() <= 1e-4 * np.abs(Rr).max()
-    assert np.abs(Y.T @ Y - np.eye(8)).max() <= 1e-4
+    assert np.allclose(np.tril(sig, -1), 0.0, atol=0) and np.all(np.diag(sig) >= 0)
+    assert np.abs(sig - Rr).max() <= 1e-4 * np.abs(Rr).max(), (n, s)
+    assert np.abs(Y.T @ Y - np.eye(s)).max() <= 1e-4, (n, s)
+    assert np.abs(Y @ sig - X).max() <= 1e-4 * np.abs(X).max(), (n, s)
 
 
 def test_adjoint_scatter_and_edge_grad(h):

@@ -212,6 +212,22 @@ def test_bgmres_convdiff(h, ortho):
     op.close()
 
 
+@pytest.mark.parametrize("s", [4, 6, 8, 12, 16, 32])
+@pytest.mark.parametrize("eta", [math.inf, 0.0])
+def test_fp32_inner_bcg_iterates(h, s, eta):
+    """The FP32 inner solve of refinement, iterate by iterate, against the
+    oracle's float32 BCG (s % 4 == 0: vectorised layout; s = 6: scalar)."""
+    prob = W.problem("vardiff3d", s=s, grid=12)
+    op = _op(h, prob, "stencil")
+    for k in (1, 2, 4):
+        X, info = h.solve("bcg", op, _dev(prob.B), tol=0.0, maxit=k, eta=eta, prec="fp32_ir",
+                          ir_max_outer=1)
+        ref = oracle.bcg_ir(prob.A, prob.B, tol=0.0, max_outer=1, inner_maxit=k, eta=eta)
+        assert info.iters == k and ref.inner_iters == [k]
+        assert _rel(X.cpu().numpy(), ref.X) <= 2e-4, (s, eta, k, _rel(X.cpu().numpy(), ref.X))
+    op.close()
+
+
 def test_bcg_ir_reaches_1e10(h):
     prob = W.problem("vardiff3d", s=4, grid=14)
     op = _op(h, prob, "stencil")
