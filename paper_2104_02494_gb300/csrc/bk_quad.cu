@@ -15,12 +15,13 @@ enum : int { kQEpiNone = 0, kQEpiSym = 1, kQEpiFull = 2 };
 // Q = A P (or Q = sub - A P), optional fused Gram left^T Q (upper triangle or
 // full), reduced deterministically over the grid into ep.gram_out.
 template <int SW, class RowOp, int kEpi>
-__global__ void __launch_bounds__(kThreads, quad_min_ctas<SW>())
+__global__ void __launch_bounds__(kThreads, (kEpi != kQEpiNone && SW <= 8) ? 2 : quad_min_ctas<SW>())
 spmm4_kernel(RowOp op, int64_t n, int s, const float* __restrict__ P, float* __restrict__ Q,
              const float* __restrict__ sub, Epi<float> ep) {
   if (ep.done && *ep.done) return;
   if (ep.only_if && !*ep.only_if) return;
   using S = QuadShape<SW>;
+  using Gram = GramOf<SW>;
   extern __shared__ double smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int qi = lane % S::LPR, rho = lane / S::LPR;
@@ -34,7 +35,7 @@ spmm4_kernel(RowOp op, int64_t n, int s, const float* __restrict__ P, float* __r
   float* l2 = stage + kWarps * 2 * S::STAGE;
   float* stl = stage + warp * 2 * S::STAGE;
   float* stq = stl + S::STAGE;
-  QuadGram<SW> g;
+  Gram g;
   if constexpr (kGram) g.init(l2);
   for (int64_t base = gw * S::RW; base < n; base += nw * S::RW) {
     const int64_t r = base + rho;
@@ -46,13 +47,7 @@ spmm4_kernel(RowOp op, int64_t n, int s, const float* __restrict__ P, float* __r
       if (Q) st4(Q + r * s + 4 * qi, q);
       if constexpr (kGram) l = ld4(ep.left + r * s + 4 * qi);
     }
-    if constexpr (kGram) {
-      st4(stl + rho * SW + 4 * qi, l);
-      st4(stq + rho * SW + 4 * qi, q);
-      __syncwarp();
-      g.trip(stl, stq);
-      __syncwarp();
-    }
+    if constexpr (kGram) g.row(l, q, stl, stq);
   }
   if constexpr (kGram) {
     g.cta_reduce(s, kEpi == kQEpiSym, l2, part);
@@ -61,11 +56,17 @@ spmm4_kernel(RowOp op, int64_t n, int s, const float* __restrict__ P, float* __r
   }
 }
 
+// Shared memory of a quad kernel with a Gram: part (doubles) | staging | slots.
+template <int SW>
+constexpr size_t quad_gram_smem_floats() {
+  return (size_t)kWarps * 2 * QuadShape<SW>::STAGE + GramOf<SW>::smem_floats();
+}
+
 template <int SW>
 static size_t spmm4_smem(int s, int epi) {
   if (epi == kQEpiNone) return 0;
   const int cnt = epi == kQEpiSym ? ut_count(s) : s * s;
-  return sizeof(double) * (size_t)((cnt + 1) & ~1) + sizeof(float) * quad_gram_floats<SW>();
+  return sizeof(double) * (size_t)((cnt + 1) & ~1) + sizeof(float) * quad_gram_smem_floats<SW>();
 }
 
 template <int SW, class RowOp, int kEpi>
@@ -194,6 +195,104 @@ update4_kernel(int64_t n, int s, const float* __restrict__ P, const float* __res
   }
 }
 
+// The same updates for SW <= 16 with the s x s coefficients in registers
+// (each lane holds its four columns of lx, then of lam: 4 SW floats) and the
+// rows exchanged by shuffles, in two phases: X <- X + P lx over all rows,
+// then R <- R - Q lam (and the rho Gram, staged 4 x 4 blocks).  Two row
+// groups per trip keep more loads in flight.
+template <int SW, bool kRho>
+__global__ void __launch_bounds__(kThreads, 2)
+update4r_kernel(int64_t n, int s, const float* __restrict__ P, const float* __restrict__ Q,
+                float* __restrict__ X, float* __restrict__ R, Ctrl* ctrl, double* gpart,
+                int only_if_reortho) {
+  if (ctrl->done) return;
+  if constexpr (kRho) {
+    if (ctrl->reortho_now) return;
+  } else {
+    if (only_if_reortho && !ctrl->reortho_now) return;
+  }
+  using S = QuadShape<SW>;
+  extern __shared__ double smem[];
+  const int cnt = kRho ? ut_count(s) : 0;
+  double* part = smem;
+  float* stage = reinterpret_cast<float*>(smem + ((cnt + 1) & ~1));
+  float* l2 = stage + kWarps * 2 * S::STAGE;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int qi = lane % S::LPR, rho = lane / S::LPR;
+  const bool qok = 4 * qi < s;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
+  const int64_t nw = (int64_t)gridDim.x * kWarps;
+  float* stl = stage + warp * 2 * S::STAGE;
+  StagedGram<SW> g;
+  if constexpr (kRho) g.init(l2);
+  float4 cf[SW];
+  load_coef<SW>(cf, ctrl->lx, s, kMaxS, qi);
+  for (int64_t base = gw * S::RW; base < n; base += 2 * nw * S::RW) {
+    const int64_t rA = base + rho, rB = base + nw * S::RW + rho;
+    const bool okA = (rA < n) && qok, okB = (rB < n) && qok;
+    const float4 pA = okA ? ld4(P + rA * s + 4 * qi) : zero4();
+    const float4 pB = okB ? ld4(P + rB * s + 4 * qi) : zero4();
+    const float4 xA = okA ? ld4(X + rA * s + 4 * qi) : zero4();
+    const float4 xB = okB ? ld4(X + rB * s + 4 * qi) : zero4();
+    const float4 dA = row_times<SW>(pA, cf, zero4());
+    const float4 dB = row_times<SW>(pB, cf, zero4());
+    if (okA) st4(X + rA * s + 4 * qi, add4(xA, dA));
+    if (okB) st4(X + rB * s + 4 * qi, add4(xB, dB));
+  }
+  load_coef<SW>(cf, ctrl->lam, s, kMaxS, qi);
+  for (int64_t base = gw * S::RW; base < n; base += 2 * nw * S::RW) {
+    const int64_t rA = base + rho, rB = base + nw * S::RW + rho;
+    const bool okA = (rA < n) && qok, okB = (rB < n) && qok;
+    const float4 qA = okA ? ld4(Q + rA * s + 4 * qi) : zero4();
+    const float4 qB = okB ? ld4(Q + rB * s + 4 * qi) : zero4();
+    const float4 zA = okA ? ld4(R + rA * s + 4 * qi) : zero4();
+    const float4 zB = okB ? ld4(R + rB * s + 4 * qi) : zero4();
+    const float4 tA = sub4(zA, row_times<SW>(qA, cf, zero4()));
+    const float4 tB = sub4(zB, row_times<SW>(qB, cf, zero4()));
+    if (okA) st4(R + rA * s + 4 * qi, tA);
+    if (okB) st4(R + rB * s + 4 * qi, tB);
+    if constexpr (kRho) {
+      const float4 gA = okA ? tA : zero4(), gB = okB ? tB : zero4();
+      g.row(gA, gA, stl, stl);
+      g.row(gB, gB, stl, stl);
+    }
+  }
+  if constexpr (kRho) {
+    g.cta_reduce(s, true, l2, part);
+    if (!grid_reduce_last(part, cnt, gpart, &ctrl->counters[kCntB])) return;
+    unpack_gram(part, s, true, ctrl->rho_new);
+  }
+}
+
+// P <- R + P beta with beta's columns in registers (SW <= 16).  Every lane
+// reads its own quad of P before the row's quads are exchanged, so P is
+// updated in place safely.
+template <int SW>
+__global__ void __launch_bounds__(kThreads, 2)
+pupdate4r_kernel(int64_t n, int s, const float* __restrict__ R, float* __restrict__ P, Ctrl* ctrl) {
+  if (ctrl->done) return;
+  using S = QuadShape<SW>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int qi = lane % S::LPR, rho = lane / S::LPR;
+  const bool qok = 4 * qi < s;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
+  const int64_t nw = (int64_t)gridDim.x * kWarps;
+  float4 cf[SW];
+  load_coef<SW>(cf, ctrl->beta, s, kMaxS, qi);
+  for (int64_t base = gw * S::RW; base < n; base += 2 * nw * S::RW) {
+    const int64_t rA = base + rho, rB = base + nw * S::RW + rho;
+    const bool okA = (rA < n) && qok, okB = (rB < n) && qok;
+    const float4 pA = okA ? ld4(P + rA * s + 4 * qi) : zero4();
+    const float4 pB = okB ? ld4(P + rB * s + 4 * qi) : zero4();
+    const float4 zA = okA ? ld4(R + rA * s + 4 * qi) : zero4();
+    const float4 zB = okB ? ld4(R + rB * s + 4 * qi) : zero4();
+    const float4 aA = row_times<SW>(pA, cf, zero4());
+    const float4 aB = row_times<SW>(pB, cf, zero4());
+    if (okA) st4(P + rA * s + 4 * qi, add4(zA, aA));
+    if (okB) st4(P + rB * s + 4 * qi, add4(zB, aB));
+  }
+}
+
 // P <- R + P beta.  The warp stages its rows of P before any lane writes P.
 template <int SW>
 __global__ void __launch_bounds__(kThreads, quad_min_ctas<SW>())
@@ -233,8 +332,29 @@ pupdate4_kernel(int64_t n, int s, const float* __restrict__ R, float* __restrict
 }
 
 template <int SW>
-static cudaError_t update4_sw(const Launch& L, int64_t n, int s, const float* P, const float* Q,
-                              float* X, float* R, Ctrl* ctrl, double* gpart, int rho_mode) {
+static cudaError_t update4r_sw(const Launch& L, int64_t n, int s, const float* P, const float* Q,
+                               float* X, float* R, Ctrl* ctrl, double* gpart, int rho_mode) {
+  using S = QuadShape<SW>;
+  cudaError_t err = cudaSuccess;
+  {
+    auto k = update4r_kernel<SW, false>;
+    const int occ = quad_occupancy(k, 0, &err);
+    if (!occ) return err;
+    k<<<quad_grid(L, occ, n, 2 * S::RW), kThreads, 0, L.stream>>>(n, s, P, Q, X, R, ctrl, gpart, rho_mode);
+    if ((err = cudaGetLastError()) != cudaSuccess || rho_mode == 0) return err;
+  }
+  auto k = update4r_kernel<SW, true>;
+  const int cnt = ut_count(s);
+  const size_t sm = sizeof(double) * (size_t)((cnt + 1) & ~1) + sizeof(float) * quad_gram_floats<SW>();
+  const int occ = quad_occupancy(k, sm, &err);
+  if (!occ) return err;
+  k<<<quad_grid(L, occ, n, 2 * S::RW), kThreads, sm, L.stream>>>(n, s, P, Q, X, R, ctrl, gpart, rho_mode);
+  return cudaGetLastError();
+}
+
+template <int SW>
+static cudaError_t update4s_sw(const Launch& L, int64_t n, int s, const float* P, const float* Q,
+                               float* X, float* R, Ctrl* ctrl, double* gpart, int rho_mode) {
   using S = QuadShape<SW>;
   cudaError_t err = cudaSuccess;
   {
@@ -255,6 +375,13 @@ static cudaError_t update4_sw(const Launch& L, int64_t n, int s, const float* P,
   return cudaGetLastError();
 }
 
+template <int SW>
+static cudaError_t update4_sw(const Launch& L, int64_t n, int s, const float* P, const float* Q,
+                              float* X, float* R, Ctrl* ctrl, double* gpart, int rho_mode) {
+  if constexpr (SW <= 16) return update4r_sw<SW>(L, n, s, P, Q, X, R, ctrl, gpart, rho_mode);
+  else return update4s_sw<SW>(L, n, s, P, Q, X, R, ctrl, gpart, rho_mode);
+}
+
 cudaError_t bcg_update4(const Launch& L, int64_t n, int s, const float* P, const float* Q, float* X,
                         float* R, Ctrl* ctrl, double* gpart, int rho_mode) {
   if (s % 4 != 0) return cudaErrorInvalidValue;
@@ -269,11 +396,18 @@ cudaError_t bcg_update4(const Launch& L, int64_t n, int s, const float* P, const
 
 template <int SW>
 static cudaError_t pupdate4_sw(const Launch& L, int64_t n, int s, const float* R, float* P, Ctrl* ctrl) {
-  auto k = pupdate4_kernel<SW>;
   cudaError_t err = cudaSuccess;
-  const int occ = quad_occupancy(k, 0, &err);
-  if (!occ) return err;
-  k<<<quad_grid(L, occ, n, QuadShape<SW>::RW), kThreads, 0, L.stream>>>(n, s, R, P, ctrl);
+  if constexpr (SW <= 16) {
+    auto k = pupdate4r_kernel<SW>;
+    const int occ = quad_occupancy(k, 0, &err);
+    if (!occ) return err;
+    k<<<quad_grid(L, occ, n, 2 * QuadShape<SW>::RW), kThreads, 0, L.stream>>>(n, s, R, P, ctrl);
+  } else {
+    auto k = pupdate4_kernel<SW>;
+    const int occ = quad_occupancy(k, 0, &err);
+    if (!occ) return err;
+    k<<<quad_grid(L, occ, n, QuadShape<SW>::RW), kThreads, 0, L.stream>>>(n, s, R, P, ctrl);
+  }
   return cudaGetLastError();
 }
 

@@ -10,13 +10,14 @@
 // float accumulators instead of one per Gram column, and every staged value
 // is read with 16-byte shared-memory loads.
 //
-// Precision: each lane sums 16 rows in float registers, adds that window
+// Precision: each lane sums 32 rows in float registers, adds that window
 // into its own float slot in shared memory, and the slots of all lanes,
 // warps and CTAs are added in double, in a fixed order (bitwise
 // reproducible for a given grid).
 #pragma once
 
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "bk_internal.h"
@@ -87,7 +88,7 @@ struct QuadShape {
   static constexpr int G = NB >= 32 ? 1 : 32 / NB;  // lanes sharing one block (row groups)
   static constexpr int RPL = RW / G;                // staged rows per lane per trip
   static constexpr int STAGE = RW * SW;             // floats of one staged operand per warp
-  static constexpr int TPF = RPL >= 16 ? 1 : 16 / RPL;  // trips per 16-row register window
+  static constexpr int TPF = RPL >= 32 ? 1 : 32 / RPL;  // trips per 32-row register window
   static constexpr int NACC = 16 * NBL;             // float accumulators per lane
 };
 
@@ -199,5 +200,151 @@ template <int SW>
 constexpr size_t quad_gram_floats() {
   return (size_t)kWarps * 2 * QuadShape<SW>::STAGE + (size_t)QuadShape<SW>::NACC * kThreads;
 }
+
+// Quad k of the calling lane's row: the LPR lanes of a row exchange their
+// quads by shuffles (s shuffles per lane for the whole row).
+template <int SW>
+__device__ __forceinline__ float4 row_quad(const float4& mine, int k) {
+  constexpr int LPR = QuadShape<SW>::LPR;
+  if constexpr (LPR == 1) {
+    return mine;
+  } else {
+    return make_float4(__shfl_sync(0xffffffffu, mine.x, k, LPR), __shfl_sync(0xffffffffu, mine.y, k, LPR),
+                       __shfl_sync(0xffffffffu, mine.z, k, LPR), __shfl_sync(0xffffffffu, mine.w, k, LPR));
+  }
+}
+
+// Row-owner Gram for SW <= 16: lane (row, quad i) adds L[r][a] M[r][4i + t]
+// for every a (the row's L quads arrive by shuffles) into SW x 4 float
+// accumulators: no shared-memory traffic per row.  Windows of kRowWin rows
+// per lane go to float slots in shared memory; the CTA sums are in double.
+template <int SW>
+struct RowGram {
+  using S = QuadShape<SW>;
+  static_assert(SW <= 16, "RowGram keeps SW x 4 accumulators per lane");
+  static constexpr int kRowWin = 32;
+  float acc[SW][4];
+  int rows;
+  float* slot;   // slot[(a * 4 + t) * kThreads]
+
+  __device__ __forceinline__ void init(float* l2) {
+#pragma unroll
+    for (int a = 0; a < SW; ++a)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) acc[a][t] = 0.f;
+    rows = 0;
+    slot = l2 + threadIdx.x;
+#pragma unroll
+    for (int e = 0; e < 4 * SW; ++e) slot[e * kThreads] = 0.f;
+  }
+  __device__ __forceinline__ void flush() {
+#pragma unroll
+    for (int a = 0; a < SW; ++a)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        slot[(a * 4 + t) * kThreads] += acc[a][t];
+        acc[a][t] = 0.f;
+      }
+    rows = 0;
+  }
+  // l, m: this lane's quads of the current row (zero for rows past n)
+  __device__ __forceinline__ void row(const float4& l, const float4& m) {
+#pragma unroll
+    for (int k = 0; k < S::NQ; ++k) {
+      const float4 lk = row_quad<SW>(l, k);
+#pragma unroll
+      for (int t2 = 0; t2 < 4; ++t2) {
+        const float la = comp4(lk, t2);
+        float* r = acc[4 * k + t2];
+        r[0] = fmaf(la, m.x, r[0]);
+        r[1] = fmaf(la, m.y, r[1]);
+        r[2] = fmaf(la, m.z, r[2]);
+        r[3] = fmaf(la, m.w, r[3]);
+      }
+    }
+    if (++rows == kRowWin) flush();
+  }
+  __device__ void cta_reduce(int s, bool sym, const float* l2, double* part) {
+    flush();
+    __syncthreads();
+    const int cnt = sym ? ut_count(s) : s * s;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      int a, c;
+      if (sym) {
+        c = 0;
+        while ((c + 1) * (c + 2) / 2 <= i) ++c;
+        a = i - c * (c + 1) / 2;
+      } else {
+        a = i / s;
+        c = i - a * s;
+      }
+      const int qi = c / 4, t = c % 4;
+      double sum = 0.0;
+      for (int w = 0; w < kWarps; ++w)
+        for (int rr = 0; rr < S::RW; ++rr)
+          sum += (double)l2[(a * 4 + t) * kThreads + w * 32 + rr * S::LPR + qi];
+      part[i] = sum;
+    }
+    __syncthreads();
+  }
+  static constexpr size_t smem_floats() { return (size_t)4 * SW * kThreads; }
+};
+
+// The block Gram with the staging interface of RowGram: row(l, m, stl, stm)
+// stages the lane's quads and adds the warp's trip (used for SW = 32).
+template <int SW>
+struct StagedGram : QuadGram<SW> {
+  using S = QuadShape<SW>;
+  __device__ __forceinline__ void row(const float4& l, const float4& m, float* stl, float* stm) {
+    const int lane = threadIdx.x & 31;
+    const int qi = lane % S::LPR, rho = lane / S::LPR;
+    st4(stl + rho * SW + 4 * qi, l);
+    if (stm != stl) st4(stm + rho * SW + 4 * qi, m);
+    __syncwarp();
+    this->trip(stl, stm);
+    __syncwarp();
+  }
+  static constexpr size_t smem_floats() { return quad_gram_floats<SW>(); }
+};
+
+template <int SW>
+struct RowGramStaged : RowGram<SW> {
+  __device__ __forceinline__ void row(const float4& l, const float4& m, float*, float*) {
+    RowGram<SW>::row(l, m);
+  }
+};
+
+// Columns 4i .. 4i + 3 of an s x s double matrix (row stride ld), every row a
+// < SW, as floats in registers (zero beyond s): 4 SW registers.
+template <int SW>
+__device__ __forceinline__ void load_coef(float4 (&cf)[SW], const double* M, int s, int ld, int qi) {
+#pragma unroll
+  for (int a = 0; a < SW; ++a) {
+    float v[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int c = 4 * qi + t;
+      v[t] = (a < s && c < s) ? (float)M[a * ld + c] : 0.f;
+    }
+    cf[a] = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+// acc + sum_a row[a] cf[a] over the quads of the lane's row (a ascending).
+template <int SW>
+__device__ __forceinline__ float4 row_times(const float4& mine, const float4 (&cf)[SW], float4 acc) {
+#pragma unroll
+  for (int k = 0; k < QuadShape<SW>::NQ; ++k) {
+    const float4 rk = row_quad<SW>(mine, k);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) acc = fma4(comp4(rk, t), cf[4 * k + t], acc);
+  }
+  return acc;
+}
+
+// Gram policy per width: shuffles for SW <= 8 (at most 32 accumulators),
+// staged 4 x 4 blocks for 16 and 32 (16 or 32 accumulators).
+template <int SW>
+using GramOf = typename std::conditional<(SW <= 8), RowGramStaged<SW>, StagedGram<SW>>::type;
 
 }  // namespace bk

@@ -4,13 +4,16 @@
 //
 // The thesis splits the rows over MPI processes; here the "processes" are
 // row tiles of one GPU:
-//   1. leaf factor   one CTA per tile of 8192/next_pow2(s) rows, held in shared
-//                    memory: Householder QR of the tile; the reflectors overwrite
-//                    the tile in Y; the tile's R factor and the triangular factor
-//                    T of its compact WY form  H_0 ... H_{s-1} = I - V T V^T
-//                    go to scratch;
-//   2. tree factor   one CTA per tree node: Householder QR of the stacked R
-//                    factors of its F = max(2, 256/s) children (FP64);
+//   1. leaf factor   one CTA per tile of 256 x RPT rows (RPT = 64 / next_pow2(s)
+//                    for FP32 blocks, 32 / next_pow2(s) for FP64), the rows in
+//                    registers: Householder QR of the tile; the reflectors
+//                    overwrite the tile in Y; the tile's R factor and the factor
+//                    F = strict_upper(V^T V) + diag(tau) of its compact WY form
+//                    H_0 ... H_{s-1} = I - V T V^T (T^{-1} = diag(1/tau) +
+//                    strict_upper(V^T V)) go to scratch;
+//   2. tree factor   the same kernel, one row per thread, on tiles of 256 rows
+//                    of the stacked R factors of the level below (stored in
+//                    FP64, arithmetic in the block's precision);
 //   3. root          sign fix: gamma = D R_root with D = sign(diag R_root);
 //   4. tree apply    top-down, each node turns its scatter factor sigma~ into
 //                    those of its children: Q_node [sigma~; 0];
@@ -118,10 +121,11 @@ __device__ __forceinline__ int warp_reduce_scatter(A (&v)[V]) {
 // F = strict_upper(V^T V) + diag(tau) (entry (c, j) = y_c, (j, j) = tau_j)
 // and never forms T: the apply solves with T^{-1} instead (tile_w).  This
 // keeps the column loop free of the serial T recursion.  The scalars are
-// computed once per column, by warp 0, and published in shared memory.
-template <typename T, int SW, int RPT>
+// computed once per column, by warp 0, and published in shared memory
+// (on GB300's narrow FP64 pipe this beats every warp forming them itself).
+template <typename TIn, typename T, int SW, int RPT>
 __global__ void __launch_bounds__(kTT)
-leaf_factor(int64_t n, int s, const T* __restrict__ X, T* __restrict__ Y, double* __restrict__ R0,
+leaf_factor(int64_t n, int s, const TIn* __restrict__ X, TIn* __restrict__ Y, double* __restrict__ R0,
             double* __restrict__ T0, const int* done, const int* flag) {
   if (tsqr_skip(done, flag)) return;
   constexpr int tile = kTT * RPT;
@@ -138,7 +142,7 @@ leaf_factor(int64_t n, int s, const T* __restrict__ X, T* __restrict__ Y, double
   for (int k = 0; k < RPT; ++k) {
     const int g = tid + k * kTT;
 #pragma unroll
-    for (int c = 0; c < SW; ++c) row[k][c] = (g < m && c < s) ? X[(r0 + g) * s + c] : T(0);
+    for (int c = 0; c < SW; ++c) row[k][c] = (g < m && c < s) ? (T)X[(r0 + g) * s + c] : T(0);
   }
   for (int i = tid; i < SW * SW; i += kTT) Tm[i] = 0.0;
 #pragma unroll
@@ -211,7 +215,7 @@ leaf_factor(int64_t n, int s, const T* __restrict__ X, T* __restrict__ Y, double
     const int g = tid + k * kTT;
     if (g < m) {
 #pragma unroll
-      for (int c = 0; c < SW; ++c) if (c < s) Y[(r0 + g) * s + c] = row[k][c];
+      for (int c = 0; c < SW; ++c) if (c < s) Y[(r0 + g) * s + c] = (TIn)row[k][c];
     }
   }
   double* Rb = R0 + (size_t)blockIdx.x * s * s;
@@ -288,13 +292,61 @@ tile_w(int64_t n, int s, int tile, const T* __restrict__ Y, const double* __rest
   for (int i = tid; i < s * s; i += kTT) TW[(size_t)blockIdx.x * s * s + i] = Wm[(i / s) * kMaxS + (i % s)];
 }
 
+// (a') the same for FP32 leaf tiles, in FP32 arithmetic: one warp per tile,
+// lane c forms column c of Z = V_1^T sigma~ and of W (registers).
+template <typename TIn, int SW>
+__global__ void __launch_bounds__(kThreads)
+tile_w_f32(int64_t n, int s, int tile, int64_t tiles, const TIn* __restrict__ Y,
+           const double* __restrict__ S0, double* __restrict__ TW, const int* done, const int* flag) {
+  if (tsqr_skip(done, flag)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t tl = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (tl >= tiles) return;
+  const int64_t r0 = tl * tile;
+  const int m = (int)((n - r0) < tile ? (n - r0) : tile);
+  const double* S = S0 + (size_t)tl * s * s;
+  double* F = TW + (size_t)tl * s * s;
+  const int c = lane;
+  const bool cok = c < s;
+  float sig[SW], w[SW];
+#pragma unroll
+  for (int g = 0; g < SW; ++g) sig[g] = (g < s && cok) ? (float)S[g * s + c] : 0.f;
+  float z[SW];
+#pragma unroll
+  for (int a = 0; a < SW; ++a) {            // Z[a][c] = sum_{g >= a} V_1[g][a] sigma~[g][c]
+    float acc = 0.f;
+#pragma unroll
+    for (int g = a; g < SW; ++g) {
+      const float v = (g >= s || a >= s) ? 0.f
+                    : (g == a ? 1.f : (g < m ? (float)Y[(r0 + g) * s + a] : 0.f));
+      acc = fmaf(v, sig[g], acc);
+    }
+    z[a] = acc;
+  }
+#pragma unroll
+  for (int a = SW - 1; a >= 0; --a) {       // W[a] = tau_a (Z[a] - sum_{b > a} F[a][b] W[b])
+    if (a >= s) { w[a] = 0.f; continue; }
+    float acc = z[a];
+#pragma unroll
+    for (int b = a + 1; b < SW; ++b)
+      if (b < s) acc = fmaf(-(float)F[a * s + b], w[b], acc);
+    w[a] = (float)F[a * s + a] * acc;
+  }
+  __syncwarp();                             // every lane has read F before W overwrites it
+  if (cok) {
+#pragma unroll
+    for (int a = 0; a < SW; ++a)
+      if (a < s) F[a * s + c] = (double)w[a];
+  }
+}
+
 // (b) apply_rows: every warp takes a contiguous chunk of rows (two row groups
 // per trip), so consecutive trips stay inside one tile and lane c keeps
 // column c of that tile's W in registers.  Lane c computes Y[r][c]; the Gram
 // Y^T Y (upper, mirrored) is accumulated in the same pass when rho_out is given.
-template <typename T, int SW>
-__global__ void __launch_bounds__(kThreads, min_ctas<T>())
-apply_rows(int64_t n, int s, int tile_shift, T* __restrict__ Y, const double* __restrict__ S0,
+template <typename TIn, typename T, int SW>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (SW >= 32 ? 2 : 4) : 1)
+apply_rows(int64_t n, int s, int tile_shift, TIn* __restrict__ Y, const double* __restrict__ S0,
            const double* __restrict__ W, double* rho_out, double* gpart, unsigned* counter,
            const int* done, const int* flag) {
   if (tsqr_skip(done, flag)) return;
@@ -340,7 +392,7 @@ apply_rows(int64_t n, int s, int tile_shift, T* __restrict__ Y, const double* __
     const bool ok = (r < hi) && (c < s);
     T v = T(0), y = T(0);
     if (ok) {
-      v = (g < s) ? (c == g ? T(1) : (c < g ? Y[r * s + c] : T(0))) : Y[r * s + c];
+      v = (g < s) ? (c == g ? T(1) : (c < g ? (T)Y[r * s + c] : T(0))) : (T)Y[r * s + c];
       if (g < s) y = (T)S0[(size_t)tl * s * s + g * s + c];
     }
 #pragma unroll
@@ -348,7 +400,7 @@ apply_rows(int64_t n, int s, int tile_shift, T* __restrict__ Y, const double* __
       const T va = sw_bcast<SW>(v, a);
       y = fma(-va, wcol[a], y);
     }
-    if (ok) Y[r * s + c] = y;
+    if (ok) Y[r * s + c] = (TIn)y;
     return ok ? y : T(0);
   };
   auto accum_row = [&](T yv) {
@@ -405,7 +457,7 @@ apply_rows(int64_t n, int s, int tile_shift, T* __restrict__ Y, const double* __
 // Gram Y^T Y accumulates in 4 x 4 register blocks.  Same terms, same order
 // as apply_rows for every output.
 template <int SW>
-__global__ void __launch_bounds__(kThreads, quad_min_ctas<SW>())
+__global__ void __launch_bounds__(kThreads, 2)
 apply4(int64_t n, int s, int tile_shift, float* __restrict__ Y, const double* __restrict__ S0,
        const double* __restrict__ W, double* rho_out, double* gpart, unsigned* counter,
        const int* done, const int* flag) {
@@ -435,16 +487,24 @@ apply4(int64_t n, int s, int tile_shift, float* __restrict__ Y, const double* __
   const int64_t hi = (lo + chunk < n) ? lo + chunk : n;
   const int64_t tmask = ((int64_t)1 << tile_shift) - 1;
   int64_t cur_tile = -1;
+  // SW <= 16: the lane's four columns of W in registers, rows by shuffles;
+  // SW = 32: W in shared memory, rows staged
+  constexpr bool kRegW = SW <= 16;
+  float4 cf[kRegW ? SW : 1];
   for (int64_t base = lo; base < hi; base += S::RW) {
     const int64_t tl = base >> tile_shift;
     if (tl != cur_tile) {
       cur_tile = tl;
-      __syncwarp();
-      for (int i = lane; i < SW * SW; i += 32) {
-        const int a = i / SW, c = i % SW;
-        ws[i] = (a < s && c < s) ? (float)W[(size_t)tl * s * s + a * s + c] : 0.f;
+      if constexpr (kRegW) {
+        load_coef<SW>(cf, W + (size_t)tl * s * s, s, s, qi);
+      } else {
+        __syncwarp();
+        for (int i = lane; i < SW * SW; i += 32) {
+          const int a = i / SW, c = i % SW;
+          ws[i] = (a < s && c < s) ? (float)W[(size_t)tl * s * s + a * s + c] : 0.f;
+        }
+        __syncwarp();
       }
-      __syncwarp();
     }
     const int64_t r = base + rho;
     const int gr = (int)(r & tmask);
@@ -463,16 +523,22 @@ apply4(int64_t n, int s, int tile_shift, float* __restrict__ Y, const double* __
       v = make_float4(vv[0], vv[1], vv[2], vv[3]);
       y = make_float4((float)sg[0], (float)sg[1], (float)sg[2], (float)sg[3]);
     }
-    st4(stv + rho * SW + 4 * qi, v);
-    __syncwarp();
+    if constexpr (kRegW) {
+      // y + sum_a (-v_a) w_a: the same roundings as y = fma(-v_a, w_a, y)
+      y = row_times<SW>(make_float4(-v.x, -v.y, -v.z, -v.w), cf, y);
+      if (ok) st4(Y + r * s + 4 * qi, y);
+    } else {
+      st4(stv + rho * SW + 4 * qi, v);
+      __syncwarp();
 #pragma unroll 4
-    for (int k = 0; k < S::NQ; ++k) {
-      const float4 vk = ld4(stv + rho * SW + 4 * k);
+      for (int k = 0; k < S::NQ; ++k) {
+        const float4 vk = ld4(stv + rho * SW + 4 * k);
 #pragma unroll
-      for (int t = 0; t < 4; ++t) y = fma4(-comp4(vk, t), ld4(ws + (4 * k + t) * SW + 4 * qi), y);
+        for (int t = 0; t < 4; ++t) y = fma4(-comp4(vk, t), ld4(ws + (4 * k + t) * SW + 4 * qi), y);
+      }
+      if (ok) st4(Y + r * s + 4 * qi, y);
+      __syncwarp();
     }
-    if (ok) st4(Y + r * s + 4 * qi, y);
-    __syncwarp();
     if (want_rho) {
       st4(stv + rho * SW + 4 * qi, ok ? y : zero4());
       __syncwarp();
@@ -508,28 +574,35 @@ static cudaError_t set_smem(K kern, size_t bytes) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <typename T, int SW, int RPT>
-static cudaError_t launch_leaves(const Launch& L, int64_t rows, int s, int64_t tiles, const T* X, T* Y,
-                                 double* Rst, double* Tf, double* rho_out, double* gpart,
+// TIn: storage of the tiles (the block's type at level 0, double in the tree);
+// T: arithmetic (the block's precision at every level).
+template <typename TIn, typename T, int SW, int RPT>
+static cudaError_t launch_leaves(const Launch& L, int64_t rows, int s, int64_t tiles, const TIn* X,
+                                 TIn* Y, double* Rst, double* Tf, double* rho_out, double* gpart,
                                  unsigned* counter, const int* done, const int* flag, bool factor) {
   if (factor) {
-    leaf_factor<T, SW, RPT><<<(unsigned)tiles, kTT, 0, L.stream>>>(rows, s, X, Y, Rst, Tf, done, flag);
+    leaf_factor<TIn, T, SW, RPT><<<(unsigned)tiles, kTT, 0, L.stream>>>(rows, s, X, Y, Rst, Tf, done, flag);
     return cudaGetLastError();
   }
   const int tile = kTT * RPT;
-  tile_w<T><<<(unsigned)tiles, kTT, 0, L.stream>>>(rows, s, tile, Y, Rst, Tf, done, flag);
+  if constexpr (sizeof(T) == 4) {
+    tile_w_f32<TIn, SW><<<(unsigned)((tiles + kWarps - 1) / kWarps), kThreads, 0, L.stream>>>(
+        rows, s, tile, tiles, Y, Rst, Tf, done, flag);
+  } else {
+    tile_w<TIn><<<(unsigned)tiles, kTT, 0, L.stream>>>(rows, s, tile, Y, Rst, Tf, done, flag);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int shift = 0;
   while ((1 << shift) < tile) ++shift;
-  if constexpr (sizeof(T) == 4 && SW >= 4) {
+  if constexpr (sizeof(TIn) == 4 && sizeof(T) == 4 && SW >= 4) {
     if (s % 4 == 0)
       return launch_apply4<SW>(L, rows, s, shift, Y, Rst, Tf, rho_out, gpart, counter, done, flag);
   }
   const int cnt = ut_count(s);
   const size_t lanes = (sizeof(T) == 4) ? (size_t)kThreads * lacc_stride(SW) : 0;
   const size_t sm = sizeof(double) * (cnt + 1 + kWarps * (cnt > 2 ? cnt : 2) + lanes) + 64;
-  auto k = apply_rows<T, SW>;
+  auto k = apply_rows<TIn, T, SW>;
   if ((e = set_smem(k, sm)) != cudaSuccess) return e;
   int64_t grid = (rows + 2 * kWarps - 1) / (2 * kWarps);
   const int64_t cap = (int64_t)L.sms * kCtasPerSm;
@@ -542,16 +615,16 @@ static cudaError_t launch_leaves(const Launch& L, int64_t rows, int s, int64_t t
 
 // Level 0 tiles hold leaf_rpt rows per thread; the tree levels (stacked R
 // factors, few rows) use one row per thread so that more CTAs share the work.
-template <typename T>
-static cudaError_t leaves(const Launch& L, int64_t rows, int s, int64_t tiles, const T* X, T* Y,
+template <typename TIn, typename T>
+static cudaError_t leaves(const Launch& L, int64_t rows, int s, int64_t tiles, const TIn* X, TIn* Y,
                           double* Rst, double* Tf, double* rho_out, double* gpart, unsigned* counter,
                           const int* done, const int* flag, bool factor, bool bottom) {
-#define BK_LEAVES(SWV)                                                                               \
-  return bottom ? launch_leaves<T, SWV, leaf_rpt(SWV, sizeof(T))>(L, rows, s, tiles, X, Y, Rst, Tf,   \
-                                                                 rho_out, gpart,                     \
-                                                  counter, done, flag, factor)                       \
-                : launch_leaves<T, SWV, 1>(L, rows, s, tiles, X, Y, Rst, Tf, rho_out, gpart, counter, \
-                                           done, flag, factor)
+#define BK_LEAVES(SWV)                                                                                 \
+  return bottom ? launch_leaves<TIn, T, SWV, leaf_rpt(SWV, sizeof(T))>(L, rows, s, tiles, X, Y, Rst,   \
+                                                                      Tf, rho_out, gpart, counter,    \
+                                                                      done, flag, factor)             \
+                : launch_leaves<TIn, T, SWV, 1>(L, rows, s, tiles, X, Y, Rst, Tf, rho_out, gpart,      \
+                                                counter, done, flag, factor)
   switch (next_pow2_s(s)) {
     case 1: BK_LEAVES(1);
     case 2: BK_LEAVES(2);
@@ -567,8 +640,10 @@ static cudaError_t leaves(const Launch& L, int64_t rows, int s, int64_t tiles, c
 int tsqr_launches(const TsqrPlan& p) { return 2 * (p.levels + 1) + 1; }
 
 // X = Y gamma (Y may alias X).  Level 0 tiles the n x s block; level l + 1
-// tiles the stacked R factors of level l (FP64) until one tile remains, whose
-// R is the root.  The scatter factors then travel down: the apply of level l
+// tiles the stacked R factors of level l (stored in FP64, factored in the
+// block's precision: an FP32 block's leaf R factors carry FP32 rounding, so
+// an FP64 tree would add nothing but FP64 work) until one tile remains,
+// whose R is the root (sign fix in FP64).  The scatter factors then travel down: the apply of level l
 // turns the sigma~ of its tiles into the stacked sigma~ of level l - 1.
 template <typename T>
 cudaError_t tsqr(const Launch& L, const TsqrPlan& p, const T* X, T* Y, double* gamma_out,
@@ -579,22 +654,22 @@ cudaError_t tsqr(const Launch& L, const TsqrPlan& p, const T* X, T* Y, double* g
   cudaError_t e;
   if (rho_out && !counter) return cudaErrorInvalidValue;
   prof_begin(L, kPhTsqrLeaf);
-  if ((e = leaves<T>(L, p.n, s, p.nodes[0], X, Y, q.R[0], q.Tf[0], nullptr, nullptr, nullptr, done,
-                     flag, true, true)) != cudaSuccess) return e;
+  if ((e = leaves<T, T>(L, p.n, s, p.nodes[0], X, Y, q.R[0], q.Tf[0], nullptr, nullptr, nullptr, done,
+                        flag, true, true)) != cudaSuccess) return e;
   prof_end(L, kPhTsqrLeaf, 1);
   prof_begin(L, kPhTsqrTree);
   for (int l = 1; l <= p.levels; ++l)
-    if ((e = leaves<double>(L, p.rows[l], s, p.nodes[l], q.R[l - 1], q.R[l - 1], q.R[l], q.Tf[l],
-                            nullptr, nullptr, nullptr, done, flag, true, false)) != cudaSuccess) return e;
+    if ((e = leaves<double, T>(L, p.rows[l], s, p.nodes[l], q.R[l - 1], q.R[l - 1], q.R[l], q.Tf[l],
+                               nullptr, nullptr, nullptr, done, flag, true, false)) != cudaSuccess) return e;
   root_fix<<<1, 256, 0, L.stream>>>(s, q.R[p.levels], gamma_out, done, flag);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int l = p.levels; l >= 1; --l)
-    if ((e = leaves<double>(L, p.rows[l], s, p.nodes[l], nullptr, q.R[l - 1], q.R[l], q.Tf[l],
-                            nullptr, nullptr, nullptr, done, flag, false, false)) != cudaSuccess) return e;
+    if ((e = leaves<double, T>(L, p.rows[l], s, p.nodes[l], nullptr, q.R[l - 1], q.R[l], q.Tf[l],
+                               nullptr, nullptr, nullptr, done, flag, false, false)) != cudaSuccess) return e;
   prof_end(L, kPhTsqrTree, 2 * p.levels + 1);
   prof_begin(L, kPhTsqrApply);
-  e = leaves<T>(L, p.n, s, p.nodes[0], nullptr, Y, q.R[0], q.Tf[0], rho_out, gpart, counter, done, flag,
-                false, true);
+  e = leaves<T, T>(L, p.n, s, p.nodes[0], nullptr, Y, q.R[0], q.Tf[0], rho_out, gpart, counter, done,
+                   flag, false, true);
   prof_end(L, kPhTsqrApply, 1);
   return e;
 }
