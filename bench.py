@@ -44,6 +44,17 @@ UNIT = "RHS*iter/s"
 FP64_PEAK_TFLOPS = 1.196   # measured FP64 FMA throughput of this GB300
 
 
+def _hbm_peak():
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6800.0   # fallback copy bandwidth of a GB300
+
+
+HBM_PEAK_GBS = _hbm_peak()
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -119,6 +130,18 @@ def aggregate(ms: float, units_per_rank: float, dist=None):
     return ms, world * units_per_rank / (ms / 1000.0)
 
 
+def spmm_alpha_ms(h, op, B, prec, iters=6):
+    """Device time per launch of the fused SpMM + alpha Gram kernel in a profiled solve."""
+    import math as _m
+    h.profile_reset()
+    h.solve("bcg", op, B, tol=0.0, maxit=iters, eta=_m.inf, prec=prec, ir_max_outer=1, profile=True,
+            record=False)
+    for nm, ms, nl in h.profile():
+        if nm == "spmm_alpha" and nl:
+            return ms / nl
+    return float("nan")
+
+
 def iteration_flops(n, s, tp_levels=None):
     """Algorithmic FP64 flops of one BCG iteration (stencil, eta = inf); FMA = 2 flops.
 
@@ -134,7 +157,9 @@ PHASE_FLOPS = {
     # algorithmic flops per launch of each phase, as functions of (n, s)
     "spmm_alpha": lambda n, s: 14 * n * s + n * s * (s + 1),
     "update_rho": lambda n, s: 4 * n * s * s,
-    "tsqr_leaf_factor": lambda n, s: 2 * n * s * s,
+    # Householder QR of the tiles (2 n s^2) and the strict upper triangle of
+    # V^T V that defines their compact WY factors (n s (s - 1))
+    "tsqr_leaf_factor": lambda n, s: 2 * n * s * s + n * s * (s - 1),
     "tsqr_leaf_apply": lambda n, s: 2 * n * s * s + n * s * (s + 1),
     "p_update": lambda n, s: 2 * n * s * s,
 }
@@ -316,6 +341,15 @@ def main():
                 m2 = time_iters(h, o2, B2, ss, 3, kk, torch)
                 sweep[f"{use}_s{ss}"] = {"rhs_iter_per_s": ss * kk / (m2 / 1000.0), "ms_per_iter": m2 / kk,
                                          "fp64_tflops": iteration_flops(pr.B.shape[0], ss) / (m2 / kk / 1000.0) / 1e12}
+                if use == "stencil":
+                    # the fused operator + Gram kernel (A P and P^T A P in one pass) against
+                    # HBM, FP32 (inner solve of refinement) and FP64
+                    for prec, w in (("fp32_ir", 4), ("fp64", 8)):
+                        t = spmm_alpha_ms(h, o2, B2, prec)
+                        by = 2 * w * pr.B.shape[0] * ss
+                        sweep[f"{use}_s{ss}"][f"spmm_bdot_{prec}"] = {
+                            "ms": t, "gbs": by / (t / 1000.0) / 1e9,
+                            "hbm_frac": by / (t / 1000.0) / 1e9 / HBM_PEAK_GBS}
                 o2.close()
                 del B2
 

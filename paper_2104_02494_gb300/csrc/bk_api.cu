@@ -88,12 +88,11 @@ bool is_host_ptr(const void* p) {
   return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
 }
 
-size_t gpart_count(const Launch& L, const TsqrPlan& tp) {
-  // largest grid of a reducing row kernel x largest partial record (two Grams + 2),
-  // or one record per TSQR leaf tile, whichever is larger
-  const size_t rows = (size_t)L.sms * kCtasPerSm * (kMM + kMM + 8);
-  const size_t tiles = tsqr_gpart_count(tp);
-  return rows > tiles ? rows : tiles;
+size_t gpart_count(const Launch& L, const TsqrPlan&) {
+  // largest grid of a reducing row kernel (every reducing kernel, the TSQR
+  // apply included, caps its grid at sms x kCtasPerSm) x largest partial
+  // record (two Grams + 2)
+  return (size_t)L.sms * kCtasPerSm * (kMM + kMM + 8);
 }
 
 void opts_or_default(const bkrylov_opts* o, bkrylov_opts* out) {

@@ -139,10 +139,6 @@ struct TsqrPlan {
 int tsqr_launches(const TsqrPlan& p);
 // elem_bytes: 8 for FP64 blocks, 4 for FP32 ones (larger leaf tiles)
 TsqrPlan tsqr_plan(int64_t n, int s, int elem_bytes = 8);
-// doubles of grid partials the fused Gram of the leaf apply needs (one record per tile)
-inline size_t tsqr_gpart_count(const TsqrPlan& p) {
-  return (size_t)p.nodes[0] * (size_t)(p.s * (p.s + 1) / 2) + 64;
-}
 // Y, gamma = Norm(X) (Y may alias X).  gamma -> ctrl-layout s x s (row stride 32).
 // If rho_out != null, also the Gram Y^T Y (row stride 32) is produced.
 // done: optional stop flag (skip when *done); reortho_flag: optional, skip unless *flag.

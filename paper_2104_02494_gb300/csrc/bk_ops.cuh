@@ -11,6 +11,19 @@
 namespace bk {
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+// Bulk prefetch of bytes [p, p + bytes) into L2 (no registers, no shared
+// memory).  Issued only when p and bytes are multiples of 16; the range must
+// lie inside one allocation: callers clip it to their arrays.
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
+  if (bytes && ((reinterpret_cast<uintptr_t>(p) | bytes) & 15u) == 0)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+// Rows [r0, r0 + count) of an n x s float block, clipped to [0, n); s % 4 == 0.
+__device__ __forceinline__ void l2_prefetch_rows(const float* base, int64_t n, int s, int64_t r0, int count) {
+  int64_t a = r0 < 0 ? 0 : r0, b = r0 + count > n ? n : r0 + count;
+  if (a < b) l2_prefetch(base + a * s, (uint32_t)((b - a) * s * sizeof(float)));
+}
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 __device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 __device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
@@ -33,6 +46,12 @@ struct CsrRow {
     T q = T(0);
     for (int j = b; j < e; ++j) q = fma(val[j], P[(int64_t)col[j] * s + c], q);
     return q;
+  }
+  static constexpr bool kLead = false;        // the column pattern is data
+  __device__ __forceinline__ int64_t lead_off() const { return 0; }
+  __device__ __forceinline__ float4 quad_lead(int64_t r, int i, int s, const float* __restrict__ P,
+                                              float4) const {
+    return quad(r, i, s, P);
   }
   __device__ __forceinline__ float4 quad(int64_t r, int i, int s, const float* __restrict__ P) const {
     const int b = row_ptr[r], e = row_ptr[r + 1];
@@ -90,6 +109,28 @@ struct Const7Row {
     if (z < nz - 1) q = fma4(czp, ld4(p + plane * s), q);
     return q;
   }
+  // In a row sweep the +z neighbour (row r + nx ny) is the row read first
+  // from DRAM; a caller may load it ahead ("lead") and pass it in.  The
+  // stencils keep kLead off: on GB300 the ring's registers cost more
+  // occupancy than the lead latency it hides.
+  static constexpr bool kLead = false;
+  __device__ __forceinline__ int64_t lead_off() const { return (int64_t)nx * ny; }
+  __device__ __forceinline__ float4 quad_lead(int64_t r, int i, int s, const float* __restrict__ P,
+                                              float4 lead) const {
+    const int64_t plane = (int64_t)nx * ny;
+    int x, y, z;
+    grid_xyz(r, dx, dy, x, y, z);
+    const float* p = P + r * s + 4 * i;
+    float4 q = zero4();
+    if (z > 0) q = fma4(czm, ld4(p - plane * s), q);
+    if (y > 0) q = fma4(cym, ld4(p - (int64_t)nx * s), q);
+    if (x > 0) q = fma4(cxm, ld4(p - s), q);
+    q = fma4(c0, ld4(p), q);
+    if (x < nx - 1) q = fma4(cxp, ld4(p + s), q);
+    if (y < ny - 1) q = fma4(cyp, ld4(p + (int64_t)nx * s), q);
+    if (z < nz - 1) q = fma4(czp, lead, q);
+    return q;
+  }
 };
 
 // Variable-coefficient 7-point FV operator with precomputed coefficients:
@@ -132,6 +173,24 @@ struct Var7Row {
     if (z < nz - 1) q = fma4(-fz[r], ld4(p + plane * s), q);
     return q;
   }
+  static constexpr bool kLead = false;
+  __device__ __forceinline__ int64_t lead_off() const { return (int64_t)nx * ny; }
+  __device__ __forceinline__ float4 quad_lead(int64_t r, int i, int s, const float* __restrict__ P,
+                                              float4 lead) const {
+    const int64_t plane = (int64_t)nx * ny;
+    int x, y, z;
+    grid_xyz(r, dx, dy, x, y, z);
+    const float* p = P + r * s + 4 * i;
+    float4 q = zero4();
+    if (z > 0) q = fma4(-fz[r - plane], ld4(p - plane * s), q);
+    if (y > 0) q = fma4(-fy[r - nx], ld4(p - (int64_t)nx * s), q);
+    if (x > 0) q = fma4(-fx[r - 1], ld4(p - s), q);
+    q = fma4(diag[r], ld4(p), q);
+    if (x < nx - 1) q = fma4(-fx[r], ld4(p + s), q);
+    if (y < ny - 1) q = fma4(-fy[r], ld4(p + (int64_t)nx * s), q);
+    if (z < nz - 1) q = fma4(-fz[r], lead, q);
+    return q;
+  }
 };
 
 // 2D per-edge diffusion: ax[y][x] (ny x (nx+1)) joins (x-1,y),(x,y); ay[y][x]
@@ -171,6 +230,23 @@ struct Edge5Row {
     if (y < ny - 1) q = fma4(-ay[(int64_t)(y + 1) * nx + x], ld4(p + (int64_t)nx * s), q);
     return q;
   }
+  static constexpr bool kLead = false;
+  __device__ __forceinline__ int64_t lead_off() const { return nx; }
+  __device__ __forceinline__ float4 quad_lead(int64_t r, int i, int s, const float* __restrict__ P,
+                                              float4 lead) const {
+    const uint32_t u = (uint32_t)r;
+    const uint32_t q1 = dx.div(u);
+    const int x = (int)(u - q1 * dx.d);
+    const int y = (int)q1;
+    const float* p = P + r * s + 4 * i;
+    float4 q = zero4();
+    if (y > 0) q = fma4(-ay[(int64_t)y * nx + x], ld4(p - (int64_t)nx * s), q);
+    if (x > 0) q = fma4(-ax[(int64_t)y * (nx + 1) + x], ld4(p - s), q);
+    q = fma4(diag[r], ld4(p), q);
+    if (x < nx - 1) q = fma4(-ax[(int64_t)y * (nx + 1) + x + 1], ld4(p + s), q);
+    if (y < ny - 1) q = fma4(-ay[(int64_t)(y + 1) * nx + x], lead, q);
+    return q;
+  }
 };
 
 // Identity "operator": the row kernel then just streams Y, which turns the
@@ -182,6 +258,11 @@ struct IdRow {
   }
   __device__ __forceinline__ float4 quad(int64_t r, int i, int s, const float* __restrict__ P) const {
     return ld4(P + r * s + 4 * i);
+  }
+  static constexpr bool kLead = true;
+  __device__ __forceinline__ int64_t lead_off() const { return 0; }
+  __device__ __forceinline__ float4 quad_lead(int64_t, int, int, const float*, float4 lead) const {
+    return lead;
   }
 };
 

@@ -30,43 +30,59 @@ spmm4_kernel(RowOp op, int64_t n, int s, const float* __restrict__ P, float* __r
   const int64_t nw = (int64_t)gridDim.x * kWarps;
   constexpr bool kGram = kEpi != kQEpiNone;
   const int cnt = kGram ? (kEpi == kQEpiSym ? ut_count(s) : s * s) : 0;
-  double* part = smem;
-  float* stage = reinterpret_cast<float*>(smem + ((cnt + 1) & ~1));
-  float* l2 = stage + kWarps * 2 * S::STAGE;
-  float* stl = stage + warp * 2 * S::STAGE;
-  float* stq = stl + S::STAGE;
+  const GramPtrs<SW> sp(smem, cnt);
   Gram g;
-  if constexpr (kGram) g.init(l2);
-  for (int64_t base = gw * S::RW; base < n; base += nw * S::RW) {
+  if constexpr (kGram) g.init(sp.slots);
+  // For a plain Gram (IdRow) both operands' rows are read first from DRAM:
+  // they are loaded two trips ahead into a register ring, so that every warp
+  // keeps three trips of DRAM reads in flight (operators with kLead off load
+  // as they go).
+  const int64_t stride = nw * S::RW;
+  const int64_t off = op.lead_off();
+  constexpr bool kLeftLead = kGram && RowOp::kLead && std::is_same<RowOp, IdRow<float>>::value;
+  auto lead_at = [&](int64_t rr) -> float4 {
+    if constexpr (RowOp::kLead) {
+      const int64_t rl = rr + off;
+      return (rr < n && qok && rl < n) ? ld4(P + rl * s + 4 * qi) : zero4();
+    } else {
+      return zero4();
+    }
+  };
+  auto left_at = [&](int64_t rr) -> float4 {
+    if constexpr (kLeftLead) return (rr < n && qok) ? ld4(ep.left + rr * s + 4 * qi) : zero4();
+    else return zero4();
+  };
+  const int64_t b0 = gw * S::RW;
+  float4 L0 = lead_at(b0 + rho), L1 = lead_at(b0 + stride + rho);
+  float4 M0 = left_at(b0 + rho), M1 = left_at(b0 + stride + rho);
+  for (int64_t base = b0; base < n; base += stride) {
+    const float4 L2 = lead_at(base + 2 * stride + rho);
+    const float4 M2 = left_at(base + 2 * stride + rho);
     const int64_t r = base + rho;
     const bool ok = (r < n) && qok;
     float4 q = zero4(), l = zero4();
     if (ok) {
-      q = op.quad(r, qi, s, P);
+      if constexpr (RowOp::kLead) q = op.quad_lead(r, qi, s, P, L0);
+      else q = op.quad(r, qi, s, P);
       if (sub) q = sub4(ld4(sub + r * s + 4 * qi), q);
       if (Q) st4(Q + r * s + 4 * qi, q);
-      if constexpr (kGram) l = ld4(ep.left + r * s + 4 * qi);
+      if constexpr (kGram) l = kLeftLead ? M0 : ld4(ep.left + r * s + 4 * qi);
     }
-    if constexpr (kGram) g.row(l, q, stl, stq);
+    if constexpr (kGram) g.row(l, q, sp.stl, sp.stm);
+    L0 = L1; L1 = L2;
+    M0 = M1; M1 = M2;
   }
   if constexpr (kGram) {
-    g.cta_reduce(s, kEpi == kQEpiSym, l2, part);
-    if (!grid_reduce_last(part, cnt, ep.gpart, ep.counter)) return;
-    unpack_gram(part, s, kEpi == kQEpiSym, ep.gram_out);
+    g.cta_reduce(s, kEpi == kQEpiSym, sp.slots, sp.part, sp.stl, sp.stm);
+    if (!grid_reduce_last(sp.part, cnt, ep.gpart, ep.counter)) return;
+    unpack_gram(sp.part, s, kEpi == kQEpiSym, ep.gram_out);
   }
-}
-
-// Shared memory of a quad kernel with a Gram: part (doubles) | staging | slots.
-template <int SW>
-constexpr size_t quad_gram_smem_floats() {
-  return (size_t)kWarps * 2 * QuadShape<SW>::STAGE + GramOf<SW>::smem_floats();
 }
 
 template <int SW>
 static size_t spmm4_smem(int s, int epi) {
   if (epi == kQEpiNone) return 0;
-  const int cnt = epi == kQEpiSym ? ut_count(s) : s * s;
-  return sizeof(double) * (size_t)((cnt + 1) & ~1) + sizeof(float) * quad_gram_smem_floats<SW>();
+  return gram_smem_bytes<SW>(epi == kQEpiSym ? ut_count(s) : s * s);
 }
 
 template <int SW, class RowOp, int kEpi>
@@ -132,22 +148,21 @@ update4_kernel(int64_t n, int s, const float* __restrict__ P, const float* __res
   using S = QuadShape<SW>;
   extern __shared__ double smem[];
   const int cnt = kRho ? ut_count(s) : 0;
-  double* part = smem;
-  float* lx = reinterpret_cast<float*>(smem + ((cnt + 1) & ~1));
+  const GramPtrs<SW> sp(smem, cnt);
+  float* lx = kRho ? sp.extra : reinterpret_cast<float*>(smem);   // s x s, row stride SW
   float* lam = lx + SW * SW;
-  float* stage = lam + SW * SW;
-  float* l2 = stage + kWarps * 2 * S::STAGE;
+  float* ustage = lam + SW * SW;           // per warp: RW rows of P, then of Q
   stage_quad_matrix<SW>(lx, ctrl->lx, s);
   stage_quad_matrix<SW>(lam, ctrl->lam, s);
-  QuadGram<SW> g;
-  if constexpr (kRho) g.init(l2);
+  GramOf<SW> g;
+  if constexpr (kRho) g.init(sp.slots);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int qi = lane % S::LPR, rho = lane / S::LPR;
   const bool qok = 4 * qi < s;
   const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
   const int64_t nw = (int64_t)gridDim.x * kWarps;
-  float* stp = stage + warp * 2 * S::STAGE;
+  float* stp = ustage + warp * 2 * S::STAGE;
   float* stq = stp + S::STAGE;
   for (int64_t base = gw * S::RW; base < n; base += nw * S::RW) {
     const int64_t r = base + rho;
@@ -182,16 +197,14 @@ update4_kernel(int64_t n, int s, const float* __restrict__ P, const float* __res
     }
     __syncwarp();
     if constexpr (kRho) {
-      st4(stp + rho * SW + 4 * qi, ok ? z4 : zero4());
-      __syncwarp();
-      g.trip(stp, stp);
-      __syncwarp();
+      const float4 zz = ok ? z4 : zero4();
+      g.row(zz, zz, sp.stl, sp.stl);
     }
   }
   if constexpr (kRho) {
-    g.cta_reduce(s, true, l2, part);
-    if (!grid_reduce_last(part, cnt, gpart, &ctrl->counters[kCntB])) return;
-    unpack_gram(part, s, true, ctrl->rho_new);
+    g.cta_reduce(s, true, sp.slots, sp.part, sp.stl, sp.stl);
+    if (!grid_reduce_last(sp.part, cnt, gpart, &ctrl->counters[kCntB])) return;
+    unpack_gram(sp.part, s, true, ctrl->rho_new);
   }
 }
 
@@ -214,20 +227,24 @@ update4r_kernel(int64_t n, int s, const float* __restrict__ P, const float* __re
   using S = QuadShape<SW>;
   extern __shared__ double smem[];
   const int cnt = kRho ? ut_count(s) : 0;
-  double* part = smem;
-  float* stage = reinterpret_cast<float*>(smem + ((cnt + 1) & ~1));
-  float* l2 = stage + kWarps * 2 * S::STAGE;
+  const GramPtrs<SW> sp(smem, cnt);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int qi = lane % S::LPR, rho = lane / S::LPR;
   const bool qok = 4 * qi < s;
   const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
   const int64_t nw = (int64_t)gridDim.x * kWarps;
-  float* stl = stage + warp * 2 * S::STAGE;
-  StagedGram<SW> g;
-  if constexpr (kRho) g.init(l2);
+  GramOf<SW> g;
+  if constexpr (kRho) g.init(sp.slots);
   float4 cf[SW];
   load_coef<SW>(cf, ctrl->lx, s, kMaxS, qi);
   for (int64_t base = gw * S::RW; base < n; base += 2 * nw * S::RW) {
+    if (lane == 0) {
+      const int64_t pb = base + 4 * nw * S::RW;     // two trips ahead, both row groups
+      l2_prefetch_rows(P, n, s, pb, S::RW);
+      l2_prefetch_rows(P, n, s, pb + nw * S::RW, S::RW);
+      l2_prefetch_rows(X, n, s, pb, S::RW);
+      l2_prefetch_rows(X, n, s, pb + nw * S::RW, S::RW);
+    }
     const int64_t rA = base + rho, rB = base + nw * S::RW + rho;
     const bool okA = (rA < n) && qok, okB = (rB < n) && qok;
     const float4 pA = okA ? ld4(P + rA * s + 4 * qi) : zero4();
@@ -241,6 +258,13 @@ update4r_kernel(int64_t n, int s, const float* __restrict__ P, const float* __re
   }
   load_coef<SW>(cf, ctrl->lam, s, kMaxS, qi);
   for (int64_t base = gw * S::RW; base < n; base += 2 * nw * S::RW) {
+    if (lane == 0) {
+      const int64_t pb = base + 4 * nw * S::RW;
+      l2_prefetch_rows(Q, n, s, pb, S::RW);
+      l2_prefetch_rows(Q, n, s, pb + nw * S::RW, S::RW);
+      l2_prefetch_rows(R, n, s, pb, S::RW);
+      l2_prefetch_rows(R, n, s, pb + nw * S::RW, S::RW);
+    }
     const int64_t rA = base + rho, rB = base + nw * S::RW + rho;
     const bool okA = (rA < n) && qok, okB = (rB < n) && qok;
     const float4 qA = okA ? ld4(Q + rA * s + 4 * qi) : zero4();
@@ -253,14 +277,14 @@ update4r_kernel(int64_t n, int s, const float* __restrict__ P, const float* __re
     if (okB) st4(R + rB * s + 4 * qi, tB);
     if constexpr (kRho) {
       const float4 gA = okA ? tA : zero4(), gB = okB ? tB : zero4();
-      g.row(gA, gA, stl, stl);
-      g.row(gB, gB, stl, stl);
+      g.row(gA, gA, sp.stl, sp.stl);
+      g.row(gB, gB, sp.stl, sp.stl);
     }
   }
   if constexpr (kRho) {
-    g.cta_reduce(s, true, l2, part);
-    if (!grid_reduce_last(part, cnt, gpart, &ctrl->counters[kCntB])) return;
-    unpack_gram(part, s, true, ctrl->rho_new);
+    g.cta_reduce(s, true, sp.slots, sp.part, sp.stl, sp.stl);
+    if (!grid_reduce_last(sp.part, cnt, gpart, &ctrl->counters[kCntB])) return;
+    unpack_gram(sp.part, s, true, ctrl->rho_new);
   }
 }
 
@@ -280,6 +304,13 @@ pupdate4r_kernel(int64_t n, int s, const float* __restrict__ R, float* __restric
   float4 cf[SW];
   load_coef<SW>(cf, ctrl->beta, s, kMaxS, qi);
   for (int64_t base = gw * S::RW; base < n; base += 2 * nw * S::RW) {
+    if (lane == 0) {
+      const int64_t pb = base + 4 * nw * S::RW;
+      l2_prefetch_rows(P, n, s, pb, S::RW);
+      l2_prefetch_rows(P, n, s, pb + nw * S::RW, S::RW);
+      l2_prefetch_rows(R, n, s, pb, S::RW);
+      l2_prefetch_rows(R, n, s, pb + nw * S::RW, S::RW);
+    }
     const int64_t rA = base + rho, rB = base + nw * S::RW + rho;
     const bool okA = (rA < n) && qok, okB = (rB < n) && qok;
     const float4 pA = okA ? ld4(P + rA * s + 4 * qi) : zero4();
@@ -344,8 +375,7 @@ static cudaError_t update4r_sw(const Launch& L, int64_t n, int s, const float* P
     if ((err = cudaGetLastError()) != cudaSuccess || rho_mode == 0) return err;
   }
   auto k = update4r_kernel<SW, true>;
-  const int cnt = ut_count(s);
-  const size_t sm = sizeof(double) * (size_t)((cnt + 1) & ~1) + sizeof(float) * quad_gram_floats<SW>();
+  const size_t sm = gram_smem_bytes<SW>(ut_count(s));
   const int occ = quad_occupancy(k, sm, &err);
   if (!occ) return err;
   k<<<quad_grid(L, occ, n, 2 * S::RW), kThreads, sm, L.stream>>>(n, s, P, Q, X, R, ctrl, gpart, rho_mode);
@@ -359,16 +389,14 @@ static cudaError_t update4s_sw(const Launch& L, int64_t n, int s, const float* P
   cudaError_t err = cudaSuccess;
   {
     auto k = update4_kernel<SW, false>;
-    const size_t sm = sizeof(double) * 2 + sizeof(float) * (2 * SW * SW + (size_t)kWarps * 2 * S::STAGE);
+    const size_t sm = sizeof(float) * (2 * SW * SW + (size_t)kWarps * 2 * S::STAGE);
     const int occ = quad_occupancy(k, sm, &err);
     if (!occ) return err;
     k<<<quad_grid(L, occ, n, S::RW), kThreads, sm, L.stream>>>(n, s, P, Q, X, R, ctrl, gpart, rho_mode);
     if ((err = cudaGetLastError()) != cudaSuccess || rho_mode == 0) return err;
   }
   auto k = update4_kernel<SW, true>;
-  const int cnt = ut_count(s);
-  const size_t sm = sizeof(double) * (size_t)((cnt + 1) & ~1) +
-                    sizeof(float) * (2 * SW * SW + quad_gram_floats<SW>());
+  const size_t sm = gram_smem_bytes<SW>(ut_count(s), 2 * SW * SW + (size_t)kWarps * 2 * S::STAGE);
   const int occ = quad_occupancy(k, sm, &err);
   if (!occ) return err;
   k<<<quad_grid(L, occ, n, S::RW), kThreads, sm, L.stream>>>(n, s, P, Q, X, R, ctrl, gpart, rho_mode);

@@ -3,16 +3,14 @@
 // every lane owns one quad: LPR = SW/4 lanes per row, RW = 32/LPR rows per
 // warp per trip, so one warp instruction moves 512 contiguous bytes.
 //
-// Block inner products L^T M (Ch. 3.3, BDOT) are accumulated as 4 x 4
-// register blocks: the warp stages its RW rows of both operands in shared
-// memory, then lane (b, g) adds the outer products of Gram block b over the
-// staged rows g, g + G, g + 2G, ...  A lane therefore keeps 16 (s = 32: 32)
-// float accumulators instead of one per Gram column, and every staged value
-// is read with 16-byte shared-memory loads.
+// Block inner products L^T M (Ch. 3.3, BDOT) fused into these kernels are a
+// dense tall-skinny contraction and run on the tensor cores (MmaGram: TF32
+// mma with the three-term split that keeps FP32 accuracy) for SW >= 8; for
+// SW = 4 the row's quads are exchanged by shuffles (RowGram).
 //
-// Precision: each lane sums 32 rows in float registers, adds that window
-// into its own float slot in shared memory, and the slots of all lanes,
-// warps and CTAs are added in double, in a fixed order (bitwise
+// Precision: partial sums are FP32 over windows of at most 32 rows per
+// accumulator (then a second FP32 level), every partial beyond is added in
+// double, and the CTA and grid sums run in a fixed order (bitwise
 // reproducible for a given grid).
 #pragma once
 
@@ -107,99 +105,7 @@ __device__ inline void stage_quad_matrix(float* dst, const double* src, int s) {
   }
 }
 
-template <int SW>
-struct QuadGram {
-  using S = QuadShape<SW>;
-  float acc[S::NBL][16];
-  int trips;
-  float* slot;   // this thread's level-2 slots: slot[e * kThreads]
 
-  __device__ __forceinline__ void init(float* l2) {
-#pragma unroll
-    for (int m = 0; m < S::NBL; ++m)
-#pragma unroll
-      for (int e = 0; e < 16; ++e) acc[m][e] = 0.f;
-    trips = 0;
-    slot = l2 + threadIdx.x;
-#pragma unroll
-    for (int e = 0; e < S::NACC; ++e) slot[e * kThreads] = 0.f;
-  }
-
-  __device__ __forceinline__ void flush() {
-#pragma unroll
-    for (int m = 0; m < S::NBL; ++m)
-#pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        slot[(m * 16 + e) * kThreads] += acc[m][e];
-        acc[m][e] = 0.f;
-      }
-    trips = 0;
-  }
-
-  // Outer products of the warp's staged rows: stl holds the left operand,
-  // stm the right one (RW rows of SW floats each; may be the same buffer).
-  __device__ __forceinline__ void trip(const float* stl, const float* stm) {
-    const int lane = threadIdx.x & 31;
-    const int b0 = S::NB >= 32 ? lane : lane % S::NB;
-    const int g = S::NB >= 32 ? 0 : lane / S::NB;
-#pragma unroll
-    for (int k = 0; k < S::RPL; ++k) {
-      const int rr = g + k * S::G;
-#pragma unroll
-      for (int m = 0; m < S::NBL; ++m) {
-        const int b = b0 + 32 * m;
-        const int bi = b / S::NQ, bj = b % S::NQ;
-        const float4 a = ld4(stl + rr * SW + 4 * bi);
-        const float4 q = ld4(stm + rr * SW + 4 * bj);
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const float at = comp4(a, t);
-          acc[m][4 * t + 0] = fmaf(at, q.x, acc[m][4 * t + 0]);
-          acc[m][4 * t + 1] = fmaf(at, q.y, acc[m][4 * t + 1]);
-          acc[m][4 * t + 2] = fmaf(at, q.z, acc[m][4 * t + 2]);
-          acc[m][4 * t + 3] = fmaf(at, q.w, acc[m][4 * t + 3]);
-        }
-      }
-    }
-    if (++trips == S::TPF) flush();
-  }
-
-  // CTA sums of entry (a, c) for a <= c (sym, packed by ut_index) or all
-  // (a, c) (row-major), in double, into part[0 .. cnt).  Every thread of the
-  // CTA calls this; l2 is the CTA's slot array.
-  __device__ void cta_reduce(int s, bool sym, const float* l2, double* part) {
-    flush();
-    __syncthreads();
-    const int cnt = sym ? ut_count(s) : s * s;
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-      int a, c;
-      if (sym) {
-        c = 0;
-        while ((c + 1) * (c + 2) / 2 <= i) ++c;
-        a = i - c * (c + 1) / 2;
-      } else {
-        a = i / s;
-        c = i - a * s;
-      }
-      const int b = (a / 4) * S::NQ + c / 4, e = (a % 4) * 4 + (c % 4);
-      const int m = S::NB >= 32 ? b / 32 : 0;
-      const int lb = S::NB >= 32 ? b % 32 : b;
-      double t = 0.0;
-      for (int w = 0; w < kWarps; ++w)
-        for (int g = 0; g < S::G; ++g)
-          t += (double)l2[(m * 16 + e) * kThreads + w * 32 + lb + g * S::NB];
-      part[i] = t;
-    }
-    __syncthreads();
-  }
-};
-
-// Shared-memory floats of the Gram machinery: per-warp staging of two
-// operands plus the level-2 slots.
-template <int SW>
-constexpr size_t quad_gram_floats() {
-  return (size_t)kWarps * 2 * QuadShape<SW>::STAGE + (size_t)QuadShape<SW>::NACC * kThreads;
-}
 
 // Quad k of the calling lane's row: the LPR lanes of a row exchange their
 // quads by shuffles (s shuffles per lane for the whole row).
@@ -290,27 +196,19 @@ struct RowGram {
   static constexpr size_t smem_floats() { return (size_t)4 * SW * kThreads; }
 };
 
-// The block Gram with the staging interface of RowGram: row(l, m, stl, stm)
-// stages the lane's quads and adds the warp's trip (used for SW = 32).
-template <int SW>
-struct StagedGram : QuadGram<SW> {
-  using S = QuadShape<SW>;
-  __device__ __forceinline__ void row(const float4& l, const float4& m, float* stl, float* stm) {
-    const int lane = threadIdx.x & 31;
-    const int qi = lane % S::LPR, rho = lane / S::LPR;
-    st4(stl + rho * SW + 4 * qi, l);
-    if (stm != stl) st4(stm + rho * SW + 4 * qi, m);
-    __syncwarp();
-    this->trip(stl, stm);
-    __syncwarp();
-  }
-  static constexpr size_t smem_floats() { return quad_gram_floats<SW>(); }
-};
+// Gram policies share one interface: slot_floats() (CTA-wide slot array),
+// stage_floats() (per warp, two operands), init(slots), row(l, m, stl, stm)
+// once per trip, cta_reduce(s, sym, slots, part, stl, stm).
 
 template <int SW>
 struct RowGramStaged : RowGram<SW> {
+  __host__ __device__ static constexpr size_t slot_floats() { return (size_t)4 * SW * kThreads; }
+  __host__ __device__ static constexpr size_t stage_floats() { return 0; }
   __device__ __forceinline__ void row(const float4& l, const float4& m, float*, float*) {
     RowGram<SW>::row(l, m);
+  }
+  __device__ void cta_reduce(int s, bool sym, const float* slots, double* part, float*, float*) {
+    RowGram<SW>::cta_reduce(s, sym, slots, part);
   }
 };
 
@@ -342,9 +240,195 @@ __device__ __forceinline__ float4 row_times(const float4& mine, const float4 (&c
   return acc;
 }
 
-// Gram policy per width: shuffles for SW <= 8 (at most 32 accumulators),
-// staged 4 x 4 blocks for 16 and 32 (16 or 32 accumulators).
+// Tensor-core Gram (FP32 blocks, SW >= 8): the warp stages k = 8 rows of
+// both operands, and L^T M accumulates through mma.m16n8k8 TF32 tiles (a
+// 16 x 8 tile of the Gram per instruction, FP32 accumulation).  Each FP32
+// operand x is split into x = big + small, big = tf32(x), small =
+// tf32(x - big), and the product is big*big' + big*small' + small*big'
+// (relative error ~ 2^-21 per product, dropped term small*small' <= 2^-22).
+// Tile (mi, nj) covers Gram rows 16 mi .. 16 mi + 15 and columns 8 nj ..
+// 8 nj + 7.  Fragment layout of mma.m16n8k8 (.tf32): with g = lane / 4 and
+// t = lane % 4, A holds (g, t), (g + 8, t), (g, t + 4), (g + 8, t + 4), B
+// holds (t, g), (t + 4, g), C holds (g, 2t), (g, 2t + 1), (g + 8, 2t),
+// (g + 8, 2t + 1).  Windows: the tensor-core accumulators take 32 rows, a
+// float register level takes 32 windows, then double slots in shared memory.
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void mma_tf32(float* d, const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
 template <int SW>
-using GramOf = typename std::conditional<(SW <= 8), RowGramStaged<SW>, StagedGram<SW>>::type;
+struct MmaGram {
+  using S = QuadShape<SW>;
+  static_assert(SW >= 8, "MmaGram needs at least 8 columns");
+  static constexpr int MT = SW >= 16 ? SW / 16 : 1;   // m tiles (SW = 8: rows 8..15 are zero)
+  static constexpr int NT = SW / 8;                    // n tiles
+  static constexpr int NTILE = MT * NT;
+  static constexpr int STR = SW <= 16 ? 24 : 40;       // staged row stride, = 8 or 24 mod 32
+  static constexpr int BUFROWS = S::RW >= 8 ? S::RW : 8;
+  static constexpr int TRIPS_PER_K = S::RW >= 8 ? 1 : 8 / S::RW;
+  static constexpr int KSTEPS = S::RW >= 8 ? S::RW / 8 : 1;
+  static constexpr int WIN1 = 4;                       // k-steps per accumulator window (32 rows)
+  static constexpr int WIN2 = 32;                      // windows per float register level
+  float c[NTILE][4];
+  float c2[NTILE][4];
+  int ks, wins, trip_in_k;
+  double* slot;                                        // slot[e * kThreads], e < 4 NTILE
+
+  __host__ __device__ static constexpr size_t slot_floats() { return (size_t)2 * 4 * NTILE * kThreads; }
+  __host__ __device__ static constexpr size_t stage_floats() { return (size_t)2 * BUFROWS * STR; }   // per warp
+
+  __device__ __forceinline__ void init(float* slots) {
+    slot = reinterpret_cast<double*>(slots) + threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < NTILE; ++i)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) { c[i][e] = 0.f; c2[i][e] = 0.f; slot[(4 * i + e) * kThreads] = 0.0; }
+    ks = 0; wins = 0; trip_in_k = 0;
+  }
+  __device__ __forceinline__ void flush2() {
+#pragma unroll
+    for (int i = 0; i < NTILE; ++i)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) { slot[(4 * i + e) * kThreads] += (double)c2[i][e]; c2[i][e] = 0.f; }
+    wins = 0;
+  }
+  __device__ __forceinline__ void flush1() {
+#pragma unroll
+    for (int i = 0; i < NTILE; ++i)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) { c2[i][e] += c[i][e]; c[i][e] = 0.f; }
+    ks = 0;
+    if (++wins == WIN2) flush2();
+  }
+  // one k-step over staged rows kb .. kb + 7 (row stride STR)
+  __device__ __forceinline__ void kstep(const float* stl, const float* stm, int kb) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    uint32_t bb[NT][2], bs[NT][2];
+#pragma unroll
+    for (int nj = 0; nj < NT; ++nj) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float x = stm[(kb + t + 4 * h) * STR + 8 * nj + g];
+        bb[nj][h] = tf32_of(x);
+        bs[nj][h] = tf32_of(x - __uint_as_float(bb[nj][h]));
+      }
+    }
+#pragma unroll
+    for (int mi = 0; mi < MT; ++mi) {
+      uint32_t ab[4], as[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int row = kb + t + ((e & 2) ? 4 : 0);
+        const int col = 16 * mi + g + ((e & 1) ? 8 : 0);
+        const float x = (col < SW) ? stl[row * STR + col] : 0.f;
+        ab[e] = tf32_of(x);
+        as[e] = tf32_of(x - __uint_as_float(ab[e]));
+      }
+#pragma unroll
+      for (int nj = 0; nj < NT; ++nj) {
+        mma_tf32(c[mi * NT + nj], ab, bb[nj]);
+        mma_tf32(c[mi * NT + nj], ab, bs[nj]);
+        mma_tf32(c[mi * NT + nj], as, bb[nj]);
+      }
+    }
+    if (++ks == WIN1) flush1();
+  }
+  // Stage the lane's quads of this trip's rows (zero for rows past n) into the
+  // warp's buffers stl / stm (BUFROWS x STR floats each; stm may equal stl)
+  // and run the k-steps that became complete.
+  __device__ __forceinline__ void row(const float4& l, const float4& m, float* stl, float* stm) {
+    const int lane = threadIdx.x & 31;
+    const int qi = lane % S::LPR, rho = lane / S::LPR;
+    const int rb = (S::RW >= 8) ? 0 : trip_in_k * S::RW;
+    __syncwarp();                              // the last k-step has read the buffers
+    st4(stl + (rb + rho) * STR + 4 * qi, l);
+    if (stm != stl) st4(stm + (rb + rho) * STR + 4 * qi, m);
+    __syncwarp();
+    if (++trip_in_k == TRIPS_PER_K) {
+      trip_in_k = 0;
+#pragma unroll
+      for (int kk = 0; kk < KSTEPS; ++kk) kstep(stl, stm, 8 * kk);
+    }
+  }
+  // Completes a partial k-step (rows not staged in it are zeroed), then sums
+  // entry (a, c) over the CTA in double into part (ut_index order if sym).
+  __device__ void cta_reduce(int s, bool sym, const float* slots, double* part, float* stl, float* stm) {
+    if constexpr (TRIPS_PER_K > 1) {
+      if (trip_in_k != 0) {
+        const int lane = threadIdx.x & 31;
+        __syncwarp();
+        for (int i = trip_in_k * S::RW * STR + lane; i < 8 * STR; i += 32) {
+          stl[i] = 0.f;
+          stm[i] = 0.f;
+        }
+        __syncwarp();
+        kstep(stl, stm, 0);
+      }
+    }
+    flush1();
+    flush2();
+    __syncthreads();
+    const double* sl = reinterpret_cast<const double*>(slots);
+    const int cnt = sym ? ut_count(s) : s * s;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      int a, cc;
+      if (sym) {
+        cc = 0;
+        while ((cc + 1) * (cc + 2) / 2 <= i) ++cc;
+        a = i - cc * (cc + 1) / 2;
+      } else {
+        a = i / s;
+        cc = i - a * s;
+      }
+      const int tile = (a / 16) * NT + cc / 8;
+      const int r = a % 16, q = cc % 8;
+      const int ln = (r % 8) * 4 + q / 2;
+      const int e = 4 * tile + (r / 8) * 2 + (q % 2);
+      double sum = 0.0;
+      for (int w = 0; w < kWarps; ++w) sum += sl[e * kThreads + w * 32 + ln];
+      part[i] = sum;
+    }
+    __syncthreads();
+  }
+};
+
+// Gram policy per width: tensor cores for SW >= 8, shuffles for SW = 4.
+template <int SW>
+using GramOf = typename std::conditional<(SW >= 8), MmaGram<SW>, RowGramStaged<SW>>::type;
+
+// Dynamic shared memory of a quad kernel with a Gram of cnt packed entries:
+// part (doubles) | slots | per-warp staging; extra_floats follow.
+template <int SW>
+inline size_t gram_smem_bytes(int cnt, size_t extra_floats = 0) {
+  using G = GramOf<SW>;
+  return sizeof(double) * (size_t)((cnt + 1) & ~1) +
+         sizeof(float) * (G::slot_floats() + (size_t)kWarps * G::stage_floats() + extra_floats);
+}
+template <int SW>
+struct GramPtrs {
+  double* part;
+  float* slots;
+  float* stl;
+  float* stm;
+  float* extra;
+  __device__ __forceinline__ GramPtrs(double* smem, int cnt) {
+    using G = GramOf<SW>;
+    part = smem;
+    slots = reinterpret_cast<float*>(smem + ((cnt + 1) & ~1));
+    float* stage = slots + G::slot_floats();
+    stl = stage + (threadIdx.x >> 5) * G::stage_floats();
+    stm = stl + G::stage_floats() / 2;
+    extra = stage + kWarps * G::stage_floats();
+  }
+};
 
 }  // namespace bk

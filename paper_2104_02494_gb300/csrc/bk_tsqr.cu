@@ -138,9 +138,22 @@ leaf_factor(int64_t n, int s, const TIn* __restrict__ X, TIn* __restrict__ Y, do
   const int64_t r0 = (int64_t)blockIdx.x * tile;
   const int m = (int)((n - r0) < tile ? (n - r0) : tile);
   T row[RPT][SW];
+  // FP32 tiles with s % 4 == 0 move their rows as float4 quads
+  constexpr bool kVec = sizeof(TIn) == 4 && sizeof(T) == 4 && SW >= 4;
+  const bool vec = kVec && (s % 4 == 0);
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
     const int g = tid + k * kTT;
+    if constexpr (kVec) {
+      if (vec) {
+#pragma unroll
+        for (int qq = 0; qq < SW / 4; ++qq) {
+          const float4 v = (g < m && 4 * qq < s) ? ld4((const float*)X + (r0 + g) * s + 4 * qq) : zero4();
+          row[k][4 * qq] = v.x; row[k][4 * qq + 1] = v.y; row[k][4 * qq + 2] = v.z; row[k][4 * qq + 3] = v.w;
+        }
+        continue;
+      }
+    }
 #pragma unroll
     for (int c = 0; c < SW; ++c) row[k][c] = (g < m && c < s) ? (T)X[(r0 + g) * s + c] : T(0);
   }
@@ -214,6 +227,16 @@ leaf_factor(int64_t n, int s, const TIn* __restrict__ X, TIn* __restrict__ Y, do
   for (int k = 0; k < RPT; ++k) {
     const int g = tid + k * kTT;
     if (g < m) {
+      if constexpr (kVec) {
+        if (vec) {
+#pragma unroll
+          for (int qq = 0; qq < SW / 4; ++qq)
+            if (4 * qq < s)
+              st4((float*)Y + (r0 + g) * s + 4 * qq,
+                  make_float4(row[k][4 * qq], row[k][4 * qq + 1], row[k][4 * qq + 2], row[k][4 * qq + 3]));
+          continue;
+        }
+      }
 #pragma unroll
       for (int c = 0; c < SW; ++c) if (c < s) Y[(r0 + g) * s + c] = (TIn)row[k][c];
     }
@@ -469,14 +492,12 @@ apply4(int64_t n, int s, int tile_shift, float* __restrict__ Y, const double* __
   const bool qok = 4 * qi < s;
   const bool want_rho = rho_out != nullptr;
   const int cnt = ut_count(s);
-  double* part = smem_d;
-  float* wt = reinterpret_cast<float*>(smem_d + ((cnt + 1) & ~1));
-  float* stage = wt + kWarps * SW * SW;
-  float* l2 = stage + kWarps * 2 * S::STAGE;
-  float* ws = wt + warp * SW * SW;
-  float* stv = stage + warp * 2 * S::STAGE;
-  QuadGram<SW> g;
-  if (want_rho) g.init(l2);
+  const GramPtrs<SW> sp(smem_d, cnt);
+  // extra: per warp the tile's W (SW = 32) and the staged V rows
+  float* ws = sp.extra + warp * (SW * SW + S::STAGE);
+  float* stv = ws + SW * SW;
+  GramOf<SW> g;
+  if (want_rho) g.init(sp.slots);
   // contiguous chunk of this warp, a multiple of RW rows; a trip never
   // straddles a tile (tiles are powers of two >= 256 rows)
   const int64_t nwarps = (int64_t)gridDim.x * kWarps;
@@ -540,16 +561,14 @@ apply4(int64_t n, int s, int tile_shift, float* __restrict__ Y, const double* __
       __syncwarp();
     }
     if (want_rho) {
-      st4(stv + rho * SW + 4 * qi, ok ? y : zero4());
-      __syncwarp();
-      g.trip(stv, stv);
-      __syncwarp();
+      const float4 yy = ok ? y : zero4();
+      g.row(yy, yy, sp.stl, sp.stl);
     }
   }
   if (!want_rho) return;
-  g.cta_reduce(s, true, l2, part);
-  if (!grid_reduce_last(part, cnt, gpart, counter)) return;
-  unpack_gram(part, s, true, rho_out);
+  g.cta_reduce(s, true, sp.slots, sp.part, sp.stl, sp.stl);
+  if (!grid_reduce_last(sp.part, cnt, gpart, counter)) return;
+  unpack_gram(sp.part, s, true, rho_out);
 }
 
 template <int SW>
@@ -558,8 +577,7 @@ static cudaError_t launch_apply4(const Launch& L, int64_t rows, int s, int shift
                                  unsigned* counter, const int* done, const int* flag) {
   auto k = apply4<SW>;
   const int cnt = ut_count(s);
-  const size_t sm = sizeof(double) * (size_t)((cnt + 1) & ~1) +
-                    sizeof(float) * ((size_t)kWarps * SW * SW + quad_gram_floats<SW>());
+  const size_t sm = gram_smem_bytes<SW>(cnt, (size_t)kWarps * (SW * SW + QuadShape<SW>::STAGE));
   cudaError_t err = cudaSuccess;
   const int occ = quad_occupancy(k, sm, &err);
   if (!occ) return err;
