@@ -66,6 +66,14 @@ def parse():
     p.add_argument("--op", default="stencil", choices=["stencil", "csr"])
     p.add_argument("--sweep", action="store_true", help="also time s in {1,4,8,16,32}, stencil and CSR")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--probe", choices=["bcg_fp64", "bcg_fp32_ir"],
+                   help="run one short solve (a target for ncu) on --workload/--grid/--s and exit")
+    p.add_argument("--phases", action="store_true",
+                   help="per-phase device time of FP32+IR and FP64 BCG iterations on --workload")
+    p.add_argument("--micro", action="store_true",
+                   help="stand-alone FP32 operator product and block inner product timings")
+    p.add_argument("--workload", default=None, help="workload of --probe / --phases")
+    p.add_argument("--maxit", type=int, default=3)
     p.add_argument("--ir", action="store_true",
                    help="time-to-1e-10 of FP32+IR vs plain FP64 BCG on the 192^3 log-normal diffusion "
                         "workload (s = 16) instead of the default line")
@@ -268,12 +276,96 @@ def time_iters(h, op, Bd, s, W, K, torch):
     return best
 
 
+def _diag_setup(args, workload, s_default):
+    import torch
+    import workloads as W
+    from paper_2104_02494_gb300 import build
+    from paper_2104_02494_gb300.api import Handle, operator_from_problem
+    build()
+    s = args.s if args.s != 8 or workload == "laplace3d" else s_default
+    prob = W.problem(workload, s=s, grid=args.grid, with_csr=False)
+    h = Handle(0)
+    op = operator_from_problem(h, prob, "stencil")
+    return h, op, prob, torch.from_numpy(prob.B).cuda(), torch
+
+
+def run_probe(args):
+    """One short solve, e.g. as the target of an ncu capture."""
+    wl = args.workload or ("laplace3d" if args.probe == "bcg_fp64" else "vardiff3d")
+    h, op, prob, B, torch = _diag_setup(args, wl, 16)
+    prec = "fp64" if args.probe == "bcg_fp64" else "fp32_ir"
+    X, info = h.solve("bcg", op, B, tol=0.0, maxit=args.maxit, eta=math.inf, prec=prec, ir_max_outer=1,
+                      record=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": args.probe, "workload": wl, "n": prob.B.shape[0], "s": prob.B.shape[1],
+                      "iters": info.iters}))
+
+
+def run_phases(args):
+    """Per-phase device time per launch of FP32+IR (inner) and FP64 BCG iterations."""
+    wl = args.workload or "vardiff3d"
+    h, op, prob, B, torch = _diag_setup(args, wl, 16)
+    out = {"workload": wl, "n": prob.B.shape[0], "s": prob.B.shape[1], "iterations": args.maxit}
+    for prec in ("fp32_ir", "fp64"):
+        for _ in range(2):   # the second run is reported
+            h.profile_reset()
+            X, info = h.solve("bcg", op, B, tol=0.0, maxit=args.maxit, eta=math.inf, prec=prec,
+                              ir_max_outer=1, profile=True, record=False)
+        out[prec] = {nm: {"ms_per_launch": ms / nl, "launches": nl} for nm, ms, nl in h.profile() if nl}
+    print(json.dumps(out))
+
+
+def run_micro(args):
+    """Stand-alone FP32 operator product (no Gram), block inner products and a copy."""
+    import torch
+    import workloads as W
+    from paper_2104_02494_gb300 import build
+    from paper_2104_02494_gb300.api import Handle, operator_from_problem
+    build()
+    h = Handle(0)
+
+    def timeit(fn, reps=20):
+        for _ in range(3):
+            fn()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(); e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record(); torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"grid": args.grid, "hbm_peak_gbs": HBM_PEAK_GBS}
+    for kind, s in (("laplace3d", 8), ("laplace3d", 16), ("laplace3d", 32), ("vardiff3d", 16)):
+        prob = W.problem(kind, s=s, grid=args.grid, with_csr=False)
+        op = operator_from_problem(h, prob, "stencil")
+        n = prob.B.shape[0]
+        P = torch.randn(n, s, device="cuda", dtype=torch.float32)
+        Q = torch.empty_like(P)
+        G = torch.empty(s, s, device="cuda", dtype=torch.float64)
+        by = 4 * n * s
+        r = {"spmm": timeit(lambda: h.spmm(op, P, Q)), "bdot_two_blocks": timeit(lambda: h.bdot(P, Q, G=G)),
+             "bdot_one_block": timeit(lambda: h.bdot(P, P, sym=True, G=G)),
+             "copy": timeit(lambda: Q.copy_(P))}
+        gbs = {"spmm": 2 * by, "bdot_two_blocks": 2 * by, "bdot_one_block": by, "copy": 2 * by}
+        out[f"{kind}_s{s}"] = {k: {"ms": v, "gbs": gbs[k] / (v / 1000.0) / 1e9,
+                                   "hbm_frac": gbs[k] / (v / 1000.0) / 1e9 / HBM_PEAK_GBS}
+                               for k, v in r.items()}
+        op.close()
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.ir:
         return run_ir(args)
+    if args.probe:
+        return run_probe(args)
+    if args.phases:
+        return run_phases(args)
+    if args.micro:
+        return run_micro(args)
     rank, world, dist = dist_init(args)
     import torch
     import workloads as W

@@ -35,29 +35,45 @@ constexpr int quad_min_ctas() { return SW >= 32 ? 2 : 3; }
 
 // Resident CTAs per SM of a kernel at a given dynamic shared memory (capped
 // at kCtasPerSm, the grid-partials budget), cached per device, kernel and
-// shared-memory size; the dynamic shared-memory attribute is set on first use.
+// shared-memory size.  The kernel's dynamic shared-memory limit is an
+// attribute of the kernel, not of a launch: it is only ever raised (to the
+// largest size requested so far), so that every cached size stays valid.
 struct OccEntry {
   int dev;
   const void* kern;
   size_t smem;
   int occ;
 };
+struct AttrEntry {
+  int dev;
+  const void* kern;
+  size_t smem_max;
+};
 
 template <typename K>
 inline int quad_occupancy(K kern, size_t smem, cudaError_t* err) {
   static std::mutex g_occ_mu;
   static std::vector<OccEntry> g_occ;
+  static std::vector<AttrEntry> g_attr;
   int dev = 0;
   if ((*err = cudaGetDevice(&dev)) != cudaSuccess) return 0;
   const void* key = reinterpret_cast<const void*>(kern);
   std::lock_guard<std::mutex> lock(g_occ_mu);
-  for (const OccEntry& e : g_occ)
-    if (e.dev == dev && e.kern == key && e.smem == smem) return e.occ;
+  AttrEntry* at = nullptr;
+  for (AttrEntry& a : g_attr)
+    if (a.dev == dev && a.kern == key) at = &a;
+  if (!at) {
+    g_attr.push_back({dev, key, 0});
+    at = &g_attr.back();
+  }
   // static shared memory counts against the 48 KB default too: always opt in
-  if (smem > 0) {
+  if (smem > at->smem_max) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) { *err = e; return 0; }
+    at->smem_max = smem;
   }
+  for (const OccEntry& e : g_occ)
+    if (e.dev == dev && e.kern == key && e.smem == smem) return e.occ;
   int occ = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
   if (e != cudaSuccess) { *err = e; return 0; }

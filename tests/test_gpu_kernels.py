@@ -145,6 +145,17 @@ def test_bdot_fp32(h, n, s):
             assert np.all(np.abs(G - ref) <= 2e-6 * bound), (n, s)
 
 
+def test_bdot_fp32_widths_sharing_a_kernel_interleaved(h):
+    # s = 12 and s = 16 run the same kernel with different shared memory:
+    # a larger size after a smaller one must still launch
+    g = np.random.default_rng(5)
+    for s in (16, 12, 16, 12, 13, 16):
+        X = g.integers(-4, 4, (5000, s)).astype(np.float32)
+        for sym in (False, True):
+            G = h.bdot(_dev(X), _dev(X), sym=sym).cpu().numpy()
+            assert np.array_equal(G, X.astype(np.float64).T @ X.astype(np.float64)), (s, sym)
+
+
 def test_bdot_fp32_integer_bit_exact(h):
     # small integers: every float product and partial sum is exact
     g = np.random.default_rng(8)
