@@ -74,6 +74,10 @@ def parse():
                    help="stand-alone FP32 operator product and block inner product timings")
     p.add_argument("--workload", default=None, help="workload of --probe / --phases")
     p.add_argument("--maxit", type=int, default=3)
+    p.add_argument("--subalgebra", action="store_true",
+                   help="block-parallel subalgebra S_BP^p: cost per iteration and time to 1e-8 over p")
+    p.add_argument("--tt", action="store_true",
+                   help="time-to-tolerance of every workload's solver (median of 5 after 1 warm-up)")
     p.add_argument("--ir", action="store_true",
                    help="time-to-1e-10 of FP32+IR vs plain FP64 BCG on the 192^3 log-normal diffusion "
                         "workload (s = 16) instead of the default line")
@@ -354,6 +358,83 @@ def run_micro(args):
     print(json.dumps(out))
 
 
+def run_tt(args):
+    """Time to tolerance of the solve call for each workload (device time, CUDA events around
+    the whole solve inside the library; median of 5 runs after 1 warm-up, of 3 for the
+    refinement case)."""
+    import torch
+    import workloads as W
+    from paper_2104_02494_gb300 import build
+    from paper_2104_02494_gb300.api import Handle, operator_from_problem
+    build()
+    h = Handle(0)
+    cases = [
+        ("poisson2d 64^2 5-point CSR, s=4, BCG eta=inf, 1e-8", "poisson2d", "csr", "bcg",
+         dict(tol=1e-8, eta=math.inf)),
+        ("laplace3d 128^3 stencil, s=8, BCG eta=inf, 1e-8", "laplace3d", "stencil", "bcg",
+         dict(tol=1e-8, eta=math.inf)),
+        ("laplace3d 128^3 stencil, s=8, BCG eta=1e4 (adaptive), 1e-8", "laplace3d", "stencil", "bcg",
+         dict(tol=1e-8, eta=1e4)),
+        ("convdiff3d 96^3 upwind stencil, s=8, BBiCGStab eta=100, 1e-8", "convdiff3d", "stencil",
+         "bbicgstab", dict(tol=1e-8, eta=100.0)),
+        ("convdiff3d 96^3 upwind stencil, s=8, BGMRes(30) CGS2 + TSQR, 1e-8", "convdiff3d", "stencil",
+         "bgmres", dict(tol=1e-8, restart=30, ortho="cgs2")),
+        ("vardiff3d 192^3 var7 stencil, s=16, FP32 BCG + FP64 refinement, 1e-10", "vardiff3d", "stencil",
+         "bcg", dict(tol=1e-10, eta=math.inf, prec="fp32_ir")),
+        ("edge2d 512^2 per-edge stencil, s=32, BCG eta=1e4, 1e-8", "edge2d", "stencil", "bcg",
+         dict(tol=1e-8, eta=1e4)),
+    ]
+    out = []
+    for label, wl, use, method, kw in cases:
+        prob = W.problem(wl, with_csr=(use == "csr"))
+        op = operator_from_problem(h, prob, use)
+        B = torch.from_numpy(prob.B).cuda()
+        times, info = [], None
+        nrep = 4 if kw.get("prec") == "fp32_ir" else 6     # the refinement case runs ~15 s
+        for rep in range(nrep):
+            X, info = h.solve(method, op, B, maxit=20000, record=False, **kw)
+            if rep:
+                times.append(info.elapsed_ms)
+        times.sort()
+        out.append({"case": label, "median_ms": times[len(times) // 2], "min_ms": times[0],
+                     "iters": info.iters, "converged": info.converged, "relres_max": info.relres_max,
+                     "n": prob.B.shape[0], "s": prob.B.shape[1]})
+        op.close()
+        del B
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "time to tolerance (solve call, device time)", "unit": "ms",
+                      "results": out}))
+
+
+def run_subalgebra(args):
+    """S_BP^p on the 128^3 Laplacian (stencil, FP64, eta = inf): device time per iteration
+    (20 iterations after 3) and time / iterations to a max-column relative residual of 1e-8,
+    for s in {16, 32} and p from s (the block case S_B) down to 1 (S_P)."""
+    import torch
+    import workloads as W
+    from paper_2104_02494_gb300 import build
+    from paper_2104_02494_gb300.api import Handle, operator_from_problem
+    build()
+    h = Handle(0)
+    out = []
+    for s in (16, 32):
+        prob = W.problem("laplace3d", s=s, grid=args.grid, with_csr=False)
+        op = operator_from_problem(h, prob, "stencil")
+        B = torch.from_numpy(prob.B).cuda()
+        for p in [q for q in (32, 16, 8, 4, 2, 1) if q <= s]:
+            h.solve("bcg", op, B, tol=0.0, maxit=3, eta=math.inf, record=False, p=p)
+            _, i20 = h.solve("bcg", op, B, tol=0.0, maxit=23, eta=math.inf, record=False, p=p)
+            _, i3 = h.solve("bcg", op, B, tol=0.0, maxit=3, eta=math.inf, record=False, p=p)
+            ms_it = (i20.elapsed_ms - i3.elapsed_ms) / 20
+            _, it = h.solve("bcg", op, B, tol=1e-8, maxit=5000, eta=math.inf, record=False, p=p)
+            out.append({"s": s, "p": p, "ms_per_iter": ms_it, "rhs_iter_per_s": s / (ms_it / 1000.0),
+                        "iters_to_1e-8": it.iters, "time_to_1e-8_ms": it.elapsed_ms,
+                        "converged": it.converged})
+        op.close()
+        del B
+    print(json.dumps({"workload": f"laplace3d {args.grid}^3 stencil, FP64, eta=inf", "results": out}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -366,6 +447,10 @@ def main():
         return run_phases(args)
     if args.micro:
         return run_micro(args)
+    if args.tt:
+        return run_tt(args)
+    if args.subalgebra:
+        return run_subalgebra(args)
     rank, world, dist = dist_init(args)
     import torch
     import workloads as W

@@ -92,6 +92,13 @@ typedef struct {
                           CUDA events on the handle's stream (adds one stream
                           synchronisation per iteration); read with
                           bkrylov_profile_get                                      (0)  */
+  int subalgebra_p;    /* BCG only: block size p of the block-parallel *-subalgebra
+                          S_BP^p (Ch. 3.1, Def. "subalgebras"; Ch. 4.3): every s x s
+                          quantity is block diagonal with s/p blocks of p x p, the
+                          normaliser is one Householder QR per p-column group.  0 or s:
+                          the block case S_B; 1: S_P (s scalar CGs sharing the operator
+                          products).  p must divide s; BK_ERR_ARG otherwise, and
+                          BK_ERR_UNSUPPORTED for BBiCGStab and BGMRes with p < s  (0) */
 } bkrylov_opts;
 
 /* Solver report.  Pointer members are HOST arrays supplied by the caller (or NULL). */

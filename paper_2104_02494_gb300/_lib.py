@@ -25,7 +25,7 @@ class bkrylov_opts(C.Structure):
         ("tol", C.c_double), ("maxit", C.c_int), ("eta", C.c_double), ("restart", C.c_int),
         ("ortho", C.c_int), ("prec", C.c_int), ("ir_inner_tol", C.c_double),
         ("ir_max_outer", C.c_int), ("forced_reortho", C.POINTER(C.c_uint8)), ("n_forced", C.c_int),
-        ("sync_every", C.c_int), ("profile", C.c_int),
+        ("sync_every", C.c_int), ("profile", C.c_int), ("subalgebra_p", C.c_int),
     ]
 
 

@@ -170,7 +170,7 @@ class Handle:
     # ---- solvers ----
     def solve(self, method: str, A: "Operator", B, X=None, *, tol=1e-8, maxit=1000, eta=math.inf,
               prec="fp64", restart=30, ortho="cgs2", ir_inner_tol=1e-5, ir_max_outer=30,
-              forced_reortho=None, sync_every=0, record=True, profile=False):
+              forced_reortho=None, sync_every=0, record=True, profile=False, p=None):
         """Run bkrylov_solve_{bcg,bbicgstab,bgmres}; returns (X, SolveInfo).
 
         B, X: float64 n x s blocks, on the device (torch CUDA tensors) or on
@@ -186,6 +186,7 @@ class Handle:
         o.prec = _PREC[prec]
         o.ir_inner_tol, o.ir_max_outer, o.sync_every = float(ir_inner_tol), int(ir_max_outer), int(sync_every)
         o.profile = 1 if profile else 0
+        o.subalgebra_p = 0 if p is None else int(p)
         forced_arr = None
         if forced_reortho is not None:
             forced_arr = (C.c_uint8 * max(1, len(forced_reortho)))(*[1 if f else 0 for f in forced_reortho])

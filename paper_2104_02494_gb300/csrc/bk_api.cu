@@ -109,6 +109,7 @@ int ctrl_upload(bkrylov_handle h, Ctrl* dev, int s, const bkrylov_opts& o, doubl
   c->eta = o.eta;
   c->eps = eps;
   c->n_forced = (o.forced_reortho && o.n_forced > 0) ? o.n_forced : 0;
+  c->sub_p = (o.subalgebra_p > 0 && o.subalgebra_p < s) ? o.subalgebra_p : s;
   for (int i = 0; i < s; ++i) c->sigma[i * kMaxS + i] = 1.0;
   BK_TRY(cudaMemcpyAsync(dev, c, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
   // the pinned staging buffer is reused: wait for the copy before returning
@@ -184,6 +185,29 @@ void bcg_layout(Alloc& a, int64_t n, int s, int maxit, const TsqrPlan& tp, const
   b->dec = dc; b->forced = fc;
 }
 
+// Normaliser of S_BP^p (Def. "normalizer"): one TSQR per p-column group of the
+// n x s block (row stride s), its R factor and Gram into the group's diagonal
+// block of gamma / rho (s x s, row stride 32).  p = s: one TSQR of the block.
+template <typename T>
+cudaError_t tsqr_groups(const Launch& L, const TsqrPlan& tp, int s, T* X, double* gamma, double* rho,
+                        void* scratch, double* gpart, unsigned* counter, const int* done,
+                        const int* flag) {
+  const int p = tp.s;
+  if (p == s) return tsqr<T>(L, tp, X, X, gamma, rho, scratch, gpart, counter, done, flag);
+  // per-phase profiling covers the groups as one normaliser phase
+  Launch Lg = L;
+  Lg.prof = nullptr;
+  prof_begin(L, kPhTsqrLeaf);
+  for (int c0 = 0; c0 < s; c0 += p) {
+    const size_t d = (size_t)c0 * (kMaxS + 1);
+    cudaError_t e = tsqr<T>(Lg, tp, X + c0, X + c0, gamma + d, rho ? rho + d : nullptr, scratch, gpart,
+                            counter, done, flag, s);
+    if (e != cudaSuccess) return e;
+  }
+  prof_end(L, kPhTsqrLeaf, (s / p) * tsqr_launches(tp));
+  return cudaSuccess;
+}
+
 // One BCG-ARO iteration (Alg. "2R-CG"): two grid-wide reductions (alpha with
 // the SpMM, rho with the update or after the normaliser).
 template <typename T>
@@ -194,22 +218,43 @@ cudaError_t bcg_iteration(const Launch& L, const OpDesc& A, int s, T* X, const B
   Epi<T> ep;
   ep.left = b.P; ep.sym = 1; ep.gram_out = c->alpha; ep.gpart = b.gpart;
   ep.counter = &c->counters[kCntA]; ep.done = &c->done;
+  // S_BP^p (tp.s = p < s): the FP64 steps restricted to the column groups
+  const int gp = tp.s;
+  constexpr bool kF64 = sizeof(T) == 8;
   prof_begin(L, kPhSpmm);
-  if ((e = spmm<T>(L, A, s, b.P, b.Q, nullptr, ep)) != cudaSuccess) return e;
+  if constexpr (kF64) {
+    if (gp < s) e = spmm_groups(L, A, s, gp, (const double*)b.P, (double*)b.Q, *(const Epi<double>*)&ep);
+    else e = spmm<T>(L, A, s, b.P, b.Q, nullptr, ep);
+  } else {
+    e = spmm<T>(L, A, s, b.P, b.Q, nullptr, ep);
+  }
+  if (e != cudaSuccess) return e;
   prof_end(L, kPhSpmm, 1);
   prof_begin(L, kPhSmall1);
   if ((e = small_bcg_1(L, c, b.forced)) != cudaSuccess) return e;
   prof_end(L, kPhSmall1, 1);
   prof_begin(L, kPhUpdate);
-  if ((e = bcg_update<T>(L, A.n, s, b.P, b.Q, X, b.R, c, b.gpart, 1)) != cudaSuccess) return e;
+  if constexpr (kF64) {
+    if (gp < s) e = bcg_update_groups(L, A.n, s, gp, (const double*)b.P, (const double*)b.Q, (double*)X,
+                                      (double*)b.R, c, b.gpart, 1);
+    else e = bcg_update<T>(L, A.n, s, b.P, b.Q, X, b.R, c, b.gpart, 1);
+  } else {
+    e = bcg_update<T>(L, A.n, s, b.P, b.Q, X, b.R, c, b.gpart, 1);
+  }
+  if (e != cudaSuccess) return e;
   prof_end(L, kPhUpdate, 2);
-  if ((e = tsqr<T>(L, tp, b.R, b.R, c->gamma, c->rho_new, b.tsqr, b.gpart, &c->counters[kCntC],
-                   &c->done, &c->reortho_now)) != cudaSuccess) return e;
+  if ((e = tsqr_groups<T>(L, tp, s, b.R, c->gamma, c->rho_new, b.tsqr, b.gpart, &c->counters[kCntC],
+                          &c->done, &c->reortho_now)) != cudaSuccess) return e;
   prof_begin(L, kPhSmall2);
   if ((e = small_bcg_2(L, c, b.hist, b.dec)) != cudaSuccess) return e;
   prof_end(L, kPhSmall2, 1);
   prof_begin(L, kPhPupdate);
-  e = bcg_pupdate<T>(L, A.n, s, b.R, b.P, c);
+  if constexpr (kF64) {
+    if (gp < s) e = bcg_pupdate_groups(L, A.n, s, gp, (const double*)b.R, (double*)b.P, c);
+    else e = bcg_pupdate<T>(L, A.n, s, b.R, b.P, c);
+  } else {
+    e = bcg_pupdate<T>(L, A.n, s, b.R, b.P, c);
+  }
   prof_end(L, kPhPupdate, 1);
   return e;
 }
@@ -222,7 +267,9 @@ int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const
                double eps, bkrylov_info* info) {
   const Launch L = launch_of(h);
   const int64_t n = A.n;
-  const TsqrPlan tp = tsqr_plan(n, s, (int)sizeof(T));
+  // S_BP^p normalises p-column groups: the TSQR plan is for width p
+  const int gp = (o.subalgebra_p > 0 && o.subalgebra_p < s) ? o.subalgebra_p : s;
+  const TsqrPlan tp = tsqr_plan(n, gp, (int)sizeof(T));
   const int maxit = o.maxit > 0 ? o.maxit : 0;
   BcgBufs<T> b;
   Bump probe(nullptr, 0);
@@ -249,7 +296,7 @@ int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const
   BK_TRY(gram<T>(L, n, s, b.R, b.R, g));
   BK_TRY(diag_sqrt(L, s, c->rho_new, c->n0));
   if (o.eta > 0) {
-    BK_TRY(tsqr<T>(L, tp, b.R, b.R, c->sigma, nullptr, b.tsqr, b.gpart, nullptr, nullptr, nullptr));
+    BK_TRY(tsqr_groups<T>(L, tp, s, b.R, c->sigma, nullptr, b.tsqr, b.gpart, nullptr, nullptr, nullptr));
   }
   BK_TRY(cudaMemcpyAsync(b.P, b.R, sizeof(T) * (size_t)n * s, cudaMemcpyDeviceToDevice, L.stream));
   g.gram_out = c->rho;
@@ -861,7 +908,13 @@ static int check_solve_args(bkrylov_handle h, bkrylov_op A, int s, const double*
   if (!h || !A || !valid_s(s) || !B || !X || (const void*)B == (const void*)X) return BK_ERR_ARG;
   if (A->d.n < s) return BK_ERR_ARG;
   if (!(o.tol >= 0.0) || o.maxit < 0 || !(o.eta >= 0.0)) return BK_ERR_ARG;
+  if (o.subalgebra_p < 0 || (o.subalgebra_p > 0 && s % o.subalgebra_p != 0)) return BK_ERR_ARG;
   return BK_OK;
+}
+
+// the block-parallel subalgebra is a BCG option
+static bool block_case(const bkrylov_opts& o, int s) {
+  return o.subalgebra_p == 0 || o.subalgebra_p == s;
 }
 
 int bkrylov_solve_bcg(bkrylov_handle h, bkrylov_op A, int s, const double* B, double* X,
@@ -893,6 +946,7 @@ int bkrylov_solve_bbicgstab(bkrylov_handle h, bkrylov_op A, int s, const double*
   opts_or_default(opts, &o);
   int rc = check_solve_args(h, A, s, B, X, o);
   if (rc) return rc;
+  if (!block_case(o, s)) return BK_ERR_UNSUPPORTED;
   if (o.prec != BK_FP64) return BK_ERR_UNSUPPORTED;
   return with_device_blocks(h, A->d.n, s, B, X, 0, [&](const double* dB, double* dX, size_t) {
     return bicg_device(h, A->d, s, dB, dX, o, info);
@@ -905,6 +959,7 @@ int bkrylov_solve_bgmres(bkrylov_handle h, bkrylov_op A, int s, const double* B,
   opts_or_default(opts, &o);
   int rc = check_solve_args(h, A, s, B, X, o);
   if (rc) return rc;
+  if (!block_case(o, s)) return BK_ERR_UNSUPPORTED;
   if (o.prec != BK_FP64) return BK_ERR_UNSUPPORTED;
   if (o.restart < 1 || o.restart > 64) return BK_ERR_ARG;
   return with_device_blocks(h, A->d.n, s, B, X, 0, [&](const double* dB, double* dX, size_t) {

@@ -39,6 +39,7 @@ struct Ctrl {
   int maxit;
   int s;
   int n_forced;
+  int sub_p;         // block size of S_BP^p (s: the block case S_B)
   double tol;
   double eta;
   double eps;        // machine epsilon of the working precision

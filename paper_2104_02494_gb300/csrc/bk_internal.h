@@ -125,6 +125,15 @@ cudaError_t adjoint_scatter(const Launch& L, const OpDesc& A, int s, const doubl
 cudaError_t edge_theta_grad(const Launch& L, const OpDesc& A, int s, const double* Lam,
                             const double* X, double* g);
 
+// ---- block-parallel subalgebra S_BP^p, FP64 (bk_group.cu): the same steps with
+// every s x s coefficient block diagonal (p x p blocks): work O(s p) per row ----
+cudaError_t spmm_groups(const Launch& L, const OpDesc& A, int s, int p, const double* P, double* Q,
+                        const Epi<double>& ep);
+cudaError_t bcg_update_groups(const Launch& L, int64_t n, int s, int p, const double* P, const double* Q,
+                              double* X, double* R, Ctrl* ctrl, double* gpart, int rho_mode);
+cudaError_t bcg_pupdate_groups(const Launch& L, int64_t n, int s, int p, const double* R, double* P,
+                               Ctrl* ctrl);
+
 // ---- TSQR (bk_tsqr.cu) ----
 struct TsqrPlan {
   int64_t n = 0;
@@ -143,9 +152,11 @@ TsqrPlan tsqr_plan(int64_t n, int s, int elem_bytes = 8);
 // If rho_out != null, also the Gram Y^T Y (row stride 32) is produced.
 // done: optional stop flag (skip when *done); reortho_flag: optional, skip unless *flag.
 template <typename T>
+// ld: row stride of X and Y (0: plan.s); a column group of a wider block is
+// normalised with X, Y pointing at its first column and ld = the block width.
 cudaError_t tsqr(const Launch& L, const TsqrPlan& plan, const T* X, T* Y, double* gamma_out,
                  double* rho_out, void* scratch, double* gpart, unsigned* counter,
-                 const int* done, const int* reortho_flag);
+                 const int* done, const int* reortho_flag, int ld = 0);
 
 // ---- small s x s kernels (bk_small.cu) ----
 cudaError_t small_bcg_init(const Launch& L, Ctrl* ctrl, int eta_positive);

@@ -259,6 +259,16 @@ __device__ int decide(Ctrl* c, const uint8_t* forced, const double* A, double* M
   return (c->eta * kap > 1.0 / sqrt(c->eps)) ? 1 : 0;
 }
 
+// Orthogonal projection onto S_BP^p (Def. "subalgebras", Ch. 3.1): entries
+// outside the p x p diagonal blocks become zero (p = s: nothing changes).
+__device__ inline void sm_project(double* M, int s, int p) {
+  if (p >= s) return;
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
+    const int a = i / s, b = i % s;
+    if (a / p != b / p) M[IDX(a, b)] = 0.0;
+  }
+}
+
 struct SmallSmem {
   double A[kMM], B[kMM], C[kMM], D[kMM], E[kMM], F[kMM];
   double rot[4 * (kMaxS + 1)];
@@ -276,6 +286,9 @@ __global__ void __launch_bounds__(kST) small_bcg_init_k(Ctrl* c) {
   sm_copy(S.A, c->rho, s);
   sm_copy(S.B, c->sigma, s);
   __syncthreads();
+  sm_project(S.A, s, c->sub_p);
+  __syncthreads();
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) c->rho[IDX(i / s, i % s)] = S.A[IDX(i / s, i % s)];
   sm_matmul(S.C, S.A, false, S.B, s);     // rho sigma
   __syncthreads();
   if (threadIdx.x < s) {
@@ -305,6 +318,8 @@ __global__ void __launch_bounds__(kST) small_bcg_1_k(Ctrl* c, const uint8_t* for
   sm_copy(S.B, c->rho, s);
   sm_copy(S.E, c->sigma, s);
   __syncthreads();
+  sm_project(S.A, s, c->sub_p);            // S_BP^p: alpha block diagonal
+  __syncthreads();
   if (!sm_all_finite(S.A, s, &S.flag)) { stop(c, BK_NONFINITE); return; }
   sm_copy(S.C, S.A, s);
   __syncthreads();
@@ -333,6 +348,8 @@ __global__ void __launch_bounds__(kST) small_bcg_2_k(Ctrl* c, double* history, u
   sm_copy(S.A, c->rho_new, s);
   sm_copy(S.B, c->sigma, s);
   if (reo) sm_copy(S.C, c->gamma, s); else sm_identity(S.C, s);
+  __syncthreads();
+  sm_project(S.A, s, c->sub_p);            // S_BP^p: rho block diagonal
   __syncthreads();
   if (!sm_all_finite(S.A, s, &S.flag)) { stop(c, BK_NONFINITE); return; }
   sm_matmul(S.D, S.C, false, S.B, s);          // sigma_new = gamma sigma

@@ -125,7 +125,7 @@ __device__ __forceinline__ int warp_reduce_scatter(A (&v)[V]) {
 // (on GB300's narrow FP64 pipe this beats every warp forming them itself).
 template <typename TIn, typename T, int SW, int RPT>
 __global__ void __launch_bounds__(kTT)
-leaf_factor(int64_t n, int s, const TIn* __restrict__ X, TIn* __restrict__ Y, double* __restrict__ R0,
+leaf_factor(int64_t n, int s, int ld, const TIn* __restrict__ X, TIn* __restrict__ Y, double* __restrict__ R0,
             double* __restrict__ T0, const int* done, const int* flag) {
   if (tsqr_skip(done, flag)) return;
   constexpr int tile = kTT * RPT;
@@ -140,7 +140,8 @@ leaf_factor(int64_t n, int s, const TIn* __restrict__ X, TIn* __restrict__ Y, do
   T row[RPT][SW];
   // FP32 tiles with s % 4 == 0 move their rows as float4 quads
   constexpr bool kVec = sizeof(TIn) == 4 && sizeof(T) == 4 && SW >= 4;
-  const bool vec = kVec && (s % 4 == 0);
+  const bool vec = kVec && (s % 4 == 0) && (ld % 4 == 0) &&
+                   ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15) == 0;
 #pragma unroll
   for (int k = 0; k < RPT; ++k) {
     const int g = tid + k * kTT;
@@ -148,14 +149,14 @@ leaf_factor(int64_t n, int s, const TIn* __restrict__ X, TIn* __restrict__ Y, do
       if (vec) {
 #pragma unroll
         for (int qq = 0; qq < SW / 4; ++qq) {
-          const float4 v = (g < m && 4 * qq < s) ? ld4((const float*)X + (r0 + g) * s + 4 * qq) : zero4();
+          const float4 v = (g < m && 4 * qq < s) ? ld4((const float*)X + (r0 + g) * ld + 4 * qq) : zero4();
           row[k][4 * qq] = v.x; row[k][4 * qq + 1] = v.y; row[k][4 * qq + 2] = v.z; row[k][4 * qq + 3] = v.w;
         }
         continue;
       }
     }
 #pragma unroll
-    for (int c = 0; c < SW; ++c) row[k][c] = (g < m && c < s) ? (T)X[(r0 + g) * s + c] : T(0);
+    for (int c = 0; c < SW; ++c) row[k][c] = (g < m && c < s) ? (T)X[(r0 + g) * ld + c] : T(0);
   }
   for (int i = tid; i < SW * SW; i += kTT) Tm[i] = 0.0;
 #pragma unroll
@@ -232,13 +233,13 @@ leaf_factor(int64_t n, int s, const TIn* __restrict__ X, TIn* __restrict__ Y, do
 #pragma unroll
           for (int qq = 0; qq < SW / 4; ++qq)
             if (4 * qq < s)
-              st4((float*)Y + (r0 + g) * s + 4 * qq,
+              st4((float*)Y + (r0 + g) * ld + 4 * qq,
                   make_float4(row[k][4 * qq], row[k][4 * qq + 1], row[k][4 * qq + 2], row[k][4 * qq + 3]));
           continue;
         }
       }
 #pragma unroll
-      for (int c = 0; c < SW; ++c) if (c < s) Y[(r0 + g) * s + c] = (TIn)row[k][c];
+      for (int c = 0; c < SW; ++c) if (c < s) Y[(r0 + g) * ld + c] = (TIn)row[k][c];
     }
   }
   double* Rb = R0 + (size_t)blockIdx.x * s * s;
@@ -278,7 +279,7 @@ __global__ void root_fix(int s, double* __restrict__ Rroot, double* __restrict__
 // tile's factor F.
 template <typename T>
 __global__ void __launch_bounds__(kTT)
-tile_w(int64_t n, int s, int tile, const T* __restrict__ Y, const double* __restrict__ S0,
+tile_w(int64_t n, int s, int ld, int tile, const T* __restrict__ Y, const double* __restrict__ S0,
        double* __restrict__ TW, const int* done, const int* flag) {
   if (tsqr_skip(done, flag)) return;
   __shared__ double Sg[kMM], Tt[kMM], Zm[kMM], V1[kMM];
@@ -289,7 +290,7 @@ tile_w(int64_t n, int s, int tile, const T* __restrict__ Y, const double* __rest
     const int a = i / s, c = i - a * s;
     Sg[a * kMaxS + c] = S0[(size_t)blockIdx.x * s * s + i];
     Tt[a * kMaxS + c] = TW[(size_t)blockIdx.x * s * s + i];
-    V1[a * kMaxS + c] = (c == a) ? 1.0 : ((c < a && a < m) ? (double)Y[(r0 + a) * s + c] : 0.0);
+    V1[a * kMaxS + c] = (c == a) ? 1.0 : ((c < a && a < m) ? (double)Y[(r0 + a) * ld + c] : 0.0);
   }
   __syncthreads();
   for (int i = tid; i < s * s; i += kTT) {          // Z = V_1^T sigma~
@@ -319,7 +320,7 @@ tile_w(int64_t n, int s, int tile, const T* __restrict__ Y, const double* __rest
 // lane c forms column c of Z = V_1^T sigma~ and of W (registers).
 template <typename TIn, int SW>
 __global__ void __launch_bounds__(kThreads)
-tile_w_f32(int64_t n, int s, int tile, int64_t tiles, const TIn* __restrict__ Y,
+tile_w_f32(int64_t n, int s, int ld, int tile, int64_t tiles, const TIn* __restrict__ Y,
            const double* __restrict__ S0, double* __restrict__ TW, const int* done, const int* flag) {
   if (tsqr_skip(done, flag)) return;
   const int lane = threadIdx.x & 31;
@@ -341,7 +342,7 @@ tile_w_f32(int64_t n, int s, int tile, int64_t tiles, const TIn* __restrict__ Y,
 #pragma unroll
     for (int g = a; g < SW; ++g) {
       const float v = (g >= s || a >= s) ? 0.f
-                    : (g == a ? 1.f : (g < m ? (float)Y[(r0 + g) * s + a] : 0.f));
+                    : (g == a ? 1.f : (g < m ? (float)Y[(r0 + g) * ld + a] : 0.f));
       acc = fmaf(v, sig[g], acc);
     }
     z[a] = acc;
@@ -369,7 +370,7 @@ tile_w_f32(int64_t n, int s, int tile, int64_t tiles, const TIn* __restrict__ Y,
 // Y^T Y (upper, mirrored) is accumulated in the same pass when rho_out is given.
 template <typename TIn, typename T, int SW>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (SW >= 32 ? 2 : 4) : 1)
-apply_rows(int64_t n, int s, int tile_shift, TIn* __restrict__ Y, const double* __restrict__ S0,
+apply_rows(int64_t n, int s, int ld, int tile_shift, TIn* __restrict__ Y, const double* __restrict__ S0,
            const double* __restrict__ W, double* rho_out, double* gpart, unsigned* counter,
            const int* done, const int* flag) {
   if (tsqr_skip(done, flag)) return;
@@ -415,7 +416,7 @@ apply_rows(int64_t n, int s, int tile_shift, TIn* __restrict__ Y, const double* 
     const bool ok = (r < hi) && (c < s);
     T v = T(0), y = T(0);
     if (ok) {
-      v = (g < s) ? (c == g ? T(1) : (c < g ? (T)Y[r * s + c] : T(0))) : (T)Y[r * s + c];
+      v = (g < s) ? (c == g ? T(1) : (c < g ? (T)Y[r * ld + c] : T(0))) : (T)Y[r * ld + c];
       if (g < s) y = (T)S0[(size_t)tl * s * s + g * s + c];
     }
 #pragma unroll
@@ -423,7 +424,7 @@ apply_rows(int64_t n, int s, int tile_shift, TIn* __restrict__ Y, const double* 
       const T va = sw_bcast<SW>(v, a);
       y = fma(-va, wcol[a], y);
     }
-    if (ok) Y[r * s + c] = (TIn)y;
+    if (ok) Y[r * ld + c] = (TIn)y;
     return ok ? y : T(0);
   };
   auto accum_row = [&](T yv) {
@@ -481,7 +482,7 @@ apply_rows(int64_t n, int s, int tile_shift, TIn* __restrict__ Y, const double* 
 // as apply_rows for every output.
 template <int SW>
 __global__ void __launch_bounds__(kThreads, 2)
-apply4(int64_t n, int s, int tile_shift, float* __restrict__ Y, const double* __restrict__ S0,
+apply4(int64_t n, int s, int ld, int tile_shift, float* __restrict__ Y, const double* __restrict__ S0,
        const double* __restrict__ W, double* rho_out, double* gpart, unsigned* counter,
        const int* done, const int* flag) {
   if (tsqr_skip(done, flag)) return;
@@ -530,7 +531,7 @@ apply4(int64_t n, int s, int tile_shift, float* __restrict__ Y, const double* __
     const int64_t r = base + rho;
     const int gr = (int)(r & tmask);
     const bool ok = (r < hi) && qok;
-    float4 v = ok ? ld4(Y + r * s + 4 * qi) : zero4();
+    float4 v = ok ? ld4(Y + r * ld + 4 * qi) : zero4();
     float4 y = zero4();
     if (ok && gr < s) {
       // top rows of the tile: V = unit lower triangle there; [sigma~; 0] term
@@ -547,7 +548,7 @@ apply4(int64_t n, int s, int tile_shift, float* __restrict__ Y, const double* __
     if constexpr (kRegW) {
       // y + sum_a (-v_a) w_a: the same roundings as y = fma(-v_a, w_a, y)
       y = row_times<SW>(make_float4(-v.x, -v.y, -v.z, -v.w), cf, y);
-      if (ok) st4(Y + r * s + 4 * qi, y);
+      if (ok) st4(Y + r * ld + 4 * qi, y);
     } else {
       st4(stv + rho * SW + 4 * qi, v);
       __syncwarp();
@@ -557,7 +558,7 @@ apply4(int64_t n, int s, int tile_shift, float* __restrict__ Y, const double* __
 #pragma unroll
         for (int t = 0; t < 4; ++t) y = fma4(-comp4(vk, t), ld4(ws + (4 * k + t) * SW + 4 * qi), y);
       }
-      if (ok) st4(Y + r * s + 4 * qi, y);
+      if (ok) st4(Y + r * ld + 4 * qi, y);
       __syncwarp();
     }
     if (want_rho) {
@@ -572,7 +573,7 @@ apply4(int64_t n, int s, int tile_shift, float* __restrict__ Y, const double* __
 }
 
 template <int SW>
-static cudaError_t launch_apply4(const Launch& L, int64_t rows, int s, int shift, float* Y,
+static cudaError_t launch_apply4(const Launch& L, int64_t rows, int s, int ld, int shift, float* Y,
                                  const double* Rst, const double* Tf, double* rho_out, double* gpart,
                                  unsigned* counter, const int* done, const int* flag) {
   auto k = apply4<SW>;
@@ -582,7 +583,7 @@ static cudaError_t launch_apply4(const Launch& L, int64_t rows, int s, int shift
   const int occ = quad_occupancy(k, sm, &err);
   if (!occ) return err;
   k<<<quad_grid(L, occ, rows, QuadShape<SW>::RW), kThreads, sm, L.stream>>>(
-      rows, s, shift, Y, Rst, Tf, rho_out, gpart, counter, done, flag);
+      rows, s, ld, shift, Y, Rst, Tf, rho_out, gpart, counter, done, flag);
   return cudaGetLastError();
 }
 
@@ -595,27 +596,30 @@ static cudaError_t set_smem(K kern, size_t bytes) {
 // TIn: storage of the tiles (the block's type at level 0, double in the tree);
 // T: arithmetic (the block's precision at every level).
 template <typename TIn, typename T, int SW, int RPT>
-static cudaError_t launch_leaves(const Launch& L, int64_t rows, int s, int64_t tiles, const TIn* X,
-                                 TIn* Y, double* Rst, double* Tf, double* rho_out, double* gpart,
-                                 unsigned* counter, const int* done, const int* flag, bool factor) {
+static cudaError_t launch_leaves(const Launch& L, int64_t rows, int s, int ld, int64_t tiles,
+                                 const TIn* X, TIn* Y, double* Rst, double* Tf, double* rho_out,
+                                 double* gpart, unsigned* counter, const int* done, const int* flag,
+                                 bool factor) {
   if (factor) {
-    leaf_factor<TIn, T, SW, RPT><<<(unsigned)tiles, kTT, 0, L.stream>>>(rows, s, X, Y, Rst, Tf, done, flag);
+    leaf_factor<TIn, T, SW, RPT><<<(unsigned)tiles, kTT, 0, L.stream>>>(rows, s, ld, X, Y, Rst, Tf, done,
+                                                                        flag);
     return cudaGetLastError();
   }
   const int tile = kTT * RPT;
   if constexpr (sizeof(T) == 4) {
     tile_w_f32<TIn, SW><<<(unsigned)((tiles + kWarps - 1) / kWarps), kThreads, 0, L.stream>>>(
-        rows, s, tile, tiles, Y, Rst, Tf, done, flag);
+        rows, s, ld, tile, tiles, Y, Rst, Tf, done, flag);
   } else {
-    tile_w<TIn><<<(unsigned)tiles, kTT, 0, L.stream>>>(rows, s, tile, Y, Rst, Tf, done, flag);
+    tile_w<TIn><<<(unsigned)tiles, kTT, 0, L.stream>>>(rows, s, ld, tile, Y, Rst, Tf, done, flag);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int shift = 0;
   while ((1 << shift) < tile) ++shift;
   if constexpr (sizeof(TIn) == 4 && sizeof(T) == 4 && SW >= 4) {
-    if (s % 4 == 0)
-      return launch_apply4<SW>(L, rows, s, shift, Y, Rst, Tf, rho_out, gpart, counter, done, flag);
+    // the quad layout needs 16-byte aligned rows
+    if (s % 4 == 0 && ld % 4 == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0)
+      return launch_apply4<SW>(L, rows, s, ld, shift, Y, Rst, Tf, rho_out, gpart, counter, done, flag);
   }
   const int cnt = ut_count(s);
   const size_t lanes = (sizeof(T) == 4) ? (size_t)kThreads * lacc_stride(SW) : 0;
@@ -626,22 +630,23 @@ static cudaError_t launch_leaves(const Launch& L, int64_t rows, int s, int64_t t
   const int64_t cap = (int64_t)L.sms * kCtasPerSm;
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
-  k<<<(unsigned)grid, kThreads, sm, L.stream>>>(rows, s, shift, Y, Rst, Tf, rho_out, gpart, counter,
-                                                 done, flag);
+  k<<<(unsigned)grid, kThreads, sm, L.stream>>>(rows, s, ld, shift, Y, Rst, Tf, rho_out, gpart,
+                                                 counter, done, flag);
   return cudaGetLastError();
 }
 
 // Level 0 tiles hold leaf_rpt rows per thread; the tree levels (stacked R
 // factors, few rows) use one row per thread so that more CTAs share the work.
 template <typename TIn, typename T>
-static cudaError_t leaves(const Launch& L, int64_t rows, int s, int64_t tiles, const TIn* X, TIn* Y,
+static cudaError_t leaves(const Launch& L, int64_t rows, int s, int ld, int64_t tiles, const TIn* X,
+                          TIn* Y,
                           double* Rst, double* Tf, double* rho_out, double* gpart, unsigned* counter,
                           const int* done, const int* flag, bool factor, bool bottom) {
 #define BK_LEAVES(SWV)                                                                                 \
-  return bottom ? launch_leaves<TIn, T, SWV, leaf_rpt(SWV, sizeof(T))>(L, rows, s, tiles, X, Y, Rst,   \
-                                                                      Tf, rho_out, gpart, counter,    \
-                                                                      done, flag, factor)             \
-                : launch_leaves<TIn, T, SWV, 1>(L, rows, s, tiles, X, Y, Rst, Tf, rho_out, gpart,      \
+  return bottom ? launch_leaves<TIn, T, SWV, leaf_rpt(SWV, sizeof(T))>(L, rows, s, ld, tiles, X, Y,   \
+                                                                      Rst, Tf, rho_out, gpart,        \
+                                                                      counter, done, flag, factor)    \
+                : launch_leaves<TIn, T, SWV, 1>(L, rows, s, ld, tiles, X, Y, Rst, Tf, rho_out, gpart,  \
                                                 counter, done, flag, factor)
   switch (next_pow2_s(s)) {
     case 1: BK_LEAVES(1);
@@ -666,35 +671,37 @@ int tsqr_launches(const TsqrPlan& p) { return 2 * (p.levels + 1) + 1; }
 template <typename T>
 cudaError_t tsqr(const Launch& L, const TsqrPlan& p, const T* X, T* Y, double* gamma_out,
                  double* rho_out, void* scratch, double* gpart, unsigned* counter, const int* done,
-                 const int* flag) {
+                 const int* flag, int ld) {
   const int s = p.s;
+  if (ld <= 0) ld = s;
+  if (ld < s) return cudaErrorInvalidValue;
   TsqrPtrs q = tsqr_ptrs(p, scratch);
   cudaError_t e;
   if (rho_out && !counter) return cudaErrorInvalidValue;
   prof_begin(L, kPhTsqrLeaf);
-  if ((e = leaves<T, T>(L, p.n, s, p.nodes[0], X, Y, q.R[0], q.Tf[0], nullptr, nullptr, nullptr, done,
-                        flag, true, true)) != cudaSuccess) return e;
+  if ((e = leaves<T, T>(L, p.n, s, ld, p.nodes[0], X, Y, q.R[0], q.Tf[0], nullptr, nullptr, nullptr,
+                        done, flag, true, true)) != cudaSuccess) return e;
   prof_end(L, kPhTsqrLeaf, 1);
   prof_begin(L, kPhTsqrTree);
   for (int l = 1; l <= p.levels; ++l)
-    if ((e = leaves<double, T>(L, p.rows[l], s, p.nodes[l], q.R[l - 1], q.R[l - 1], q.R[l], q.Tf[l],
+    if ((e = leaves<double, T>(L, p.rows[l], s, s, p.nodes[l], q.R[l - 1], q.R[l - 1], q.R[l], q.Tf[l],
                                nullptr, nullptr, nullptr, done, flag, true, false)) != cudaSuccess) return e;
   root_fix<<<1, 256, 0, L.stream>>>(s, q.R[p.levels], gamma_out, done, flag);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (int l = p.levels; l >= 1; --l)
-    if ((e = leaves<double, T>(L, p.rows[l], s, p.nodes[l], nullptr, q.R[l - 1], q.R[l], q.Tf[l],
+    if ((e = leaves<double, T>(L, p.rows[l], s, s, p.nodes[l], nullptr, q.R[l - 1], q.R[l], q.Tf[l],
                                nullptr, nullptr, nullptr, done, flag, false, false)) != cudaSuccess) return e;
   prof_end(L, kPhTsqrTree, 2 * p.levels + 1);
   prof_begin(L, kPhTsqrApply);
-  e = leaves<T, T>(L, p.n, s, p.nodes[0], nullptr, Y, q.R[0], q.Tf[0], rho_out, gpart, counter, done,
-                   flag, false, true);
+  e = leaves<T, T>(L, p.n, s, ld, p.nodes[0], nullptr, Y, q.R[0], q.Tf[0], rho_out, gpart, counter,
+                   done, flag, false, true);
   prof_end(L, kPhTsqrApply, 1);
   return e;
 }
 
 template cudaError_t tsqr<double>(const Launch&, const TsqrPlan&, const double*, double*, double*,
-                                  double*, void*, double*, unsigned*, const int*, const int*);
+                                  double*, void*, double*, unsigned*, const int*, const int*, int);
 template cudaError_t tsqr<float>(const Launch&, const TsqrPlan&, const float*, float*, double*,
-                                 double*, void*, double*, unsigned*, const int*, const int*);
+                                 double*, void*, double*, unsigned*, const int*, const int*, int);
 
 }  // namespace bk

@@ -212,6 +212,37 @@ def test_bgmres_convdiff(h, ortho):
     op.close()
 
 
+@pytest.mark.parametrize("eta", [math.inf, 0.0])
+@pytest.mark.parametrize("s,p,use", [(8, 1, "stencil"), (8, 2, "csr"), (8, 4, "stencil"),
+                                     (12, 4, "stencil"), (32, 8, "stencil"), (6, 3, "csr")])
+def test_bcg_block_parallel_subalgebra(h, s, p, use, eta):
+    """S_BP^p (block-diagonal s x s quantities, one normaliser per p-column
+    group): GPU iterates against the oracle's, FP64, 1e-12."""
+    prob = W.problem("laplace3d", s=s, grid=14)
+    op = _op(h, prob, use)
+    ref = oracle.bcg(prob.A, prob.B, tol=1e-8, maxit=400, eta=eta, p=p, record_iterates=20)
+    for k in (1, 3, 10, 20):
+        Xk, info = _gpu_iterate(h, "bcg", op, prob.B, k, eta=eta, p=p)
+        assert _rel(Xk, ref.iterates[k - 1]) <= 1e-12, (k, _rel(Xk, ref.iterates[k - 1]))
+    X, info = h.solve("bcg", op, _dev(prob.B), tol=1e-8, maxit=400, eta=eta, p=p)
+    assert info.converged and ref.converged and abs(info.iters - ref.iters) <= 2
+    op.close()
+
+
+def test_block_parallel_subalgebra_fp32_ir_and_errors(h):
+    from paper_2104_02494_gb300.api import BkError
+    prob = W.problem("vardiff3d", s=16, grid=12)
+    op = _op(h, prob, "stencil")
+    X, info = h.solve("bcg", op, _dev(prob.B), tol=1e-10, maxit=5000, prec="fp32_ir", p=4)
+    true = oracle.col_norms(prob.B - oracle.spmm(prob.A, X.cpu().numpy())) / oracle.col_norms(prob.B)
+    assert info.converged and true.max() <= 1e-10
+    with pytest.raises(BkError):                 # p must divide s
+        h.solve("bcg", op, _dev(prob.B), tol=1e-8, maxit=10, p=5)
+    with pytest.raises(BkError):                 # BCG only
+        h.solve("bbicgstab", op, _dev(prob.B), tol=1e-8, maxit=10, p=4)
+    op.close()
+
+
 @pytest.mark.parametrize("s", [4, 6, 8, 12, 16, 32])
 @pytest.mark.parametrize("eta", [math.inf, 0.0])
 def test_fp32_inner_bcg_iterates(h, s, eta):

@@ -86,6 +86,24 @@ def test_parallel_subalgebra_equals_independent_scalar_cgs():
             assert rel <= 1e-12
 
 
+@pytest.mark.parametrize("eta", [0.0, math.inf])
+@pytest.mark.parametrize("s,p", [(4, 2), (6, 3), (8, 4)])
+def test_block_parallel_subalgebra_equals_independent_group_solves(s, p, eta):
+    """S_BP^p (Def. "subalgebras"): every s x s quantity is block diagonal, so
+    the solve splits into s/p independent block-CG solves on the p-column
+    groups of B, each in the block case S_B with block size p (the operator
+    products are shared, the arithmetic is not)."""
+    A = W.lap2d5(11, 9)
+    B = W.normal_block(A.n, s, 6)
+    r = oracle.bcg(A, B, tol=1e-10, maxit=200, eta=eta, p=p, record_iterates=12)
+    for c0 in range(0, s, p):
+        g = oracle.bcg(A, B[:, c0:c0 + p], tol=1e-10, maxit=200, eta=eta, record_iterates=12)
+        for k in range(min(12, len(g.iterates), len(r.iterates))):
+            ref = g.iterates[k]
+            rel = np.abs(r.iterates[k][:, c0:c0 + p] - ref).max() / np.abs(ref).max()
+            assert rel <= 1e-12, (c0, k, rel)
+
+
 def test_bcg_chebyshev_bound():
     A = W.lap2d5(16, 16)
     Ad = A.to_dense()
