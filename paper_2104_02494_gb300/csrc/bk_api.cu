@@ -27,6 +27,7 @@ struct bkrylov_ctx {
   size_t ws_cap[2] = {0, 0};
   Ctrl* host_ctrl = nullptr;          // pinned staging of the control block
   Prof prof;                          // per-phase timing of profiled solves
+  cudaStream_t cap_stream = nullptr;  // private stream for capturing iteration graphs (lazy)
 };
 
 const char* const bk::kPhaseNames[kNumPhases] = {
@@ -259,6 +260,37 @@ cudaError_t bcg_iteration(const Launch& L, const OpDesc& A, int s, T* X, const B
   return e;
 }
 
+// A batch of solver iterations captured as one CUDA graph (destroyed with the
+// object).  capture(h, k, step) records k calls of step(Launch) on the
+// handle's private capture stream; nothing runs until the graph is launched.
+struct GraphBatch {
+  cudaGraphExec_t exec = nullptr;
+  bool failed = false;
+  ~GraphBatch() { if (exec) cudaGraphExecDestroy(exec); }
+  template <typename Step>
+  int capture(bkrylov_handle h, int k, Step step) {
+    if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return BK_ERR_CUDA;
+    Launch Lc;
+    Lc.stream = h->cap_stream;
+    Lc.sms = h->sms;
+    if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) return BK_ERR_CUDA;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < k && e == cudaSuccess; ++i) e = step(Lc);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &g);
+    if (e != cudaSuccess || ee != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();          // clear the capture error; nothing was enqueued
+      return BK_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { exec = nullptr; return BK_ERR_CUDA; }
+    return BK_OK;
+  }
+};
+
 // launches of one iteration (the TSQR tree has 2 * levels + 1 launches)
 int bcg_launches_per_iter(const TsqrPlan& tp) { return 6 + tsqr_launches(tp); }
 
@@ -305,14 +337,30 @@ int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const
   Launch Lp = L;
   if (o.profile) Lp.prof = &h->prof;
   int batch = o.sync_every > 0 ? o.sync_every : (n >= (1 << 20) ? 4 : 16);
+  // Small problems are bound by kernel launches: after the first batch (which
+  // also settles every kernel's launch attributes), a batch of iterations is
+  // captured once as a CUDA graph on a private stream and replayed on the
+  // handle's stream.  The iteration has no host-side branch (every decision is
+  // in the control block), so the replay is the same kernel sequence.
+  const bool use_graph = !o.profile && (size_t)n * s <= ((size_t)1 << 20) && maxit > 2 * batch;
+  GraphBatch gb;
   int enq = 0;
   while (true) {
     if ((rc = ctrl_peek(h, c))) return rc;
     if (h->host_ctrl->done != kDoneRunning || enq >= maxit) break;
     const int todo = (maxit - enq) < batch ? (maxit - enq) : batch;
-    for (int i = 0; i < todo; ++i) {
-      BK_TRY(bcg_iteration<T>(Lp, A, s, X, b, tp));
-      prof_collect(Lp.prof);
+    if (use_graph && !gb.failed && enq > 0 && todo == batch && !gb.exec) {
+      // a capture that the runtime refuses leaves the direct launches below in charge
+      if (gb.capture(h, batch, [&](const Launch& Lc) { return bcg_iteration<T>(Lc, A, s, X, b, tp); }))
+        gb.failed = true;
+    }
+    if (gb.exec && todo == batch) {
+      BK_TRY(cudaGraphLaunch(gb.exec, L.stream));
+    } else {
+      for (int i = 0; i < todo; ++i) {
+        BK_TRY(bcg_iteration<T>(Lp, A, s, X, b, tp));
+        prof_collect(Lp.prof);
+      }
     }
     enq += todo;
   }
@@ -716,6 +764,7 @@ int bkrylov_destroy(bkrylov_handle h) {
     if (h->prof.e[i]) cudaEventDestroy(h->prof.e[i]);
   }
   if (h->own_stream) cudaStreamDestroy(h->stream);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
   return BK_OK;
 }

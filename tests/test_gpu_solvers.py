@@ -122,6 +122,20 @@ def test_bcg_full_size_laplace_first_iterates(h):
     op.close()
 
 
+def test_bcg_graph_replay_equals_direct_launches(h):
+    """Small problems replay captured batches of iterations (CUDA graph); a
+    profiled solve launches every kernel directly: bitwise the same X."""
+    prob = W.problem("poisson2d")                       # 64^2, s = 4
+    op = _op(h, prob, "csr")
+    Xg, ig = h.solve("bcg", op, _dev(prob.B), tol=1e-8, maxit=1000)
+    Xd, idr = h.solve("bcg", op, _dev(prob.B), tol=1e-8, maxit=1000, profile=True)
+    assert ig.iters == idr.iters and ig.iters > 40
+    assert np.array_equal(Xg.cpu().numpy(), Xd.cpu().numpy())
+    ref = oracle.bcg(prob.A, prob.B, tol=1e-8, maxit=1000, eta=math.inf)
+    assert abs(ig.iters - ref.iters) <= 2
+    op.close()
+
+
 def test_bcg_host_buffers_equal_device(h):
     prob = W.problem("poisson2d", s=4, grid=40)
     op = _op(h, prob, "csr")
