@@ -20,7 +20,8 @@ they are used.
 
 Parity pins (checked by ``tests/test_oracle_*.py`` without a GPU): dense direct
 solves, closed-form eigenvalues, LAPACK QR after sign fixing, Galerkin and
-A-conjugacy invariants, block CG at s = 1 against textbook scalar CG, finite
+A-conjugacy invariants, block CG at s = 1 against textbook scalar CG (and preconditioned CG),
+the energy minimisation over the preconditioned block Krylov space, finite
 termination in ceil(n/s) steps, the Chebyshev error bound, BGMRes monotone
 residuals, finite differences for the adjoint.  Functions without such a pin
 are marked "parity unpinned" in their docstring (none at present).
@@ -32,11 +33,12 @@ from .bbicgstab import bbicgstab
 from .bgmres import bgmres
 from .tsqr import tsqr
 from .ir import bcg_ir
+from .precond import jacobi_inverse_diagonal, apply_diagonal
 from .adjoint import dense_adjoint, adjoint_scatter, edge_theta_grad
 
 __all__ = [
     "spmm", "gram", "householder_qr", "normalizer", "kappa_d", "chol_solve", "lu_solve",
     "col_norms", "reortho_decision", "project_subalgebra", "bcg", "scalar_cg",
     "BCGResult", "bbicgstab", "bgmres", "tsqr", "bcg_ir", "dense_adjoint",
-    "adjoint_scatter", "edge_theta_grad",
+    "adjoint_scatter", "edge_theta_grad", "jacobi_inverse_diagonal", "apply_diagonal",
 ]

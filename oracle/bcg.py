@@ -2,7 +2,8 @@
 
 ``bcg`` follows Alg. "bcgaro" (BCG-ARO, Ch. 4.3) in the grouping of
 Alg. "2R-CG" (Ch. 8.1), which the thesis states is arithmetically identical.
-M = I throughout (no preconditioner), so Z = R-bar.
+The preconditioner M is optional (M = I when none is given, so Z = R-bar):
+Z = M^{-1} R-bar, rho = <Z, R-bar>, P = Z + P beta (Alg. "bcgaro").
 
 Readings (the thesis is silent or ambiguous here):
   * residual R = B - A X (the algorithms' sign; Ch. 4.1);
@@ -12,7 +13,8 @@ Readings (the thesis is silent or ambiguous here):
   * re-orthonormalisation criterion: see ``blockops.reortho_decision``;
   * ||R_i|| = ||R-bar sigma_i||: with re-orthonormalisation this is the column
     norm of sigma (the thesis prints Q^k, meaning R-bar^k); without it,
-    sqrt((sigma^T rho sigma)_ii), which needs no extra pass since M = I;
+    sqrt((sigma^T G sigma)_ii) with the Euclidean Gram G = R-bar^T R-bar, which
+    is rho when M = I and a Gram of its own otherwise (rho = R-bar^T M^{-1} R-bar);
   * beta = rho_k^{-1} gamma^T rho_{k+1} as printed in Alg. "bcgro";
   * alpha and rho are formed as upper triangles and mirrored;
   * breakdown (Cholesky of alpha or rho fails) stops with the current X.
@@ -28,6 +30,7 @@ import numpy as np
 
 from .blockops import (Breakdown, chol_solve, col_norms, gram, kappa_d, normalizer,
                        project_subalgebra, reortho_decision, spmm)
+from .precond import apply_diagonal
 
 
 @dataclass
@@ -45,8 +48,8 @@ class BCGResult:
 
 def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit: int = 1000,
         eta: float = math.inf, p: int | None = None, forced=None, record_iterates: int = 0,
-        dtype=np.float64, eps: float | None = None, apply_A=None) -> BCGResult:
-    """Alg. "bcgaro" (2R grouping, Alg. "2R-CG") for A X = B, M = I.
+        dtype=np.float64, eps: float | None = None, apply_A=None, Minv=None) -> BCGResult:
+    """Alg. "bcgaro" (2R grouping, Alg. "2R-CG") for A X = B.
 
     A: CSR (attributes n, row_ptr, col, val) or None when ``apply_A`` is given.
     p: block size of the *-subalgebra S_BP^p (None or s: block case S_B).
@@ -54,12 +57,21 @@ def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit
         in iteration k (used to replay another implementation's decisions).
     dtype: arithmetic of the n x s blocks (float32 for the inner solve of
         iterative refinement); all s x s quantities stay float64.
+    Minv: the preconditioner M^{-1}: None (M = I), a vector (a diagonal
+        M^{-1}, e.g. ``precond.jacobi_inverse_diagonal(A)``) or a callable
+        V -> M^{-1} V.  M must be symmetric positive definite (Ch. 4).
     """
     B = np.asarray(B)
     n, s = B.shape
     if eps is None:
         eps = float(np.finfo(dtype).eps)
     op = apply_A if apply_A is not None else (lambda V: spmm(A, V, dtype=dtype))
+    if Minv is None:
+        prec = None
+    elif callable(Minv):
+        prec = lambda V: np.asarray(Minv(V), dtype=dtype)
+    else:
+        prec = lambda V: apply_diagonal(Minv, V, dtype)
     X = np.zeros((n, s), dtype=dtype) if X0 is None else np.array(X0, dtype=dtype, copy=True)
     B = B.astype(dtype, copy=False)
 
@@ -71,9 +83,13 @@ def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit
         Rb = Rb.astype(dtype)
     else:
         Rb, sigma = R, np.eye(s)
-    P = Rb.copy()
-    rho = gram(Rb, Rb, p)
-    res = _resid_from(sigma, rho, p, reortho=False)
+    G = gram(Rb, Rb, p)                 # Euclidean R-bar^T R-bar
+    if prec is None:
+        P, rho = Rb.copy(), G
+    else:
+        P = prec(Rb)                    # P^0 = M^{-1} R-bar^0
+        rho = gram(P, Rb, p)            # rho^0 = <P^0, R-bar^0>
+    res = _resid_from(sigma, G, p, reortho=False)
     relres = np.where(n0 > 0, res / n0_safe, 0.0)
     out = BCGResult(X, 0, 0, bool(relres.max(initial=0.0) <= tol), "ok", relres)
     if out.converged:
@@ -100,8 +116,8 @@ def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit
             out.reorths += 1
         else:
             Rb, gamma = Rt, np.eye(s)
-        rho_new = gram(Rb, Rb, p)
-        res = _resid_from(sigma, rho_new, p, reortho=reo)
+        G = None if reo else gram(Rb, Rb, p)
+        res = _resid_from(sigma, G, p, reortho=reo)
         relres = np.where(n0 > 0, res / n0_safe, 0.0)
         out.history.append(float(relres.max(initial=0.0)))
         out.decisions.append(reo)
@@ -112,53 +128,68 @@ def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit
         if relres.max(initial=0.0) <= tol:
             out.converged = True
             return out
+        if prec is None:
+            Z = Rb
+            rho_new = G if G is not None else gram(Rb, Rb, p)
+        else:
+            Z = prec(Rb)                # Z^{k+1} = M^{-1} R-bar^{k+1}
+            rho_new = gram(Z, Rb, p)    # rho^{k+1} = <Z^{k+1}, R-bar^{k+1}>
         try:
             beta = chol_solve(rho, gamma.T @ rho_new)
         except Breakdown:
             out.status = "breakdown"; return out
         beta = project_subalgebra(beta, p)
-        P = Rb + P @ beta.astype(dtype)
+        P = Z + P @ beta.astype(dtype)
         rho = rho_new
     out.status = "not_converged"
     return out
 
 
-def _resid_from(sigma, rho, p, reortho):
-    """Column norms of the true residual R = R-bar sigma (Ch. 4.3, after Alg. "bcgro")."""
+def _resid_from(sigma, G, p, reortho):
+    """Column norms of the true residual R = R-bar sigma (Ch. 4.3, after Alg. "bcgro").
+
+    G is the Euclidean Gram R-bar^T R-bar (unused after a re-orthonormalisation,
+    where R-bar has orthonormal columns)."""
     if reortho:
         return col_norms(sigma)
-    M = project_subalgebra(sigma.T @ rho @ sigma, p)
+    M = project_subalgebra(sigma.T @ G @ sigma, p)
     return np.sqrt(np.maximum(np.diag(M), 0.0))
 
 
 def scalar_cg(A, b: np.ndarray, x0=None, tol: float = 1e-8, maxit: int = 1000,
-              record_iterates: int = 0, apply_A=None):
-    """Textbook conjugate gradients for one right-hand side (Ch. 2, Hestenes-Stiefel).
+              record_iterates: int = 0, apply_A=None, minv=None):
+    """Textbook (preconditioned) conjugate gradients for one right-hand side (Ch. 2).
 
-    Independent of ``bcg``: scalar step lengths r.r / p.Ap and r'.r' / r.r,
-    stopping on ||r|| / ||r0|| <= tol.  Returns (x, iters, history, iterates).
+    Independent of ``bcg``: Hestenes-Stiefel with z = M^{-1} r, step length
+    r.z / p.Ap and direction update z' + (r'.z' / r.z) p (M = I when ``minv``,
+    the diagonal of M^{-1}, is None), stopping on ||r|| / ||r0|| <= tol.
+    Returns (x, iters, history, iterates).
     """
     op = apply_A if apply_A is not None else (lambda v: spmm(A, v[:, None])[:, 0])
+    pre = (lambda v: v) if minv is None else (lambda v: np.asarray(minv, dtype=np.float64) * v)
     b = np.asarray(b, dtype=np.float64)
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
     r = b - op(x)
-    p = r.copy()
-    rr = float(r @ r)
-    r0 = math.sqrt(rr)
+    z = pre(r)
+    p = z.copy()
+    rz = float(r @ z)
+    r0 = math.sqrt(float(r @ r))
     hist, its = [], []
     if r0 == 0:
         return x, 0, hist, its
     for k in range(maxit):
         q = op(p)
-        a = rr / float(p @ q)
+        a = rz / float(p @ q)
         x = x + a * p
         r = r - a * q
-        rr_new = float(r @ r)
-        hist.append(math.sqrt(rr_new) / r0)
+        rn = math.sqrt(float(r @ r))
+        hist.append(rn / r0)
         if k < record_iterates:
             its.append(x.copy())
-        if math.sqrt(rr_new) / r0 <= tol:
+        if rn / r0 <= tol:
             return x, k + 1, hist, its
-        p = r + (rr_new / rr) * p
-        rr = rr_new
+        z = pre(r)
+        rz_new = float(r @ z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
     return x, maxit, hist, its

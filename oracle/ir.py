@@ -40,7 +40,8 @@ class IRResult:
 
 
 def bcg_ir(A, B: np.ndarray, tol: float = 1e-10, inner_tol: float = 1e-5, max_outer: int = 20,
-           inner_maxit: int = 5000, eta: float = math.inf) -> IRResult:
+           inner_maxit: int = 5000, eta: float = math.inf, Minv=None) -> IRResult:
+    """Refinement loop above; ``Minv`` (optional, see ``bcg``) preconditions the inner solve."""
     B = np.asarray(B, dtype=np.float64)
     n, s = B.shape
     X = np.zeros((n, s))
@@ -58,7 +59,8 @@ def bcg_ir(A, B: np.ndarray, tol: float = 1e-10, inner_tol: float = 1e-5, max_ou
             break
         scale = np.where(nr > 0, nr, 1.0)
         Rs = (R / scale[None, :]).astype(np.float32)
-        inner = bcg(A, Rs, tol=inner_tol, maxit=inner_maxit, eta=eta, dtype=np.float32)
+        inner = bcg(A, Rs, tol=inner_tol, maxit=inner_maxit, eta=eta, dtype=np.float32,
+                    Minv=Minv)
         out.inner_iters.append(inner.iters)
         X += inner.X.astype(np.float64) * scale[None, :]
         out.outer = it + 1

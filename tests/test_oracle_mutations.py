@@ -73,6 +73,25 @@ def _bcg_battery_passes(bcg_fn):
         for k in range(20):
             if np.abs(r.iterates[k][:, 0] - xs[k]).max() > 1e-12 * np.abs(xs[k]).max():
                 return False
+        # Jacobi-preconditioned: the energy minimiser over K_k(M^{-1}A, M^{-1}R^0)
+        # (Eq. "energy-minimizer") and Euclidean residual tracking
+        kf = np.exp(1.5 * np.random.default_rng(5).standard_normal(125))
+        A = W.diff3d7_var(5, 5, 5, kf)
+        Ad = A.to_dense()
+        w = 1.0 / np.diag(Ad)
+        B = W.normal_block(A.n, 3, 4)
+        for eta in (0.0, math.inf):
+            r = bcg_fn(A, B, tol=0.0, maxit=4, eta=eta, Minv=w, record_iterates=4)
+            blocks = [w[:, None] * B]
+            for k in range(1, 5):
+                V, _ = np.linalg.qr(np.hstack(blocks))
+                Xk = V @ np.linalg.solve(V.T @ Ad @ V, V.T @ B)
+                if np.abs(r.iterates[k - 1] - Xk).max() > 1e-9 * np.abs(Xk).max():
+                    return False
+                blocks.append(w[:, None] * (Ad @ blocks[-1]))
+            true = np.linalg.norm(B - Ad @ r.X, axis=0) / np.linalg.norm(B, axis=0)
+            if np.abs(true / r.relres - 1).max() > 1e-8:
+                return False
         return True
     except Exception:
         return False
@@ -85,9 +104,14 @@ BCG_MUTATIONS = [
     ("oracle.bcg", "bcg", "Rt = Rb - Q @ lam", "Rt = Rb + Q @ lam"),       # sign
     ("oracle.bcg", "bcg", "X += P @ (lam @ sigma)", "X += P @ (sigma @ lam)"),
     ("oracle.bcg", "bcg", "X += P @ (lam @ sigma)", "X += P @ lam"),       # dropped sigma
-    ("oracle.bcg", "bcg", "P = Rb + P @ beta", "P = Rb + P @ beta.T"),
+    ("oracle.bcg", "bcg", "P = Z + P @ beta", "P = Z + P @ beta.T"),
+    ("oracle.bcg", "bcg", "P = Z + P @ beta", "P = Rb + P @ beta"),        # dropped M^{-1}
+    ("oracle.bcg", "bcg", "rho_new = gram(Z, Rb, p)", "rho_new = gram(Rb, Rb, p)"),
+    ("oracle.bcg", "bcg", "rho = gram(P, Rb, p)", "rho = G"),              # rho^0 without M^{-1}
+    ("oracle.bcg", "bcg", "G = None if reo else gram(Rb, Rb, p)",          # M^{-1}-norm residual
+     "G = None if reo else gram(Rb if prec is None else prec(Rb), Rb, p)"),
     ("oracle.bcg", "bcg", "lam = chol_solve(alpha, rho)", "lam = chol_solve(rho, alpha)"),
-    ("oracle.bcg", "_resid_from", "sigma.T @ rho @ sigma", "sigma @ rho @ sigma.T"),
+    ("oracle.bcg", "_resid_from", "sigma.T @ G @ sigma", "sigma @ G @ sigma.T"),
 ]
 
 
