@@ -99,6 +99,14 @@ typedef struct {
                           the block case S_B; 1: S_P (s scalar CGs sharing the operator
                           products).  p must divide s; BK_ERR_ARG otherwise, and
                           BK_ERR_UNSUPPORTED for BBiCGStab and BGMRes with p < s  (0) */
+  bkrylov_op precond;  /* BCG only: an operator applying M^-1 of Alg. "bcgaro" (Ch. 4.3),
+                          M symmetric positive definite (Ch. 4): each iteration forms
+                          Z = M^-1 R-bar, rho = <Z, R-bar> and P = Z + P beta; the
+                          stopping test stays on the Euclidean ||R_i||.  Any operator
+                          of the same n may serve; bkrylov_op_jacobi builds point
+                          Jacobi.  Applies to the FP32 inner solves of FP32_IR too.
+                          NULL: M = I.  BK_ERR_ARG if its n differs from A's;
+                          BK_ERR_UNSUPPORTED for BBiCGStab and BGMRes            (NULL) */
 } bkrylov_opts;
 
 /* Solver report.  Pointer members are HOST arrays supplied by the caller (or NULL). */
@@ -137,6 +145,16 @@ int bkrylov_op_csr(bkrylov_handle h, int64_t n, int64_t nnz, const int32_t* row_
    (owned, n doubles). */
 int bkrylov_op_stencil(bkrylov_handle h, int kind, int nx, int ny, int nz,
                        const double* coeffs, bkrylov_op* A);
+/* Diagonal operator (Q = D P, row i scaled by d[i]): DEVICE array of n doubles, copied
+   (owned by the operator).  Used as a diagonal preconditioner M^{-1} (bkrylov_opts.precond)
+   or as an operator of its own. */
+int bkrylov_op_diag(bkrylov_handle h, int64_t n, const double* d, bkrylov_op* M);
+/* Point Jacobi preconditioner M = diag(A) (Ch. 2, the Jacobi splitting), returned as the
+   diagonal operator M^{-1} = diag(1 / a_ii), computed on the device from any operator
+   kind (CSR: the stored entries with column == row, summed).  Synchronises the handle's
+   stream; BK_ERR_ARG (nothing kept) when some a_ii is zero or not finite.  Destroy the
+   result with bkrylov_op_destroy; it does not borrow A. */
+int bkrylov_op_jacobi(bkrylov_handle h, bkrylov_op A, bkrylov_op* M);
 int bkrylov_op_destroy(bkrylov_op A);
 int bkrylov_op_size(bkrylov_op A, int64_t* n, int64_t* nnz);
 

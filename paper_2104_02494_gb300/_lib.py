@@ -26,6 +26,7 @@ class bkrylov_opts(C.Structure):
         ("ortho", C.c_int), ("prec", C.c_int), ("ir_inner_tol", C.c_double),
         ("ir_max_outer", C.c_int), ("forced_reortho", C.POINTER(C.c_uint8)), ("n_forced", C.c_int),
         ("sync_every", C.c_int), ("profile", C.c_int), ("subalgebra_p", C.c_int),
+        ("precond", C.c_void_p),
     ]
 
 
@@ -50,6 +51,8 @@ SIGNATURES = [
                                  C.POINTER(C.c_void_p)]),
     ("bkrylov_op_stencil", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                      C.POINTER(C.c_void_p)]),
+    ("bkrylov_op_diag", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("bkrylov_op_jacobi", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
     ("bkrylov_op_destroy", C.c_int, [C.c_void_p]),
     ("bkrylov_op_size", C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     ("bkrylov_spmm", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),

@@ -110,6 +110,23 @@ class Handle:
         self._ops.append(op)
         return op
 
+    def op_diag(self, d: torch.Tensor) -> "Operator":
+        """Diagonal operator diag(d) (d: float64 CUDA vector, copied)."""
+        assert d.is_cuda and d.dtype == torch.float64 and d.dim() == 1
+        M = C.c_void_p()
+        _check(self.lib.bkrylov_op_diag(self.h, d.numel(), _ptr(d), C.byref(M)), "bkrylov_op_diag")
+        op = Operator(self, M, d.numel(), kind="diag")
+        self._ops.append(op)
+        return op
+
+    def op_jacobi(self, A: "Operator") -> "Operator":
+        """Point Jacobi preconditioner M^{-1} = diag(A)^{-1} as a diagonal operator."""
+        M = C.c_void_p()
+        _check(self.lib.bkrylov_op_jacobi(self.h, A.ptr, C.byref(M)), "bkrylov_op_jacobi")
+        op = Operator(self, M, A.n, kind="diag")
+        self._ops.append(op)
+        return op
+
     # ---- single kernels ----
     def spmm(self, A: "Operator", P: torch.Tensor, Q: torch.Tensor | None = None) -> torch.Tensor:
         Q = torch.empty_like(P) if Q is None else Q
@@ -170,12 +187,14 @@ class Handle:
     # ---- solvers ----
     def solve(self, method: str, A: "Operator", B, X=None, *, tol=1e-8, maxit=1000, eta=math.inf,
               prec="fp64", restart=30, ortho="cgs2", ir_inner_tol=1e-5, ir_max_outer=30,
-              forced_reortho=None, sync_every=0, record=True, profile=False, p=None):
+              forced_reortho=None, sync_every=0, record=True, profile=False, p=None, precond=None):
         """Run bkrylov_solve_{bcg,bbicgstab,bgmres}; returns (X, SolveInfo).
 
         B, X: float64 n x s blocks, on the device (torch CUDA tensors) or on
         the host (numpy / CPU tensors; copied inside the call).  X is updated
-        in place and starts from zero when not given.
+        in place and starts from zero when not given.  ``p``: block size of
+        the block-parallel subalgebra (BCG); ``precond``: an Operator applying
+        M^{-1} (BCG, e.g. ``op_jacobi(A)``).
         """
         s = B.shape[1]
         if X is None:
@@ -187,6 +206,7 @@ class Handle:
         o.ir_inner_tol, o.ir_max_outer, o.sync_every = float(ir_inner_tol), int(ir_max_outer), int(sync_every)
         o.profile = 1 if profile else 0
         o.subalgebra_p = 0 if p is None else int(p)
+        o.precond = None if precond is None else precond.ptr.value
         forced_arr = None
         if forced_reortho is not None:
             forced_arr = (C.c_uint8 * max(1, len(forced_reortho)))(*[1 if f else 0 for f in forced_reortho])

@@ -32,7 +32,7 @@ struct bkrylov_ctx {
 
 const char* const bk::kPhaseNames[kNumPhases] = {
     "spmm_alpha", "small_1", "update_rho", "tsqr_leaf_factor", "tsqr_tree", "tsqr_leaf_apply",
-    "tsqr_rho_gram", "small_2", "p_update"};
+    "tsqr_rho_gram", "small_2", "p_update", "precond_rho"};
 
 struct bkrylov_op_s {
   bkrylov_handle h = nullptr;
@@ -111,6 +111,7 @@ int ctrl_upload(bkrylov_handle h, Ctrl* dev, int s, const bkrylov_opts& o, doubl
   c->eps = eps;
   c->n_forced = (o.forced_reortho && o.n_forced > 0) ? o.n_forced : 0;
   c->sub_p = (o.subalgebra_p > 0 && o.subalgebra_p < s) ? o.subalgebra_p : s;
+  c->has_prec = o.precond != nullptr;
   for (int i = 0; i < s; ++i) c->sigma[i * kMaxS + i] = 1.0;
   BK_TRY(cudaMemcpyAsync(dev, c, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
   // the pinned staging buffer is reused: wait for the copy before returning
@@ -161,6 +162,8 @@ int finish_info(bkrylov_handle h, const Ctrl* dev, int s, const double* hist_dev
 template <typename T>
 struct BcgBufs {
   T *R, *P, *Q;
+  T* Z = nullptr;              // M^{-1} R-bar (preconditioned solves only)
+  const OpDesc* M = nullptr;   // the preconditioner M^{-1}, or null (M = I)
   void* tsqr;
   double* gpart;
   Ctrl* ctrl;
@@ -171,11 +174,12 @@ struct BcgBufs {
 
 template <typename T, typename Alloc>
 void bcg_layout(Alloc& a, int64_t n, int s, int maxit, const TsqrPlan& tp, const Launch& L,
-                BcgBufs<T>* b) {
+                BcgBufs<T>* b, bool prec) {
   const size_t ns = (size_t)n * s;
   auto r = a.template take<T>(ns);
   auto p = a.template take<T>(ns);
   auto q = a.template take<T>(ns);
+  b->Z = prec ? a.template take<T>(ns) : nullptr;
   auto t = a.template take<char>(tp.bytes);
   auto g = a.template take<double>(gpart_count(L, tp));
   auto c = a.template take<Ctrl>(1);
@@ -244,17 +248,34 @@ cudaError_t bcg_iteration(const Launch& L, const OpDesc& A, int s, T* X, const B
   }
   if (e != cudaSuccess) return e;
   prof_end(L, kPhUpdate, 2);
-  if ((e = tsqr_groups<T>(L, tp, s, b.R, c->gamma, c->rho_new, b.tsqr, b.gpart, &c->counters[kCntC],
-                          &c->done, &c->reortho_now)) != cudaSuccess) return e;
+  // preconditioned: after a re-orthonormalisation only rho = <Z, R-bar> is needed
+  if ((e = tsqr_groups<T>(L, tp, s, b.R, c->gamma, b.M ? nullptr : c->rho_new, b.tsqr, b.gpart,
+                          &c->counters[kCntC], &c->done, &c->reortho_now)) != cudaSuccess) return e;
+  if (b.M) {
+    // Z = M^{-1} R-bar and rho_m = R-bar^T Z in one fused operator pass
+    Epi<T> pz;
+    pz.left = b.R; pz.sym = 1; pz.gram_out = c->rho_m; pz.gpart = b.gpart;
+    pz.counter = &c->counters[kCntA]; pz.done = &c->done;
+    prof_begin(L, kPhPrec);
+    if constexpr (kF64) {
+      if (gp < s) e = spmm_groups(L, *b.M, s, gp, (const double*)b.R, (double*)b.Z, *(const Epi<double>*)&pz);
+      else e = spmm<T>(L, *b.M, s, b.R, b.Z, nullptr, pz);
+    } else {
+      e = spmm<T>(L, *b.M, s, b.R, b.Z, nullptr, pz);
+    }
+    if (e != cudaSuccess) return e;
+    prof_end(L, kPhPrec, 1);
+  }
+  const T* Zn = b.M ? b.Z : b.R;     // P = Z + P beta
   prof_begin(L, kPhSmall2);
   if ((e = small_bcg_2(L, c, b.hist, b.dec)) != cudaSuccess) return e;
   prof_end(L, kPhSmall2, 1);
   prof_begin(L, kPhPupdate);
   if constexpr (kF64) {
-    if (gp < s) e = bcg_pupdate_groups(L, A.n, s, gp, (const double*)b.R, (double*)b.P, c);
-    else e = bcg_pupdate<T>(L, A.n, s, b.R, b.P, c);
+    if (gp < s) e = bcg_pupdate_groups(L, A.n, s, gp, (const double*)Zn, (double*)b.P, c);
+    else e = bcg_pupdate<T>(L, A.n, s, Zn, b.P, c);
   } else {
-    e = bcg_pupdate<T>(L, A.n, s, b.R, b.P, c);
+    e = bcg_pupdate<T>(L, A.n, s, Zn, b.P, c);
   }
   prof_end(L, kPhPupdate, 1);
   return e;
@@ -292,12 +313,16 @@ struct GraphBatch {
 };
 
 // launches of one iteration (the TSQR tree has 2 * levels + 1 launches)
-int bcg_launches_per_iter(const TsqrPlan& tp) { return 6 + tsqr_launches(tp); }
+int bcg_launches_per_iter(const TsqrPlan& tp, bool prec = false) {
+  return 6 + tsqr_launches(tp) + (prec ? 1 : 0);
+}
 
 template <typename T>
 int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const bkrylov_opts& o,
                double eps, bkrylov_info* info) {
   const Launch L = launch_of(h);
+  const OpDesc* M = o.precond ? &o.precond->d : nullptr;
+  if (M && sizeof(T) == 4) BK_TRY(op_make_fp32(L, o.precond->d));
   const int64_t n = A.n;
   // S_BP^p normalises p-column groups: the TSQR plan is for width p
   const int gp = (o.subalgebra_p > 0 && o.subalgebra_p < s) ? o.subalgebra_p : s;
@@ -305,11 +330,12 @@ int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const
   const int maxit = o.maxit > 0 ? o.maxit : 0;
   BcgBufs<T> b;
   Bump probe(nullptr, 0);
-  bcg_layout<T>(probe, n, s, maxit, tp, L, &b);
+  bcg_layout<T>(probe, n, s, maxit, tp, L, &b, M != nullptr);
   int rc = ensure_ws(h, 0, probe.off + 4096);
   if (rc) return rc;
   Bump bump(h->ws[0], h->ws_cap[0]);
-  bcg_layout<T>(bump, n, s, maxit, tp, L, &b);
+  bcg_layout<T>(bump, n, s, maxit, tp, L, &b, M != nullptr);
+  b.M = M;
   if ((rc = ctrl_upload(h, b.ctrl, s, o, eps))) return rc;
   if (o.forced_reortho && o.n_forced > 0) {
     const int nf = o.n_forced < maxit + 1 ? o.n_forced : maxit + 1;
@@ -330,9 +356,17 @@ int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const
   if (o.eta > 0) {
     BK_TRY(tsqr_groups<T>(L, tp, s, b.R, c->sigma, nullptr, b.tsqr, b.gpart, nullptr, nullptr, nullptr));
   }
-  BK_TRY(cudaMemcpyAsync(b.P, b.R, sizeof(T) * (size_t)n * s, cudaMemcpyDeviceToDevice, L.stream));
   g.gram_out = c->rho;
   BK_TRY(gram<T>(L, n, s, b.R, b.R, g));
+  if (M) {
+    // P^0 = M^{-1} R-bar^0 and rho_m = R-bar^T P^0 (the init kernel takes rho from it
+    // after the norms test, which uses the Euclidean Gram above)
+    Epi<T> pz;
+    pz.left = b.R; pz.sym = 1; pz.gram_out = c->rho_m; pz.gpart = b.gpart; pz.counter = &c->counters[kCntA];
+    BK_TRY(spmm<T>(L, *M, s, b.R, b.P, nullptr, pz));
+  } else {
+    BK_TRY(cudaMemcpyAsync(b.P, b.R, sizeof(T) * (size_t)n * s, cudaMemcpyDeviceToDevice, L.stream));
+  }
   BK_TRY(small_bcg_init(L, c, o.eta > 0));
   Launch Lp = L;
   if (o.profile) Lp.prof = &h->prof;
@@ -838,6 +872,53 @@ int bkrylov_op_stencil(bkrylov_handle h, int kind, int nx, int ny, int nz, const
   return BK_OK;
 }
 
+int bkrylov_op_diag(bkrylov_handle h, int64_t n, const double* d, bkrylov_op* M) {
+  if (!h || !M || n <= 0 || !d) return BK_ERR_ARG;
+  bkrylov_op op = new (std::nothrow) bkrylov_op_s();
+  if (!op) return BK_ERR_ALLOC;
+  op->h = h;
+  OpDesc& o = op->d;
+  o.kind = kOpDiag;
+  o.n = n;
+  o.nnz = n;
+  o.coef_len = n;
+  if (cudaMalloc(&o.coef, sizeof(double) * (size_t)n) != cudaSuccess) { delete op; return BK_ERR_ALLOC; }
+  if (cudaMemcpyAsync(o.coef, d, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, h->stream) !=
+      cudaSuccess) {
+    cudaFree(o.coef); delete op; return BK_ERR_CUDA;
+  }
+  *M = op;
+  return BK_OK;
+}
+
+int bkrylov_op_jacobi(bkrylov_handle h, bkrylov_op A, bkrylov_op* M) {
+  if (!h || !A || !M) return BK_ERR_ARG;
+  const Launch L = launch_of(h);
+  bkrylov_op op = new (std::nothrow) bkrylov_op_s();
+  if (!op) return BK_ERR_ALLOC;
+  op->h = h;
+  OpDesc& o = op->d;
+  o.kind = kOpDiag;
+  o.n = A->d.n;
+  o.nnz = o.n;
+  o.coef_len = o.n;
+  int* bad = nullptr;
+  int bad_h = 0;
+  auto fail = [&](int rc) { if (bad) cudaFree(bad); if (o.coef) cudaFree(o.coef); delete op; return rc; };
+  if (cudaMalloc(&o.coef, sizeof(double) * (size_t)o.n) != cudaSuccess) { o.coef = nullptr; return fail(BK_ERR_ALLOC); }
+  if (cudaMalloc(&bad, sizeof(int)) != cudaSuccess) { bad = nullptr; return fail(BK_ERR_ALLOC); }
+  if (cudaMemsetAsync(bad, 0, sizeof(int), L.stream) != cudaSuccess) return fail(BK_ERR_CUDA);
+  if (jacobi_inverse_diagonal(L, A->d, o.coef, bad) != cudaSuccess) return fail(BK_ERR_CUDA);
+  if (cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, L.stream) != cudaSuccess ||
+      cudaStreamSynchronize(L.stream) != cudaSuccess)
+    return fail(BK_ERR_CUDA);
+  cudaFree(bad);
+  bad = nullptr;
+  if (bad_h) return fail(BK_ERR_ARG);
+  *M = op;
+  return BK_OK;
+}
+
 int bkrylov_op_destroy(bkrylov_op A) {
   if (!A) return BK_ERR_ARG;
   if (A->h) cudaStreamSynchronize(A->h->stream);
@@ -958,6 +1039,7 @@ static int check_solve_args(bkrylov_handle h, bkrylov_op A, int s, const double*
   if (A->d.n < s) return BK_ERR_ARG;
   if (!(o.tol >= 0.0) || o.maxit < 0 || !(o.eta >= 0.0)) return BK_ERR_ARG;
   if (o.subalgebra_p < 0 || (o.subalgebra_p > 0 && s % o.subalgebra_p != 0)) return BK_ERR_ARG;
+  if (o.precond && o.precond->d.n != A->d.n) return BK_ERR_ARG;
   return BK_OK;
 }
 
@@ -995,7 +1077,7 @@ int bkrylov_solve_bbicgstab(bkrylov_handle h, bkrylov_op A, int s, const double*
   opts_or_default(opts, &o);
   int rc = check_solve_args(h, A, s, B, X, o);
   if (rc) return rc;
-  if (!block_case(o, s)) return BK_ERR_UNSUPPORTED;
+  if (!block_case(o, s) || o.precond) return BK_ERR_UNSUPPORTED;
   if (o.prec != BK_FP64) return BK_ERR_UNSUPPORTED;
   return with_device_blocks(h, A->d.n, s, B, X, 0, [&](const double* dB, double* dX, size_t) {
     return bicg_device(h, A->d, s, dB, dX, o, info);
@@ -1008,7 +1090,7 @@ int bkrylov_solve_bgmres(bkrylov_handle h, bkrylov_op A, int s, const double* B,
   opts_or_default(opts, &o);
   int rc = check_solve_args(h, A, s, B, X, o);
   if (rc) return rc;
-  if (!block_case(o, s)) return BK_ERR_UNSUPPORTED;
+  if (!block_case(o, s) || o.precond) return BK_ERR_UNSUPPORTED;
   if (o.prec != BK_FP64) return BK_ERR_UNSUPPORTED;
   if (o.restart < 1 || o.restart > 64) return BK_ERR_ARG;
   return with_device_blocks(h, A->d.n, s, B, X, 0, [&](const double* dB, double* dX, size_t) {

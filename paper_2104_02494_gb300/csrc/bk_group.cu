@@ -251,6 +251,10 @@ cudaError_t spmm_groups(const Launch& L, const OpDesc& A, int s, int p, const do
                           A.edges + (int64_t)A.ny * (A.nx + 1)};
       return spmm_grp_op(L, op, n, s, p, P, Q, ep);
     }
+    case kOpDiag: {
+      DiagRow<double> op{A.coef};
+      return spmm_grp_op(L, op, n, s, p, P, Q, ep);
+    }
     default: return cudaErrorInvalidValue;
   }
 }

@@ -11,7 +11,7 @@ namespace bk {
 
 struct Ctrl;
 
-enum OpKind { kOpCsr = 0, kOpConst7 = 1, kOpVar7 = 2, kOpEdge5 = 3 };
+enum OpKind { kOpCsr = 0, kOpConst7 = 1, kOpVar7 = 2, kOpEdge5 = 3, kOpDiag = 4 };
 
 struct OpDesc {
   int kind = kOpCsr;
@@ -26,6 +26,7 @@ struct OpDesc {
   double c7[7] = {0, 0, 0, 0, 0, 0, 0};
   // VAR7: owned diag + faces to the +x/+y/+z neighbour (0 at the boundary), 4 arrays of n.
   // EDGE5: owned diag (n); borrowed edge coefficients (ny*(nx+1) + (ny+1)*nx).
+  // DIAG: owned entries (n) of the diagonal operator.
   double* coef = nullptr;          // owned double coefficient arrays
   float* coef32 = nullptr;         // owned float copy (lazy)
   const double* edges = nullptr;   // EDGE5 borrowed
@@ -50,7 +51,7 @@ struct Epi {
 // Optional per-phase device timing (CUDA events on the launching stream).
 enum Phase : int {
   kPhSpmm = 0, kPhSmall1, kPhUpdate, kPhTsqrLeaf, kPhTsqrTree, kPhTsqrApply, kPhTsqrGram,
-  kPhSmall2, kPhPupdate, kNumPhases
+  kPhSmall2, kPhPupdate, kPhPrec, kNumPhases
 };
 struct Prof {
   static constexpr int kMax = 16;
@@ -99,6 +100,9 @@ cudaError_t spmm(const Launch& L, const OpDesc& A, int s, const T* in, T* out, c
                  const Epi<T>& ep);
 cudaError_t op_prepare_stencil(const Launch& L, OpDesc& A, const double* coeffs);
 cudaError_t op_make_fp32(const Launch& L, OpDesc& A);
+// out[i] = 1 / a_ii of A (point Jacobi, M = diag(A)); *bad = 1 when some a_ii is
+// zero or not finite (that entry is written as 0).
+cudaError_t jacobi_inverse_diagonal(const Launch& L, const OpDesc& A, double* out, int* bad);
 int spmm_grid(const Launch& L, int64_t n, int s);
 
 // ---- row kernels (bk_rows.cu) ----

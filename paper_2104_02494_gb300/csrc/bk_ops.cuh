@@ -249,6 +249,27 @@ struct Edge5Row {
   }
 };
 
+// Diagonal operator out_r = w_r in_r (a diagonal preconditioner M^{-1}, e.g.
+// point Jacobi w = 1 / diag(A)); one coefficient per row.
+template <typename T>
+struct DiagRow {
+  const T* __restrict__ w;
+  __device__ __forceinline__ T operator()(int64_t r, int c, int s, const T* __restrict__ P) const {
+    return w[r] * P[r * s + c];
+  }
+  __device__ __forceinline__ float4 quad(int64_t r, int i, int s, const float* __restrict__ P) const {
+    const float d = w[r];
+    const float4 v = ld4(P + r * s + 4 * i);
+    return make_float4(d * v.x, d * v.y, d * v.z, d * v.w);
+  }
+  static constexpr bool kLead = false;
+  __device__ __forceinline__ int64_t lead_off() const { return 0; }
+  __device__ __forceinline__ float4 quad_lead(int64_t r, int i, int s, const float* __restrict__ P,
+                                              float4) const {
+    return quad(r, i, s, P);
+  }
+};
+
 // Identity "operator": the row kernel then just streams Y, which turns the
 // fused epilogue into a stand-alone block inner product X^T Y (BDOT).
 template <typename T>

@@ -128,6 +128,8 @@ template cudaError_t spmm4<Edge5Row<float>>(const Launch&, const Edge5Row<float>
                                             const float*, float*, const float*, const Epi<float>&);
 template cudaError_t spmm4<IdRow<float>>(const Launch&, const IdRow<float>&, int64_t, int,
                                          const float*, float*, const float*, const Epi<float>&);
+template cudaError_t spmm4<DiagRow<float>>(const Launch&, const DiagRow<float>&, int64_t, int,
+                                           const float*, float*, const float*, const Epi<float>&);
 
 // -------------------------------------------------------- BCG updates ----
 // X <- X + P lx, R <- R - Q lam (lx = lambda sigma); with kRho also

@@ -306,6 +306,15 @@ __global__ void __launch_bounds__(kST) small_bcg_init_k(Ctrl* c) {
     else if (mx <= c->tol) { c->done = kDoneConverged; c->status = BK_OK; }
     else if (c->maxit <= 0) { c->done = kDoneStopped; c->status = BK_NOT_CONVERGED; }
   }
+  if (c->has_prec) {
+    // preconditioned: rho^0 = <P^0, R-bar^0> (the Euclidean Gram above only gave the norms)
+    __syncthreads();
+    sm_copy(S.A, c->rho_m, s);
+    __syncthreads();
+    sm_project(S.A, s, c->sub_p);
+    __syncthreads();
+    for (int i = threadIdx.x; i < s * s; i += blockDim.x) c->rho[IDX(i / s, i % s)] = S.A[IDX(i / s, i % s)];
+  }
 }
 
 // lambda = alpha^{-1} rho, the re-orthonormalisation decision, lx = lambda sigma.
@@ -345,7 +354,10 @@ __global__ void __launch_bounds__(kST) small_bcg_2_k(Ctrl* c, double* history, u
   const int s = c->s;
   const int reo = c->reortho_now;
   const int k = c->iter;
-  sm_copy(S.A, c->rho_new, s);
+  const int pre = c->has_prec;
+  // A: the Euclidean Gram for the norms (not needed after a re-orthonormalisation
+  // when preconditioned; then rho_new was not formed and A takes rho_m at once)
+  sm_copy(S.A, (pre && reo) ? c->rho_m : c->rho_new, s);
   sm_copy(S.B, c->sigma, s);
   if (reo) sm_copy(S.C, c->gamma, s); else sm_identity(S.C, s);
   __syncthreads();
@@ -386,6 +398,14 @@ __global__ void __launch_bounds__(kST) small_bcg_2_k(Ctrl* c, double* history, u
   if (s_conv > 0) {
     if (threadIdx.x == 0) { c->done = kDoneConverged; c->status = BK_OK; }
     return;
+  }
+  if (pre && !reo) {
+    // the new rho = <Z, R-bar> replaces the Euclidean Gram used for the norms
+    sm_copy(S.A, c->rho_m, s);
+    __syncthreads();
+    sm_project(S.A, s, c->sub_p);
+    __syncthreads();
+    if (!sm_all_finite(S.A, s, &S.flag)) { stop(c, BK_NONFINITE); return; }
   }
   // beta = rho_old^{-1} gamma^T rho_new
   sm_matmul(S.E, S.C, true, S.A, s);

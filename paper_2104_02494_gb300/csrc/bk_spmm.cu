@@ -260,6 +260,11 @@ cudaError_t spmm(const Launch& L, const OpDesc& A, int s, const T* in, T* out, c
       Edge5Row<T> op{A.nx, A.ny, FastDiv((uint32_t)A.nx), dg, e, e + (int64_t)A.ny * (A.nx + 1)};
       return launch_op<T>(L, op, n, s, in, out, sub, ep);
     }
+    case kOpDiag: {
+      DiagRow<T> op{pick<T>(A.coef, A.coef32)};
+      if (!op.w) return cudaErrorInvalidValue;
+      return launch_op<T>(L, op, n, s, in, out, sub, ep);
+    }
     default: return cudaErrorInvalidValue;
   }
 }
@@ -353,13 +358,42 @@ cudaError_t op_prepare_stencil(const Launch& L, OpDesc& A, const double* coeffs)
   return cudaSuccess;
 }
 
+// Point Jacobi: the diagonal a_ii of every operator kind, inverted.  CSR sums
+// the stored entries with column == row (none stored: a_ii = 0).
+__global__ void jacobi_kernel(OpDesc A, double* __restrict__ out, int* __restrict__ bad) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < A.n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    double d = 0.0;
+    switch (A.kind) {
+      case kOpCsr:
+        for (int32_t j = A.row_ptr[r]; j < A.row_ptr[r + 1]; ++j)
+          if (A.col[j] == r) d += A.val[j];
+        break;
+      case kOpConst7: d = A.c7[0]; break;
+      case kOpVar7:
+      case kOpEdge5: d = A.coef[r]; break;
+      case kOpDiag: d = A.coef[r]; break;
+      default: break;
+    }
+    const bool ok = d != 0.0 && isfinite(d);
+    out[r] = ok ? 1.0 / d : 0.0;
+    if (!ok) *bad = 1;
+  }
+}
+
+cudaError_t jacobi_inverse_diagonal(const Launch& L, const OpDesc& A, double* out, int* bad) {
+  if (A.kind == kOpCsr && A.nnz > 0 && (!A.col || !A.val)) return cudaErrorInvalidValue;
+  jacobi_kernel<<<elem_grid(L, A.n), 256, 0, L.stream>>>(A, out, bad);
+  return cudaGetLastError();
+}
+
 cudaError_t op_make_fp32(const Launch& L, OpDesc& A) {
   cudaError_t e = cudaSuccess;
   if (A.kind == kOpCsr && !A.val32) {
     if ((e = cudaMalloc(&A.val32, sizeof(float) * (size_t)(A.nnz > 0 ? A.nnz : 1))) != cudaSuccess) return e;
     return cast_block(L, A.nnz, A.val, A.val32);
   }
-  if ((A.kind == kOpVar7 || A.kind == kOpEdge5) && !A.coef32) {
+  if ((A.kind == kOpVar7 || A.kind == kOpEdge5 || A.kind == kOpDiag) && !A.coef32) {
     if ((e = cudaMalloc(&A.coef32, sizeof(float) * (size_t)A.coef_len)) != cudaSuccess) return e;
     if ((e = cast_block(L, A.coef_len, A.coef, A.coef32)) != cudaSuccess) return e;
   }
