@@ -16,7 +16,7 @@ rho Gram), s x s step, direction update.
              in, X copied out inside the call), host wall clock around the call;
   roofline   the dominant kernel phase, timed live with CUDA events (profiled
              solve), against the FP64 FMA rate of this GPU (the path is bound by
-             FP64 arithmetic at s = 8, see DESIGN.md);
+             FP64 arithmetic at s = 8: the FP64 ridge point is ~0.19 flop/byte);
   cpu_baseline  the FP64 oracle (numpy/scipy) on the host cores, a bounded
              number of iterations of the same workload.
 
@@ -41,7 +41,9 @@ import numpy as np  # noqa: E402
 
 METRIC = "block-CG RHS*iter/s (128^3 Laplacian, FP64, QR-stabilised BCG)"
 UNIT = "RHS*iter/s"
-FP64_PEAK_TFLOPS = 1.196   # measured FP64 FMA throughput of this GB300
+# FP64 FMA peak of a GB300: 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flops = 1.259 TFLOP/s
+# (the part's nominal 1.25 TFLOP/s FP64 rate at its maximum SM clock)
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
 
 
 def _hbm_peak():
@@ -78,6 +80,10 @@ def parse():
                    help="block-parallel subalgebra S_BP^p: cost per iteration and time to 1e-8 over p")
     p.add_argument("--tt", action="store_true",
                    help="time-to-tolerance of every workload's solver (median of 5 after 1 warm-up)")
+    p.add_argument("--precond", action="store_true",
+                   help="point-Jacobi preconditioned BCG against M = I on the variable-coefficient "
+                        "workloads: time and iterations to tolerance, cost per iteration, and the "
+                        "fused M^-1 + Gram pass against its roofline")
     p.add_argument("--ir", action="store_true",
                    help="time-to-1e-10 of FP32+IR vs plain FP64 BCG on the 192^3 log-normal diffusion "
                         "workload (s = 16) instead of the default line")
@@ -435,6 +441,76 @@ def run_subalgebra(args):
     print(json.dumps({"workload": f"laplace3d {args.grid}^3 stencil, FP64, eta=inf", "results": out}))
 
 
+def run_precond(args):
+    """Point Jacobi (M = diag(A)) against M = I for BCG on the variable-coefficient
+    workloads.  Per case and M: device time and iterations to tolerance (two runs after a
+    short warm-up, the smaller time kept), device time per iteration (23 minus 3
+    iterations, over 20), and for Jacobi the profiled per-launch time of the fused pass
+    Z = M^-1 R-bar, rho = R-bar^T Z with its algorithmic bytes n (2s + 1) w and flops
+    n (s + s (s + 1))."""
+    import torch
+    import workloads as W
+    from paper_2104_02494_gb300 import build
+    from paper_2104_02494_gb300.api import Handle, operator_from_problem
+    build()
+    h = Handle(0)
+    cases = [
+        ("vardiff3d 192^3 var7 stencil, s=16, FP32 BCG + FP64 refinement, 1e-10", "vardiff3d", None, 16,
+         dict(tol=1e-10, eta=math.inf, prec="fp32_ir")),
+        ("vardiff3d 128^3 var7 stencil, s=8, FP64 BCG eta=1e4, 1e-8", "vardiff3d", 128, 8,
+         dict(tol=1e-8, eta=1e4)),
+        ("edge2d 512^2 per-edge stencil, s=32, FP64 BCG eta=1e4, 1e-8", "edge2d", None, 32,
+         dict(tol=1e-8, eta=1e4)),
+    ]
+    out = []
+    for label, wl, grid, s, kw in cases:
+        prob = W.problem(wl, s=s, grid=grid, with_csr=False)
+        op = operator_from_problem(h, prob, "stencil")
+        Mj = h.op_jacobi(op)
+        B = torch.from_numpy(prob.B).cuda()
+        n = prob.B.shape[0]
+        w = 4 if kw.get("prec") == "fp32_ir" else 8
+        row = {"case": label, "n": n, "s": s}
+        for name, M in (("identity", None), ("jacobi", Mj)):
+            h.solve("bcg", op, B, maxit=3, record=False, precond=M, **kw)
+            times = []
+            for _ in range(2):
+                _, info = h.solve("bcg", op, B, maxit=20000, record=False, precond=M, **kw)
+                times.append(info.elapsed_ms)
+            pk = dict(kw, prec="fp64" if w == 8 else "fp32_ir", tol=0.0)
+            if w == 4:
+                pk["ir_max_outer"] = 1
+            _, i23 = h.solve("bcg", op, B, maxit=23, record=False, precond=M, **pk)
+            _, i3 = h.solve("bcg", op, B, maxit=3, record=False, precond=M, **pk)
+            r = {"time_ms": min(times), "iters": info.iters, "converged": info.converged,
+                 "relres_max": info.relres_max, "outer": info.outer,
+                 "ms_per_iter": (i23.elapsed_ms - i3.elapsed_ms) / 20}
+            if M is not None:
+                h.profile_reset()
+                h.solve("bcg", op, B, maxit=20, record=False, precond=M, profile=True, **pk)
+                prof = {p[0]: (p[1], p[2]) for p in h.profile()}
+                ms, nl = prof["precond_rho"]
+                per = ms / max(nl, 1)
+                nbytes = n * (2 * s + 1) * w
+                flops = n * (s + s * (s + 1))
+                r["precond_pass"] = {"ms_per_launch": per, "launches": nl,
+                                     "gbs": nbytes / (per / 1e3) / 1e9,
+                                     "hbm_frac": nbytes / (per / 1e3) / 1e9 / HBM_PEAK_GBS,
+                                     "tflops": flops / (per / 1e3) / 1e12}
+                if w == 8:
+                    r["precond_pass"]["fp64_frac"] = r["precond_pass"]["tflops"] / FP64_PEAK_TFLOPS
+                r["phases_ms_per_iter"] = {k: v[0] / 20 for k, v in prof.items() if v[1] > 0}
+            row[name] = r
+        row["speedup"] = row["identity"]["time_ms"] / row["jacobi"]["time_ms"]
+        out.append(row)
+        Mj.close()
+        op.close()
+        del B
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "BCG time to tolerance, point Jacobi vs M = I (device time)",
+                      "results": out}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -451,6 +527,8 @@ def main():
         return run_tt(args)
     if args.subalgebra:
         return run_subalgebra(args)
+    if args.precond:
+        return run_precond(args)
     rank, world, dist = dist_init(args)
     import torch
     import workloads as W
@@ -494,7 +572,7 @@ def main():
     achieved = flops / (dom_ms / 1000.0) / 1e12
     roofline = {"bound": "alu", "kernel": dom[0], "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "measured FP64 FMA throughput (probe, DESIGN.md)",
+                "peak_source": "derived: 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop",
                 "hbm_achieved_gbs": PHASE_BYTES[dom[0]](n, s) / (dom_ms / 1000.0) / 1e9}
 
     # end to end through the C ABI with host buffers
