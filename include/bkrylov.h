@@ -226,6 +226,12 @@ int bkrylov_profile_count(void);
 int bkrylov_profile_get(bkrylov_handle h, int i, const char** name, double* total_ms,
                         long long* launches);
 int bkrylov_profile_reset(bkrylov_handle h);
+/* Diagonally scaled condition number kappa_D(A) = kappa_2(D^-1/2 A D^-1/2), D = diag(A)
+   (Ch. 4.3, Def. "Diagonally scaled condition number"), the quantity of the adaptive
+   re-orthonormalisation test, by the solvers' own device routine.  A: DEVICE s x s
+   symmetric, row-major; kappa: DEVICE double (+inf when a diagonal entry or the smallest
+   eigenvalue of the scaled matrix is <= 0).  Enqueued on the handle's stream. */
+int bkrylov_kappa_d(bkrylov_handle h, int s, const double* A, double* kappa);
 /* Kernel launches of one BCG iteration for an n x s block (host-only, no GPU). */
 int bkrylov_bcg_launches_per_iteration(int64_t n, int s);
 

@@ -43,12 +43,15 @@ class BCGResult:
     relres: np.ndarray               # final per-column relative residual (from sigma/rho)
     history: list = field(default_factory=list)    # max relative residual per iteration
     decisions: list = field(default_factory=list)  # re-orthonormalised in iteration k?
+    kappas: list = field(default_factory=list)     # kappa_D(alpha^k) when 0 < eta < inf, else None
+    alphas: list = field(default_factory=list)     # alpha^k (projected), when record_alpha
     iterates: list = field(default_factory=list)   # X^{k+1} for the first record_iterates steps
 
 
 def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit: int = 1000,
         eta: float = math.inf, p: int | None = None, forced=None, record_iterates: int = 0,
-        dtype=np.float64, eps: float | None = None, apply_A=None, Minv=None) -> BCGResult:
+        dtype=np.float64, eps: float | None = None, apply_A=None, Minv=None,
+        record_alpha: bool = False) -> BCGResult:
     """Alg. "bcgaro" (2R grouping, Alg. "2R-CG") for A X = B.
 
     A: CSR (attributes n, row_ptr, col, val) or None when ``apply_A`` is given.
@@ -106,6 +109,9 @@ def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit
             reo = bool(forced[k])
         else:
             reo = reortho_decision(eta, alpha, eps)
+        out.kappas.append(kappa_d(alpha) if 0.0 < eta < math.inf else None)
+        if record_alpha:
+            out.alphas.append(alpha.copy())
         # X^{k+1} = X^k + P^k lambda^k sigma^k (uses the old sigma)
         X += P @ (lam @ sigma).astype(dtype)
         Rt = Rb - Q @ lam.astype(dtype)

@@ -74,6 +74,7 @@ SIGNATURES = [
     ("bkrylov_profile_get", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
                                       C.POINTER(C.c_longlong)]),
     ("bkrylov_profile_reset", C.c_int, [C.c_void_p]),
+    ("bkrylov_kappa_d", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     ("bkrylov_bcg_launches_per_iteration", C.c_int, [C.c_int64, C.c_int]),
     ("bkrylov_adjoint_scatter", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                           C.c_void_p]),

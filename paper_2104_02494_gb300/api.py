@@ -170,6 +170,13 @@ class Handle:
                "bkrylov_edge_theta_grad")
         return g
 
+    def kappa_d(self, A: torch.Tensor) -> float:
+        """kappa_D of an s x s symmetric float64 CUDA matrix (the adaptive criterion's)."""
+        out = torch.empty(1, dtype=torch.float64, device=A.device)
+        A = A.contiguous()
+        _check(self.lib.bkrylov_kappa_d(self.h, A.shape[0], _ptr(A), _ptr(out)), "bkrylov_kappa_d")
+        return float(out.item())
+
     # ---- measurement ----
     def profile(self):
         """[(phase, total_ms, launches)] accumulated by solves run with profile=True."""

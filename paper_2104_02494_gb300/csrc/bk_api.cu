@@ -1115,6 +1115,12 @@ int bkrylov_profile_reset(bkrylov_handle h) {
   return BK_OK;
 }
 
+int bkrylov_kappa_d(bkrylov_handle h, int s, const double* A, double* kappa) {
+  if (!h || !valid_s(s) || !A || !kappa) return BK_ERR_ARG;
+  BK_TRY(small_kappa_d(launch_of(h), s, A, kappa));
+  return BK_OK;
+}
+
 int bkrylov_bcg_launches_per_iteration(int64_t n, int s) {
   if (n < 1 || s < 1 || s > kMaxS) return -1;
   return bcg_launches_per_iter(tsqr_plan(n, s));

@@ -170,6 +170,8 @@ cudaError_t small_bicg_1(const Launch& L, Ctrl* ctrl, const uint8_t* forced);
 cudaError_t small_bicg_2(const Launch& L, Ctrl* ctrl);
 cudaError_t small_bicg_3(const Launch& L, Ctrl* ctrl, double* history, uint8_t* decisions);
 cudaError_t small_set_identity(const Launch& L, double* M, int s);
+// kappa_D of an s x s symmetric matrix A (row stride s, device) into *out (device).
+cudaError_t small_kappa_d(const Launch& L, int s, const double* A, double* out);
 cudaError_t small_colnorms_from_gram(const Launch& L, Ctrl* ctrl);
 
 // BGMRes small kernels

@@ -157,12 +157,59 @@ __device__ void sm_lu_solve(const double* LU, const int* piv, const double* B, d
   __syncthreads();
 }
 
-// kappa_D(A) = kappa_2(D^-1/2 A D^-1/2), D = diag(A)  (Def. in Ch. 4.3), by
-// cyclic Jacobi with a round-robin ordering (s/2 disjoint rotations per round,
-// applied together).  +inf when a diagonal entry or an eigenvalue is <= 0.
-// M and M2 are shared work matrices.
-__device__ double sm_kappa_d(const double* A, int s, double* M, double* M2, double* rot, int* flag) {
-  __shared__ double s_kappa;
+// Number of eigenvalues of the symmetric tridiagonal T = tridiag(e, d, e)
+// below x: the sign changes of the Sturm sequence of T - x I's leading
+// principal minors p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (Wilkinson,
+// "The Algebraic Eigenvalue Problem", 1965, Ch. 5).  No division: the two
+// latest terms are rescaled together by 2^-+400 when they leave
+// [2^-400, 2^400], which keeps their signs and ratio; an exact zero takes the
+// sign opposite to its predecessor (x moved off the root of that minor).
+__device__ int sturm_count(const double* d, const double* e2, int s, double x) {
+  // signs, zeros and exponents are read from the bit pattern (integer ALU): the
+  // FP64 pipe only carries the recurrence itself
+  int cnt = 0;
+  long long sprev = 0;                 // sign bit of the previous term (1: negative)
+  double pm1 = 1.0, p = d[0] - x;
+  for (int i = 0;; ++i) {
+    long long b = __double_as_longlong(p);
+    if ((b << 1) == 0) {               // +-0: take the sign opposite to the predecessor
+      p = sprev ? 0x1p-600 : -0x1p-600;
+      b = __double_as_longlong(p);
+    }
+    const long long sg = (long long)((unsigned long long)b >> 63);
+    cnt += (int)(sg != sprev);
+    sprev = sg;
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex > 1023 + 400) { p *= 0x1p-400; pm1 *= 0x1p-400; }
+    else if (ex < 1023 - 400) { p *= 0x1p400; pm1 *= 0x1p400; }
+    if (i + 1 >= s) break;
+    const double pn = fma(d[i + 1] - x, p, -e2[i] * pm1);
+    pm1 = p;
+    p = pn;
+  }
+  return cnt;
+}
+
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// kappa_D(A) = kappa_2(D^-1/2 A D^-1/2), D = diag(A)  (Def. in Ch. 4.3): the
+// ratio of the extreme eigenvalues of the scaled matrix M.  M is reduced to a
+// symmetric tridiagonal T = Q^T M Q by s - 2 Householder reflections (Golub &
+// Van Loan, "Matrix Computations", Alg. 8.3.1: p = tau M' v, w = p -
+// (tau p^T v / 2) v, M' -= v w^T + w v^T, with the two products of each entry
+// added in an order that keeps M' exactly symmetric), and T's smallest and
+// largest eigenvalues are bracketed from its Gershgorin interval by
+// multisection on Sturm counts (64 points per round: the bracket shrinks by 65
+// per round, until it is within 8 eps ||T||, the accuracy to which the
+// eigenvalues of M are determined at all, or after 12 rounds).
+// +inf when a diagonal entry of A or the smallest
+// eigenvalue is <= 0.  M and M2 are shared work matrices; rot is unused.
+__device__ double sm_kappa_d(const double* A, int s, double* M, double* M2, double*, int* flag) {
+  __shared__ double s_tau, s_lo[2], s_hi[2];
   if (threadIdx.x == 0) *flag = 1;
   __syncthreads();
   for (int i = threadIdx.x; i < s; i += blockDim.x)
@@ -174,70 +221,110 @@ __device__ double sm_kappa_d(const double* A, int s, double* M, double* M2, doub
     M[IDX(a, c)] = A[IDX(a, c)] / sqrt(A[IDX(a, a)] * A[IDX(c, c)]);
   }
   __syncthreads();
-  const int N = (s % 2) ? s + 1 : s;          // players incl. a dummy for odd s
-  // rot[4*i]: partner index (or -1), rot[4*i+1] c, rot[4*i+2] role sign (+1 for p, -1 for q), rot[4*i+3] sn
-  for (int sweep = 0; sweep < 40 && s > 1; ++sweep) {
-    for (int round = 0; round < N - 1; ++round) {
-      if (threadIdx.x < N / 2) {
-        const int i = threadIdx.x;
-        auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + round) % (N - 1)) + 1; };
-        int p = player(i), q = player(N - 1 - i);
-        if (p > q) { const int t = p; p = q; q = t; }
-        if (q < s) {
-          const double app = M[IDX(p, p)], aqq = M[IDX(q, q)], apq = M[IDX(p, q)];
-          double cs = 1.0, sn = 0.0;
-          if (apq != 0.0) {
-            const double th = (aqq - app) / (2.0 * apq);
-            const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-            cs = 1.0 / sqrt(t * t + 1.0);
-            sn = t * cs;
-          }
-          rot[4 * p] = q; rot[4 * p + 1] = cs; rot[4 * p + 2] = 1.0; rot[4 * p + 3] = sn;
-          rot[4 * q] = p; rot[4 * q + 1] = cs; rot[4 * q + 2] = -1.0; rot[4 * q + 3] = sn;
-        } else if (p < s) {
-          rot[4 * p] = -1.0; rot[4 * p + 1] = 1.0; rot[4 * p + 2] = 1.0; rot[4 * p + 3] = 0.0;
-        }
+  if (s == 1) return 1.0;
+  double* v = M2;            // Householder vector (entries k+1 .. s-1 at 0 .. m-1)
+  double* w = M2 + 32;       // w = p - K v
+  double* dd = M2 + 64;      // diagonal of T
+  double* e2 = M2 + 96;      // squared off-diagonal of T
+  double* ee = M2 + 128;     // off-diagonal of T
+  double* part = M2 + 160;   // 8 warps x 32 partial sums of M' v
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  for (int k = 0; k + 2 < s; ++k) {
+    const int m = s - k - 1;
+    if (warp == 0) {
+      const double x = lane < m ? M[IDX(k + 1 + lane, k)] : 0.0;
+      const double x0 = __shfl_sync(0xffffffffu, x, 0);
+      const double tail = warp_sum(lane > 0 ? x * x : 0.0);
+      double tau = 0.0, alpha = x0;
+      if (tail > 0.0) {
+        const double sig = sqrt(fma(x0, x0, tail));
+        alpha = x0 >= 0.0 ? -sig : sig;
+        const double v0 = x0 - alpha;
+        tau = 2.0 / fma(v0, v0, tail);
+        if (lane < m) v[lane] = lane == 0 ? v0 : x;
       }
-      __syncthreads();
-      // M2 = J^T M J; column i of J: (row i: c, row partner: -sn) for a p-role
-      // index, (row partner: sn, row i: c) for a q-role index.
-      for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-        const int i = e / s, j = e % s;
-        const int pi = (int)rot[4 * i], pj = (int)rot[4 * j];
-        const double ci = rot[4 * i + 1], cj = rot[4 * j + 1];
-        const double oi = (pi < 0) ? 0.0 : (rot[4 * i + 2] > 0 ? -rot[4 * i + 3] : rot[4 * i + 3]);
-        const double oj = (pj < 0) ? 0.0 : (rot[4 * j + 2] > 0 ? -rot[4 * j + 3] : rot[4 * j + 3]);
-        double v = ci * cj * M[IDX(i, j)];
-        if (pj >= 0) v = fma(ci * oj, M[IDX(i, pj)], v);
-        if (pi >= 0) v = fma(oi * cj, M[IDX(pi, j)], v);
-        if (pi >= 0 && pj >= 0) v = fma(oi * oj, M[IDX(pi, pj)], v);
-        M2[IDX(i, j)] = v;
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-        const int i = e / s, j = e % s;
-        M[IDX(i, j)] = (i == j || (int)rot[4 * i] != j) ? M2[IDX(i, j)] : 0.0;
-      }
-      __syncthreads();
-    }
-    // convergence: every off-diagonal entry negligible relative to its diagonal pair
-    if (threadIdx.x == 0) *flag = 1;
-    __syncthreads();
-    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-      const int i = e / s, j = e % s;
-      if (i != j && fabs(M[IDX(i, j)]) > 1e-16 * sqrt(fabs(M[IDX(i, i)] * M[IDX(j, j)]))) *flag = 0;
+      if (lane == 0) { dd[k] = M[IDX(k, k)]; ee[k] = alpha; s_tau = tau; }
     }
     __syncthreads();
-    if (*flag) break;
+    const double tau = s_tau;
+    if (tau == 0.0) {                         // column already reduced
+      __syncthreads();                        // every thread has read s_tau
+      continue;
+    }
+    double acc = 0.0;
+    if (lane < m)
+      for (int i = warp; i < m; i += nw) acc = fma(M[IDX(k + 1 + i, k + 1 + lane)], v[i], acc);
+    part[warp * 32 + lane] = acc;
+    __syncthreads();
+    if (warp == 0) {
+      double pj = 0.0;
+      for (int q = 0; q < nw; ++q) pj += part[q * 32 + lane];
+      pj = lane < m ? tau * pj : 0.0;
+      const double vj = lane < m ? v[lane] : 0.0;
+      const double K = 0.5 * tau * warp_sum(pj * vj);
+      if (lane < m) w[lane] = fma(-K, vj, pj);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = e / m, j = e % m;
+      const double u = __dadd_rn(__dmul_rn(v[i], w[j]), __dmul_rn(w[i], v[j]));
+      M[IDX(k + 1 + i, k + 1 + j)] -= u;
+    }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    double lo = M[IDX(0, 0)], hi = lo;
-    for (int i = 1; i < s; ++i) { lo = fmin(lo, M[IDX(i, i)]); hi = fmax(hi, M[IDX(i, i)]); }
-    s_kappa = (lo > 0.0) ? hi / lo : INFINITY;
+    dd[s - 2] = M[IDX(s - 2, s - 2)];
+    ee[s - 2] = M[IDX(s - 1, s - 2)];
+    dd[s - 1] = M[IDX(s - 1, s - 1)];
   }
   __syncthreads();
-  return s_kappa;
+  // Gershgorin interval of T (warp 0), then multisection: threads 0..63 bracket
+  // the smallest eigenvalue (first point with count >= 1), 64..127 the largest
+  // (first point with count >= s).
+  if (warp == 0) {
+    double lo = INFINITY, hi = -INFINITY;
+    if (lane < s) {
+      const double r = (lane > 0 ? fabs(ee[lane - 1]) : 0.0) + (lane < s - 1 ? fabs(ee[lane]) : 0.0);
+      lo = dd[lane] - r;
+      hi = dd[lane] + r;
+      if (lane < s - 1) e2[lane] = ee[lane] * ee[lane];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+    }
+    if (lane < 2) { s_lo[lane] = lo; s_hi[lane] = hi; }
+  }
+  __syncthreads();
+  __shared__ int s_first[4];
+  // stop when both brackets are within 8 eps ||T|| (the accuracy to which
+  // the eigenvalues of M are determined at all), after 12 rounds at most
+  const double gnorm = fmax(fabs(s_lo[0]), fabs(s_hi[0]));
+  for (int round = 0; round < 12; ++round) {
+    bool done = true;              // uniform: every thread reads the same brackets
+    for (int q = 0; q < 2; ++q) done = done && (s_hi[q] - s_lo[q] <= 0x1p-49 * gnorm);
+    if (done) break;
+    const int g = (threadIdx.x >> 6) & 1, t = threadIdx.x & 63;
+    const double lo = s_lo[g], hi = s_hi[g];
+    const double step = (hi - lo) / 65.0;
+    bool in = false;
+    if (threadIdx.x < 128) in = sturm_count(dd, e2, s, lo + step * (t + 1)) >= (g == 0 ? 1 : s);
+    // first point (per group of two warps) at or above the eigenvalue; 64: none
+    const unsigned bal = __ballot_sync(0xffffffffu, in);
+    if (threadIdx.x < 128 && lane == 0) s_first[warp] = bal ? (warp & 1) * 32 + __ffs(bal) - 1 : 64;
+    __syncthreads();
+    if (threadIdx.x < 128 && t == 0) {
+      const int f = min(s_first[2 * g], s_first[2 * g + 1]);
+      // the eigenvalue lies in (x_{f-1}, x_f], x_{-1} = lo, x_64 = hi
+      s_lo[g] = f == 0 ? lo : lo + step * f;
+      s_hi[g] = f == 64 ? hi : lo + step * (f + 1);
+    }
+    __syncthreads();
+  }
+  const double lmin = 0.5 * (s_lo[0] + s_hi[0]), lmax = 0.5 * (s_lo[1] + s_hi[1]);
+  return (lmin > 0.0 && s_hi[0] > 0.0) ? lmax / lmin : INFINITY;
 }
 
 // max that propagates NaN (fmax would drop it)
@@ -430,6 +517,24 @@ static cudaError_t launch_small(void (*k)(Ctrl*), const Launch& L, Ctrl* c) {
 }
 
 cudaError_t small_bcg_init(const Launch& L, Ctrl* c, int) { return launch_small(small_bcg_init_k, L, c); }
+
+// The adaptive criterion's kappa_D on its own (the same device routine).
+__global__ void __launch_bounds__(kST) small_kappa_d_k(int s, const double* A, double* out) {
+  extern __shared__ double smraw[];
+  SmallSmem& S = *reinterpret_cast<SmallSmem*>(smraw);
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) S.A[IDX(i / s, i % s)] = A[i];
+  __syncthreads();
+  const double k = sm_kappa_d(S.A, s, S.B, S.C, S.rot, &S.flag);
+  if (threadIdx.x == 0) *out = k;
+}
+
+cudaError_t small_kappa_d(const Launch& L, int s, const double* A, double* out) {
+  const size_t sm = sizeof(SmallSmem);
+  cudaError_t e = cudaFuncSetAttribute(small_kappa_d_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  small_kappa_d_k<<<1, kST, sm, L.stream>>>(s, A, out);
+  return cudaGetLastError();
+}
 
 cudaError_t small_bcg_1(const Launch& L, Ctrl* c, const uint8_t* forced) {
   const size_t sm = sizeof(SmallSmem);

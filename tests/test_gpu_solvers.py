@@ -98,6 +98,62 @@ def test_bcg_adaptive_eta_with_replay(h):
     op.close()
 
 
+def _spd_scaled(s, cond, seed, block=None):
+    g = np.random.default_rng(seed)
+    Qm, _ = np.linalg.qr(g.standard_normal((s, s)))
+    A = (Qm * np.geomspace(1.0, cond, s)) @ Qm.T
+    d = 10.0 ** g.uniform(-3, 3, s)
+    A = d[:, None] * A * d[None, :]
+    if block:                                   # S_BP^p: block diagonal
+        for a in range(s):
+            for b in range(s):
+                if a // block != b // block:
+                    A[a, b] = 0.0
+    return np.triu(A) + np.triu(A, 1).T
+
+
+def test_kappa_d_matches_oracle(h):
+    """The device kappa_D (Householder tridiagonalisation + Sturm multisection)
+    against the oracle's (LAPACK eigenvalues of the scaled matrix): both
+    determine the extreme eigenvalues to about eps ||M||, so they agree to
+    ~ s kappa eps relative."""
+    eps = 2.0 ** -52
+    cases = [(s, c, seed) for seed, (s, c) in enumerate(
+        [(1, 1.0), (2, 3.0), (3, 1e2), (5, 1e6), (8, 1e3), (8, 1e10), (13, 50.0), (16, 1e4),
+         (16, 1e8), (24, 1e5), (31, 1e7), (32, 10.0), (32, 1e4), (32, 1e9), (32, 1e12)])]
+    for s, cond, seed in cases:
+        for block in (None, s // 2 if s % 2 == 0 and s >= 4 else None):
+            A = _spd_scaled(s, cond, seed, block)
+            ref = oracle.kappa_d(A)
+            got = h.kappa_d(_dev(A))
+            assert abs(got - ref) <= (1e-9 + 2 * s * ref * eps) * ref, (s, cond, block, got, ref)
+    assert h.kappa_d(_dev(np.eye(7))) == 1.0
+    assert math.isinf(h.kappa_d(_dev(np.array([[1.0, 2.0], [2.0, 1.0]]))))     # indefinite
+    assert math.isinf(h.kappa_d(_dev(np.array([[0.0, 0.0], [0.0, 1.0]]))))     # zero diagonal
+
+
+@pytest.mark.parametrize("name,grid,s", [("vardiff3d", 12, 4), ("vardiff3d", 12, 16), ("edge2d", 48, 32)])
+def test_bcg_adaptive_decisions_over_widths(h, name, grid, s):
+    """The adaptive criterion eta kappa_D(alpha) > 1/sqrt(eps), decided by the
+    device routine on the oracle's own alpha^k, agrees with the oracle's
+    decision wherever kappa_D is not within 1 % of the threshold; a
+    free-running GPU solve (whose iterates drift from the oracle's after some
+    tens of iterations) matches its counts."""
+    prob = W.problem(name, grid=grid, s=s)
+    op = _op(h, prob, "stencil")
+    ref = oracle.bcg(prob.A, prob.B, tol=1e-8, maxit=2000, eta=1e4, record_alpha=True)
+    assert 0 < sum(ref.decisions) < len(ref.decisions)       # the criterion is exercised
+    X, info = h.solve("bcg", op, _dev(prob.B), tol=1e-8, maxit=2000, eta=1e4)
+    assert info.converged and ref.converged and abs(info.iters - ref.iters) <= 2
+    assert abs(sum(info.decisions) - sum(ref.decisions)) <= 2
+    thr = 2.0 ** 26                                         # 1 / sqrt(eps), FP64
+    for k, alpha in enumerate(ref.alphas):
+        kap = h.kappa_d(_dev(alpha))
+        if abs(1e4 * ref.kappas[k] / thr - 1.0) >= 0.01:
+            assert (1e4 * kap > thr) == ref.decisions[k], (k, kap, ref.kappas[k])
+    op.close()
+
+
 def test_bcg_s1_equals_scalar_cg(h):
     prob = W.problem("laplace3d", s=1, grid=12)
     op = _op(h, prob, "stencil")
