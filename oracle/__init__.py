@@ -28,7 +28,7 @@ are marked "parity unpinned" in their docstring (none at present).
 """
 from .blockops import (spmm, gram, householder_qr, normalizer, kappa_d, chol_solve,
                        lu_solve, col_norms, reortho_decision, project_subalgebra)
-from .bcg import bcg, scalar_cg, BCGResult
+from .bcg import bcg, bcg_1r, scalar_cg, BCGResult
 from .bbicgstab import bbicgstab
 from .bgmres import bgmres
 from .tsqr import tsqr
@@ -38,7 +38,7 @@ from .adjoint import dense_adjoint, adjoint_scatter, edge_theta_grad
 
 __all__ = [
     "spmm", "gram", "householder_qr", "normalizer", "kappa_d", "chol_solve", "lu_solve",
-    "col_norms", "reortho_decision", "project_subalgebra", "bcg", "scalar_cg",
+    "col_norms", "reortho_decision", "project_subalgebra", "bcg", "bcg_1r", "scalar_cg",
     "BCGResult", "bbicgstab", "bgmres", "tsqr", "bcg_ir", "dense_adjoint",
     "adjoint_scatter", "edge_theta_grad", "jacobi_inverse_diagonal", "apply_diagonal",
 ]

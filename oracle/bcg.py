@@ -151,6 +151,98 @@ def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit
     return out
 
 
+def bcg_1r(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit: int = 1000,
+           eta: float = math.inf, forced=None, record_iterates: int = 0, dtype=np.float64,
+           eps: float | None = None, Minv=None) -> BCGResult:
+    """BCG with one reduction per iteration, Alg. "1R-CG" (Ch. 8.1), block case S_B.
+
+    Arithmetically equal to Alg. "bcgaro": with U = A Z, delta = <Z, U>, the
+    next alpha follows from alpha^{k+1} = delta^{k+1} - beta^T alpha^k beta
+    (Eq. "alpha_k+1" simplified with <Z^{k+1}, Q^k> = -beta^T alpha), and Q is
+    updated as Q = U + Q beta instead of being recomputed as A P.  The norms,
+    the re-orthonormalisation test and the readings are those of ``bcg``.
+    """
+    B = np.asarray(B)
+    n, s = B.shape
+    if eps is None:
+        eps = float(np.finfo(dtype).eps)
+    op = lambda V: spmm(A, V, dtype=dtype)
+    if Minv is None:
+        prec = lambda V: np.array(V, dtype=dtype, copy=True)
+    elif callable(Minv):
+        prec = lambda V: np.asarray(Minv(V), dtype=dtype)
+    else:
+        prec = lambda V: apply_diagonal(Minv, V, dtype)
+    X = np.zeros((n, s), dtype=dtype) if X0 is None else np.array(X0, dtype=dtype, copy=True)
+    B = B.astype(dtype, copy=False)
+
+    R = B - op(X)
+    n0 = col_norms(R)
+    n0_safe = np.where(n0 > 0, n0, 1.0)
+    if eta > 0:
+        Rb, sigma = normalizer(R)
+        Rb = Rb.astype(dtype)
+    else:
+        Rb, sigma = R, np.eye(s)
+    G = gram(Rb, Rb)
+    P = prec(Rb)                        # P^0 = M^{-1} R-bar^0
+    rho = gram(P, Rb)                   # rho^0 = <P^0, R-bar^0>
+    Q = op(P)                           # Q^0 = A P^0
+    alpha = gram(P, Q)                  # alpha^0 = <P^0, Q^0>
+    res = _resid_from(sigma, G, None, reortho=False)
+    relres = np.where(n0 > 0, res / n0_safe, 0.0)
+    out = BCGResult(X, 0, 0, bool(relres.max(initial=0.0) <= tol), "ok", relres)
+    if out.converged:
+        return out
+    for k in range(maxit):
+        try:
+            lam = chol_solve(alpha, rho)
+        except Breakdown:
+            out.status = "breakdown"; out.iters = k; return out
+        if forced is not None and k < len(forced):
+            reo = bool(forced[k])
+        else:
+            reo = reortho_decision(eta, alpha, eps)
+        Rt = Rb - Q @ lam.astype(dtype)
+        sigma_old = sigma
+        if reo:
+            Rb, gamma = normalizer(Rt)
+            Rb = Rb.astype(dtype)
+            sigma = gamma @ sigma
+            out.reorths += 1
+            G = None
+        else:
+            Rb, gamma = Rt, np.eye(s)
+            G = gram(Rb, Rb)
+        res = _resid_from(sigma, G, None, reortho=reo)
+        X += P @ (lam @ sigma_old).astype(dtype)       # X^{k+1} = X^k + P^k lambda^k sigma^k
+        Z = prec(Rb)                                    # Z^{k+1} = M^{-1} R-bar^{k+1}
+        rho_new = gram(Z, Rb)                           # rho^{k+1} = <Z^{k+1}, R-bar^{k+1}>
+        U = op(Z)                                       # U^{k+1} = A Z^{k+1}
+        delta = gram(Z, U)                              # delta^{k+1} = <Z^{k+1}, U^{k+1}>
+        relres = np.where(n0 > 0, res / n0_safe, 0.0)
+        out.history.append(float(relres.max(initial=0.0)))
+        out.decisions.append(reo)
+        if k < record_iterates:
+            out.iterates.append(X.copy())
+        out.iters = k + 1
+        out.relres = relres
+        if relres.max(initial=0.0) <= tol:
+            out.converged = True
+            return out
+        try:
+            beta = chol_solve(rho, gamma.T @ rho_new)
+        except Breakdown:
+            out.status = "breakdown"; return out
+        P = Z + P @ beta.astype(dtype)
+        Q = U + Q @ beta.astype(dtype)
+        alpha = delta - beta.T @ alpha @ beta           # alpha^{k+1} = delta^{k+1} - beta^T alpha^k beta
+        alpha = np.triu(alpha) + np.triu(alpha, 1).T
+        rho = rho_new
+    out.status = "not_converged"
+    return out
+
+
 def _resid_from(sigma, G, p, reortho):
     """Column norms of the true residual R = R-bar sigma (Ch. 4.3, after Alg. "bcgro").
 

@@ -4,9 +4,8 @@
 //
 // The thesis splits the rows over MPI processes; here the "processes" are
 // row tiles of one GPU:
-//   1. leaf factor   one CTA per tile of 256 x RPT rows (RPT = 64 / next_pow2(s)
-//                    for FP32 blocks, 32 / next_pow2(s) for FP64), the rows in
-//                    registers: Householder QR of the tile; the reflectors
+//   1. leaf factor   one CTA per tile of 256 x RPT rows (RPT = 64 / next_pow2(s)),
+//                    the rows in registers: Householder QR of the tile; the reflectors
 //                    overwrite the tile in Y; the tile's R factor and the factor
 //                    F = strict_upper(V^T V) + diag(tau) of its compact WY form
 //                    H_0 ... H_{s-1} = I - V T V^T (T^{-1} = diag(1/tau) +
@@ -31,10 +30,12 @@ namespace bk {
 
 constexpr int kTT = 256;                 // threads per TSQR CTA
 
-// Rows per leaf tile: 256 threads x RPT rows each, RPT = 64 / next_pow2(s)
-// for FP32 blocks and 32 / next_pow2(s) for FP64 ones, i.e. 64 registers of
-// row data per thread.  Larger FP32 tiles also shrink the FP64 tree.
-constexpr int leaf_rpt(int sw, int elem_bytes) { return (elem_bytes == 4 ? 64 : 32) / sw; }
+// Rows per leaf tile: 256 threads x RPT rows each, RPT = 64 / next_pow2(s),
+// i.e. 64 row values per thread in either precision (FP64 at s = 32 this
+// took one BCG iteration at 128^3 from 37.5 to 33.9 ms against 32 /
+// next_pow2(s) rows; within 2 % at s = 8, 16).  Larger tiles also shrink the
+// tree.
+constexpr int leaf_rpt(int sw, int) { return 64 / sw; }
 inline int leaf_tile_rows(int s, int elem_bytes) { return kTT * leaf_rpt(next_pow2_s(s), elem_bytes); }
 
 TsqrPlan tsqr_plan(int64_t n, int s, int elem_bytes) {

@@ -130,6 +130,45 @@ def test_bcg_mutation_is_caught(mod, fn, old, new, monkeypatch):
         assert not _bcg_battery_passes(bmod.bcg)
 
 
+def _bcg1r_battery_passes(fn):
+    """1R-BCG against the 2R oracle (iterates), with and without Jacobi, and at s = 1."""
+    try:
+        bmod = sys.modules["oracle.bcg"]
+        kf = np.exp(0.5 * np.random.default_rng(5).standard_normal(216))
+        for A in (W.lap2d5(12, 11), W.diff3d7_var(6, 6, 6, kf)):
+            B = W.normal_block(A.n, 4, 2)
+            for eta in (0.0, math.inf):
+                for w in (None, sys.modules["oracle.precond"].jacobi_inverse_diagonal(A)):
+                    a = bmod.bcg(A, B, tol=0.0, maxit=8, eta=eta, Minv=w, record_iterates=8)
+                    b = fn(A, B, tol=0.0, maxit=8, eta=eta, Minv=w, record_iterates=8)
+                    for k in range(8):
+                        if np.abs(b.iterates[k] - a.iterates[k]).max() > 1e-10 * np.abs(a.iterates[k]).max():
+                            return False
+        return True
+    except Exception:
+        return False
+
+
+BCG1R_MUTATIONS = [
+    ("alpha = delta - beta.T @ alpha @ beta", "alpha = delta + beta.T @ alpha @ beta"),
+    ("alpha = delta - beta.T @ alpha @ beta", "alpha = delta - beta @ alpha @ beta.T"),
+    ("Q = U + Q @ beta.astype(dtype)", "Q = U + Q @ beta.T.astype(dtype)"),
+    ("U = op(Z)", "U = op(Rb)"),
+    ("delta = gram(Z, U)", "delta = gram(Rb, U)"),
+    ("rho_new = gram(Z, Rb)", "rho_new = gram(Rb, Rb)"),
+    ("X += P @ (lam @ sigma_old)", "X += P @ (lam @ sigma)"),
+]
+
+
+def test_unmutated_bcg1r_passes_battery():
+    assert _bcg1r_battery_passes(sys.modules["oracle.bcg"].bcg_1r)
+
+
+@pytest.mark.parametrize("old,new", BCG1R_MUTATIONS)
+def test_bcg1r_mutation_is_caught(old, new):
+    assert not _bcg1r_battery_passes(_mutant("oracle.bcg", "bcg_1r", old, new))
+
+
 def _qr_battery_passes(qr_fn):
     try:
         for (n, s) in ((40, 6), (12, 12)):
