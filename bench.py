@@ -84,6 +84,9 @@ def parse():
                    help="point-Jacobi preconditioned BCG against M = I on the variable-coefficient "
                         "workloads: time and iterations to tolerance, cost per iteration, and the "
                         "fused M^-1 + Gram pass against its roofline")
+    p.add_argument("--one-reduction", action="store_true",
+                   help="BCG with one reduction per iteration (Alg. 1R-CG) against the default "
+                        "two-reduction schedule: time per iteration and to tolerance")
     p.add_argument("--ir", action="store_true",
                    help="time-to-1e-10 of FP32+IR vs plain FP64 BCG on the 192^3 log-normal diffusion "
                         "workload (s = 16) instead of the default line")
@@ -511,6 +514,54 @@ def run_precond(args):
                       "results": out}))
 
 
+def run_one_reduction(args):
+    """Alg. "1R-CG" against Alg. "2R-CG" on one GPU: device time to tolerance (the smaller
+    of two runs after a warm-up), iterations, and time per iteration (23 minus 3
+    iterations, over 20)."""
+    import torch
+    import workloads as W
+    from paper_2104_02494_gb300 import build
+    from paper_2104_02494_gb300.api import Handle, operator_from_problem
+    build()
+    h = Handle(0)
+    cases = [
+        ("poisson2d 64^2 5-point CSR, s=4, FP64 BCG eta=inf, 1e-8", "poisson2d", "csr", None, 4, False,
+         dict(tol=1e-8, eta=math.inf)),
+        ("laplace3d 128^3 stencil, s=8, FP64 BCG eta=inf, 1e-8", "laplace3d", "stencil", None, 8, False,
+         dict(tol=1e-8, eta=math.inf)),
+        ("vardiff3d 128^3 var7 stencil, s=8, FP64 BCG eta=1e4, Jacobi, 1e-8", "vardiff3d", "stencil", 128, 8,
+         True, dict(tol=1e-8, eta=1e4)),
+    ]
+    out = []
+    for label, wl, use, grid, s, jac, kw in cases:
+        prob = W.problem(wl, s=s, grid=grid, with_csr=(use == "csr"))
+        op = operator_from_problem(h, prob, use)
+        M = h.op_jacobi(op) if jac else None
+        B = torch.from_numpy(prob.B).cuda()
+        row = {"case": label}
+        for name, one in (("two_reductions", False), ("one_reduction", True)):
+            h.solve("bcg", op, B, maxit=3, record=False, precond=M, one_reduction=one, **kw)
+            times = []
+            for _ in range(2):
+                _, info = h.solve("bcg", op, B, maxit=20000, record=False, precond=M, one_reduction=one, **kw)
+                times.append(info.elapsed_ms)
+            pk = dict(kw, tol=0.0)
+            if kw.get("prec") == "fp32_ir":
+                pk["ir_max_outer"] = 1
+            _, i23 = h.solve("bcg", op, B, maxit=23, record=False, precond=M, one_reduction=one, **pk)
+            _, i3 = h.solve("bcg", op, B, maxit=3, record=False, precond=M, one_reduction=one, **pk)
+            row[name] = {"time_ms": min(times), "iters": info.iters, "converged": info.converged,
+                         "relres_max": info.relres_max, "ms_per_iter": (i23.elapsed_ms - i3.elapsed_ms) / 20}
+        out.append(row)
+        if M is not None:
+            M.close()
+        op.close()
+        del B
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "BCG time to tolerance, one vs two reductions per iteration (device time)",
+                      "results": out}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -529,6 +580,8 @@ def main():
         return run_subalgebra(args)
     if args.precond:
         return run_precond(args)
+    if args.one_reduction:
+        return run_one_reduction(args)
     rank, world, dist = dist_init(args)
     import torch
     import workloads as W

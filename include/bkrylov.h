@@ -107,6 +107,12 @@ typedef struct {
                           Jacobi.  Applies to the FP32 inner solves of FP32_IR too.
                           NULL: M = I.  BK_ERR_ARG if its n differs from A's;
                           BK_ERR_UNSUPPORTED for BBiCGStab and BGMRes            (NULL) */
+  int one_reduction;   /* BCG only: 1 = the schedule of Alg. "1R-CG" (Ch. 8.1): U = A Z and
+                          delta = <Z, U> after the preconditioner, Q = U + Q beta,
+                          alpha = delta - beta^T alpha beta, arithmetically equal to the
+                          default two-reduction schedule (Alg. "2R-CG") at two more block
+                          vectors and one more block update per iteration.  Needs the
+                          block case (BK_ERR_UNSUPPORTED with subalgebra_p < s)     (0) */
 } bkrylov_opts;
 
 /* Solver report.  Pointer members are HOST arrays supplied by the caller (or NULL). */

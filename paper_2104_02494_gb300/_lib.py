@@ -26,7 +26,7 @@ class bkrylov_opts(C.Structure):
         ("ortho", C.c_int), ("prec", C.c_int), ("ir_inner_tol", C.c_double),
         ("ir_max_outer", C.c_int), ("forced_reortho", C.POINTER(C.c_uint8)), ("n_forced", C.c_int),
         ("sync_every", C.c_int), ("profile", C.c_int), ("subalgebra_p", C.c_int),
-        ("precond", C.c_void_p),
+        ("precond", C.c_void_p), ("one_reduction", C.c_int),
     ]
 
 

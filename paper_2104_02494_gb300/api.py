@@ -194,14 +194,15 @@ class Handle:
     # ---- solvers ----
     def solve(self, method: str, A: "Operator", B, X=None, *, tol=1e-8, maxit=1000, eta=math.inf,
               prec="fp64", restart=30, ortho="cgs2", ir_inner_tol=1e-5, ir_max_outer=30,
-              forced_reortho=None, sync_every=0, record=True, profile=False, p=None, precond=None):
+              forced_reortho=None, sync_every=0, record=True, profile=False, p=None, precond=None,
+              one_reduction=False):
         """Run bkrylov_solve_{bcg,bbicgstab,bgmres}; returns (X, SolveInfo).
 
         B, X: float64 n x s blocks, on the device (torch CUDA tensors) or on
         the host (numpy / CPU tensors; copied inside the call).  X is updated
         in place and starts from zero when not given.  ``p``: block size of
         the block-parallel subalgebra (BCG); ``precond``: an Operator applying
-        M^{-1} (BCG, e.g. ``op_jacobi(A)``).
+        M^{-1} (BCG, e.g. ``op_jacobi(A)``); ``one_reduction``: the 1R-BCG schedule.
         """
         s = B.shape[1]
         if X is None:
@@ -214,6 +215,7 @@ class Handle:
         o.profile = 1 if profile else 0
         o.subalgebra_p = 0 if p is None else int(p)
         o.precond = None if precond is None else precond.ptr.value
+        o.one_reduction = 1 if one_reduction else 0
         forced_arr = None
         if forced_reortho is not None:
             forced_arr = (C.c_uint8 * max(1, len(forced_reortho)))(*[1 if f else 0 for f in forced_reortho])

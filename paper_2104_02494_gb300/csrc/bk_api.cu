@@ -112,6 +112,7 @@ int ctrl_upload(bkrylov_handle h, Ctrl* dev, int s, const bkrylov_opts& o, doubl
   c->n_forced = (o.forced_reortho && o.n_forced > 0) ? o.n_forced : 0;
   c->sub_p = (o.subalgebra_p > 0 && o.subalgebra_p < s) ? o.subalgebra_p : s;
   c->has_prec = o.precond != nullptr;
+  c->one_r = o.one_reduction != 0;
   for (int i = 0; i < s; ++i) c->sigma[i * kMaxS + i] = 1.0;
   BK_TRY(cudaMemcpyAsync(dev, c, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
   // the pinned staging buffer is reused: wait for the copy before returning
@@ -163,6 +164,7 @@ template <typename T>
 struct BcgBufs {
   T *R, *P, *Q;
   T* Z = nullptr;              // M^{-1} R-bar (preconditioned solves only)
+  T* U = nullptr;              // A Z (the one-reduction schedule only)
   const OpDesc* M = nullptr;   // the preconditioner M^{-1}, or null (M = I)
   void* tsqr;
   double* gpart;
@@ -174,12 +176,13 @@ struct BcgBufs {
 
 template <typename T, typename Alloc>
 void bcg_layout(Alloc& a, int64_t n, int s, int maxit, const TsqrPlan& tp, const Launch& L,
-                BcgBufs<T>* b, bool prec) {
+                BcgBufs<T>* b, bool prec, bool one_r) {
   const size_t ns = (size_t)n * s;
   auto r = a.template take<T>(ns);
   auto p = a.template take<T>(ns);
   auto q = a.template take<T>(ns);
   b->Z = prec ? a.template take<T>(ns) : nullptr;
+  b->U = one_r ? a.template take<T>(ns) : nullptr;
   auto t = a.template take<char>(tp.bytes);
   auto g = a.template take<double>(gpart_count(L, tp));
   auto c = a.template take<Ctrl>(1);
@@ -281,6 +284,48 @@ cudaError_t bcg_iteration(const Launch& L, const OpDesc& A, int s, T* X, const B
   return e;
 }
 
+// One iteration of Alg. "1R-CG" (block case): the operator is applied to Z
+// after the preconditioner, fused with delta = Z^T U, and alpha comes from the
+// recursion alpha = delta - beta^T alpha beta in the small kernel; Q is
+// updated like P (Q = U + Q beta) instead of being recomputed.
+template <typename T>
+cudaError_t bcg_iteration_1r(const Launch& L, const OpDesc& A, int s, T* X, const BcgBufs<T>& b,
+                             const TsqrPlan& tp) {
+  Ctrl* c = b.ctrl;
+  cudaError_t e;
+  prof_begin(L, kPhSmall1);
+  if ((e = small_bcg_1(L, c, b.forced)) != cudaSuccess) return e;
+  prof_end(L, kPhSmall1, 1);
+  prof_begin(L, kPhUpdate);
+  if ((e = bcg_update<T>(L, A.n, s, b.P, b.Q, X, b.R, c, b.gpart, 1)) != cudaSuccess) return e;
+  prof_end(L, kPhUpdate, 2);
+  if ((e = tsqr_groups<T>(L, tp, s, b.R, c->gamma, b.M ? nullptr : c->rho_new, b.tsqr, b.gpart,
+                          &c->counters[kCntC], &c->done, &c->reortho_now)) != cudaSuccess) return e;
+  if (b.M) {
+    Epi<T> pz;
+    pz.left = b.R; pz.sym = 1; pz.gram_out = c->rho_m; pz.gpart = b.gpart;
+    pz.counter = &c->counters[kCntA]; pz.done = &c->done;
+    prof_begin(L, kPhPrec);
+    if ((e = spmm<T>(L, *b.M, s, b.R, b.Z, nullptr, pz)) != cudaSuccess) return e;
+    prof_end(L, kPhPrec, 1);
+  }
+  const T* Zn = b.M ? b.Z : b.R;
+  Epi<T> ed;                                      // U = A Z, delta = Z^T U
+  ed.left = Zn; ed.sym = 1; ed.gram_out = c->delta; ed.gpart = b.gpart;
+  ed.counter = &c->counters[kCntA]; ed.done = &c->done;
+  prof_begin(L, kPhSpmm);
+  if ((e = spmm<T>(L, A, s, Zn, b.U, nullptr, ed)) != cudaSuccess) return e;
+  prof_end(L, kPhSpmm, 1);
+  prof_begin(L, kPhSmall2);
+  if ((e = small_bcg_2(L, c, b.hist, b.dec)) != cudaSuccess) return e;
+  prof_end(L, kPhSmall2, 1);
+  prof_begin(L, kPhPupdate);
+  if ((e = bcg_pupdate<T>(L, A.n, s, Zn, b.P, c)) != cudaSuccess) return e;    // P = Z + P beta
+  e = bcg_pupdate<T>(L, A.n, s, b.U, b.Q, c);                                  // Q = U + Q beta
+  prof_end(L, kPhPupdate, 2);
+  return e;
+}
+
 // A batch of solver iterations captured as one CUDA graph (destroyed with the
 // object).  capture(h, k, step) records k calls of step(Launch) on the
 // handle's private capture stream; nothing runs until the graph is launched.
@@ -330,11 +375,12 @@ int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const
   const int maxit = o.maxit > 0 ? o.maxit : 0;
   BcgBufs<T> b;
   Bump probe(nullptr, 0);
-  bcg_layout<T>(probe, n, s, maxit, tp, L, &b, M != nullptr);
+  const bool one_r = o.one_reduction != 0;
+  bcg_layout<T>(probe, n, s, maxit, tp, L, &b, M != nullptr, one_r);
   int rc = ensure_ws(h, 0, probe.off + 4096);
   if (rc) return rc;
   Bump bump(h->ws[0], h->ws_cap[0]);
-  bcg_layout<T>(bump, n, s, maxit, tp, L, &b, M != nullptr);
+  bcg_layout<T>(bump, n, s, maxit, tp, L, &b, M != nullptr, one_r);
   b.M = M;
   if ((rc = ctrl_upload(h, b.ctrl, s, o, eps))) return rc;
   if (o.forced_reortho && o.n_forced > 0) {
@@ -367,6 +413,12 @@ int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const
   } else {
     BK_TRY(cudaMemcpyAsync(b.P, b.R, sizeof(T) * (size_t)n * s, cudaMemcpyDeviceToDevice, L.stream));
   }
+  if (one_r) {
+    // Alg. "1R-CG": Q^0 = A P^0 and alpha^0 = <P^0, Q^0> before the loop
+    Epi<T> pa;
+    pa.left = b.P; pa.sym = 1; pa.gram_out = c->alpha; pa.gpart = b.gpart; pa.counter = &c->counters[kCntA];
+    BK_TRY(spmm<T>(L, A, s, b.P, b.Q, nullptr, pa));
+  }
   BK_TRY(small_bcg_init(L, c, o.eta > 0));
   Launch Lp = L;
   if (o.profile) Lp.prof = &h->prof;
@@ -385,14 +437,14 @@ int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const
     const int todo = (maxit - enq) < batch ? (maxit - enq) : batch;
     if (use_graph && !gb.failed && enq > 0 && todo == batch && !gb.exec) {
       // a capture that the runtime refuses leaves the direct launches below in charge
-      if (gb.capture(h, batch, [&](const Launch& Lc) { return bcg_iteration<T>(Lc, A, s, X, b, tp); }))
+      if (gb.capture(h, batch, [&](const Launch& Lc) { return (one_r ? bcg_iteration_1r<T>(Lc, A, s, X, b, tp) : bcg_iteration<T>(Lc, A, s, X, b, tp)); }))
         gb.failed = true;
     }
     if (gb.exec && todo == batch) {
       BK_TRY(cudaGraphLaunch(gb.exec, L.stream));
     } else {
       for (int i = 0; i < todo; ++i) {
-        BK_TRY(bcg_iteration<T>(Lp, A, s, X, b, tp));
+        BK_TRY((one_r ? bcg_iteration_1r<T>(Lp, A, s, X, b, tp) : bcg_iteration<T>(Lp, A, s, X, b, tp)));
         prof_collect(Lp.prof);
       }
     }
@@ -1054,6 +1106,7 @@ int bkrylov_solve_bcg(bkrylov_handle h, bkrylov_op A, int s, const double* B, do
   opts_or_default(opts, &o);
   int rc = check_solve_args(h, A, s, B, X, o);
   if (rc) return rc;
+  if (o.one_reduction && !block_case(o, s)) return BK_ERR_UNSUPPORTED;
   const int64_t n = A->d.n;
   if (o.prec == BK_FP64) {
     return with_device_blocks(h, n, s, B, X, 0, [&](const double* dB, double* dX, size_t) {
@@ -1077,7 +1130,7 @@ int bkrylov_solve_bbicgstab(bkrylov_handle h, bkrylov_op A, int s, const double*
   opts_or_default(opts, &o);
   int rc = check_solve_args(h, A, s, B, X, o);
   if (rc) return rc;
-  if (!block_case(o, s) || o.precond) return BK_ERR_UNSUPPORTED;
+  if (!block_case(o, s) || o.precond || o.one_reduction) return BK_ERR_UNSUPPORTED;
   if (o.prec != BK_FP64) return BK_ERR_UNSUPPORTED;
   return with_device_blocks(h, A->d.n, s, B, X, 0, [&](const double* dB, double* dX, size_t) {
     return bicg_device(h, A->d, s, dB, dX, o, info);
@@ -1090,7 +1143,7 @@ int bkrylov_solve_bgmres(bkrylov_handle h, bkrylov_op A, int s, const double* B,
   opts_or_default(opts, &o);
   int rc = check_solve_args(h, A, s, B, X, o);
   if (rc) return rc;
-  if (!block_case(o, s) || o.precond) return BK_ERR_UNSUPPORTED;
+  if (!block_case(o, s) || o.precond || o.one_reduction) return BK_ERR_UNSUPPORTED;
   if (o.prec != BK_FP64) return BK_ERR_UNSUPPORTED;
   if (o.restart < 1 || o.restart > 64) return BK_ERR_ARG;
   return with_device_blocks(h, A->d.n, s, B, X, 0, [&](const double* dB, double* dX, size_t) {

@@ -41,6 +41,7 @@ struct Ctrl {
   int n_forced;
   int sub_p;         // block size of S_BP^p (s: the block case S_B)
   int has_prec;      // BCG with a preconditioner M^{-1} (rho_m carries rho)
+  int one_r;         // BCG with one reduction (Alg. "1R-CG"): alpha from delta
   double tol;
   double eta;
   double eps;        // machine epsilon of the working precision
@@ -53,6 +54,7 @@ struct Ctrl {
   double rho[kMM];       // BCG rho   = Rb^T Rb      | BBiCGStab R^T R (kappa_D, norms)
   double rho_new[kMM];   // BCG: R-bar^T R-bar of the new residual block (Euclidean)
   double rho_m[kMM];     // BCG with M: <Z, R-bar> = R-bar^T M^{-1} R-bar
+  double delta[kMM];     // 1R-BCG: <Z, U> = Z^T A Z
   double sigma[kMM];
   double gamma[kMM];     // normalizer R factor of the last TSQR (diag >= 0)
   double lam[kMM];       // lambda

@@ -505,6 +505,20 @@ __global__ void __launch_bounds__(kST) small_bcg_2_k(Ctrl* c, double* history, u
     c->beta[IDX(a, b)] = S.E[IDX(a, b)];
     c->rho[IDX(a, b)] = S.A[IDX(a, b)];
   }
+  if (c->one_r) {
+    // Alg. "1R-CG": alpha^{k+1} = delta^{k+1} - beta^T alpha^k beta (upper triangle, mirrored)
+    sm_copy(S.B, c->alpha, s);
+    __syncthreads();
+    sm_matmul(S.F, S.B, false, S.E, s);        // alpha beta
+    __syncthreads();
+    sm_matmul(S.C, S.E, true, S.F, s);         // beta^T alpha beta
+    __syncthreads();
+    for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
+      const int a = i / s, b = i % s;
+      const int u = a < b ? a : b, v = a < b ? b : a;
+      c->alpha[IDX(a, b)] = c->delta[IDX(u, v)] - S.C[IDX(u, v)];
+    }
+  }
   if (threadIdx.x == 0 && c->iter >= c->maxit) { c->done = kDoneStopped; c->status = BK_NOT_CONVERGED; }
 }
 
