@@ -45,6 +45,11 @@ UNIT = "RHS*iter/s"
 # (the part's nominal 1.25 TFLOP/s FP64 rate at its maximum SM clock)
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
 
+# DRAM bytes (read + write) per launch of a kernel phase, from one ncu --set full capture
+# of the current kernel on the same workload (the level-0 TSQR leaf factor at 128^3, s = 8:
+# 134.349 MB read + 79.423 MB written); keyed by (phase, grid, s, operator).
+NCU_TRAFFIC = {("tsqr_leaf_factor", 128, 8, "stencil"): 134.349056e6 + 79.423488e6}
+
 
 def _hbm_peak():
     try:
@@ -623,8 +628,10 @@ def main():
     dom_ms = dom[1] / max(dom[2], 1)
     flops = PHASE_FLOPS[dom[0]](n, s)
     achieved = flops / (dom_ms / 1000.0) / 1e12
+    traffic = NCU_TRAFFIC.get((dom[0], args.grid, s, args.op))
     roofline = {"bound": "alu", "kernel": dom[0], "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu dram read + write)" if traffic else None,
                 "peak_source": "derived: 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop",
                 "hbm_achieved_gbs": PHASE_BYTES[dom[0]](n, s) / (dom_ms / 1000.0) / 1e9}
 
