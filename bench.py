@@ -99,7 +99,9 @@ def parse():
 
 
 def run_ir(args):
-    """FP32 inner BCG (to 1e-5) + FP64 refinement vs plain FP64 BCG, both to 1e-10."""
+    """FP32 inner BCG (to 1e-5) + FP64 refinement vs plain FP64 BCG, both to 1e-10; then the
+    same pair with point Jacobi, the refinement's inner solve with the adaptive criterion
+    (eta = 1: a QR only when kappa_D(alpha) > 1 / sqrt(eps_fp32)) and FP64 with eta = 1e4."""
     import torch
     import workloads as W
     from paper_2104_02494_gb300 import build
@@ -109,26 +111,34 @@ def run_ir(args):
     prob = W.problem("vardiff3d", s=16, grid=grid, with_csr=False)
     h = Handle(0)
     op = operator_from_problem(h, prob, "stencil")
+    M = h.op_jacobi(op)
     Bd = torch.from_numpy(prob.B).cuda()
     nb = torch.linalg.vector_norm(Bd, dim=0)
     out = {}
-    for prec in ("fp32_ir", "fp64"):
+    runs = [("fp32_ir", "fp32_ir", math.inf, None), ("fp64", "fp64", math.inf, None),
+            ("fp32_ir_jacobi_eta1", "fp32_ir", 1.0, M), ("fp64_jacobi_eta1e4", "fp64", 1e4, M)]
+    for name, prec, eta, pre in runs:
         X = torch.zeros_like(Bd)
         t0 = time.perf_counter()
-        X, info = h.solve("bcg", op, Bd, X, tol=1e-10, maxit=20000, eta=math.inf, prec=prec, record=False)
+        X, info = h.solve("bcg", op, Bd, X, tol=1e-10, maxit=20000, eta=eta, prec=prec, record=False,
+                          precond=pre)
         wall = time.perf_counter() - t0
         R = h.residual(op, Bd, X)
         rel = float((torch.linalg.vector_norm(R, dim=0) / nb).max())
-        out[prec] = {"device_s": info.elapsed_ms / 1000.0, "wall_s": wall, "iters": info.iters,
+        out[name] = {"device_s": info.elapsed_ms / 1000.0, "wall_s": wall, "iters": info.iters,
                      "outer": info.outer, "reorths": info.reorths, "converged": info.converged,
-                     "true_relres_max": rel}
+                     "true_relres_max": rel, "eta": eta, "jacobi": pre is not None}
     line = {"metric": "time to max-column relative residual 1e-10 (192^3 log-normal diffusion, s=16)",
             "value": out["fp32_ir"]["device_s"], "unit": "s", "higher_is_better": False,
             "n_gpus": 1, "dtype": "f32 inner + f64 refinement", "data": "synthetic",
             "config": {"workload": f"vardiff3d {grid}^3 var7 stencil, s=16, eta=inf"},
             "fp64_reference": out["fp64"], "fp32_ir": out["fp32_ir"],
-            "speedup_vs_fp64": out["fp64"]["device_s"] / out["fp32_ir"]["device_s"]}
+            "speedup_vs_fp64": out["fp64"]["device_s"] / out["fp32_ir"]["device_s"],
+            "jacobi": {"fp32_ir_eta1": out["fp32_ir_jacobi_eta1"], "fp64_eta1e4": out["fp64_jacobi_eta1e4"],
+                       "speedup_vs_fp64": out["fp64_jacobi_eta1e4"]["device_s"]
+                       / out["fp32_ir_jacobi_eta1"]["device_s"]}}
     print(json.dumps(line))
+    M.close()
     h.close()
 
 
@@ -395,6 +405,8 @@ def run_tt(args):
          "bgmres", dict(tol=1e-8, restart=30, ortho="cgs2")),
         ("vardiff3d 192^3 var7 stencil, s=16, FP32 BCG + FP64 refinement, 1e-10", "vardiff3d", "stencil",
          "bcg", dict(tol=1e-10, eta=math.inf, prec="fp32_ir")),
+        ("vardiff3d 192^3 var7 stencil, s=16, FP32 BCG (Jacobi, eta=1) + FP64 refinement, 1e-10", "vardiff3d",
+         "stencil", "bcg", dict(tol=1e-10, eta=1.0, prec="fp32_ir", jacobi=True)),
         ("edge2d 512^2 per-edge stencil, s=32, BCG eta=1e4, 1e-8", "edge2d", "stencil", "bcg",
          dict(tol=1e-8, eta=1e4)),
     ]
@@ -403,16 +415,20 @@ def run_tt(args):
         prob = W.problem(wl, with_csr=(use == "csr"))
         op = operator_from_problem(h, prob, use)
         B = torch.from_numpy(prob.B).cuda()
+        kw = dict(kw)
+        M = h.op_jacobi(op) if kw.pop("jacobi", False) else None
         times, info = [], None
         nrep = 4 if kw.get("prec") == "fp32_ir" else 6     # the refinement case runs ~15 s
         for rep in range(nrep):
-            X, info = h.solve(method, op, B, maxit=20000, record=False, **kw)
+            X, info = h.solve(method, op, B, maxit=20000, record=False, precond=M, **kw)
             if rep:
                 times.append(info.elapsed_ms)
         times.sort()
         out.append({"case": label, "median_ms": times[len(times) // 2], "min_ms": times[0],
                      "iters": info.iters, "converged": info.converged, "relres_max": info.relres_max,
                      "n": prob.B.shape[0], "s": prob.B.shape[1]})
+        if M is not None:
+            M.close()
         op.close()
         del B
         torch.cuda.empty_cache()
