@@ -358,9 +358,7 @@ struct GraphBatch {
 };
 
 // launches of one iteration (the TSQR tree has 2 * levels + 1 launches)
-int bcg_launches_per_iter(const TsqrPlan& tp, bool prec = false) {
-  return 6 + tsqr_launches(tp) + (prec ? 1 : 0);
-}
+int bcg_launches_per_iter(const TsqrPlan& tp) { return 6 + tsqr_launches(tp); }
 
 template <typename T>
 int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const bkrylov_opts& o,

@@ -207,8 +207,8 @@ __device__ inline double warp_sum(double v) {
 // per round, until it is within 8 eps ||T||, the accuracy to which the
 // eigenvalues of M are determined at all, or after 12 rounds).
 // +inf when a diagonal entry of A or the smallest
-// eigenvalue is <= 0.  M and M2 are shared work matrices; rot is unused.
-__device__ double sm_kappa_d(const double* A, int s, double* M, double* M2, double*, int* flag) {
+// eigenvalue is <= 0.  M and M2 are shared work matrices.
+__device__ double sm_kappa_d(const double* A, int s, double* M, double* M2, int* flag) {
   __shared__ double s_tau, s_lo[2], s_hi[2];
   if (threadIdx.x == 0) *flag = 1;
   __syncthreads();
@@ -337,12 +337,12 @@ __device__ inline void stop(Ctrl* c, int status) {
 // re-orthonormalisation decision (Eq. "reortho_criterion", read as
 // eta * kappa_D > 1/sqrt(eps); eta = 0 never, eta = inf always)
 __device__ int decide(Ctrl* c, const uint8_t* forced, const double* A, double* M, double* M2,
-                      double* rot, int* flag) {
+                      int* flag) {
   const int k = c->iter;
   if (forced && k < c->n_forced) return forced[k] ? 1 : 0;
   if (c->eta == 0.0) return 0;
   if (isinf(c->eta)) return 1;
-  const double kap = sm_kappa_d(A, c->s, M, M2, rot, flag);
+  const double kap = sm_kappa_d(A, c->s, M, M2, flag);
   return (c->eta * kap > 1.0 / sqrt(c->eps)) ? 1 : 0;
 }
 
@@ -358,7 +358,6 @@ __device__ inline void sm_project(double* M, int s, int p) {
 
 struct SmallSmem {
   double A[kMM], B[kMM], C[kMM], D[kMM], E[kMM], F[kMM];
-  double rot[4 * (kMaxS + 1)];
   double red[kST];
   double w[kMaxS], tau[kMaxS];
   int flag;
@@ -421,7 +420,7 @@ __global__ void __launch_bounds__(kST) small_bcg_1_k(Ctrl* c, const uint8_t* for
   __syncthreads();
   if (!sm_cholesky(S.C, s, &S.flag)) { stop(c, BK_BREAKDOWN); return; }
   sm_chol_solve(S.C, S.B, S.D, s);            // D = lambda
-  const int reo = decide(c, forced, S.A, S.B, S.C, S.rot, &S.flag);   // clobbers B, C
+  const int reo = decide(c, forced, S.A, S.B, S.C, &S.flag);   // clobbers B, C
   __syncthreads();
   sm_matmul(S.B, S.D, false, S.E, s);          // lx = lambda sigma
   __syncthreads();
@@ -538,7 +537,7 @@ __global__ void __launch_bounds__(kST) small_kappa_d_k(int s, const double* A, d
   SmallSmem& S = *reinterpret_cast<SmallSmem*>(smraw);
   for (int i = threadIdx.x; i < s * s; i += blockDim.x) S.A[IDX(i / s, i % s)] = A[i];
   __syncthreads();
-  const double k = sm_kappa_d(S.A, s, S.B, S.C, S.rot, &S.flag);
+  const double k = sm_kappa_d(S.A, s, S.B, S.C, &S.flag);
   if (threadIdx.x == 0) *out = k;
 }
 
@@ -586,7 +585,7 @@ __global__ void __launch_bounds__(kST) small_bicg_1_k(Ctrl* c, const uint8_t* fo
   sm_lu_solve(S.A, piv, S.B, S.D, s);          // D = lambda-hat
   sm_copy(S.C, c->rho, s);
   __syncthreads();
-  const int reo = decide(c, forced, S.C, S.B, S.F, S.rot, &S.flag);
+  const int reo = decide(c, forced, S.C, S.B, S.F, &S.flag);
   __syncthreads();
   sm_matmul(S.B, S.D, false, S.E, s);          // lx = lambda-hat sigma
   __syncthreads();
