@@ -81,6 +81,9 @@ def parse():
                    help="stand-alone FP32 operator product and block inner product timings")
     p.add_argument("--workload", default=None, help="workload of --probe / --phases")
     p.add_argument("--maxit", type=int, default=3)
+    p.add_argument("--eta", type=float, default=math.inf,
+                   help="re-orthonormalisation parameter of --probe / --phases (inf: every iteration)")
+    p.add_argument("--jacobi", action="store_true", help="point-Jacobi preconditioner in --probe / --phases")
     p.add_argument("--subalgebra", action="store_true",
                    help="block-parallel subalgebra S_BP^p: cost per iteration and time to 1e-8 over p")
     p.add_argument("--tt", action="store_true",
@@ -322,8 +325,9 @@ def run_probe(args):
     wl = args.workload or ("laplace3d" if args.probe == "bcg_fp64" else "vardiff3d")
     h, op, prob, B, torch = _diag_setup(args, wl, 16)
     prec = "fp64" if args.probe == "bcg_fp64" else "fp32_ir"
-    X, info = h.solve("bcg", op, B, tol=0.0, maxit=args.maxit, eta=math.inf, prec=prec, ir_max_outer=1,
-                      record=False)
+    M = h.op_jacobi(op) if args.jacobi else None
+    X, info = h.solve("bcg", op, B, tol=0.0, maxit=args.maxit, eta=args.eta, prec=prec, ir_max_outer=1,
+                      record=False, precond=M)
     torch.cuda.synchronize()
     print(json.dumps({"probe": args.probe, "workload": wl, "n": prob.B.shape[0], "s": prob.B.shape[1],
                       "iters": info.iters}))
@@ -333,12 +337,14 @@ def run_phases(args):
     """Per-phase device time per launch of FP32+IR (inner) and FP64 BCG iterations."""
     wl = args.workload or "vardiff3d"
     h, op, prob, B, torch = _diag_setup(args, wl, 16)
-    out = {"workload": wl, "n": prob.B.shape[0], "s": prob.B.shape[1], "iterations": args.maxit}
+    out = {"workload": wl, "n": prob.B.shape[0], "s": prob.B.shape[1], "iterations": args.maxit,
+           "eta": args.eta, "jacobi": args.jacobi}
+    M = h.op_jacobi(op) if args.jacobi else None
     for prec in ("fp32_ir", "fp64"):
         for _ in range(2):   # the second run is reported
             h.profile_reset()
-            X, info = h.solve("bcg", op, B, tol=0.0, maxit=args.maxit, eta=math.inf, prec=prec,
-                              ir_max_outer=1, profile=True, record=False)
+            X, info = h.solve("bcg", op, B, tol=0.0, maxit=args.maxit, eta=args.eta, prec=prec,
+                              ir_max_outer=1, profile=True, record=False, precond=M)
         out[prec] = {nm: {"ms_per_launch": ms / nl, "launches": nl} for nm, ms, nl in h.profile() if nl}
     print(json.dumps(out))
 

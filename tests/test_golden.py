@@ -1,0 +1,72 @@
+"""The stored expected values of tests/golden/ (written by tests/golden/make_golden.py from the
+oracle alone): the oracle still reproduces them (CPU), and the GPU solvers match them (-m gpu).
+
+Residual histories are compared relatively (1e-9 on the CPU, where only the BLAS build may
+differ; 1e-8 on the GPU, whose Gram summation order differs), decisions and iteration
+counts exactly.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "bcg_poisson2d_12x11_s3.json")))
+
+
+def _problems():
+    A = W.lap2d5(12, 11)
+    B = W.normal_block(A.n, 3, 0)
+    k = np.exp(1.5 * np.random.default_rng(5).standard_normal(125))
+    Av = W.diff3d7_var(5, 5, 5, k)
+    Bv = W.normal_block(Av.n, 3, 1)
+    return A, B, Av, Bv
+
+
+CASES = [("bcg_eta_inf", "bcg", math.inf, False, False), ("bcg_eta_0", "bcg", 0.0, False, False),
+         ("bcg_eta_1e4", "bcg", 1e4, False, False), ("bcg_1r_eta_inf", "bcg_1r", math.inf, False, False),
+         ("bcg_jacobi_vardiff_eta_inf", "bcg", math.inf, True, True)]
+
+
+def _check(got_hist, got_dec, got_iters, ref, tol):
+    assert got_iters == ref["iters"]
+    assert list(got_dec) == ref["decisions"]
+    h = np.array(got_hist[:len(ref["history"])])
+    r = np.array(ref["history"])
+    assert np.all(np.abs(h - r) <= tol * np.abs(r)), np.abs(h / r - 1).max()
+
+
+@pytest.mark.parametrize("key,fn,eta,jacobi,var", CASES)
+def test_oracle_reproduces_golden(key, fn, eta, jacobi, var):
+    A, B, Av, Bv = _problems()
+    M, R = (Av, Bv) if var else (A, B)
+    w = oracle.jacobi_inverse_diagonal(M) if jacobi else None
+    r = getattr(oracle, fn)(M, R, tol=1e-10, maxit=500, eta=eta, Minv=w)
+    _check(r.history, r.decisions, r.iters, GOLD[key], 1e-9)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("key,fn,eta,jacobi,var", CASES)
+def test_gpu_matches_golden(key, fn, eta, jacobi, var):
+    import torch
+    from paper_2104_02494_gb300 import build
+    from paper_2104_02494_gb300.api import Handle
+    build()
+    A, B, Av, Bv = _problems()
+    M, R = (Av, Bv) if var else (A, B)
+    dv = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    with Handle(0) as h:
+        op = h.op_csr(dv(M.row_ptr), dv(M.col), dv(M.val))
+        P = h.op_jacobi(op) if jacobi else None
+        X, info = h.solve("bcg", op, dv(R), tol=1e-10, maxit=500, eta=eta, precond=P,
+                          one_reduction=(fn == "bcg_1r"))
+        _check(info.history, info.decisions, info.iters, GOLD[key], 1e-8)
+        ref_row = np.array(GOLD[key]["X_first_row"])
+        assert np.abs(X.cpu().numpy()[0] - ref_row).max() <= 1e-9 * np.abs(ref_row).max()
+        if P is not None:
+            P.close()
+        op.close()
