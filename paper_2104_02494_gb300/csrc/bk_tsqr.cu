@@ -4,7 +4,8 @@
 //
 // The thesis splits the rows over MPI processes; here the "processes" are
 // row tiles of one GPU:
-//   1. leaf factor   one CTA per tile of 256 x RPT rows (RPT = 64 / next_pow2(s)),
+//   1. leaf factor   one CTA per tile of 256 x RPT rows (RPT = 64 / next_pow2(s);
+//                    32 / next_pow2(s) for FP64 blocks of width <= 4),
 //                    the rows in registers: Householder QR of the tile; the reflectors
 //                    overwrite the tile in Y; the tile's R factor and the factor
 //                    F = strict_upper(V^T V) + diag(tau) of its compact WY form
@@ -31,11 +32,11 @@ namespace bk {
 constexpr int kTT = 256;                 // threads per TSQR CTA
 
 // Rows per leaf tile: 256 threads x RPT rows each, RPT = 64 / next_pow2(s),
-// i.e. 64 row values per thread in either precision (FP64 at s = 32 this
-// took one BCG iteration at 128^3 from 37.5 to 33.9 ms against 32 /
-// next_pow2(s) rows; within 2 % at s = 8, 16).  Larger tiles also shrink the
-// tree.
-constexpr int leaf_rpt(int sw, int) { return 64 / sw; }
+// i.e. 64 row values per thread, except FP64 blocks of width <= 4, which keep
+// 32 values (measured on a 128^3 BCG iteration against 32 values: s = 32
+// 37.5 -> 33.9 ms, s = 16 and 8 about 1.5 % faster, s = 4 3 % slower).
+// Larger tiles also shrink the tree.
+constexpr int leaf_rpt(int sw, int elem_bytes) { return (elem_bytes == 8 && sw <= 4 ? 32 : 64) / sw; }
 inline int leaf_tile_rows(int s, int elem_bytes) { return kTT * leaf_rpt(next_pow2_s(s), elem_bytes); }
 
 TsqrPlan tsqr_plan(int64_t n, int s, int elem_bytes) {
