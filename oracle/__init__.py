@@ -34,11 +34,12 @@ from .bgmres import bgmres
 from .tsqr import tsqr
 from .ir import bcg_ir
 from .precond import jacobi_inverse_diagonal, apply_diagonal
+from .localized import LocalizedArnoldi
 from .adjoint import dense_adjoint, adjoint_scatter, edge_theta_grad
 
 __all__ = [
     "spmm", "gram", "householder_qr", "normalizer", "kappa_d", "chol_solve", "lu_solve",
     "col_norms", "reortho_decision", "project_subalgebra", "bcg", "bcg_1r", "scalar_cg",
     "BCGResult", "bbicgstab", "bgmres", "tsqr", "bcg_ir", "dense_adjoint",
-    "adjoint_scatter", "edge_theta_grad", "jacobi_inverse_diagonal", "apply_diagonal",
+    "adjoint_scatter", "edge_theta_grad", "jacobi_inverse_diagonal", "apply_diagonal", "LocalizedArnoldi",
 ]

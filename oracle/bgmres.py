@@ -5,7 +5,10 @@ Follows Alg. "bgmres" (Ch. 5.1) with M = I:
   * Arnoldi step W = A V^k, orthogonalised against V^0..V^k either by block
     modified Gram-Schmidt (Alg. "block-arnoldi") or by classical block
     Gram-Schmidt repeated twice (CGS2, Ch. 9.1: all projections of one pass
-    in one batch, #it = 2), then V^{k+1}, gamma = Norm(W);
+    in one batch, #it = 2), then V^{k+1}, gamma = Norm(W); or the whole
+    basis kept as a distributed S-QR decomposition over row tiles by the
+    localized Arnoldi method (Ch. 9.3, ``localized.py``), whose global
+    R-factor gives the Hessenberg column and gamma at once;
   * the new Hessenberg column is rotated by the previous block Givens factors
     Q_0 .. Q_{k-1}, then the 2s x s block [h_kk; gamma] is QR-factorised by
     Householder (full 2s x 2s Q_k), and [sigma^k; sigma^{k+1}] <- Q_k^T [sigma^k; 0];
@@ -29,6 +32,7 @@ import numpy as np
 
 from .bcg import BCGResult
 from .blockops import col_norms, normalizer, spmm
+from .localized import LocalizedArnoldi
 
 
 def _full_householder_qr(M: np.ndarray):
@@ -53,8 +57,10 @@ def _full_householder_qr(M: np.ndarray):
 
 
 def bgmres(A, B: np.ndarray, X0=None, tol: float = 1e-8, restart: int = 30, maxit: int = 1000,
-           ortho: str = "mgs", apply_A=None) -> BCGResult:
-    """Alg. "bgmres" with restart length ``restart``; ``maxit`` counts Arnoldi steps."""
+           ortho: str = "mgs", apply_A=None, tile_rows: int = 2048) -> BCGResult:
+    """Alg. "bgmres" with restart length ``restart``; ``maxit`` counts Arnoldi steps.
+
+    ortho: "mgs", "cgs2" or "localized" (row tiles of ``tile_rows`` rows)."""
     B = np.asarray(B, dtype=np.float64)
     n, s = B.shape
     op = apply_A if apply_A is not None else (lambda V: spmm(A, V))
@@ -66,7 +72,11 @@ def bgmres(A, B: np.ndarray, X0=None, tol: float = 1e-8, restart: int = 30, maxi
     total = 0
     while total < maxit:
         R = B - op(X)
-        V0, sig0 = normalizer(R)
+        if ortho == "localized":
+            la = LocalizedArnoldi(n, s, tile_rows)
+            V0, sig0 = la.extend(R)
+        else:
+            V0, sig0 = normalizer(R)
         m = min(restart, maxit - total)
         V = [V0]
         H = np.zeros(((m + 1) * s, m * s))
@@ -88,10 +98,14 @@ def bgmres(A, B: np.ndarray, X0=None, tol: float = 1e-8, restart: int = 30, maxi
                     hp = Vk.T @ W
                     W = W - Vk @ hp
                     h[:(k + 1) * s] += hp
-            else:
+            elif ortho != "localized":
                 raise ValueError(ortho)
-            Vn, gamma = normalizer(W)
-            h[(k + 1) * s:] = gamma
+            if ortho == "localized":
+                Vn, col = la.extend(W)
+                h[:] = col
+            else:
+                Vn, gamma = normalizer(W)
+                h[(k + 1) * s:] = gamma
             for j in range(k):
                 blk = h[j * s:(j + 2) * s]
                 h[j * s:(j + 2) * s] = G[j].T @ blk

@@ -169,6 +169,41 @@ def test_bcg1r_mutation_is_caught(old, new):
     assert not _bcg1r_battery_passes(_mutant("oracle.bcg", "bcg_1r", old, new))
 
 
+def _localized_battery_passes(cls):
+    """Distributed S-QR = LAPACK QR of the concatenated blocks (signs fixed), 1, 5 and 8 tiles."""
+    try:
+        for n, s, tile in ((200, 3, 200), (200, 3, 40), (301, 4, 40)):
+            g = np.random.default_rng(n + tile)
+            blocks = [g.standard_normal((n, s)) for _ in range(4)]
+            la = cls(n, s, tile)
+            Xs = [la.extend(Wb)[0] for Wb in blocks]
+            Q, R = np.linalg.qr(np.hstack(blocks))
+            d = np.sign(np.diag(R))
+            if np.abs(np.hstack(Xs) - Q * d).max() > 1e-11:
+                return False
+        return True
+    except Exception:
+        return False
+
+
+LOCALIZED_MUTATIONS = [
+    ("S[q] = S[q] - zi[q] @ ri", "S[q] = S[q] + zi[q] @ ri"),
+    ("ri = sum(zi[q].T @ S[q] for q in range(len(ch)))", "ri = sum(zi[q].T @ S[q] for q in range(1))"),
+    ("acc += _pad(comp[q], L) @ rt[ii * s:(ii + 1) * s]", "acc += _pad(comp[q], L) @ rt[:s]"),
+    ("Wp = Wp - self.P[p][j] @ zj", "Wp = Wp - self.P[p][j] @ zj.T"),
+    ("coef = list(self.node_basis[(top, 0)][-1])", "coef = list(self.node_basis[(top, 0)][0])"),
+]
+
+
+def test_unmutated_localized_passes_battery():
+    assert _localized_battery_passes(sys.modules["oracle.localized"].LocalizedArnoldi)
+
+
+@pytest.mark.parametrize("old,new", LOCALIZED_MUTATIONS)
+def test_localized_mutation_is_caught(old, new):
+    assert not _localized_battery_passes(_mutant("oracle.localized", "LocalizedArnoldi", old, new))
+
+
 def _qr_battery_passes(qr_fn):
     try:
         for (n, s) in ((40, 6), (12, 12)):
