@@ -409,6 +409,10 @@ def run_tt(args):
          "bbicgstab", dict(tol=1e-8, eta=100.0)),
         ("convdiff3d 96^3 upwind stencil, s=8, BGMRes(30) CGS2 + TSQR, 1e-8", "convdiff3d", "stencil",
          "bgmres", dict(tol=1e-8, restart=30, ortho="cgs2")),
+        ("convdiff3d 96^3 upwind stencil, s=8, BGMRes(30) localized Arnoldi, 1e-8", "convdiff3d", "stencil",
+         "bgmres", dict(tol=1e-8, restart=30, ortho="localized")),
+        ("convdiff3d 96^3 upwind stencil, s=8, BGMRes(30) block MGS, 1e-8", "convdiff3d", "stencil",
+         "bgmres", dict(tol=1e-8, restart=30, ortho="mgs")),
         ("vardiff3d 192^3 var7 stencil, s=16, FP32 BCG + FP64 refinement, 1e-10", "vardiff3d", "stencil",
          "bcg", dict(tol=1e-10, eta=math.inf, prec="fp32_ir")),
         ("vardiff3d 192^3 var7 stencil, s=16, FP32 BCG (Jacobi, eta=1) + FP64 refinement, 1e-10", "vardiff3d",

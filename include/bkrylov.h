@@ -79,7 +79,11 @@ typedef struct {
                           (Ch. 4.3, Eq. "reortho_criterion", read as 1/sqrt(eps))   (INFINITY) */
   int restart;         /* BGMRes restart length m                              (30)   */
   int ortho;           /* BGMRes orthogonalisation: 0 = CGS2 (two classical passes),
-                          1 = block MGS                                         (0)    */
+                          1 = block MGS, 2 = localized Arnoldi (Ch. 9.3: the basis kept as a
+                          distributed S-QR decomposition over the row tiles, one tree
+                          reduction per step; s <= 16, every row tile at least s rows and
+                          restart small enough for its tree nodes' shared memory, else
+                          BK_ERR_UNSUPPORTED)                                   (0)    */
   int prec;            /* bkrylov_prec: FP64, FP32, or FP32 inner + FP64 refinement (FP64) */
   double ir_inner_tol; /* relative tolerance of each FP32 inner solve          (1e-5)  */
   int ir_max_outer;    /* refinement steps limit                               (30)    */
@@ -88,7 +92,7 @@ typedef struct {
   int n_forced;
   int sync_every;      /* iterations enqueued between host checks of the stop flag;
                           0 = automatic                                          (0)  */
-  int profile;         /* BCG only: time every kernel phase of every iteration with
+  int profile;         /* BCG and BGMRes: time every kernel phase of every iteration with
                           CUDA events on the handle's stream (adds one stream
                           synchronisation per iteration); read with
                           bkrylov_profile_get                                      (0)  */

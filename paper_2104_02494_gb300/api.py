@@ -209,7 +209,7 @@ class Handle:
             X = torch.zeros_like(B) if isinstance(B, torch.Tensor) else np.zeros_like(B)
         o = L.default_opts()
         o.tol, o.maxit, o.eta, o.restart = float(tol), int(maxit), float(eta), int(restart)
-        o.ortho = {"cgs2": 0, "mgs": 1}[ortho]
+        o.ortho = {"cgs2": 0, "mgs": 1, "localized": 2}[ortho]
         o.prec = _PREC[prec]
         o.ir_inner_tol, o.ir_max_outer, o.sync_every = float(ir_inner_tol), int(ir_max_outer), int(sync_every)
         o.profile = 1 if profile else 0

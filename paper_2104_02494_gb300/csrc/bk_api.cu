@@ -32,7 +32,8 @@ struct bkrylov_ctx {
 
 const char* const bk::kPhaseNames[kNumPhases] = {
     "spmm_alpha", "small_1", "update_rho", "tsqr_leaf_factor", "tsqr_tree", "tsqr_leaf_apply",
-    "tsqr_rho_gram", "small_2", "p_update", "precond_rho"};
+    "tsqr_rho_gram", "small_2", "p_update", "precond_rho", "gmres_orthogonalise", "localized_tree",
+    "localized_assemble"};
 
 struct bkrylov_op_s {
   bkrylov_handle h = nullptr;
@@ -631,7 +632,8 @@ int bicg_device(bkrylov_handle h, const OpDesc& A, int s, const double* B, doubl
 // ------------------------------------------------------------- BGMRes ----
 int gmres_device(bkrylov_handle h, const OpDesc& A, int s, const double* B, double* X,
                  const bkrylov_opts& o, bkrylov_info* info) {
-  const Launch L = launch_of(h);
+  Launch L = launch_of(h);
+  if (o.profile) L.prof = &h->prof;
   const int64_t n = A.n;
   const size_t ns = (size_t)n * s;
   const int m = o.restart > 0 ? o.restart : 30;
@@ -639,9 +641,24 @@ int gmres_device(bkrylov_handle h, const OpDesc& A, int s, const double* B, doub
   const TsqrPlan tp = tsqr_plan(n, s);
   const size_t ss = (size_t)s * s;
   const size_t gmg = (size_t)L.sms * 4 * kMM + (size_t)8 * (m + 1) * kMM;
+  // localized Arnoldi (ortho 2): the local bases (m + 1 more blocks) and the tree
+  const bool loc = o.ortho == 2;
+  LocalArnoldi la;
+  size_t la_bytes = 0;
+  if (loc) {
+    la_bytes = local_arnoldi_bytes(n, s, m, tp.tile, &la);
+    const int64_t last = n - (la.tiles - 1) * (int64_t)tp.tile;
+    if (s > 16 || last < s || m + 1 > 72 || la.reduce_smem > 200 * 1024) return BK_ERR_UNSUPPORTED;
+  }
+  char* la_base = nullptr;
+  double* Pbase = nullptr;
   auto layout = [&](auto& a, double** V, double** Hc, double** Ht, double** H, double** Gq,
                     double** sig, double** zeta, double*** Vp, void** ts, double** gp,
                     double** gmp, Ctrl** c, double** hs) {
+    if (loc) {
+      Pbase = a.template take<double>(ns * (m + 1));
+      la_base = a.template take<char>(la_bytes);
+    }
     *V = a.template take<double>(ns * (m + 1));
     *Hc = a.template take<double>((size_t)(m + 1) * kMM);
     *Ht = a.template take<double>((size_t)(m + 1) * kMM);
@@ -674,6 +691,11 @@ int gmres_device(bkrylov_handle h, const OpDesc& A, int s, const double* B, doub
   for (int j = 0; j <= m; ++j) vp[j] = V + ns * j;
   BK_TRY(cudaMemcpyAsync(Vp, vp.data(), sizeof(double*) * (m + 1), cudaMemcpyHostToDevice, L.stream));
   BK_TRY(cudaStreamSynchronize(L.stream));
+  if (loc) {
+    std::vector<double*> pb(m + 1);
+    for (int j = 0; j <= m; ++j) pb[j] = Pbase + ns * j;
+    if ((rc = local_arnoldi_layout(la_base, &la, pb.data(), L.stream))) return rc;
+  }
   cudaEvent_t e0, e1;
   BK_TRY(cudaEventCreate(&e0));
   BK_TRY(cudaEventCreate(&e1));
@@ -690,29 +712,45 @@ int gmres_device(bkrylov_handle h, const OpDesc& A, int s, const double* B, doub
   while (total < maxit) {
     if (!first) BK_TRY(spmm<double>(L, A, s, X, V, B, none));     // restart residual
     first = false;
-    BK_TRY(tsqr<double>(L, tp, V, V, c->gamma, nullptr, ts, gp, nullptr, nullptr, nullptr));
+    if (loc) {                                     // V^0 sigma^0 = R^0 as a distributed S-QR
+      BK_TRY(local_arnoldi_begin(L, la));
+      BK_TRY(local_arnoldi_extend(L, la, tp, ts, 0, V, V, Hc, c->gamma));
+    } else {
+      BK_TRY(tsqr<double>(L, tp, V, V, c->gamma, nullptr, ts, gp, nullptr, nullptr, nullptr));
+    }
     BK_TRY(init_sig(L, s, c->gamma, sig, m + 1));
     int k_done = 0;
     bool conv = false;
     for (int k = 0; k < m && total < maxit; ++k) {
       double* W = vp[k + 1];
+      prof_begin(L, kPhSpmm);
       BK_TRY(spmm<double>(L, A, s, vp[k], W, nullptr, none));
-      if (o.ortho == 1) {                          // block MGS (Alg. "block-arnoldi")
+      prof_end(L, kPhSpmm, 1);
+      if (loc) {                                   // localized Arnoldi (Ch. 9.3)
+        BK_TRY(local_arnoldi_extend(L, la, tp, ts, k + 1, W, W, Hc, c->gamma));
+      } else if (o.ortho == 1) {                   // block MGS (Alg. "block-arnoldi")
+        prof_begin(L, kPhOrtho);
         for (int j = 0; j <= k; ++j) {
           Epi<double> gj;
           gj.sym = 0; gj.gram_out = Hc + (size_t)j * kMM; gj.gpart = gp; gj.counter = &c->counters[kCntA];
           BK_TRY(gram<double>(L, n, s, vp[j], W, gj));
           BK_TRY(block_axpy<double>(L, n, s, vp[j], Hc + (size_t)j * kMM, -1.0, W, 1.0, nullptr));
         }
+        prof_end(L, kPhOrtho, 2 * (k + 1));
       } else {                                     // CGS2 (Ch. 9.1, #it = 2)
+        prof_begin(L, kPhOrtho);
         BK_TRY(multi_gram(L, n, s, Vp, k + 1, W, Hc, 0, gmp, nullptr, nullptr));
         BK_TRY(multi_axpy(L, n, s, Vp, k + 1, Hc, W, -1.0, nullptr));
         BK_TRY(multi_gram(L, n, s, Vp, k + 1, W, Ht, 0, gmp, nullptr, nullptr));
         BK_TRY(multi_axpy(L, n, s, Vp, k + 1, Ht, W, -1.0, nullptr));
         BK_TRY(vec_add(L, (int64_t)(k + 1) * kMM, Ht, Hc, nullptr));
+        prof_end(L, kPhOrtho, 5);
       }
-      BK_TRY(tsqr<double>(L, tp, W, W, c->gamma, nullptr, ts, gp, nullptr, nullptr, nullptr));
+      if (!loc) BK_TRY(tsqr<double>(L, tp, W, W, c->gamma, nullptr, ts, gp, nullptr, nullptr, nullptr));
+      prof_begin(L, kPhSmall2);
       BK_TRY(small_gmres_step(L, c, Hc, H, Gq, sig, k, m, hs, total));
+      prof_end(L, kPhSmall2, 1);
+      prof_collect(L.prof);
       ++total;
       k_done = k + 1;
       if ((rc = ctrl_peek(h, c))) return rc;
@@ -1143,7 +1181,7 @@ int bkrylov_solve_bgmres(bkrylov_handle h, bkrylov_op A, int s, const double* B,
   if (rc) return rc;
   if (!block_case(o, s) || o.precond || o.one_reduction) return BK_ERR_UNSUPPORTED;
   if (o.prec != BK_FP64) return BK_ERR_UNSUPPORTED;
-  if (o.restart < 1 || o.restart > 64) return BK_ERR_ARG;
+  if (o.restart < 1 || o.restart > 64 || o.ortho < 0 || o.ortho > 2) return BK_ERR_ARG;
   return with_device_blocks(h, A->d.n, s, B, X, 0, [&](const double* dB, double* dX, size_t) {
     return gmres_device(h, A->d, s, dB, dX, o, info);
   });

@@ -51,7 +51,7 @@ struct Epi {
 // Optional per-phase device timing (CUDA events on the launching stream).
 enum Phase : int {
   kPhSpmm = 0, kPhSmall1, kPhUpdate, kPhTsqrLeaf, kPhTsqrTree, kPhTsqrApply, kPhTsqrGram,
-  kPhSmall2, kPhPupdate, kPhPrec, kNumPhases
+  kPhSmall2, kPhPupdate, kPhPrec, kPhOrtho, kPhLaTree, kPhLaAssemble, kNumPhases
 };
 struct Prof {
   static constexpr int kMax = 16;
@@ -152,6 +152,37 @@ struct TsqrPlan {
 int tsqr_launches(const TsqrPlan& p);
 // elem_bytes: 8 for FP64 blocks, 4 for FP32 ones (larger leaf tiles)
 TsqrPlan tsqr_plan(int64_t n, int s, int elem_bytes = 8);
+// Leaf tiles of X (FP64) factored on their own: Y_t = Q_t explicit, R_t (s x s) at Rloc + t * ldr.
+cudaError_t tsqr_local_q(const Launch& L, const TsqrPlan& p, const double* X, double* Y, double* Rloc,
+                         int64_t ldr, void* scratch);
+// ---- localized Arnoldi (bk_local.cu) ----
+// Device layout of the distributed S-QR decomposition of one BGMRes cycle (see bk_local.cu).
+struct LocalArnoldi {
+  int s = 0, m1 = 0, mx = 0;         // block size, max basis vectors, max blocks per vector
+  int64_t n = 0, tiles = 0;
+  int tile_rows = 0;
+  int levels = 0;                    // tree levels above the tiles
+  int64_t nodes[24] = {0};           // nodes per level (level 0 = tiles)
+  double** Pb = nullptr;             // device array of m1 local-basis block pointers
+  double* Pbh[72] = {nullptr};       // the same pointers on the host (m1 <= 65)
+  double* Zt = nullptr;              // [tiles][mx s][s]  local R-factors of the newest block
+  double* Zl = nullptr;              // [tiles][mx s][s]  coefficients of the newest basis vector
+  double* NB[24] = {nullptr};        // level l: [nodes][m1][2][mx s][s] node bases
+  double* Rout[24] = {nullptr};      // level l: [nodes][mx s][s] R-factors passed up
+  double* Cin[24] = {nullptr};       // level l: [nodes][mx s][s] coefficients passed down
+  size_t nb_bytes[24] = {0};
+  size_t reduce_smem = 0;
+};
+size_t local_arnoldi_bytes(int64_t n, int s, int m, int tile_rows, LocalArnoldi* la);
+// Lay out `la` in `base` (local_arnoldi_bytes of it); Pb gets its device pointer array.
+int local_arnoldi_layout(void* base, LocalArnoldi* la, double* const* pb_host, cudaStream_t st);
+// Start a cycle: node bases zeroed.
+cudaError_t local_arnoldi_begin(const Launch& L, const LocalArnoldi& la);
+// Extend by W (overwritten): k1 basis vectors so far (0 at the cycle start).  Writes
+// the new basis vector into V, the projections into Hc (k1 blocks, row stride 32)
+// and the normalisation factor into gamma (row stride 32).
+cudaError_t local_arnoldi_extend(const Launch& L, const LocalArnoldi& la, const TsqrPlan& tp, void* tsqr_scratch,
+                                 int k1, double* W, double* V, double* Hc, double* gamma);
 // Y, gamma = Norm(X) (Y may alias X).  gamma -> ctrl-layout s x s (row stride 32).
 // If rho_out != null, also the Gram Y^T Y (row stride 32) is produced.
 // done: optional stop flag (skip when *done); reortho_flag: optional, skip unless *flag.

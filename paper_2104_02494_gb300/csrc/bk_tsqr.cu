@@ -701,6 +701,38 @@ cudaError_t tsqr(const Launch& L, const TsqrPlan& p, const T* X, T* Y, double* g
   return e;
 }
 
+// Row tiles factored on their own (the local normaliser of the localized
+// Arnoldi method): every leaf tile t of X gets its Householder QR X_t = Q_t R_t;
+// Y_t = Q_t (explicit, s orthonormal columns on the tile) and R_t goes to
+// Rloc + t * ldr (s x s, row-major).  No tree: the level-0 scatter factors
+// are set to the identity before the apply.
+__global__ void tile_r_out(int64_t tiles, int s, double* __restrict__ Rst, double* __restrict__ Rloc,
+                           int64_t ldr) {
+  const int64_t ss = (int64_t)s * s;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tiles * ss;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = i / ss;
+    const int e = (int)(i % ss);
+    Rloc[t * ldr + e] = Rst[i];
+    Rst[i] = (e / s == e % s) ? 1.0 : 0.0;
+  }
+}
+
+cudaError_t tsqr_local_q(const Launch& L, const TsqrPlan& p, const double* X, double* Y, double* Rloc,
+                         int64_t ldr, void* scratch) {
+  const int s = p.s;
+  TsqrPtrs q = tsqr_ptrs(p, scratch);
+  cudaError_t e;
+  if ((e = leaves<double, double>(L, p.n, s, s, p.nodes[0], X, Y, q.R[0], q.Tf[0], nullptr, nullptr,
+                                  nullptr, nullptr, nullptr, true, true)) != cudaSuccess) return e;
+  int64_t g = (p.nodes[0] * s * s + 255) / 256;
+  if (g > (int64_t)L.sms * 8) g = (int64_t)L.sms * 8;
+  tile_r_out<<<(unsigned)(g < 1 ? 1 : g), 256, 0, L.stream>>>(p.nodes[0], s, q.R[0], Rloc, ldr);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return leaves<double, double>(L, p.n, s, s, p.nodes[0], nullptr, Y, q.R[0], q.Tf[0], nullptr, nullptr,
+                                nullptr, nullptr, nullptr, false, true);
+}
+
 template cudaError_t tsqr<double>(const Launch&, const TsqrPlan&, const double*, double*, double*,
                                   double*, void*, double*, unsigned*, const int*, const int*, int);
 template cudaError_t tsqr<float>(const Launch&, const TsqrPlan&, const float*, float*, double*,
