@@ -57,10 +57,11 @@ def _full_householder_qr(M: np.ndarray):
 
 
 def bgmres(A, B: np.ndarray, X0=None, tol: float = 1e-8, restart: int = 30, maxit: int = 1000,
-           ortho: str = "mgs", apply_A=None, tile_rows: int = 2048) -> BCGResult:
+           ortho: str = "mgs", apply_A=None, tile_rows: int = 2048, fanin: int = 2) -> BCGResult:
     """Alg. "bgmres" with restart length ``restart``; ``maxit`` counts Arnoldi steps.
 
-    ortho: "mgs", "cgs2" or "localized" (row tiles of ``tile_rows`` rows)."""
+    ortho: "mgs", "cgs2" or "localized" (row tiles of ``tile_rows`` rows, a tree of
+    ``fanin`` children per node)."""
     B = np.asarray(B, dtype=np.float64)
     n, s = B.shape
     op = apply_A if apply_A is not None else (lambda V: spmm(A, V))
@@ -73,7 +74,7 @@ def bgmres(A, B: np.ndarray, X0=None, tol: float = 1e-8, restart: int = 30, maxi
     while total < maxit:
         R = B - op(X)
         if ortho == "localized":
-            la = LocalizedArnoldi(n, s, tile_rows)
+            la = LocalizedArnoldi(n, s, tile_rows, fanin)
             V0, sig0 = la.extend(R)
         else:
             V0, sig0 = normalizer(R)

@@ -9,7 +9,8 @@ Extending the basis by a block W:
   1. every tile orthonormalises W_p against its local basis by block modified
      Gram-Schmidt and normalises the rest (Householder): the local R-factor
      zeta~_p = [<P_p^0, W_p>; ...; <P_p^k, W_p>; r_p];
-  2. a binary tree over the tiles (the same tree in every step) reduces the
+  2. a tree over the tiles (the same tree in every step; binary as printed,
+     or ``fanin`` children per node) reduces the
      local R-factors: each node stacks its children's vectors, orthonormalises
      the stack against the node's own basis (modified Gram-Schmidt in the
      inner product of stacked coefficient vectors), normalises the rest and
@@ -38,21 +39,22 @@ def _pad(v: np.ndarray, rows: int) -> np.ndarray:
 class LocalizedArnoldi:
     """The distributed S-QR decomposition of the basis built so far (block case S_B)."""
 
-    def __init__(self, n: int, s: int, tile_rows: int):
+    def __init__(self, n: int, s: int, tile_rows: int, fanin: int = 2):
         self.s = s
+        self.fanin = fanin
         self.tiles = [(a, min(a + tile_rows, n)) for a in range(0, n, tile_rows)]
         if self.tiles[-1][1] - self.tiles[-1][0] < s:
             # a local S-QR needs at least s rows on every tile (local orthonormality)
             raise ValueError("the last row tile has fewer than s rows")
         self.sizes = [len(self.tiles)]
         while self.sizes[-1] > 1:
-            self.sizes.append((self.sizes[-1] + 1) // 2)
+            self.sizes.append((self.sizes[-1] + fanin - 1) // fanin)
         self.P = [[] for _ in self.tiles]                    # local bases P_p^j
         self.node_basis = {(l, i): [] for l in range(1, len(self.sizes))
                            for i in range(self.sizes[l])}    # list of [zeta^i_c for c in children]
 
     def _children(self, l: int, i: int):
-        return [c for c in (2 * i, 2 * i + 1) if c < self.sizes[l - 1]]
+        return [c for c in range(self.fanin * i, self.fanin * (i + 1)) if c < self.sizes[l - 1]]
 
     def extend(self, W: np.ndarray):
         """Add the block W: returns (X^{k+1}, rho) with W = sum_j X^j rho_j over the new basis."""

@@ -162,12 +162,13 @@ struct LocalArnoldi {
   int64_t n = 0, tiles = 0;
   int tile_rows = 0;
   int levels = 0;                    // tree levels above the tiles
+  int fanin = 2;                     // children per tree node
   int64_t nodes[24] = {0};           // nodes per level (level 0 = tiles)
   double** Pb = nullptr;             // device array of m1 local-basis block pointers
   double* Pbh[72] = {nullptr};       // the same pointers on the host (m1 <= 65)
   double* Zt = nullptr;              // [tiles][mx s][s]  local R-factors of the newest block
   double* Zl = nullptr;              // [tiles][mx s][s]  coefficients of the newest basis vector
-  double* NB[24] = {nullptr};        // level l: [nodes][m1][2][mx s][s] node bases
+  double* NB[24] = {nullptr};        // level l: [nodes][m1][fanin][mx s][s] node bases
   double* Rout[24] = {nullptr};      // level l: [nodes][mx s][s] R-factors passed up
   double* Cin[24] = {nullptr};       // level l: [nodes][mx s][s] coefficients passed down
   size_t nb_bytes[24] = {0};

@@ -13,8 +13,9 @@
 //      the local coefficients go to Zt[t][j];
 //   2. the rest of the tile is normalised by the tile Householder QR of the
 //      TSQR normaliser (tsqr_local_q): P_t^{k+1} explicit, its R to Zt[t][k+1];
-//   3. la_reduce, one launch per tree level, one CTA per node (binary tree
-//      over the tiles, the same in every step): the children's vectors are
+//   3. la_reduce, one launch per tree level, one CTA per node (a tree of
+//      `fanin` children per node over the tiles, the same in every step; the
+//      thesis prints the binary one): the children's vectors are
 //      stacked, orthonormalised against the node's own basis by modified
 //      Gram-Schmidt and normalised by a CTA Householder QR (diag(R) >= 0);
 //      the node stores the new basis vector and passes its R-factor up; the
@@ -166,19 +167,19 @@ la_assemble(int64_t n, int s, int tile_rows, int k2, const double* const* __rest
 }
 
 // ---- 3. tree reduction, one CTA per node ----------------------------------------
-// child_out: [nchild][mx s][s] (K2 = k1 + 1 blocks valid); NB: [nodes][m1][2][mx s][s];
-// Rout: [nodes][mx s][s].  Shared memory: S (2 mx s x s), C (as S, at least 256 s),
+// child_out: [nchild][mx s][s] (K2 = k1 + 1 blocks valid); NB: [nodes][m1][F][mx s][s];
+// Rout: [nodes][mx s][s].  Shared memory: S (F mx s x s), C (as S, at least 256 s),
 // rho (s x s), red (256), w, tau (32 each), the sign vector (32).  256 threads.
 __global__ void __launch_bounds__(256)
-la_reduce(int64_t nchild, int s, int k1, int mx, int m1, const double* __restrict__ child_out,
+la_reduce(int64_t nchild, int s, int k1, int mx, int m1, int F, const double* __restrict__ child_out,
           double* __restrict__ NB, double* __restrict__ Rout) {
   extern __shared__ double sm[];
   const int K2 = k1 + 1, Lr = K2 * s;
   const int64_t node = blockIdx.x;
-  const int64_t c0 = 2 * node;
-  const int nc = (c0 + 1 < nchild) ? 2 : 1;
+  const int64_t c0 = (int64_t)F * node;
+  const int nc = (int)((nchild - c0) < F ? (nchild - c0) : F);
   const int mrows = nc * Lr;
-  const size_t cap = (size_t)2 * mx * s * s;
+  const size_t cap = (size_t)F * mx * s * s;
   const size_t capc = cap > (size_t)256 * s ? cap : (size_t)256 * s;   // C also holds 256 s partials
   double* S = sm;
   double* C = S + cap;
@@ -194,10 +195,10 @@ la_reduce(int64_t nchild, int s, int k1, int mx, int m1, const double* __restric
     S[i] = child_out[(c0 + q) * vec + (size_t)rr * s + col];
   }
   __syncthreads();
-  double* nbn = NB + (size_t)node * m1 * 2 * vec;
+  double* nbn = NB + (size_t)node * m1 * F * vec;
   double* rout = Rout + (size_t)node * vec;
   for (int i = 0; i < k1; ++i) {
-    const double* Zi = nbn + (size_t)i * 2 * vec;         // [2][mx s][s], rows < (i + 1) s non-zero
+    const double* Zi = nbn + (size_t)i * F * vec;         // [F][mx s][s], rows < (i + 1) s non-zero
     const int li = (i + 1) * s;
     {
       // thread (a, part): rho_i[a][:] over the rows part, part + np, ... (s chains
@@ -243,7 +244,7 @@ la_reduce(int64_t nchild, int s, int k1, int mx, int m1, const double* __restric
   cta_apply_q(S, tau, mrows, s, C, red, w);
   if (tid < s) dsg[tid] = (S[tid * s + tid] < 0.0) ? -1.0 : 1.0;
   __syncthreads();
-  double* nbk = nbn + (size_t)k1 * 2 * vec;
+  double* nbk = nbn + (size_t)k1 * F * vec;
   for (int i = tid; i < mrows * s; i += nt) {
     const int row = i / s, col = i % s, q = row / Lr, rr = row % Lr;
     nbk[q * vec + (size_t)rr * s + col] = C[i] * dsg[col];
@@ -257,17 +258,17 @@ la_reduce(int64_t nchild, int s, int k1, int mx, int m1, const double* __restric
 // ---- 4. back-propagation, one CTA per node --------------------------------------
 // cin: [nodes][mx s][s] (K2 blocks valid); cout: [nchild][mx s][s].
 __global__ void __launch_bounds__(256)
-la_backprop(int64_t nchild, int s, int k1, int mx, int m1, const double* __restrict__ cin,
+la_backprop(int64_t nchild, int s, int k1, int mx, int m1, int F, const double* __restrict__ cin,
             const double* __restrict__ NB, double* __restrict__ cout) {
   extern __shared__ double rt[];                          // K2 s x s
   const int K2 = k1 + 1, Lr = K2 * s;
   const int64_t node = blockIdx.x;
-  const int64_t c0 = 2 * node;
-  const int nc = (c0 + 1 < nchild) ? 2 : 1;
+  const int64_t c0 = (int64_t)F * node;
+  const int nc = (int)((nchild - c0) < F ? (nchild - c0) : F);
   const size_t vec = (size_t)mx * s * s;
   for (int i = threadIdx.x; i < Lr * s; i += blockDim.x) rt[i] = cin[node * vec + i];
   __syncthreads();
-  const double* nbn = NB + (size_t)node * m1 * 2 * vec;
+  const double* nbn = NB + (size_t)node * m1 * F * vec;
   // one output row per thread, its s columns as independent chains
   for (int row = threadIdx.x; row < nc * Lr; row += blockDim.x) {
     const int q = row / Lr, rr = row % Lr;
@@ -275,7 +276,7 @@ la_backprop(int64_t nchild, int s, int k1, int mx, int m1, const double* __restr
 #pragma unroll
     for (int b = 0; b < kLocMaxS; ++b) acc[b] = 0.0;
     for (int ii = rr / s; ii <= k1; ++ii) {                // zeta^ii_q is zero below (ii + 1) s rows
-      const double* Z = nbn + (size_t)ii * 2 * vec + q * vec + (size_t)rr * s;
+      const double* Z = nbn + (size_t)ii * F * vec + q * vec + (size_t)rr * s;
       for (int a = 0; a < s; ++a) {
         const double z = Z[a];
         const double* R = rt + (ii * s + a) * s;
@@ -310,20 +311,28 @@ size_t local_arnoldi_bytes(int64_t n, int s, int m, int tile_rows, LocalArnoldi*
   LocalArnoldi& a = *la;
   a.s = s; a.n = n; a.m1 = m + 1; a.mx = m + 1; a.tile_rows = tile_rows;
   a.tiles = (n + tile_rows - 1) / tile_rows;
+  // fan-in: the widest of 8, 4, 2 whose node fits 200 KB of shared memory
+  auto smem_of = [&](int F) {
+    const size_t cap = (size_t)F * a.mx * s * s;
+    return sizeof(double) * (cap + (cap > (size_t)256 * s ? cap : (size_t)256 * s) + (size_t)s * s + 256 + 96);
+  };
+  a.fanin = 2;
+  for (int F : {8, 4}) {
+    if (smem_of(F) <= 200 * 1024) { a.fanin = F; break; }
+  }
+  a.reduce_smem = smem_of(a.fanin);
   a.nodes[0] = a.tiles;
   a.levels = 0;
   while (a.nodes[a.levels] > 1 && a.levels < 23) {
-    a.nodes[a.levels + 1] = (a.nodes[a.levels] + 1) / 2;
+    a.nodes[a.levels + 1] = (a.nodes[a.levels] + a.fanin - 1) / a.fanin;
     ++a.levels;
   }
   const size_t vec = (size_t)a.mx * s * s * sizeof(double);
   size_t b = al256(sizeof(double*) * (size_t)a.m1) + 2 * al256(vec * (size_t)a.tiles);
   for (int l = 1; l <= a.levels; ++l) {
-    a.nb_bytes[l] = (size_t)a.nodes[l] * a.m1 * 2 * vec;
+    a.nb_bytes[l] = (size_t)a.nodes[l] * a.m1 * a.fanin * vec;
     b += al256(a.nb_bytes[l]) + 2 * al256(vec * (size_t)a.nodes[l]);
   }
-  const size_t cap = (size_t)2 * a.mx * s * s;
-  a.reduce_smem = sizeof(double) * (cap + (cap > (size_t)256 * s ? cap : (size_t)256 * s) + (size_t)s * s + 256 + 96);
   return b;
 }
 
@@ -419,7 +428,7 @@ cudaError_t local_arnoldi_extend(const Launch& L, const LocalArnoldi& la, const 
     for (int l = 1; l <= la.levels; ++l) {
       const double* child = (l == 1) ? la.Zt : la.Rout[l - 1];
       la_reduce<<<(unsigned)la.nodes[l], 256, la.reduce_smem, L.stream>>>(la.nodes[l - 1], s, k1, la.mx, la.m1,
-                                                                          child, la.NB[l], la.Rout[l]);
+                                                                          la.fanin, child, la.NB[l], la.Rout[l]);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     la_root_out<<<1, 256, 0, L.stream>>>(s, k1, la.Rout[la.levels], Hc, gamma, la.Cin[la.levels]);
@@ -429,7 +438,7 @@ cudaError_t local_arnoldi_extend(const Launch& L, const LocalArnoldi& la, const 
     for (int l = la.levels; l >= 1; --l) {
       double* out = (l == 1) ? la.Zl : la.Cin[l - 1];
       la_backprop<<<(unsigned)la.nodes[l], 256, bsm, L.stream>>>(la.nodes[l - 1], s, k1, la.mx, la.m1,
-                                                                  la.Cin[l], la.NB[l], out);
+                                                                  la.fanin, la.Cin[l], la.NB[l], out);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
   }

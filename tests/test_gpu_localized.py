@@ -3,9 +3,9 @@
 The GPU's row tiles are the FP64 TSQR leaf tiles (256 x 64 / next_pow2(s) rows,
 256 x 32 / next_pow2(s) for s <= 4); the oracle runs the same tiling.  Checked:
 the iterate after the first Arnoldi steps against the oracle's localized
-BGMRes (1e-11), converged solves against block MGS (same step count, true
-residual at the tolerance), one tile (no tree) and odd tile counts (nodes with
-one child), and the unsupported shapes.
+BGMRes with the same tree fan-in (1e-11), converged solves against block MGS
+(same step count, true residual at the tolerance), one tile (no tree) and tile
+counts that leave nodes with fewer children, and the unsupported shapes.
 """
 import numpy as np
 import pytest
@@ -41,6 +41,16 @@ def _tile(s):
     return 256 * (32 if sw <= 4 else 64) // sw
 
 
+def _fanin(s, restart):
+    """The library's tree fan-in: the widest of 8, 4, 2 whose node fits 200 KB of shared memory."""
+    mx = restart + 1
+    for F in (8, 4):
+        cap = F * mx * s * s
+        if 8 * (cap + max(cap, 256 * s) + s * s + 352) <= 200 * 1024:
+            return F
+    return 2
+
+
 def _op(h, prob, use="stencil"):
     from paper_2104_02494_gb300.api import operator_from_problem
     return operator_from_problem(h, prob, use)
@@ -53,7 +63,8 @@ def test_localized_first_steps_and_final(h, grid, s):
     tile = _tile(s)
     for k in (1, 3, 8):
         X, info = h.solve("bgmres", op, _dev(prob.B), tol=0.0, maxit=k, restart=10, ortho="localized")
-        ref = oracle.bgmres(prob.A, prob.B, tol=0.0, restart=10, maxit=k, ortho="localized", tile_rows=tile)
+        ref = oracle.bgmres(prob.A, prob.B, tol=0.0, restart=10, maxit=k, ortho="localized", tile_rows=tile,
+                            fanin=_fanin(s, 10))
         assert info.iters == k
         assert _rel(X.cpu().numpy(), ref.X) <= 1e-11, (k, _rel(X.cpu().numpy(), ref.X))
     X, info = h.solve("bgmres", op, _dev(prob.B), tol=1e-8, maxit=400, restart=10, ortho="localized")

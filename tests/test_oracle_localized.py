@@ -27,11 +27,12 @@ def _qr_fixed(M):
     return Q * d, R * d[:, None]
 
 
+@pytest.mark.parametrize("fanin", [2, 3, 4])
 @pytest.mark.parametrize("n,s,tile", [(300, 3, 300), (300, 3, 64), (301, 4, 40), (258, 2, 16)])
-def test_distributed_qr_is_a_qr_of_the_concatenated_blocks(n, s, tile):
+def test_distributed_qr_is_a_qr_of_the_concatenated_blocks(n, s, tile, fanin):
     g = np.random.default_rng(n + s + tile)
     blocks = [g.standard_normal((n, s)) for _ in range(6)]
-    la = LocalizedArnoldi(n, s, tile)
+    la = LocalizedArnoldi(n, s, tile, fanin)
     Xs, cols = [], []
     for Wb in blocks:
         X, rho = la.extend(Wb)
@@ -64,11 +65,12 @@ def test_locally_rank_deficient_tiles():
     assert np.abs(np.hstack(Xs) - Q).max() <= 1e-11
 
 
-@pytest.mark.parametrize("tile", [1000, 500, 200, 143, 64])
-def test_bgmres_localized_equals_mgs_and_cgs2(tile):
+@pytest.mark.parametrize("tile,fanin", [(1000, 2), (500, 2), (200, 2), (143, 2), (64, 2), (64, 4), (64, 8)])
+def test_bgmres_localized_equals_mgs_and_cgs2(tile, fanin):
     prob = W.problem("convdiff3d", grid=10)
     a = oracle.bgmres(prob.A, prob.B, tol=1e-9, restart=8, maxit=60, ortho="mgs")
-    b = oracle.bgmres(prob.A, prob.B, tol=1e-9, restart=8, maxit=60, ortho="localized", tile_rows=tile)
+    b = oracle.bgmres(prob.A, prob.B, tol=1e-9, restart=8, maxit=60, ortho="localized", tile_rows=tile,
+                      fanin=fanin)
     c = oracle.bgmres(prob.A, prob.B, tol=1e-9, restart=8, maxit=60, ortho="cgs2")
     assert a.converged and b.converged and a.iters == b.iters == c.iters
     assert np.abs(b.X - a.X).max() <= 1e-10 * np.abs(a.X).max()
