@@ -61,6 +61,18 @@ def test_1r_iterates_and_final(h, name, grid, s, use, K, eta):
     op.close()
 
 
+@pytest.mark.parametrize("s", [1, 3])
+def test_1r_narrow_blocks(h, s):
+    prob = W.problem("laplace3d", grid=12, s=s)
+    op = _op(h, prob, "stencil")
+    ref = oracle.bcg_1r(prob.A, prob.B, tol=1e-8, maxit=500, eta=math.inf, record_iterates=10)
+    X, _ = h.solve("bcg", op, _dev(prob.B), tol=0.0, maxit=10, eta=math.inf, one_reduction=True)
+    assert _rel(X.cpu().numpy(), ref.iterates[9]) <= 1e-12
+    X, info = h.solve("bcg", op, _dev(prob.B), tol=1e-8, maxit=500, eta=math.inf, one_reduction=True)
+    assert info.converged and abs(info.iters - ref.iters) <= 2
+    op.close()
+
+
 def test_1r_jacobi_and_adaptive_replay(h):
     prob = W.problem("vardiff3d", grid=12, s=8)
     op = _op(h, prob, "stencil")

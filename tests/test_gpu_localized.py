@@ -75,6 +75,18 @@ def test_localized_first_steps_and_final(h, grid, s):
     op.close()
 
 
+@pytest.mark.parametrize("s,restart", [(2, 1), (8, 2), (8, 30)])
+def test_localized_restart_lengths(h, s, restart):
+    """Short and long cycles (restart 1: one basis vector per cycle)."""
+    prob = W.problem("convdiff3d", grid=20, s=s)
+    op = _op(h, prob)
+    ref = oracle.bgmres(prob.A, prob.B, tol=0.0, restart=restart, maxit=6, ortho="localized",
+                        tile_rows=_tile(s), fanin=_fanin(s, restart))
+    X, info = h.solve("bgmres", op, _dev(prob.B), tol=0.0, maxit=6, restart=restart, ortho="localized")
+    assert info.iters == 6 and _rel(X.cpu().numpy(), ref.X) <= 1e-11
+    op.close()
+
+
 def test_localized_unsupported_shapes(h):
     from paper_2104_02494_gb300.api import BkError
     prob = W.problem("convdiff3d", grid=24, s=32)
