@@ -242,6 +242,12 @@ int bkrylov_profile_reset(bkrylov_handle h);
    symmetric, row-major; kappa: DEVICE double (+inf when a diagonal entry or the smallest
    eigenvalue of the scaled matrix is <= 0).  Enqueued on the handle's stream. */
 int bkrylov_kappa_d(bkrylov_handle h, int s, const double* A, double* kappa);
+/* The adaptive re-orthonormalisation decision as the solvers take it: *decision = 1 when
+   eta * kappa_D(A) > 1 / sqrt(eps) (Ch. 4.3, Eq. "reortho_criterion"; eta = 0 never, INFINITY
+   always).  kappa_D is first bracketed in FP32; where it is below 2^10 and eta kappa_D is more
+   than 1 % off the threshold that decides, otherwise the FP64 kappa_D of bkrylov_kappa_d does.
+   A: DEVICE s x s symmetric, row-major; decision: DEVICE int.  Enqueued on the stream. */
+int bkrylov_reortho_decision(bkrylov_handle h, int s, const double* A, double eta, double eps, int* decision);
 /* Kernel launches of one BCG iteration for an n x s block (host-only, no GPU). */
 int bkrylov_bcg_launches_per_iteration(int64_t n, int s);
 

@@ -75,6 +75,8 @@ SIGNATURES = [
                                       C.POINTER(C.c_longlong)]),
     ("bkrylov_profile_reset", C.c_int, [C.c_void_p]),
     ("bkrylov_kappa_d", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    ("bkrylov_reortho_decision", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_double, C.c_double,
+                                           C.c_void_p]),
     ("bkrylov_bcg_launches_per_iteration", C.c_int, [C.c_int64, C.c_int]),
     ("bkrylov_adjoint_scatter", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                           C.c_void_p]),

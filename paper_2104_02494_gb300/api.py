@@ -177,6 +177,14 @@ class Handle:
         _check(self.lib.bkrylov_kappa_d(self.h, A.shape[0], _ptr(A), _ptr(out)), "bkrylov_kappa_d")
         return float(out.item())
 
+    def reortho_decision(self, A: torch.Tensor, eta: float, eps: float = 2.0 ** -52) -> bool:
+        """The solvers' re-orthonormalisation decision for the s x s matrix A (float64, CUDA)."""
+        out = torch.zeros(1, dtype=torch.int32, device=A.device)
+        A = A.contiguous()
+        _check(self.lib.bkrylov_reortho_decision(self.h, A.shape[0], _ptr(A), float(eta), float(eps), _ptr(out)),
+               "bkrylov_reortho_decision")
+        return bool(out.item())
+
     # ---- measurement ----
     def profile(self):
         """[(phase, total_ms, launches)] accumulated by solves run with profile=True."""

@@ -1210,6 +1210,12 @@ int bkrylov_kappa_d(bkrylov_handle h, int s, const double* A, double* kappa) {
   return BK_OK;
 }
 
+int bkrylov_reortho_decision(bkrylov_handle h, int s, const double* A, double eta, double eps, int* decision) {
+  if (!h || !valid_s(s) || !A || !decision || !(eta >= 0.0) || !(eps > 0.0)) return BK_ERR_ARG;
+  BK_TRY(small_criterion(launch_of(h), s, eta, eps, A, decision));
+  return BK_OK;
+}
+
 int bkrylov_bcg_launches_per_iteration(int64_t n, int s) {
   if (n < 1 || s < 1 || s > kMaxS) return -1;
   return bcg_launches_per_iter(tsqr_plan(n, s));

@@ -204,6 +204,8 @@ cudaError_t small_bicg_3(const Launch& L, Ctrl* ctrl, double* history, uint8_t* 
 cudaError_t small_set_identity(const Launch& L, double* M, int s);
 // kappa_D of an s x s symmetric matrix A (row stride s, device) into *out (device).
 cudaError_t small_kappa_d(const Launch& L, int s, const double* A, double* out);
+// The re-orthonormalisation decision eta kappa_D(A) > 1/sqrt(eps) as the solvers take it.
+cudaError_t small_criterion(const Launch& L, int s, double eta, double eps, const double* A, int* out);
 cudaError_t small_colnorms_from_gram(const Launch& L, Ctrl* ctrl);
 
 // BGMRes small kernels

@@ -6,6 +6,8 @@
 // All matrices live in shared memory with row stride 32 (kMaxS).
 #include <math.h>
 
+#include <type_traits>
+
 #include "bk_common.cuh"
 #include "bk_hh.cuh"
 #include "bk_internal.h"
@@ -157,40 +159,66 @@ __device__ void sm_lu_solve(const double* LU, const int* piv, const double* B, d
   __syncthreads();
 }
 
+// Bit-level constants of the two precisions the eigenvalue bracketing runs in.
+template <typename R> struct KBits;
+template <> struct KBits<double> {
+  using I = long long;
+  static constexpr int kMant = 52, kExpMask = 0x7ff, kBias = 1023, kShift = 400;
+  static __device__ __forceinline__ I bits(double v) { return __double_as_longlong(v); }
+  static __device__ __forceinline__ double tiny() { return 0x1p-600; }
+  static __device__ __forceinline__ double up() { return 0x1p400; }
+  static __device__ __forceinline__ double down() { return 0x1p-400; }
+  static __device__ __forceinline__ double stop() { return 0x1p-49; }   // 8 eps
+};
+template <> struct KBits<float> {
+  using I = int;
+  static constexpr int kMant = 23, kExpMask = 0xff, kBias = 127, kShift = 60;
+  static __device__ __forceinline__ I bits(float v) { return __float_as_int(v); }
+  static __device__ __forceinline__ float tiny() { return 0x1p-100f; }
+  static __device__ __forceinline__ float up() { return 0x1p60f; }
+  static __device__ __forceinline__ float down() { return 0x1p-60f; }
+  static __device__ __forceinline__ float stop() { return 0x1p-20f; }   // 8 eps
+};
+
 // Number of eigenvalues of the symmetric tridiagonal T = tridiag(e, d, e)
 // below x: the sign changes of the Sturm sequence of T - x I's leading
 // principal minors p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (Wilkinson,
 // "The Algebraic Eigenvalue Problem", 1965, Ch. 5).  No division: the two
-// latest terms are rescaled together by 2^-+400 when they leave
-// [2^-400, 2^400], which keeps their signs and ratio; an exact zero takes the
-// sign opposite to its predecessor (x moved off the root of that minor).
-__device__ int sturm_count(const double* d, const double* e2, int s, double x) {
-  // signs, zeros and exponents are read from the bit pattern (integer ALU): the
-  // FP64 pipe only carries the recurrence itself
+// latest terms are rescaled together when they leave [2^-K, 2^K] (K = 400 in
+// double, 60 in float), which keeps their signs and ratio; an exact zero takes
+// the sign opposite to its predecessor (x moved off the root of that minor).
+// Signs, zeros and exponents are read from the bit pattern (integer ALU): the
+// floating-point pipe only carries the recurrence itself.
+template <typename R>
+__device__ int sturm_count(const R* d, const R* e2, int s, R x) {
+  using B = KBits<R>;
+  using I = typename B::I;
+  constexpr int kSignShift = 8 * (int)sizeof(R) - 1;
   int cnt = 0;
-  long long sprev = 0;                 // sign bit of the previous term (1: negative)
-  double pm1 = 1.0, p = d[0] - x;
+  I sprev = 0;                          // sign bit of the previous term (1: negative)
+  R pm1 = R(1), p = d[0] - x;
   for (int i = 0;; ++i) {
-    long long b = __double_as_longlong(p);
-    if ((b << 1) == 0) {               // +-0: take the sign opposite to the predecessor
-      p = sprev ? 0x1p-600 : -0x1p-600;
-      b = __double_as_longlong(p);
+    I b = B::bits(p);
+    if (((typename std::make_unsigned<I>::type)b << 1) == 0) {   // +-0: the sign opposite to the predecessor
+      p = sprev ? B::tiny() : -B::tiny();
+      b = B::bits(p);
     }
-    const long long sg = (long long)((unsigned long long)b >> 63);
+    const I sg = (I)((typename std::make_unsigned<I>::type)b >> kSignShift);
     cnt += (int)(sg != sprev);
     sprev = sg;
-    const int ex = (int)((b >> 52) & 0x7ff);
-    if (ex > 1023 + 400) { p *= 0x1p-400; pm1 *= 0x1p-400; }
-    else if (ex < 1023 - 400) { p *= 0x1p400; pm1 *= 0x1p400; }
+    const int ex = (int)((b >> B::kMant) & B::kExpMask);
+    if (ex > B::kBias + B::kShift) { p *= B::down(); pm1 *= B::down(); }
+    else if (ex < B::kBias - B::kShift) { p *= B::up(); pm1 *= B::up(); }
     if (i + 1 >= s) break;
-    const double pn = fma(d[i + 1] - x, p, -e2[i] * pm1);
+    const R pn = fma(d[i + 1] - x, p, -e2[i] * pm1);
     pm1 = p;
     p = pn;
   }
   return cnt;
 }
 
-__device__ inline double warp_sum(double v) {
+template <typename R>
+__device__ inline R warp_sum(R v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   return v;
@@ -208,8 +236,9 @@ __device__ inline double warp_sum(double v) {
 // eigenvalues of M are determined at all, or after 12 rounds).
 // +inf when a diagonal entry of A or the smallest
 // eigenvalue is <= 0.  M and M2 are shared work matrices.
-__device__ double sm_kappa_d(const double* A, int s, double* M, double* M2, int* flag) {
-  __shared__ double s_tau, s_lo[2], s_hi[2];
+template <typename R>
+__device__ double sm_kappa_d_t(const double* A, int s, R* M, R* M2, int* flag, double* lo_hi = nullptr) {
+  __shared__ R s_tau, s_lo[2], s_hi[2];
   if (threadIdx.x == 0) *flag = 1;
   __syncthreads();
   for (int i = threadIdx.x; i < s; i += blockDim.x)
@@ -218,57 +247,63 @@ __device__ double sm_kappa_d(const double* A, int s, double* M, double* M2, int*
   if (!*flag) return INFINITY;
   for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
     const int a = i / s, c = i % s;
-    M[IDX(a, c)] = A[IDX(a, c)] / sqrt(A[IDX(a, a)] * A[IDX(c, c)]);
+    M[IDX(a, c)] = (R)(A[IDX(a, c)] / sqrt(A[IDX(a, a)] * A[IDX(c, c)]));
   }
   __syncthreads();
-  if (s == 1) return 1.0;
-  double* v = M2;            // Householder vector (entries k+1 .. s-1 at 0 .. m-1)
-  double* w = M2 + 32;       // w = p - K v
-  double* dd = M2 + 64;      // diagonal of T
-  double* e2 = M2 + 96;      // squared off-diagonal of T
-  double* ee = M2 + 128;     // off-diagonal of T
-  double* part = M2 + 160;   // 8 warps x 32 partial sums of M' v
+  if (s == 1) {
+    if (lo_hi && threadIdx.x == 0) { lo_hi[0] = 1.0; lo_hi[1] = 1.0; }
+    __syncthreads();
+    return 1.0;
+  }
+  R* v = M2;                 // Householder vector (entries k+1 .. s-1 at 0 .. m-1)
+  R* w = M2 + 32;            // w = p - K v
+  R* dd = M2 + 64;           // diagonal of T
+  R* e2 = M2 + 96;           // squared off-diagonal of T
+  R* ee = M2 + 128;          // off-diagonal of T
+  R* part = M2 + 160;        // 8 warps x 32 partial sums of M' v
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nw = blockDim.x >> 5;
   for (int k = 0; k + 2 < s; ++k) {
     const int m = s - k - 1;
     if (warp == 0) {
-      const double x = lane < m ? M[IDX(k + 1 + lane, k)] : 0.0;
-      const double x0 = __shfl_sync(0xffffffffu, x, 0);
-      const double tail = warp_sum(lane > 0 ? x * x : 0.0);
-      double tau = 0.0, alpha = x0;
-      if (tail > 0.0) {
-        const double sig = sqrt(fma(x0, x0, tail));
-        alpha = x0 >= 0.0 ? -sig : sig;
-        const double v0 = x0 - alpha;
-        tau = 2.0 / fma(v0, v0, tail);
+      const R x = lane < m ? M[IDX(k + 1 + lane, k)] : R(0);
+      const R x0 = __shfl_sync(0xffffffffu, x, 0);
+      const R tail = warp_sum<R>(lane > 0 ? x * x : R(0));
+      R tau = R(0), alpha = x0;
+      if (tail > R(0)) {
+        const R sig = sqrt(fma(x0, x0, tail));
+        alpha = x0 >= R(0) ? -sig : sig;
+        const R v0 = x0 - alpha;
+        tau = R(2) / fma(v0, v0, tail);
         if (lane < m) v[lane] = lane == 0 ? v0 : x;
       }
       if (lane == 0) { dd[k] = M[IDX(k, k)]; ee[k] = alpha; s_tau = tau; }
     }
     __syncthreads();
-    const double tau = s_tau;
-    if (tau == 0.0) {                         // column already reduced
+    const R tau = s_tau;
+    if (tau == R(0)) {                        // column already reduced
       __syncthreads();                        // every thread has read s_tau
       continue;
     }
-    double acc = 0.0;
+    R acc = R(0);
     if (lane < m)
       for (int i = warp; i < m; i += nw) acc = fma(M[IDX(k + 1 + i, k + 1 + lane)], v[i], acc);
     part[warp * 32 + lane] = acc;
     __syncthreads();
     if (warp == 0) {
-      double pj = 0.0;
+      R pj = R(0);
       for (int q = 0; q < nw; ++q) pj += part[q * 32 + lane];
-      pj = lane < m ? tau * pj : 0.0;
-      const double vj = lane < m ? v[lane] : 0.0;
-      const double K = 0.5 * tau * warp_sum(pj * vj);
+      pj = lane < m ? tau * pj : R(0);
+      const R vj = lane < m ? v[lane] : R(0);
+      const R K = R(0.5) * tau * warp_sum<R>(pj * vj);
       if (lane < m) w[lane] = fma(-K, vj, pj);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
       const int i = e / m, j = e % m;
-      const double u = __dadd_rn(__dmul_rn(v[i], w[j]), __dmul_rn(w[i], v[j]));
+      R u;
+      if constexpr (sizeof(R) == 8) u = __dadd_rn(__dmul_rn(v[i], w[j]), __dmul_rn(w[i], v[j]));
+      else u = __fadd_rn(__fmul_rn(v[i], w[j]), __fmul_rn(w[i], v[j]));
       M[IDX(k + 1 + i, k + 1 + j)] -= u;
     }
     __syncthreads();
@@ -283,9 +318,9 @@ __device__ double sm_kappa_d(const double* A, int s, double* M, double* M2, int*
   // the smallest eigenvalue (first point with count >= 1), 64..127 the largest
   // (first point with count >= s).
   if (warp == 0) {
-    double lo = INFINITY, hi = -INFINITY;
+    R lo = R(INFINITY), hi = R(-INFINITY);
     if (lane < s) {
-      const double r = (lane > 0 ? fabs(ee[lane - 1]) : 0.0) + (lane < s - 1 ? fabs(ee[lane]) : 0.0);
+      const R r = (lane > 0 ? fabs(ee[lane - 1]) : R(0)) + (lane < s - 1 ? fabs(ee[lane]) : R(0));
       lo = dd[lane] - r;
       hi = dd[lane] + r;
       if (lane < s - 1) e2[lane] = ee[lane] * ee[lane];
@@ -301,16 +336,16 @@ __device__ double sm_kappa_d(const double* A, int s, double* M, double* M2, int*
   __shared__ int s_first[4];
   // stop when both brackets are within 8 eps ||T|| (the accuracy to which
   // the eigenvalues of M are determined at all), after 12 rounds at most
-  const double gnorm = fmax(fabs(s_lo[0]), fabs(s_hi[0]));
+  const R gnorm = fmax(fabs(s_lo[0]), fabs(s_hi[0]));
   for (int round = 0; round < 12; ++round) {
     bool done = true;              // uniform: every thread reads the same brackets
-    for (int q = 0; q < 2; ++q) done = done && (s_hi[q] - s_lo[q] <= 0x1p-49 * gnorm);
+    for (int q = 0; q < 2; ++q) done = done && (s_hi[q] - s_lo[q] <= KBits<R>::stop() * gnorm);
     if (done) break;
     const int g = (threadIdx.x >> 6) & 1, t = threadIdx.x & 63;
-    const double lo = s_lo[g], hi = s_hi[g];
-    const double step = (hi - lo) / 65.0;
+    const R lo = s_lo[g], hi = s_hi[g];
+    const R step = (hi - lo) / R(65);
     bool in = false;
-    if (threadIdx.x < 128) in = sturm_count(dd, e2, s, lo + step * (t + 1)) >= (g == 0 ? 1 : s);
+    if (threadIdx.x < 128) in = sturm_count<R>(dd, e2, s, lo + step * R(t + 1)) >= (g == 0 ? 1 : s);
     // first point (per group of two warps) at or above the eigenvalue; 64: none
     const unsigned bal = __ballot_sync(0xffffffffu, in);
     if (threadIdx.x < 128 && lane == 0) s_first[warp] = bal ? (warp & 1) * 32 + __ffs(bal) - 1 : 64;
@@ -318,13 +353,20 @@ __device__ double sm_kappa_d(const double* A, int s, double* M, double* M2, int*
     if (threadIdx.x < 128 && t == 0) {
       const int f = min(s_first[2 * g], s_first[2 * g + 1]);
       // the eigenvalue lies in (x_{f-1}, x_f], x_{-1} = lo, x_64 = hi
-      s_lo[g] = f == 0 ? lo : lo + step * f;
-      s_hi[g] = f == 64 ? hi : lo + step * (f + 1);
+      s_lo[g] = f == 0 ? lo : lo + step * R(f);
+      s_hi[g] = f == 64 ? hi : lo + step * R(f + 1);
     }
     __syncthreads();
   }
-  const double lmin = 0.5 * (s_lo[0] + s_hi[0]), lmax = 0.5 * (s_lo[1] + s_hi[1]);
-  return (lmin > 0.0 && s_hi[0] > 0.0) ? lmax / lmin : INFINITY;
+  const double lmin = 0.5 * ((double)s_lo[0] + (double)s_hi[0]);
+  const double lmax = 0.5 * ((double)s_lo[1] + (double)s_hi[1]);
+  if (lo_hi && threadIdx.x == 0) { lo_hi[0] = lmin; lo_hi[1] = lmax; }
+  __syncthreads();
+  return (lmin > 0.0 && s_hi[0] > R(0)) ? lmax / lmin : INFINITY;
+}
+
+__device__ double sm_kappa_d(const double* A, int s, double* M, double* M2, int* flag) {
+  return sm_kappa_d_t<double>(A, s, M, M2, flag);
 }
 
 // max that propagates NaN (fmax would drop it)
@@ -336,14 +378,29 @@ __device__ inline void stop(Ctrl* c, int status) {
 
 // re-orthonormalisation decision (Eq. "reortho_criterion", read as
 // eta * kappa_D > 1/sqrt(eps); eta = 0 never, eta = inf always)
-__device__ int decide(Ctrl* c, const uint8_t* forced, const double* A, double* M, double* M2,
-                      int* flag) {
+__device__ int criterion(double eta, double eps, int s, const double* A, double* M, double* M2, int* flag) {
+  if (eta == 0.0) return 0;
+  if (isinf(eta)) return 1;
+  const double thr = 1.0 / sqrt(eps);
+  // first in FP32: where kappa_D < 2^10 the FP32 eigenvalues fix it to ~0.1 %
+  // (absolute error ~ s eps_32 ||M||), so a decision more than 1 % off the
+  // threshold is the FP64 one; otherwise (and for every larger kappa_D) FP64
+  __shared__ double lh[2];
+  const double k32 = sm_kappa_d_t<float>(A, s, reinterpret_cast<float*>(M), reinterpret_cast<float*>(M2),
+                                         flag, lh);
+  if (lh[0] > 0.0 && lh[0] > lh[1] * 0x1p-10 && isfinite(k32)) {
+    const double x = eta * k32;
+    if (x < 0.99 * thr) return 0;
+    if (x > 1.01 * thr) return 1;
+  }
+  const double kap = sm_kappa_d(A, s, M, M2, flag);
+  return (eta * kap > thr) ? 1 : 0;
+}
+
+__device__ int decide(Ctrl* c, const uint8_t* forced, const double* A, double* M, double* M2, int* flag) {
   const int k = c->iter;
   if (forced && k < c->n_forced) return forced[k] ? 1 : 0;
-  if (c->eta == 0.0) return 0;
-  if (isinf(c->eta)) return 1;
-  const double kap = sm_kappa_d(A, c->s, M, M2, flag);
-  return (c->eta * kap > 1.0 / sqrt(c->eps)) ? 1 : 0;
+  return criterion(c->eta, c->eps, c->s, A, M, M2, flag);
 }
 
 // Orthogonal projection onto S_BP^p (Def. "subalgebras", Ch. 3.1): entries
@@ -539,6 +596,24 @@ __global__ void __launch_bounds__(kST) small_kappa_d_k(int s, const double* A, d
   __syncthreads();
   const double k = sm_kappa_d(S.A, s, S.B, S.C, &S.flag);
   if (threadIdx.x == 0) *out = k;
+}
+
+// The re-orthonormalisation criterion on its own (the solvers' decision routine).
+__global__ void __launch_bounds__(kST) small_criterion_k(int s, double eta, double eps, const double* A, int* out) {
+  extern __shared__ double smraw[];
+  SmallSmem& S = *reinterpret_cast<SmallSmem*>(smraw);
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) S.A[IDX(i / s, i % s)] = A[i];
+  __syncthreads();
+  const int d = criterion(eta, eps, s, S.A, S.B, S.C, &S.flag);
+  if (threadIdx.x == 0) *out = d;
+}
+
+cudaError_t small_criterion(const Launch& L, int s, double eta, double eps, const double* A, int* out) {
+  const size_t sm = sizeof(SmallSmem);
+  cudaError_t e = cudaFuncSetAttribute(small_criterion_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  small_criterion_k<<<1, kST, sm, L.stream>>>(s, eta, eps, A, out);
+  return cudaGetLastError();
 }
 
 cudaError_t small_kappa_d(const Launch& L, int s, const double* A, double* out) {

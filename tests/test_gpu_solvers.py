@@ -151,7 +151,34 @@ def test_bcg_adaptive_decisions_over_widths(h, name, grid, s):
         kap = h.kappa_d(_dev(alpha))
         if abs(1e4 * ref.kappas[k] / thr - 1.0) >= 0.01:
             assert (1e4 * kap > thr) == ref.decisions[k], (k, kap, ref.kappas[k])
+            # the solvers' routine (FP32 bracketing first, FP64 near the threshold)
+            assert h.reortho_decision(_dev(alpha), 1e4) == ref.decisions[k], k
     op.close()
+
+
+def test_reortho_decision_routine_across_kappa(h):
+    """eta kappa_D > 1/sqrt(eps) by the solvers' routine against the oracle's kappa_D on
+    matrices from kappa_D = 1 to 1e12, for thresholds on both sides (FP64 and FP32 eps)."""
+    for s, cond, seed in [(1, 1.0, 0), (3, 1e2, 1), (8, 1e3, 2), (8, 3e5, 3), (16, 1e4, 4), (16, 1e9, 5),
+                          (32, 50.0, 6), (32, 1e12, 7), (5, 2e3, 8), (12, 6.7e3, 9)]:
+        A = _spd_scaled(s, cond, seed)
+        kap = oracle.kappa_d(A)
+        for eps in (2.0 ** -52, 2.0 ** -23):
+            thr = 1.0 / math.sqrt(eps)
+            for eta in (0.0, 1e-3, 1.0, 1e2, 1e4, 1e6, math.inf):
+                ref = eta > 0 and (math.isinf(eta) or eta * kap > thr)
+                if eta not in (0.0, math.inf) and abs(eta * kap / thr - 1.0) < 1e-6:
+                    continue
+                assert h.reortho_decision(_dev(A), eta, eps) == ref, (s, cond, eps, eta, kap)
+    # kappa_D below 2^10, eta 1.5 % on either side of the threshold: taken in FP32
+    for s, cond, seed in [(8, 300.0, 11), (16, 40.0, 12), (32, 900.0, 13)]:
+        A = _spd_scaled(s, cond, seed)
+        kap = oracle.kappa_d(A)
+        assert kap < 1000.0
+        for eps in (2.0 ** -52, 2.0 ** -23):
+            thr = 1.0 / math.sqrt(eps)
+            assert h.reortho_decision(_dev(A), 1.015 * thr / kap, eps)
+            assert not h.reortho_decision(_dev(A), 0.985 * thr / kap, eps)
 
 
 def test_bcg_s1_equals_scalar_cg(h):
