@@ -32,12 +32,33 @@ __device__ void sm_identity(double* dst, int s) {
 }
 
 // C = op(A) B with op(A) = A or A^T (C must not alias A or B).
+// A thread forms up to four entries at once (independent FMA chains).
 __device__ void sm_matmul(double* C, const double* A, bool transA, const double* B, int s) {
-  for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
-    const int a = i / s, c = i % s;
-    double acc = 0.0;
-    for (int k = 0; k < s; ++k) acc = fma(transA ? A[IDX(k, a)] : A[IDX(a, k)], B[IDX(k, c)], acc);
-    C[IDX(a, c)] = acc;
+  const int n = s * s, nt = blockDim.x;
+  for (int i0 = threadIdx.x; i0 < n; i0 += 4 * nt) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int a[4], c[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * nt;
+      a[u] = i < n ? i / s : 0;
+      c[u] = i < n ? i % s : 0;
+    }
+    const int per = (n - i0 + nt - 1) / nt;          // this thread's entries (<= 4), no idle FMAs
+    if (per >= 4) {
+      for (int k = 0; k < s; ++k) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          acc[u] = fma(transA ? A[IDX(k, a[u])] : A[IDX(a[u], k)], B[IDX(k, c[u])], acc[u]);
+      }
+    } else {
+      for (int u = 0; u < per; ++u)
+        for (int k = 0; k < s; ++k)
+          acc[u] = fma(transA ? A[IDX(k, a[u])] : A[IDX(a[u], k)], B[IDX(k, c[u])], acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i0 + u * nt < n) C[IDX(a[u], c[u])] = acc[u];
   }
 }
 
@@ -54,21 +75,18 @@ __device__ bool sm_all_finite(const double* A, int s, int* flag) {
 
 // In-place Cholesky A = L L^T (lower triangle of A overwritten by L).
 // Fails (returns false) on a non-positive or non-finite pivot, which is the
-// LAPACK potrf criterion.
+// LAPACK potrf criterion.  Every thread forms the pivot's square root itself
+// (no barrier between the pivot and the column scaling).
 __device__ bool sm_cholesky(double* A, int s, int* flag) {
   if (threadIdx.x == 0) *flag = 1;
   __syncthreads();
   for (int k = 0; k < s; ++k) {
-    if (threadIdx.x == 0) {
-      const double d = A[IDX(k, k)];
-      if (!(d > 0.0) || !isfinite(d)) *flag = 0;
-      else A[IDX(k, k)] = sqrt(d);
-    }
-    __syncthreads();
-    if (!*flag) return false;
-    const double lkk = A[IDX(k, k)];
+    const double d = A[IDX(k, k)];
+    if (!(d > 0.0) || !isfinite(d)) return false;      // uniform: every thread read the same pivot
+    const double lkk = sqrt(d);
     for (int i = k + 1 + threadIdx.x; i < s; i += blockDim.x) A[IDX(i, k)] /= lkk;
     __syncthreads();
+    if (threadIdx.x == 0) A[IDX(k, k)] = lkk;
     const int r = s - k - 1;
     for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
       const int i = k + 1 + e / r, j = k + 1 + e % r;
@@ -79,20 +97,27 @@ __device__ bool sm_cholesky(double* A, int s, int* flag) {
   return true;
 }
 
-// X = (L L^T)^{-1} B, one thread per right-hand-side column (X may alias B).
+// X = (L L^T)^{-1} B (X may alias B).  One warp per right-hand-side column,
+// lane i holding row i; column-oriented substitution: once x_i is final it is
+// broadcast by a shuffle and every later row subtracts its term, so the
+// dependent chain per column is 2 s steps (the terms are subtracted in the
+// same order k = 0, 1, ... as a row-oriented sweep).
 __device__ void sm_chol_solve(const double* L, const double* B, double* X, int s) {
-  const int c = threadIdx.x;
-  if (c < s) {
-    for (int i = 0; i < s; ++i) {           // forward: L y = b
-      double v = B[IDX(i, c)];
-      for (int k = 0; k < i; ++k) v = fma(-L[IDX(i, k)], X[IDX(k, c)], v);
-      X[IDX(i, c)] = v / L[IDX(i, i)];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double dinv = (lane < s) ? 1.0 / L[IDX(lane, lane)] : 0.0;
+  for (int c = warp; c < s; c += nw) {
+    double v = (lane < s) ? B[IDX(lane, c)] : 0.0;
+    for (int i = 0; i < s; ++i) {                      // forward: L y = b
+      const double yi = __shfl_sync(0xffffffffu, v * dinv, i);
+      if (lane > i && lane < s) v = fma(-L[IDX(lane, i)], yi, v);
+      if (lane == i) v = yi;
     }
-    for (int i = s - 1; i >= 0; --i) {      // backward: L^T x = y
-      double v = X[IDX(i, c)];
-      for (int k = i + 1; k < s; ++k) v = fma(-L[IDX(k, i)], X[IDX(k, c)], v);
-      X[IDX(i, c)] = v / L[IDX(i, i)];
+    for (int i = s - 1; i >= 0; --i) {                 // backward: L^T x = y
+      const double xi = __shfl_sync(0xffffffffu, v * dinv, i);
+      if (lane < i) v = fma(-L[IDX(i, lane)], xi, v);
+      if (lane == i) v = xi;
     }
+    if (lane < s) X[IDX(lane, c)] = v;
   }
   __syncthreads();
 }
@@ -509,20 +534,24 @@ __global__ void __launch_bounds__(kST) small_bcg_2_k(Ctrl* c, double* history, u
   if (!sm_all_finite(S.A, s, &S.flag)) { stop(c, BK_NONFINITE); return; }
   sm_matmul(S.D, S.C, false, S.B, s);          // sigma_new = gamma sigma
   __syncthreads();
-  if (threadIdx.x < s) {
-    const int i = threadIdx.x;
-    double v = 0.0;
-    if (reo) {
-      for (int r = 0; r < s; ++r) v = fma(S.D[IDX(r, i)], S.D[IDX(r, i)], v);
-    } else {
-      for (int r = 0; r < s; ++r) {
-        double t = 0.0;
-        for (int q = 0; q < s; ++q) t = fma(S.A[IDX(r, q)], S.D[IDX(q, i)], t);
-        v = fma(S.D[IDX(r, i)], t, v);
+  if (!reo) {
+    sm_matmul(S.F, S.A, false, S.D, s);        // rho sigma_new
+    __syncthreads();
+  }
+  {
+    // column norms ||R-bar sigma e_i||^2 = (sigma^T rho sigma)_ii (sigma_i^T sigma_i after a
+    // re-orthonormalisation): one warp per column, a shuffle sum over the rows
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = threadIdx.x >> 5; i < s; i += nw) {
+      double v = 0.0;
+      if (lane < s) v = S.D[IDX(lane, i)] * (reo ? S.D[IDX(lane, i)] : S.F[IDX(lane, i)]);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (lane == 0) {
+        const double n0 = c->n0[i];
+        c->relres[i] = (!isfinite(n0) || isnan(v)) ? NAN : (n0 > 0.0 ? sqrt(fmax(v, 0.0)) / n0 : 0.0);
       }
     }
-    const double n0 = c->n0[i];
-    c->relres[i] = (!isfinite(n0) || isnan(v)) ? NAN : (n0 > 0.0 ? sqrt(fmax(v, 0.0)) / n0 : 0.0);
   }
   __syncthreads();
   __shared__ int s_conv;
