@@ -277,7 +277,7 @@ def _bbicg_battery_passes(fn):
 
 
 BBICG_MUTATIONS = [
-    ("X += omega * (Th @ sigma_new)", "X += omega * (Th @ sigma)"),      # reading c9 reversed
+    ("X += omega * (Th @ sigma_new)", "X += omega * (Th @ sigma)"),      # the printed sigma^k
     ("X += Ph @ (lam @ sigma)", "X += Ph @ (sigma @ lam)"),
     ("beta = -lu_solve", "beta = lu_solve"),
     ("Ph = Rh + (Ph - omega * Qh) @ beta", "Ph = Rh + (Ph + omega * Qh) @ beta"),  # the derivation's "+omega"
