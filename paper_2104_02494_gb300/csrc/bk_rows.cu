@@ -449,25 +449,25 @@ cudaError_t ir_colnorms(const Launch& L, int64_t n, int s, const double* R, doub
 }
 
 // R32 = R / norm (column scaling, norm = sqrt(norms2), zero columns left unscaled).
+// Element-wise over the row-major n x s block with a block size and grid stride
+// that are multiples of s, so that every thread stays on one column and forms
+// its scale factor once (FP64 square roots and divisions per element would make
+// these passes FP64-bound).
 __global__ void ir_to_fp32_kernel(int64_t total, int s, const double* __restrict__ R,
                                   const double* __restrict__ norms2, float* __restrict__ R32) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double n2 = norms2[i % s];
-    const double sc = n2 > 0.0 ? 1.0 / sqrt(n2) : 1.0;
+  const double n2 = norms2[threadIdx.x % s];
+  const double sc = n2 > 0.0 ? 1.0 / sqrt(n2) : 1.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
     R32[i] = (float)(R[i] * sc);
-  }
 }
 
-// X += D32 * norm (undo the column scaling).
+// X += D32 * norm (undo the column scaling), same launch shape.
 __global__ void ir_accumulate_kernel(int64_t total, int s, const float* __restrict__ D32,
                                      const double* __restrict__ norms2, double* __restrict__ X) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double n2 = norms2[i % s];
-    const double sc = n2 > 0.0 ? sqrt(n2) : 1.0;
+  const double n2 = norms2[threadIdx.x % s];
+  const double sc = n2 > 0.0 ? sqrt(n2) : 1.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
     X[i] += (double)D32[i] * sc;
-  }
 }
 
 static int elem_grid2(const Launch& L, int64_t count) {
@@ -477,17 +477,29 @@ static int elem_grid2(const Launch& L, int64_t count) {
   return (int)(g < 1 ? 1 : g);
 }
 
+// Block size (256 / s) * s: a multiple of s, so the column of element i is threadIdx.x % s.
+static int col_block(int s) { return (256 / s) * s; }
+
+static int col_grid(const Launch& L, int64_t total, int bs) {
+  int64_t g = (total + bs - 1) / bs;
+  const int64_t cap = (int64_t)L.sms * 8;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
 cudaError_t ir_to_fp32(const Launch& L, int64_t n, int s, const double* R, const double* norms2,
                        float* R32) {
   const int64_t total = n * s;
-  ir_to_fp32_kernel<<<elem_grid2(L, total), 256, 0, L.stream>>>(total, s, R, norms2, R32);
+  const int bs = col_block(s);
+  ir_to_fp32_kernel<<<col_grid(L, total, bs), bs, 0, L.stream>>>(total, s, R, norms2, R32);
   return cudaGetLastError();
 }
 
 cudaError_t ir_accumulate(const Launch& L, int64_t n, int s, const float* D32, const double* norms2,
                           double* X) {
   const int64_t total = n * s;
-  ir_accumulate_kernel<<<elem_grid2(L, total), 256, 0, L.stream>>>(total, s, D32, norms2, X);
+  const int bs = col_block(s);
+  ir_accumulate_kernel<<<col_grid(L, total, bs), bs, 0, L.stream>>>(total, s, D32, norms2, X);
   return cudaGetLastError();
 }
 
