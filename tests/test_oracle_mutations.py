@@ -271,6 +271,15 @@ def _bbicg_battery_passes(fn):
             true = np.linalg.norm(B - Ad @ r.X, axis=0) / np.linalg.norm(B, axis=0)
             if true.max() > 1e-9 or np.abs(true - r.relres).max() > 1e-9:
                 return False
+        # the normalised iteration commutes with every change of basis C of the
+        # right-hand sides: X_k(B C) = X_k(B) C
+        C = np.eye(3) * 2.0 + 0.5 * np.random.default_rng(7).standard_normal((3, 3))
+        a = fn(A, B, tol=0.0, maxit=6, eta=math.inf, record_iterates=6)
+        c = fn(A, B @ C, tol=0.0, maxit=6, eta=math.inf, record_iterates=6)
+        for k in range(6):
+            ref = a.iterates[k] @ C
+            if np.abs(c.iterates[k] - ref).max() > 1e-10 * np.abs(ref).max():
+                return False
         return True
     except Exception:
         return False
@@ -282,6 +291,9 @@ BBICG_MUTATIONS = [
     ("beta = -lu_solve", "beta = lu_solve"),
     ("Ph = Rh + (Ph - omega * Qh) @ beta", "Ph = Rh + (Ph + omega * Qh) @ beta"),  # the derivation's "+omega"
     ("omega = float(np.sum(Uh * Sh)) / uu", "omega = float(np.sum(Uh * Sh)) / uu ** 0.5"),
+    ("gram(R0s, Uh, sym=False)", "gram(Uh, R0s, sym=False)"),   # transposed shadow Gram in beta
+    ("gram(R0s, Rh, sym=False)", "gram(Rh, R0s, sym=False)"),   # transposed shadow Gram in lambda
+    ("sigma_new = gamma @ sigma", "sigma_new = sigma @ gamma"),
 ]
 
 
@@ -303,7 +315,21 @@ def _bgmres_battery_passes(fn):
         if not r.converged:
             return False
         true = np.linalg.norm(B - Ad @ r.X, axis=0) / np.linalg.norm(B, axis=0)
-        return true.max() <= 1e-9 and np.abs(true - r.relres).max() <= 1e-9
+        if true.max() > 1e-9 or np.abs(true - r.relres).max() > 1e-9:
+            return False
+        # X_k - X_0 is the column-wise least-squares solution over K_k(A, R0)
+        X0 = 0.1 * W.normal_block(A.n, 3, 2)
+        R0 = B - Ad @ X0
+        blocks = [R0]
+        for k in range(1, 5):
+            V, _ = np.linalg.qr(np.hstack(blocks))
+            ref = X0 + V @ np.linalg.lstsq(Ad @ V, R0, rcond=None)[0]
+            for ortho in ("mgs", "cgs2"):
+                got = fn(A, B, X0=X0, tol=0.0, restart=8, maxit=k, ortho=ortho).X
+                if np.abs(got - ref).max() > 1e-9 * np.abs(ref).max():
+                    return False
+            blocks.append(Ad @ blocks[-1])
+        return True
     except Exception:
         return False
 
@@ -313,6 +339,8 @@ BGMRES_MUTATIONS = [
     ("W = W - V[j] @ hj", "W = W + V[j] @ hj"),
     ("sig[k * s:(k + 2) * s] = Qk.T @ pair", "sig[k * s:(k + 2) * s] = Qk @ pair"),
     ("for j in range(l + 1, k_done):", "for j in range(l + 2, k_done):"),
+    ("h[:(k + 1) * s] += hp", "h[:(k + 1) * s] = hp"),          # CGS2 drops the first pass's coefficients
+    ("for j in range(k):", "for j in range(k - 1):"),            # one earlier Givens factor not applied
 ]
 
 
