@@ -40,11 +40,12 @@ class IRResult:
 
 
 def bcg_ir(A, B: np.ndarray, tol: float = 1e-10, inner_tol: float = 1e-5, max_outer: int = 20,
-           inner_maxit: int = 5000, eta: float = math.inf, Minv=None) -> IRResult:
-    """Refinement loop above; ``Minv`` (optional, see ``bcg``) preconditions the inner solve."""
+           inner_maxit: int = 5000, eta: float = math.inf, Minv=None, X0=None) -> IRResult:
+    """Refinement loop above from X0 (zero when not given); ``Minv`` (optional, see
+    ``bcg``) preconditions the inner solve."""
     B = np.asarray(B, dtype=np.float64)
     n, s = B.shape
-    X = np.zeros((n, s))
+    X = np.zeros((n, s)) if X0 is None else np.array(X0, dtype=np.float64, copy=True)
     nb = col_norms(B)
     nb_safe = np.where(nb > 0, nb, 1.0)
     out = IRResult(X, 0)

@@ -247,6 +247,24 @@ def test_ir_reaches_fp64_accuracy():
     assert true32.max() > 1e-9
 
 
+def test_ir_from_an_initial_guess():
+    """Refinement from X0: the first outer step is X0 plus the zero-start step on
+    A D = B - A X0 (exactly: the same FP64 residual, the same inner solve), and
+    the loop still reaches 1e-10 relative to ||B||."""
+    N = 7
+    k = np.exp(1.5 * np.random.default_rng(2).standard_normal(N ** 3))
+    A = W.diff3d7_var(N, N, N, k)
+    B = W.normal_block(A.n, 4, 3)
+    X0 = 0.3 * W.normal_block(A.n, 4, 4)
+    R0 = B - oracle.spmm(A, X0)
+    a = oracle.bcg_ir(A, B, tol=0.0, max_outer=1, inner_maxit=6, X0=X0)
+    b = oracle.bcg_ir(A, R0, tol=0.0, max_outer=1, inner_maxit=6)
+    assert np.array_equal(a.X, X0 + b.X)
+    r = oracle.bcg_ir(A, B, tol=1e-10, X0=X0)
+    assert r.converged
+    assert (oracle.col_norms(B - oracle.spmm(A, r.X)) / oracle.col_norms(B)).max() <= 1e-10
+
+
 def test_adjoint_dense_matches_central_differences():
     nx = ny = 6; s = 3
     g = np.random.default_rng(3)
