@@ -351,3 +351,233 @@ def test_unmutated_bgmres_passes_battery():
 @pytest.mark.parametrize("old,new", BGMRES_MUTATIONS)
 def test_bgmres_mutation_is_caught(old, new):
     assert not _bgmres_battery_passes(_mutant("oracle.bgmres", "bgmres", old, new))
+
+
+# ---------------------------------------------------------------------------
+# TSQR tree (Ch. 7.3): Y and sigma of the tree equal one Householder QR.
+
+def _tsqr_battery_passes(fn):
+    try:
+        X = np.random.default_rng(3).standard_normal((300, 6))
+        Y1, s1 = sys.modules["oracle.blockops"].householder_qr(X)
+        for parts, fanin in ((2, 2), (7, 2), (9, 3)):
+            Y, sig = fn(X, parts, fanin)
+            if np.abs(sig - s1).max() > 1e-12 * np.abs(s1).max() or np.abs(Y - Y1).max() > 1e-12:
+                return False
+        return True
+    except Exception:
+        return False
+
+
+TSQR_MUTATIONS = [
+    ("_reduce", "T = node_Q[gi] @ up[gi]", "T = node_Q[gi]"),                 # scatter factor not carried down
+    ("_reduce", "out.append(T[j * s:(j + 1) * s])", "out.append(T[:s])"),
+    ("_reduce", "Qg, Rg = householder_qr(np.vstack(g))", "Qg, Rg = householder_qr(np.vstack(g[::-1]))"),
+    ("tsqr", "Qs[i] @ Y_parts[i]", "Qs[i] @ Y_parts[i].T"),
+]
+
+
+def _tsqr_with(fname, old, new):
+    mod = sys.modules["oracle.tsqr"]
+    m = _mutant("oracle.tsqr", fname, old, new)
+    if fname == "tsqr":
+        return m
+    saved = mod._reduce
+    def run(X, parts, fanin):
+        mod._reduce = m
+        try:
+            return mod.tsqr(X, parts, fanin)
+        finally:
+            mod._reduce = saved
+    return run
+
+
+def test_unmutated_tsqr_passes_battery():
+    assert _tsqr_battery_passes(sys.modules["oracle.tsqr"].tsqr)
+
+
+@pytest.mark.parametrize("fname,old,new", TSQR_MUTATIONS)
+def test_tsqr_mutation_is_caught(fname, old, new):
+    assert not _tsqr_battery_passes(_tsqr_with(fname, old, new))
+
+
+# ---------------------------------------------------------------------------
+# kappa_D (Ch. 4.3): closed forms and invariance under diagonal scaling.
+
+def _kappa_battery_passes(fn):
+    try:
+        if abs(fn(np.diag([1.0, 7.0, 1e-6])) - 1.0) > 1e-12:
+            return False
+        for c in (0.3, -0.9):
+            M = np.array([[1.0, c], [c, 1.0]])
+            D = np.diag([3.0, 0.01])
+            ref = (1 + abs(c)) / (1 - abs(c))
+            for A in (M, D @ M @ D):
+                if abs(fn(A) - ref) > 1e-12 * ref:
+                    return False
+        # 3 x 3: the eigenvalues of the unit-diagonal matrix by LAPACK
+        C = np.array([[1.0, 0.5, 0.2], [0.5, 1.0, -0.3], [0.2, -0.3, 1.0]])
+        ev = np.linalg.eigvalsh(C)
+        D = np.diag([2.0, 0.5, 7.0])
+        return abs(fn(D @ C @ D) - ev[-1] / ev[0]) <= 1e-12 * ev[-1] / ev[0]
+    except Exception:
+        return False
+
+
+KAPPA_MUTATIONS = [
+    ("r = 1.0 / np.sqrt(d)", "r = 1.0 / d"),
+    ("M = alpha * r[:, None] * r[None, :]", "M = alpha * r[:, None] * r[:, None]"),
+    ("return float(ev[-1] / ev[0])", "return float(ev[-1] / ev[1])"),
+]
+
+
+def test_unmutated_kappa_passes_battery():
+    assert _kappa_battery_passes(sys.modules["oracle.blockops"].kappa_d)
+
+
+@pytest.mark.parametrize("old,new", KAPPA_MUTATIONS)
+def test_kappa_mutation_is_caught(old, new):
+    assert not _kappa_battery_passes(_mutant("oracle.blockops", "kappa_d", old, new))
+
+
+# ---------------------------------------------------------------------------
+# Iterative refinement: reaches 1e-10 in a few outer steps, from zero and from X0.
+
+def _ir_battery_passes(fn):
+    try:
+        N = 6
+        k = np.exp(1.0 * np.random.default_rng(1).standard_normal(N ** 3))
+        A = W.diff3d7_var(N, N, N, k)
+        B = W.normal_block(A.n, 3, 0)
+        for X0 in (None, 0.3 * W.normal_block(A.n, 3, 5)):
+            r = fn(A, B, tol=1e-10, inner_tol=1e-5, max_outer=6, X0=X0)
+            true = np.linalg.norm(B - A.to_dense() @ r.X, axis=0) / np.linalg.norm(B, axis=0)
+            if not r.converged or true.max() > 1e-10 or np.abs(true - r.relres).max() > 1e-12:
+                return False
+        # the first outer step from X0 is X0 plus the zero-start step on B - A X0
+        X0 = 0.3 * W.normal_block(A.n, 3, 5)
+        a = fn(A, B, tol=0.0, max_outer=1, inner_maxit=4, X0=X0)
+        b = fn(A, B - A.to_dense() @ X0, tol=0.0, max_outer=1, inner_maxit=4)
+        return np.abs(a.X - (X0 + b.X)).max() <= 1e-12 * np.abs(a.X).max()
+    except Exception:
+        return False
+
+
+IR_MUTATIONS = [
+    ("X += inner.X.astype(np.float64) * scale[None, :]", "X += inner.X.astype(np.float64)"),
+    ("Rs = (R / scale[None, :])", "Rs = (R * scale[None, :])"),
+    ("out.relres = np.where(nb > 0, nr / nb_safe, 0.0)", "out.relres = np.where(nb > 0, nr / nb_safe ** 2, 0.0)"),
+    ("X = np.zeros((n, s)) if X0 is None else", "X = np.zeros((n, s)) if True else"),
+]
+
+
+def test_unmutated_ir_passes_battery():
+    assert _ir_battery_passes(sys.modules["oracle.ir"].bcg_ir)
+
+
+@pytest.mark.parametrize("old,new", IR_MUTATIONS)
+def test_ir_mutation_is_caught(old, new):
+    assert not _ir_battery_passes(_mutant("oracle.ir", "bcg_ir", old, new))
+
+
+# ---------------------------------------------------------------------------
+# Adjoint: every edge's theta-gradient against central differences on a 3 x 3
+# grid, the CSR scatter against the dense dL/dA, and the dense adjoint on a
+# non-symmetric matrix (where A^T != A) against central differences.
+
+def _edge_fd_battery_passes(grad_fn, scatter_fn):
+    try:
+        nx = ny = 3; s = 2
+        g = np.random.default_rng(8)
+        thx = 0.4 * g.standard_normal((ny, nx + 1)); thy = 0.4 * g.standard_normal((ny + 1, nx))
+        B = g.standard_normal((nx * ny, s)); Xt = g.standard_normal((nx * ny, s))
+        oracle_mod = sys.modules["oracle.adjoint"]
+
+        def loss(tx, ty):
+            return oracle_mod.dense_adjoint(W.edge2d5(nx, ny, np.exp(tx), np.exp(ty)).to_dense(), B, Xt)
+
+        L, X, Lam, dA = loss(thx, thy)
+        gx, gy = grad_fn(nx, ny, np.exp(thx), np.exp(thy), Lam, X)
+        h = 1e-6
+        for arr, gr, is_x in ((thx, gx, True), (thy, gy, False)):
+            for idx in np.ndindex(arr.shape):
+                p = arr.copy(); p[idx] += h
+                m = arr.copy(); m[idx] -= h
+                fd = ((loss(p, thy) if is_x else loss(thx, p))[0]
+                      - (loss(m, thy) if is_x else loss(thx, m))[0]) / (2 * h)
+                if abs(gr[idx] - fd) > 1e-6 * abs(fd) + 1e-9:
+                    return False
+        Acsr = W.edge2d5(nx, ny, np.exp(thx), np.exp(thy))
+        rows = np.repeat(np.arange(Acsr.n), np.diff(Acsr.row_ptr))
+        return np.allclose(scatter_fn(Acsr, Lam, X), dA[rows, Acsr.col], rtol=1e-13, atol=1e-13)
+    except Exception:
+        return False
+
+
+def _dense_adjoint_nonsym_passes(fn):
+    try:
+        A = W.const7(3, 3, 2, W.convdiff3d7_coeffs(3, pe=20.0)).to_dense()
+        g = np.random.default_rng(2)
+        B = g.standard_normal((A.shape[0], 2)); Xt = g.standard_normal(B.shape)
+        L, X, Lam, dA = fn(A, B, Xt)
+        h = 1e-6
+        for (i, j) in ((0, 0), (0, 1), (1, 0), (5, 4), (4, 5)):
+            p = A.copy(); p[i, j] += h
+            m = A.copy(); m[i, j] -= h
+            fd = (fn(p, B, Xt)[0] - fn(m, B, Xt)[0]) / (2 * h)
+            if abs(dA[i, j] - fd) > 1e-6 * abs(fd) + 1e-9:
+                return False
+        for idx in ((0, 0), (7, 1)):
+            p = B.copy(); p[idx] += h
+            m = B.copy(); m[idx] -= h
+            fd = (fn(A, p, Xt)[0] - fn(A, m, Xt)[0]) / (2 * h)
+            if abs(Lam[idx] - fd) > 1e-6 * abs(fd) + 1e-9:
+                return False
+        return True
+    except Exception:
+        return False
+
+
+EDGE_GRAD_MUTATIONS = [
+    ("gx[:, nx] = -ax[:, nx] * np.sum(L3[:, nx - 1, :] * X3[:, nx - 1, :], axis=1)",
+     "gx[:, nx] = -ax[:, nx] * np.sum(L3[:, nx - 2, :] * X3[:, nx - 1, :], axis=1)"),
+    ("gy[ny, :] = -ay[ny, :] * np.sum(L3[ny - 1, :, :] * X3[ny - 1, :, :], axis=1)",
+     "gy[ny, :] = -ay[ny, :] * np.sum(L3[ny - 1, :, :] * X3[ny - 2, :, :], axis=1)"),
+    ("dl = L3[:, 1:, :] - L3[:, :-1, :]", "dl = L3[:, 1:, :] + L3[:, :-1, :]"),
+    ("gy[1:ny, :] = -ay[1:ny, :]", "gy[1:ny, :] = ay[1:ny, :]"),
+    ("gy[0, :] = -ay[0, :] * np.sum(L3[0, :, :] * X3[0, :, :], axis=1)",
+     "gy[0, :] = -ay[0, :] * np.sum(L3[0, :, :] * X3[1, :, :], axis=1)"),
+]
+SCATTER_MUTATIONS = [
+    ("Lam[rows], X[cols]", "Lam[cols], X[rows]"),
+    ("return -np.einsum", "return np.einsum"),
+]
+DENSE_ADJOINT_MUTATIONS = [
+    ("Lam = np.linalg.solve(Adense.T, G)", "Lam = np.linalg.solve(Adense, G)"),
+    ("dA = -Lam @ X.T", "dA = -X @ Lam.T"),
+]
+
+
+def test_unmutated_adjoint_passes_batteries():
+    mod = sys.modules["oracle.adjoint"]
+    assert _edge_fd_battery_passes(mod.edge_theta_grad, mod.adjoint_scatter)
+    assert _dense_adjoint_nonsym_passes(mod.dense_adjoint)
+
+
+@pytest.mark.parametrize("old,new", EDGE_GRAD_MUTATIONS)
+def test_edge_grad_mutation_is_caught(old, new):
+    mod = sys.modules["oracle.adjoint"]
+    m = _mutant("oracle.adjoint", "edge_theta_grad", old, new)
+    assert not _edge_fd_battery_passes(m, mod.adjoint_scatter)
+
+
+@pytest.mark.parametrize("old,new", SCATTER_MUTATIONS)
+def test_scatter_mutation_is_caught(old, new):
+    mod = sys.modules["oracle.adjoint"]
+    m = _mutant("oracle.adjoint", "adjoint_scatter", old, new)
+    assert not _edge_fd_battery_passes(mod.edge_theta_grad, m)
+
+
+@pytest.mark.parametrize("old,new", DENSE_ADJOINT_MUTATIONS)
+def test_dense_adjoint_mutation_is_caught(old, new):
+    assert not _dense_adjoint_nonsym_passes(_mutant("oracle.adjoint", "dense_adjoint", old, new))
