@@ -23,7 +23,10 @@ solves, closed-form eigenvalues, LAPACK QR after sign fixing, Galerkin and
 A-conjugacy invariants, block CG at s = 1 against textbook scalar CG (and preconditioned CG),
 the energy minimisation over the preconditioned block Krylov space, finite
 termination in ceil(n/s) steps, the Chebyshev error bound, BGMRes monotone
-residuals, finite differences for the adjoint.  Functions without such a pin
+residuals and its column-wise least-squares characterisation, the commutation
+of the block methods with a change of basis of the right-hand sides,
+rank-deficient right-hand sides, finite differences for the adjoint, and
+planted one-token mistakes that every battery must reject.  Functions without such a pin
 are marked "parity unpinned" in their docstring (none at present).
 """
 from .blockops import (spmm, gram, householder_qr, normalizer, kappa_d, chol_solve,
