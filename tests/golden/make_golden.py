@@ -1,8 +1,9 @@
-"""Write the stored expected values of tests/golden/ from the oracle alone.
+"""Write the oracle-derived expected values of tests/golden/.
 
-The thesis prints no small worked example whose numbers can be reproduced here
-(its tables are measured on SuiteSparse matrices with SSOR / ILU
-preconditioners), so the stored values are the oracle's own, written by this
+The thesis's one small worked example (Ch. 2, Ex. "nonconverging_gmres") is
+stored by hand in gmres_cyclic_shift.json with its citation; its numeric tables
+are measured on SuiteSparse matrices with SSOR / ILU preconditioners, so the
+other stored values are the oracle's own, written by this
 script, which imports nothing but ``oracle`` and ``workloads``:
 
   bcg_poisson2d_12x11_s3.json  Alg. "bcgaro" (Ch. 4.3), 12 x 11 Dirichlet Poisson

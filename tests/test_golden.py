@@ -1,5 +1,9 @@
-"""The stored expected values of tests/golden/ (written by tests/golden/make_golden.py from the
-oracle alone): the oracle still reproduces them (CPU), and the GPU solvers match them (-m gpu).
+"""The stored expected values of tests/golden/.
+
+bcg_poisson2d_12x11_s3.json is written by tests/golden/make_golden.py from the oracle alone:
+the oracle still reproduces it (CPU), and the GPU solvers match it (-m gpu).
+gmres_cyclic_shift.json is the thesis's own worked example (Ch. 2, Ex. "nonconverging_gmres"):
+GMRes on the cyclic shift with b = e_1 cannot improve on x = 0 before n steps and is exact at n.
 
 Residual histories are compared relatively (1e-9 on the CPU, where only the BLAS build may
 differ; 1e-8 on the GPU, whose Gram summation order differs), decisions and iteration
@@ -69,4 +73,68 @@ def test_gpu_matches_golden(key, fn, eta, jacobi, var):
         assert np.abs(X.cpu().numpy()[0] - ref_row).max() <= 1e-9 * np.abs(ref_row).max()
         if P is not None:
             P.close()
+        op.close()
+
+
+CYCLIC = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "gmres_cyclic_shift.json")))
+
+
+def _cyclic(n, transposed):
+    """The example's matrix: the printed form (superdiagonal and bottom-left corner) or its
+    transpose (subdiagonal and top-right corner, the form the example's text describes)."""
+    rows = list(range(n - 1)) + [n - 1]
+    cols = list(range(1, n)) + [0]
+    if transposed:
+        rows, cols = cols, rows
+    return W.csr_from_triples(n, rows, cols, np.ones(n))
+
+
+@pytest.mark.parametrize("n", CYCLIC["n"])
+@pytest.mark.parametrize("transposed", [False, True])
+@pytest.mark.parametrize("ortho", ["mgs", "cgs2", "localized"])
+def test_oracle_gmres_stalls_on_the_cyclic_shift(n, transposed, ortho):
+    A = _cyclic(n, transposed)
+    b = np.zeros((n, 1)); b[0, 0] = 1.0
+    for k in range(1, n):
+        r = oracle.bgmres(A, b, tol=0.0, restart=n, maxit=k, ortho=ortho, tile_rows=n)
+        assert np.abs(r.X).max() <= 1e-14, (k, np.abs(r.X).max())
+        assert abs(r.history[-1] - CYCLIC["relative_residual_before_n"]) <= 1e-14
+    r = oracle.bgmres(A, b, tol=0.0, restart=n, maxit=n, ortho=ortho, tile_rows=n)
+    sol = np.zeros(n); sol[n - 1 if transposed else 1] = 1.0        # e_n resp. e_2
+    assert np.abs(r.X[:, 0] - sol).max() <= 1e-13
+    assert r.history[-1] <= 1e-13
+
+
+@pytest.mark.parametrize("n", CYCLIC["n"])
+def test_oracle_bbicgstab_breaks_down_on_the_cyclic_shift(n):
+    """BiCGStab's first coefficient divides by r0^T A r0 = A[0][0] = 0: a breakdown, X untouched."""
+    A = _cyclic(n, False)
+    b = np.zeros((n, 1)); b[0, 0] = 1.0
+    for eta in (0.0, math.inf):
+        r = oracle.bbicgstab(A, b, tol=1e-12, maxit=2 * n, eta=eta)
+        assert r.status == "breakdown" and r.iters == 0 and np.all(r.X == 0.0)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("ortho", ["mgs", "cgs2", "localized"])
+def test_gpu_gmres_stalls_on_the_cyclic_shift(ortho):
+    import torch
+    from paper_2104_02494_gb300 import build
+    from paper_2104_02494_gb300.api import Handle
+    build()
+    n = CYCLIC["n"][1]
+    A = _cyclic(n, False)
+    b = np.zeros((n, 1)); b[0, 0] = 1.0
+    dv = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    with Handle(0) as h:
+        op = h.op_csr(dv(A.row_ptr), dv(A.col), dv(A.val))
+        for k in (1, n // 2, n - 1):
+            X, info = h.solve("bgmres", op, dv(b), tol=0.0, maxit=k, restart=n, ortho=ortho)
+            assert np.abs(X.cpu().numpy()).max() <= 1e-14 and abs(info.relres_max - 1.0) <= 1e-14
+        X, info = h.solve("bgmres", op, dv(b), tol=1e-12, maxit=n, restart=n, ortho=ortho)
+        sol = np.zeros(n); sol[1] = 1.0
+        assert info.converged and info.iters == n
+        assert np.abs(X.cpu().numpy()[:, 0] - sol).max() <= 1e-13
+        X, info = h.solve("bbicgstab", op, dv(b), tol=1e-12, maxit=2 * n, eta=math.inf)
+        assert info.status == 5 and np.all(X.cpu().numpy() == 0.0)
         op.close()
