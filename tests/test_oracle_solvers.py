@@ -265,6 +265,43 @@ def test_ir_from_an_initial_guess():
     assert (oracle.col_norms(B - oracle.spmm(A, r.X)) / oracle.col_norms(B)).max() <= 1e-10
 
 
+def _lap2d_eigvecs(nx, ny, modes):
+    """Closed-form eigenpairs of the unscaled 5-point Dirichlet Laplacian (rows x fastest):
+    v(x, y) = sin(j pi (x+1)/(nx+1)) sin(k pi (y+1)/(ny+1)),
+    lambda = 4 - 2 cos(j pi/(nx+1)) - 2 cos(k pi/(ny+1))."""
+    x = np.arange(nx); y = np.arange(ny)
+    V, lam = [], []
+    for j, k in modes:
+        v = np.outer(np.sin(k * np.pi * (y + 1) / (ny + 1)), np.sin(j * np.pi * (x + 1) / (nx + 1)))
+        V.append(v.ravel())
+        lam.append(4 - 2 * np.cos(j * np.pi / (nx + 1)) - 2 * np.cos(k * np.pi / (ny + 1)))
+    return np.array(V).T, np.array(lam)
+
+
+def test_one_step_when_r0_spans_an_invariant_subspace():
+    """Ch. 2 (after Thm. "cg_convergence"): a residual of grade 1 (an eigenvector) is solved in one
+    iteration; in the block methods, R0 = V C with V s eigenvectors spans an A-invariant subspace,
+    so X^1 = A^{-1} B = V diag(lambda)^{-1} C for BCG, 1R-BCG and BGMRes (every orthonormalisation)."""
+    nx, ny = 7, 6
+    A = W.lap2d5(nx, ny)
+    V, lam = _lap2d_eigvecs(nx, ny, [(1, 1), (2, 3), (5, 2)])
+    assert np.abs(A.to_dense() @ V - V * lam).max() <= 1e-13
+    C = np.eye(3) * 2.0 + 0.5 * np.random.default_rng(3).standard_normal((3, 3))
+    B = V @ C
+    Xs = (V / lam) @ C
+    for eta in (0.0, math.inf):
+        for r in (oracle.bcg(A, B, tol=1e-12, maxit=10, eta=eta),
+                  oracle.bcg_1r(A, B, tol=1e-12, maxit=10, eta=eta)):
+            assert r.converged and r.iters == 1, (eta, r.iters)
+            assert np.abs(r.X - Xs).max() <= 1e-12 * np.abs(Xs).max()
+    for ortho in ("mgs", "cgs2", "localized"):
+        r = oracle.bgmres(A, B, tol=1e-12, restart=10, maxit=10, ortho=ortho, tile_rows=16)
+        assert r.converged and r.iters == 1, (ortho, r.iters)
+        assert np.abs(r.X - Xs).max() <= 1e-12 * np.abs(Xs).max()
+    x, its, _, _ = oracle.scalar_cg(A, V[:, 1], tol=1e-12, maxit=10)
+    assert its == 1 and np.abs(x - V[:, 1] / lam[1]).max() <= 1e-12
+
+
 def test_adjoint_dense_matches_central_differences():
     nx = ny = 6; s = 3
     g = np.random.default_rng(3)
