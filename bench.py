@@ -20,6 +20,10 @@ rho Gram), s x s step, direction update.
   cpu_baseline  the FP64 oracle (numpy/scipy) on the host cores, a bounded
              number of iterations of the same workload.
 
+--impl reference times the oracle alone as the reference arm: W warm-up and
+exactly K timed BCG iterations of the same workload on the host cores (the K
+timed as the difference of a (W + K)- and a W-iteration oracle solve).
+
 Every n x s block is 134 MB > 129 MB L2, so no L2 flush is needed between
 timed iterations ("inputs larger than L2").
 """
