@@ -113,28 +113,3 @@ def test_oracle_bbicgstab_breaks_down_on_the_cyclic_shift(n):
     for eta in (0.0, math.inf):
         r = oracle.bbicgstab(A, b, tol=1e-12, maxit=2 * n, eta=eta)
         assert r.status == "breakdown" and r.iters == 0 and np.all(r.X == 0.0)
-
-
-@pytest.mark.gpu
-@pytest.mark.parametrize("ortho", ["mgs", "cgs2", "localized"])
-def test_gpu_gmres_stalls_on_the_cyclic_shift(ortho):
-    import torch
-    from paper_2104_02494_gb300 import build
-    from paper_2104_02494_gb300.api import Handle
-    build()
-    n = CYCLIC["n"][1]
-    A = _cyclic(n, False)
-    b = np.zeros((n, 1)); b[0, 0] = 1.0
-    dv = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    with Handle(0) as h:
-        op = h.op_csr(dv(A.row_ptr), dv(A.col), dv(A.val))
-        for k in (1, n // 2, n - 1):
-            X, info = h.solve("bgmres", op, dv(b), tol=0.0, maxit=k, restart=n, ortho=ortho)
-            assert np.abs(X.cpu().numpy()).max() <= 1e-14 and abs(info.relres_max - 1.0) <= 1e-14
-        X, info = h.solve("bgmres", op, dv(b), tol=1e-12, maxit=n, restart=n, ortho=ortho)
-        sol = np.zeros(n); sol[1] = 1.0
-        assert info.converged and info.iters == n
-        assert np.abs(X.cpu().numpy()[:, 0] - sol).max() <= 1e-13
-        X, info = h.solve("bbicgstab", op, dv(b), tol=1e-12, maxit=2 * n, eta=math.inf)
-        assert info.status == 5 and np.all(X.cpu().numpy() == 0.0)
-        op.close()
