@@ -17,6 +17,9 @@ import pytest
 import oracle  # noqa: F401  (loads the submodules)
 import workloads as W
 
+# planted mistakes are expected to overflow or divide by zero on the way to failing a pin
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
 
 def _mutant(modname, fname, old, new):
     mod = sys.modules[modname]
