@@ -302,6 +302,28 @@ def test_one_step_when_r0_spans_an_invariant_subspace():
     assert its == 1 and np.abs(x - V[:, 1] / lam[1]).max() <= 1e-12
 
 
+@pytest.mark.parametrize("jacobi", [False, True])
+def test_scalar_cg_reference_is_the_krylov_energy_minimiser(jacobi):
+    """The textbook (P)CG used as a reference by other pins, pinned on its own: x_k minimises
+    ||x - x*||_A over x0 + K_k(M^{-1}A, M^{-1}r0), built and solved densely (Ch. 2)."""
+    N = 5
+    k = np.exp(1.2 * np.random.default_rng(6).standard_normal(N ** 3))
+    A = W.diff3d7_var(N, N, N, k)
+    Ad = A.to_dense()
+    w = 1.0 / np.diag(Ad) if jacobi else np.ones(A.n)
+    b = W.normal_block(A.n, 1, 2)[:, 0]
+    x0 = 0.1 * W.normal_block(A.n, 1, 3)[:, 0]
+    x, its, hist, xs = oracle.scalar_cg(A, b, x0=x0, tol=0.0, maxit=6, record_iterates=6,
+                                        minv=w if jacobi else None)
+    r0 = b - Ad @ x0
+    blocks = [w * r0]
+    for kk in range(1, 7):
+        V, _ = np.linalg.qr(np.column_stack(blocks))
+        ref = x0 + V @ np.linalg.solve(V.T @ Ad @ V, V.T @ r0)
+        assert np.abs(xs[kk - 1] - ref).max() <= 1e-10 * np.abs(ref).max(), kk
+        blocks.append(w * (Ad @ blocks[-1]))
+
+
 def test_adjoint_dense_matches_central_differences():
     nx = ny = 6; s = 3
     g = np.random.default_rng(3)
