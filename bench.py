@@ -69,13 +69,15 @@ HBM_PEAK_GBS = _hbm_peak()
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=None,
+                   help="timed steps (default 300 for the native arm, 20 for the reference arm)")
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--s", type=int, default=8)
     p.add_argument("--grid", type=int, default=128)
     p.add_argument("--op", default="stencil", choices=["stencil", "csr"])
-    p.add_argument("--sweep", action="store_true", help="also time s in {1,4,8,16,32}, stencil and CSR")
+    p.add_argument("--no-extra", action="store_true",
+                   help="skip the rest of the metric (the s sweep and the FP32+IR vs FP64 time to 1e-10)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--probe", choices=["bcg_fp64", "bcg_fp32_ir"],
                    help="run one short solve (a target for ncu) on --workload/--grid/--s and exit")
@@ -102,7 +104,10 @@ def parse():
     p.add_argument("--ir", action="store_true",
                    help="time-to-1e-10 of FP32+IR vs plain FP64 BCG on the 192^3 log-normal diffusion "
                         "workload (s = 16) instead of the default line")
-    return p.parse_args()
+    a = p.parse_args()
+    if a.steps is None:
+        a.steps = 20 if a.impl == "reference" else 300
+    return a
 
 
 def run_ir(args):
@@ -217,10 +222,12 @@ PHASE_BYTES = {
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling (every 100 ms) while the GPU work of the run executes: the timed
+    region first, then the sweep and refinement parts of the line.  Samples with the GPU
+    more than half busy count as under load; the median SM clock is taken over those."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, dev=0):
         self.dev = dev
@@ -247,21 +254,26 @@ class Clocks:
     def summary(self):
         if not self.p or not self.out:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm, mx, reasons = [], None, set()
+        sm, mx, reasons, total = [], None, set(), 0
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1])); mx = float(f[2])
+                clk, mx_, util = float(f[1]), float(f[2]), float(f[9])
             except ValueError:
                 continue
+            total += 1
+            mx = mx_
             for nm, v in zip(names, f[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
+            if util > 50:
+                sm.append(clk)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": total, "samples_under_load": len(sm),
+                "covers": "timed region, then the sweep and refinement runs"}
 
 
 def cpu_baseline(prob, s, iters=3):
@@ -373,41 +385,56 @@ def run_phases(args):
 
 
 def run_micro(args):
-    """Stand-alone FP32 operator product (no Gram), block inner products and a copy."""
+    """Stand-alone FP32 kernels against HBM: the operator product alone and with its fused
+    Gram (alpha = P^T A P), block inner products of one and two blocks, and a copy.  Every
+    repetition is timed on its own with CUDA events after an L2 flush (a 512 MB write)."""
     import torch
     import workloads as W
     from paper_2104_02494_gb300 import build
     from paper_2104_02494_gb300.api import Handle, operator_from_problem
     build()
     h = Handle(0)
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
     def timeit(fn, reps=20):
         for _ in range(3):
             fn()
-        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(); e0.record()
+        tot = 0.0
         for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
             fn()
-        e1.record(); torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
+            e1.record()
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / reps
 
-    out = {"grid": args.grid, "hbm_peak_gbs": HBM_PEAK_GBS}
-    for kind, s in (("laplace3d", 8), ("laplace3d", 16), ("laplace3d", 32), ("vardiff3d", 16)):
-        prob = W.problem(kind, s=s, grid=args.grid, with_csr=False)
+    out = {"hbm_peak_gbs": HBM_PEAK_GBS, "l2": "flushed before every timed launch"}
+    cases = [("laplace3d", 8, 128), ("laplace3d", 16, 128), ("laplace3d", 32, 128), ("vardiff3d", 8, 192),
+             ("vardiff3d", 16, 192)]
+    for kind, s, grid in cases:
+        prob = W.problem(kind, s=s, grid=grid if args.grid == 128 else args.grid, with_csr=False)
         op = operator_from_problem(h, prob, "stencil")
         n = prob.B.shape[0]
         P = torch.randn(n, s, device="cuda", dtype=torch.float32)
         Q = torch.empty_like(P)
         G = torch.empty(s, s, device="cuda", dtype=torch.float64)
         by = 4 * n * s
-        r = {"spmm": timeit(lambda: h.spmm(op, P, Q)), "bdot_two_blocks": timeit(lambda: h.bdot(P, Q, G=G)),
+        coef = 4 * n if kind == "vardiff3d" else 0     # one coefficient k per cell (algorithmic)
+        r = {"spmm": timeit(lambda: h.spmm(op, P, Q)),
+             "spmm_gram": timeit(lambda: h.spmm_gram(op, P, Q, G=G)),
+             "bdot_two_blocks": timeit(lambda: h.bdot(P, Q, G=G)),
              "bdot_one_block": timeit(lambda: h.bdot(P, P, sym=True, G=G)),
              "copy": timeit(lambda: Q.copy_(P))}
-        gbs = {"spmm": 2 * by, "bdot_two_blocks": 2 * by, "bdot_one_block": by, "copy": 2 * by}
-        out[f"{kind}_s{s}"] = {k: {"ms": v, "gbs": gbs[k] / (v / 1000.0) / 1e9,
-                                   "hbm_frac": gbs[k] / (v / 1000.0) / 1e9 / HBM_PEAK_GBS}
-                               for k, v in r.items()}
+        gbs = {"spmm": 2 * by + coef, "spmm_gram": 2 * by + coef, "bdot_two_blocks": 2 * by,
+               "bdot_one_block": by, "copy": 2 * by}
+        out[f"{kind}{grid}_s{s}"] = {k: {"ms": v, "gbs": gbs[k] / (v / 1000.0) / 1e9,
+                                        "hbm_frac": gbs[k] / (v / 1000.0) / 1e9 / HBM_PEAK_GBS}
+                                    for k, v in r.items()}
         op.close()
+        del P, Q
+        torch.cuda.empty_cache()
     print(json.dumps(out))
 
 
@@ -616,6 +643,93 @@ def run_one_reduction(args):
                       "results": out}))
 
 
+def _flush_timer(torch):
+    """Device time (ms) of one call after an L2 flush (a 512 MB write), CUDA events."""
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def timeit(fn, reps=10, warm=3):
+        for _ in range(warm):
+            fn()
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(); fn(); e1.record()
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / reps
+    return timeit
+
+
+def run_sweep(h, args, prob, torch):
+    """The s in {1, 4, 8, 16, 32} half of the metric on the 128^3 Laplacian, stencil and CSR:
+    FP64 BCG (eta = inf) RHS*iter/s over 10 steady-state iterations (after 3), the FP64 rate
+    of the iteration against the FP64 peak, and the fused operator + Gram pass (Q = A P with
+    alpha = P^T Q, bkrylov_spmm_gram) in FP32 against the measured HBM copy bandwidth
+    (algorithmic bytes: P read, Q written, plus the CSR arrays)."""
+    import workloads as W
+    from paper_2104_02494_gb300.api import operator_from_problem
+    n = prob.B.shape[0]
+    B32 = W.normal_block(n, 32, 0)               # the Laplacian's B is the first s columns of this draw
+    timeit = _flush_timer(torch)
+    out = {}
+    for use in ("stencil", "csr"):
+        op = operator_from_problem(h, prob, use)
+        for ss in (1, 4, 8, 16, 32):
+            B2 = torch.from_numpy(np.ascontiguousarray(B32[:, :ss])).cuda()
+            kk = 10
+            m2 = time_iters(h, op, B2, ss, 3, kk, torch)
+            fl = iteration_flops(n, ss)
+            e = {"rhs_iter_per_s": ss * kk / (m2 / 1000.0), "ms_per_iter": m2 / kk,
+                 "fp64_tflops": fl / (m2 / kk / 1000.0) / 1e12}
+            e["fp64_frac"] = e["fp64_tflops"] / FP64_PEAK_TFLOPS
+            P32 = B2.float()
+            Q32 = torch.empty_like(P32)
+            G = torch.empty(ss, ss, dtype=torch.float64, device="cuda")
+            t = timeit(lambda: h.spmm_gram(op, P32, Q32, G=G))
+            by = 2 * 4 * n * ss + (prob.A.nnz * 8 + 4 * (n + 1) if use == "csr" else 0)
+            e["spmm_bdot_fp32"] = {"ms": t, "gbs": by / (t / 1000.0) / 1e9,
+                                   "hbm_frac": by / (t / 1000.0) / 1e9 / HBM_PEAK_GBS}
+            out[f"{use}_s{ss}"] = e
+            del B2, P32, Q32
+        op.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_ir_pair(h, args, torch):
+    """The FP32+IR vs FP64 half of the metric: time to a max-column relative residual of 1e-10
+    on the 192^3 log-normal diffusion workload (s = 16), both with point Jacobi: FP64 BCG with
+    the adaptive criterion at eta = 1e4 against FP32 inner BCG (to 1e-5, eta = 1) inside FP64
+    refinement.  Device time of the solve call; the true residual is recomputed in FP64 by the
+    library.  One untimed 3-iteration solve of each first."""
+    import workloads as W
+    from paper_2104_02494_gb300.api import operator_from_problem
+    prob = W.problem("vardiff3d", s=16, with_csr=False)
+    op = operator_from_problem(h, prob, "stencil")
+    M = h.op_jacobi(op)
+    Bd = torch.from_numpy(prob.B).cuda()
+    nb = torch.linalg.vector_norm(Bd, dim=0)
+    out = {"workload": "vardiff3d 192^3 var7 stencil, s=16, point Jacobi, to 1e-10"}
+    for name, prec, eta in (("fp64", "fp64", 1e4), ("fp32_ir", "fp32_ir", 1.0)):
+        h.solve("bcg", op, Bd, tol=1e-10, maxit=3, eta=eta, prec=prec, record=False, precond=M,
+                ir_max_outer=1)
+        X = torch.zeros_like(Bd)
+        X, info = h.solve("bcg", op, Bd, X, tol=1e-10, maxit=20000, eta=eta, prec=prec, record=False,
+                          precond=M)
+        R = h.residual(op, Bd, X)
+        out[name] = {"seconds": info.elapsed_ms / 1000.0, "iters": info.iters, "outer": info.outer,
+                     "reorths": info.reorths, "converged": bool(info.converged), "eta": eta,
+                     "true_relres_max": float((torch.linalg.vector_norm(R, dim=0) / nb).max())}
+    out["speedup_fp32_ir_vs_fp64"] = out["fp64"]["seconds"] / out["fp32_ir"]["seconds"]
+    M.close()
+    op.close()
+    del Bd
+    torch.cuda.empty_cache()
+    return out
+
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -659,8 +773,8 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    with Clocks(dev) as clk:
-        ms = time_iters(h, op, Bd, s, Wm, K, torch)
+    clk = Clocks(dev).__enter__()
+    ms = time_iters(h, op, Bd, s, Wm, K, torch)
     torch.cuda.synchronize()
     ms, value = aggregate(ms, s * K, dist)
     if dist:
@@ -693,29 +807,11 @@ def main():
     e2e = {"value": s * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * Bh.nbytes / K,
            "d2h_bytes_per_step": Xh.nbytes / K, "note": "setup (residual, first QR) included"}
 
-    sweep = None
-    if args.sweep and rank == 0:
-        sweep = {}
-        for use in ("stencil", "csr"):
-            for ss in (1, 4, 8, 16, 32):
-                pr = W.problem("laplace3d", s=ss, grid=args.grid, with_csr=(use == "csr"))
-                o2 = operator_from_problem(h, pr, use)
-                B2 = torch.from_numpy(pr.B).cuda()
-                kk = max(3, min(K, 10))
-                m2 = time_iters(h, o2, B2, ss, 3, kk, torch)
-                sweep[f"{use}_s{ss}"] = {"rhs_iter_per_s": ss * kk / (m2 / 1000.0), "ms_per_iter": m2 / kk,
-                                         "fp64_tflops": iteration_flops(pr.B.shape[0], ss) / (m2 / kk / 1000.0) / 1e12}
-                if use == "stencil":
-                    # the fused operator + Gram kernel (A P and P^T A P in one pass) against
-                    # HBM, FP32 (inner solve of refinement) and FP64
-                    for prec, w in (("fp32_ir", 4), ("fp64", 8)):
-                        t = spmm_alpha_ms(h, o2, B2, prec)
-                        by = 2 * w * pr.B.shape[0] * ss
-                        sweep[f"{use}_s{ss}"][f"spmm_bdot_{prec}"] = {
-                            "ms": t, "gbs": by / (t / 1000.0) / 1e9,
-                            "hbm_frac": by / (t / 1000.0) / 1e9 / HBM_PEAK_GBS}
-                o2.close()
-                del B2
+    sweep = ir = None
+    if rank == 0 and not args.no_extra:
+        sweep = run_sweep(h, args, prob, torch)
+        ir = run_ir_pair(h, args, torch)
+    clk.__exit__(None, None, None)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -735,6 +831,8 @@ def main():
                 "clocks": clk.summary(), "gpu_launches": launches}
         if sweep:
             line["sweep"] = sweep
+        if ir:
+            line["ir"] = ir
         print(json.dumps(line))
     h.close()
     if dist:

@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define BKRYLOV_VERSION 100
+#define BKRYLOV_VERSION 200
 #define BKRYLOV_MAX_S 32
 
 typedef struct bkrylov_ctx* bkrylov_handle;   /* owns workspace + stream binding */
@@ -67,24 +67,34 @@ typedef enum {
      ny*(nx+1) horizontal edges (a_x[y][x] joins cells (x-1,y),(x,y)) followed by
      (ny+1)*nx vertical edges (a_y[y][x] joins (x,y-1),(x,y)); BORROWED (the caller
      keeps it alive until bkrylov_op_destroy). */
-  BK_STENCIL_EDGE5 = 2
+  BK_STENCIL_EDGE5 = 2,
+  /* BK_STENCIL_EDGE5 parameterised by log-coefficients: coeffs holds theta_e in the same
+     layout and the operator forms and owns a_e = exp(theta_e) at creation (theta is not
+     kept).  The per-edge model of the differentiable solve, a_e = exp(theta_e). */
+  BK_STENCIL_EDGE5_LOG = 3
 } bkrylov_stencil_kind;
 
-/* Solver options (bkrylov_opts_default fills the defaults noted here). */
+/* Solver options (bkrylov_opts_default fills the defaults noted here).  The tolerance
+   and the iteration limit are arguments of the solve calls. */
 typedef struct {
-  double tol;          /* stop when max_i ||R_i|| / ||R0_i|| <= tol           (1e-8)  */
-  int maxit;           /* iteration limit (Arnoldi steps for BGMRes)          (1000)  */
   double eta;          /* re-orthonormalisation parameter: 0 never, INFINITY always;
                           otherwise re-orthonormalise when eta*kappa_D > 1/sqrt(eps)
                           (Ch. 4.3, Eq. "reortho_criterion", read as 1/sqrt(eps))   (INFINITY) */
   int restart;         /* BGMRes restart length m                              (30)   */
-  int ortho;           /* BGMRes orthogonalisation: 0 = CGS2 (two classical passes),
-                          1 = block MGS, 2 = localized Arnoldi (Ch. 9.3: the basis kept as a
-                          distributed S-QR decomposition over the row tiles, one tree
-                          reduction per step; s <= 16, every row tile at least s rows and
-                          restart small enough for its tree nodes' shared memory, else
-                          BK_ERR_UNSUPPORTED)                                   (0)    */
-  int prec;            /* bkrylov_prec: FP64, FP32, or FP32 inner + FP64 refinement (FP64) */
+  int ortho;           /* BGMRes orthogonalisation: 0 = CGS2 (two classical passes, Ch. 9.1),
+                          1 = block MGS (Alg. "block-arnoldi"), 2 = localized Arnoldi (Ch. 9.3:
+                          the basis kept as a distributed S-QR decomposition over the row
+                          tiles, one tree reduction per step; s <= 16, every row tile at least
+                          s rows and restart small enough for its tree nodes' shared memory,
+                          else BK_ERR_UNSUPPORTED).  The default is block MGS: on one GPU the
+                          thesis's reasons for CGS2 and the localized method (fewer global
+                          reductions) cost nothing, and MGS does half of CGS2's FP64 work
+                          (measured 1.6x faster to 1e-8 on the 96^3 convection-diffusion
+                          workload at s = 8)                                     (1)    */
+  int prec;            /* bkrylov_prec of the solve: BK_FP64; BK_FP32 (BCG only: FP32 blocks
+                          and products, every s x s quantity in FP64, eps = 2^-23 in the
+                          criterion); BK_FP32_IR (BCG only: FP32 inner solves inside FP64
+                          iterative refinement)                                 (FP64) */
   double ir_inner_tol; /* relative tolerance of each FP32 inner solve          (1e-5)  */
   int ir_max_outer;    /* refinement steps limit                               (30)    */
   const uint8_t* forced_reortho; /* HOST, optional: decision of iteration k (k < n_forced)
@@ -111,6 +121,11 @@ typedef struct {
                           Jacobi.  Applies to the FP32 inner solves of FP32_IR too.
                           NULL: M = I.  BK_ERR_ARG if its n differs from A's;
                           BK_ERR_UNSUPPORTED for BBiCGStab and BGMRes            (NULL) */
+  int norm_mode;       /* stopping measure of the relative residual (Ch. 4.1 "break if ||R||
+                          < tol" names no norm): 0 = max_i ||R_i|| / ||R0_i||, a reduction in
+                          every column; 1 = ||R||_F / ||R0||_F.  For FP32_IR it is the
+                          outer test (relative to ||B||); the inner solves test every
+                          column.  Other values: BK_ERR_ARG                      (0)    */
   int one_reduction;   /* BCG only: 1 = the schedule of Alg. "1R-CG" (Ch. 8.1): U = A Z and
                           delta = <Z, U> after the preconditioner, Q = U + Q beta,
                           alpha = delta - beta^T alpha beta, arithmetically equal to the
@@ -128,7 +143,8 @@ typedef struct {
   int outer;           /* refinement steps (FP32_IR), else 0                          */
   double relres_max;   /* final max_i ||R_i|| / ||R0_i|| as tracked by the method     */
   double* relres;      /* [s]      final per-column relative residuals, or NULL        */
-  double* history;     /* [maxit]  max relative residual after each iteration, or NULL */
+  double* history;     /* [maxit]  stopping measure (norm_mode) after each iteration
+                                   (after each outer step for FP32_IR), or NULL        */
   uint8_t* decisions;  /* [maxit]  re-orthonormalised in iteration k?, or NULL          */
   int history_len;     /* capacity of history/decisions (entries written <= this)      */
   double elapsed_ms;   /* device time of the solve (CUDA events)                      */
@@ -145,11 +161,15 @@ int bkrylov_version(void);
 void bkrylov_opts_default(bkrylov_opts* o);
 
 /* ---- operators (BOP, Ch. 3.3 Table "kernels") ---------------------------------- */
-/* CSR matrix, n x n, int32 row_ptr[n+1] and col[nnz] (columns sorted within a row),
-   double val[nnz]; all device arrays BORROWED until bkrylov_op_destroy.  A float copy
-   of val is made (owned by the operator) the first time an FP32 product is asked for. */
+/* CSR matrix, n x n, int32 row_ptr[n+1] and col[nnz] (columns sorted within a row), val[nnz]
+   of precision val_prec: BK_FP64 (double) or BK_FP32 (float); all device arrays BORROWED
+   until bkrylov_op_destroy.  FP64 values: a float copy (owned) is made the first time an
+   FP32 product is asked for.  FP32 values: the FP64 products (FP64 solvers, the outer
+   residual of refinement) use an owned double widening made here (exact), so the operator
+   is the same matrix in both precisions.  Errors: BK_ERR_ARG (another val_prec, n < 1,
+   nnz < 0 or > INT32_MAX, null arrays), BK_ERR_ALLOC. */
 int bkrylov_op_csr(bkrylov_handle h, int64_t n, int64_t nnz, const int32_t* row_ptr,
-                   const int32_t* col, const double* val, bkrylov_op* A);
+                   const int32_t* col, const void* val, int val_prec, bkrylov_op* A);
 /* Matrix-free stencil (see bkrylov_stencil_kind).  n = nx*ny*nz.  VAR7 precomputes the
    3 face coefficients of every cell (owned, 3n doubles); EDGE5 precomputes the diagonal
    (owned, n doubles). */
@@ -165,11 +185,28 @@ int bkrylov_op_diag(bkrylov_handle h, int64_t n, const double* d, bkrylov_op* M)
    stream; BK_ERR_ARG (nothing kept) when some a_ii is zero or not finite.  Destroy the
    result with bkrylov_op_destroy; it does not borrow A. */
 int bkrylov_op_jacobi(bkrylov_handle h, bkrylov_op A, bkrylov_op* M);
+/* At = A^T as an operator of its own (the adjoint solve A^T Lambda = dL/dX of a
+   differentiable solve needs it for a non-symmetric A).  CSR: the transposed arrays are
+   formed on the device and owned by At (columns sorted within every row; synchronises
+   the handle's stream); CONST7: the -/+ coefficient of every direction swapped.
+   VAR7, EDGE5 and diagonal operators are symmetric by construction (use A itself):
+   BK_ERR_UNSUPPORTED.  At does not borrow A. */
+int bkrylov_op_transpose(bkrylov_handle h, bkrylov_op A, bkrylov_op* At);
 int bkrylov_op_destroy(bkrylov_op A);
 int bkrylov_op_size(bkrylov_op A, int64_t* n, int64_t* nnz);
 
 /* Q = A P (BOP).  P, Q: n x s blocks of precision prec (BK_FP64 or BK_FP32). */
 int bkrylov_spmm(bkrylov_handle h, bkrylov_op A, int s, const void* P, void* Q, int prec);
+/* Q = A P with the block inner product G = P^T Q fused into the same pass over the block:
+   the operator product of an iteration with its Gram alpha = P^T A P (Ch. 3.3, Table
+   "kernels": BOP followed by BDOT; Ch. 4.1, Eq. "cg_alpha").  sym != 0 computes the upper
+   triangle and mirrors it (G exactly symmetric).  P, Q: n x s blocks of precision prec
+   (BK_FP64 or BK_FP32), P != Q; G: s x s row-major doubles, device.  FP32 stencil operators
+   with s % 4 == 0 and sym != 0 run the pipelined marching kernel (tensor copies of halo
+   tiles into a shared-memory ring).  Errors: BK_ERR_ARG (nothing enqueued) for a null
+   pointer, P == Q, s outside 1..32 or another prec. */
+int bkrylov_spmm_gram(bkrylov_handle h, bkrylov_op A, int s, const void* P, void* Q, double* G, int sym,
+                      int prec);
 /* R = B - A X (the residual of Alg. "bcg", first line). */
 int bkrylov_residual(bkrylov_handle h, bkrylov_op A, int s, const void* B, const void* X,
                      void* R, int prec);
@@ -208,24 +245,32 @@ int bkrylov_tsqr(bkrylov_handle h, int64_t n, int s, const void* X, void* Y, dou
                  int prec);
 
 /* ---- solvers --------------------------------------------------------------------- */
-/* B (read) and X (in: X0, out: solution) are n x s double blocks, either device
-   pointers or HOST pointers (then the library copies them to and from the device
-   inside the call).  opts may be NULL (defaults); info may be NULL.
-   Returns BK_OK, BK_NOT_CONVERGED, BK_BREAKDOWN or BK_NONFINITE (X is the last
-   iterate in the last three cases), or an error code. */
+/* Solve A X = B for the n x s block X (Ch. 3, Eq. "blocklinearsystem"; the algorithms'
+   inputs X0, B, tol, maxit).  B (read) and X (in: X0, out: the solution) are n x s
+   row-major blocks of double (prec BK_FP64 and BK_FP32_IR) or float (prec BK_FP32),
+   either device pointers or HOST pointers (then the library copies them to and from the
+   device inside the call).  tol: the stopping tolerance of the relative residual in the
+   measure opts->norm_mode (>= 0); maxit: iteration limit (Arnoldi steps for BGMRes; inner
+   iterations of each refinement step for FP32_IR; >= 0).  opts may be NULL (defaults);
+   info may be NULL.  Returns BK_OK, BK_NOT_CONVERGED, BK_BREAKDOWN, BK_NONFINITE or
+   BK_TIMEOUT (X is the last iterate in those cases), or an error code: BK_ERR_ARG
+   (nothing enqueued) for null pointers, B == X, s outside 1..32, n < s, tol < 0,
+   maxit < 0, eta < 0 or another norm_mode. */
 /* Block CG with adaptive residual re-orthonormalisation, Alg. "bcgaro" (Ch. 4.3)
-   scheduled as Alg. "2R-CG" (Ch. 8.1); prec = BK_FP32_IR runs FP32 inner solves
-   inside FP64 iterative refinement (B - A X in FP64). */
-int bkrylov_solve_bcg(bkrylov_handle h, bkrylov_op A, int s, const double* B, double* X,
-                      const bkrylov_opts* opts, bkrylov_info* info);
+   scheduled as Alg. "2R-CG" (Ch. 8.1); prec = BK_FP32 solves with FP32 blocks (the
+   thesis's single-precision runs, Ch. 4.4), BK_FP32_IR runs FP32 inner solves inside FP64
+   iterative refinement (B - A X in FP64).  The block-parallel subalgebra (subalgebra_p
+   < s) is FP64 only (BK_ERR_UNSUPPORTED otherwise). */
+int bkrylov_solve_bcg(bkrylov_handle h, bkrylov_op A, int s, const void* B, void* X, double tol,
+                      int maxit, const bkrylov_opts* opts, bkrylov_info* info);
 /* Block BiCGStab with adaptive re-orthonormalisation, Alg. "BlockBiCGStab_with_reortho"
    (Ch. 6.2).  FP64 only. */
-int bkrylov_solve_bbicgstab(bkrylov_handle h, bkrylov_op A, int s, const double* B,
-                            double* X, const bkrylov_opts* opts, bkrylov_info* info);
-/* Restarted block GMRes, Alg. "bgmres" (Ch. 5.1), CGS2 (Ch. 9.1) or MGS Arnoldi and the
-   TSQR normalizer.  FP64 only. */
-int bkrylov_solve_bgmres(bkrylov_handle h, bkrylov_op A, int s, const double* B,
-                         double* X, const bkrylov_opts* opts, bkrylov_info* info);
+int bkrylov_solve_bbicgstab(bkrylov_handle h, bkrylov_op A, int s, const void* B, void* X,
+                            double tol, int maxit, const bkrylov_opts* opts, bkrylov_info* info);
+/* Restarted block GMRes, Alg. "bgmres" (Ch. 5.1), block MGS (Alg. "block-arnoldi"),
+   CGS2 (Ch. 9.1) or localized Arnoldi (Ch. 9.3) and the TSQR normalizer.  FP64 only. */
+int bkrylov_solve_bgmres(bkrylov_handle h, bkrylov_op A, int s, const void* B, void* X,
+                         double tol, int maxit, const bkrylov_opts* opts, bkrylov_info* info);
 
 /* ---- measurement ----------------------------------------------------------------- */
 /* Number of timed phases of a BCG iteration (spmm_alpha, small_1, update_rho,

@@ -31,12 +31,13 @@ import math
 import numpy as np
 
 from .bcg import BCGResult
-from .blockops import (Breakdown, col_norms, gram, lu_solve, normalizer, reortho_decision, spmm)
+from .blockops import (Breakdown, col_norms, gram, lu_solve, normalizer, reortho_decision, spmm,
+                       stop_measure)
 
 
 def bbicgstab(A, B: np.ndarray, X0=None, tol: float = 1e-8, maxit: int = 1000,
               eta: float = 100.0, forced=None, record_iterates: int = 0, apply_A=None,
-              eps: float | None = None) -> BCGResult:
+              eps: float | None = None, norm: str = "max") -> BCGResult:
     B = np.asarray(B, dtype=np.float64)
     n, s = B.shape
     eps = float(np.finfo(np.float64).eps) if eps is None else eps
@@ -84,13 +85,13 @@ def bbicgstab(A, B: np.ndarray, X0=None, tol: float = 1e-8, maxit: int = 1000,
         rhoRR = gram(Rh, Rh)
         M = sigma_new.T @ rhoRR @ sigma_new
         relres = np.where(n0 > 0, np.sqrt(np.maximum(np.diag(M), 0.0)) / n0_safe, 0.0)
-        out.history.append(float(relres.max(initial=0.0)))
+        out.history.append(stop_measure(relres, n0, norm))
         out.decisions.append(reo)
         if k < record_iterates:
             out.iterates.append(X.copy())
         out.iters = k + 1
         out.relres = relres
-        if relres.max(initial=0.0) <= tol:
+        if stop_measure(relres, n0, norm) <= tol:
             out.converged = True
             return out
         try:

@@ -29,7 +29,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from .blockops import (Breakdown, chol_solve, col_norms, gram, kappa_d, normalizer,
-                       project_subalgebra, reortho_decision, spmm)
+                       project_subalgebra, reortho_decision, spmm, stop_measure)
 from .precond import apply_diagonal
 
 
@@ -51,7 +51,7 @@ class BCGResult:
 def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit: int = 1000,
         eta: float = math.inf, p: int | None = None, forced=None, record_iterates: int = 0,
         dtype=np.float64, eps: float | None = None, apply_A=None, Minv=None,
-        record_alpha: bool = False) -> BCGResult:
+        record_alpha: bool = False, norm: str = "max") -> BCGResult:
     """Alg. "bcgaro" (2R grouping, Alg. "2R-CG") for A X = B.
 
     A: CSR (attributes n, row_ptr, col, val) or None when ``apply_A`` is given.
@@ -63,6 +63,8 @@ def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit
     Minv: the preconditioner M^{-1}: None (M = I), a vector (a diagonal
         M^{-1}, e.g. ``precond.jacobi_inverse_diagonal(A)``) or a callable
         V -> M^{-1} V.  M must be symmetric positive definite (Ch. 4).
+    norm: the stopping measure, "max" (max-column) or "fro" (Frobenius), see
+        ``blockops.stop_measure``; the history records the same measure.
     """
     B = np.asarray(B)
     n, s = B.shape
@@ -94,7 +96,7 @@ def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit
         rho = gram(P, Rb, p)            # rho^0 = <P^0, R-bar^0>
     res = _resid_from(sigma, G, p, reortho=False)
     relres = np.where(n0 > 0, res / n0_safe, 0.0)
-    out = BCGResult(X, 0, 0, bool(relres.max(initial=0.0) <= tol), "ok", relres)
+    out = BCGResult(X, 0, 0, bool(stop_measure(relres, n0, norm) <= tol), "ok", relres)
     if out.converged:
         return out
     for k in range(maxit):
@@ -125,13 +127,13 @@ def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit
         G = None if reo else gram(Rb, Rb, p)
         res = _resid_from(sigma, G, p, reortho=reo)
         relres = np.where(n0 > 0, res / n0_safe, 0.0)
-        out.history.append(float(relres.max(initial=0.0)))
+        out.history.append(stop_measure(relres, n0, norm))
         out.decisions.append(reo)
         if k < record_iterates:
             out.iterates.append(X.copy())
         out.iters = k + 1
         out.relres = relres
-        if relres.max(initial=0.0) <= tol:
+        if stop_measure(relres, n0, norm) <= tol:
             out.converged = True
             return out
         if prec is None:
@@ -153,7 +155,7 @@ def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit
 
 def bcg_1r(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit: int = 1000,
            eta: float = math.inf, forced=None, record_iterates: int = 0, dtype=np.float64,
-           eps: float | None = None, Minv=None) -> BCGResult:
+           eps: float | None = None, Minv=None, norm: str = "max") -> BCGResult:
     """BCG with one reduction per iteration, Alg. "1R-CG" (Ch. 8.1), block case S_B.
 
     Arithmetically equal to Alg. "bcgaro": with U = A Z, delta = <Z, U>, the
@@ -191,7 +193,7 @@ def bcg_1r(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, ma
     alpha = gram(P, Q)                  # alpha^0 = <P^0, Q^0>
     res = _resid_from(sigma, G, None, reortho=False)
     relres = np.where(n0 > 0, res / n0_safe, 0.0)
-    out = BCGResult(X, 0, 0, bool(relres.max(initial=0.0) <= tol), "ok", relres)
+    out = BCGResult(X, 0, 0, bool(stop_measure(relres, n0, norm) <= tol), "ok", relres)
     if out.converged:
         return out
     for k in range(maxit):
@@ -221,13 +223,13 @@ def bcg_1r(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, ma
         U = op(Z)                                       # U^{k+1} = A Z^{k+1}
         delta = gram(Z, U)                              # delta^{k+1} = <Z^{k+1}, U^{k+1}>
         relres = np.where(n0 > 0, res / n0_safe, 0.0)
-        out.history.append(float(relres.max(initial=0.0)))
+        out.history.append(stop_measure(relres, n0, norm))
         out.decisions.append(reo)
         if k < record_iterates:
             out.iterates.append(X.copy())
         out.iters = k + 1
         out.relres = relres
-        if relres.max(initial=0.0) <= tol:
+        if stop_measure(relres, n0, norm) <= tol:
             out.converged = True
             return out
         try:

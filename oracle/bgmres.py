@@ -31,7 +31,7 @@ from __future__ import annotations
 import numpy as np
 
 from .bcg import BCGResult
-from .blockops import col_norms, normalizer, spmm
+from .blockops import col_norms, normalizer, spmm, stop_measure
 from .localized import LocalizedArnoldi
 
 
@@ -57,7 +57,8 @@ def _full_householder_qr(M: np.ndarray):
 
 
 def bgmres(A, B: np.ndarray, X0=None, tol: float = 1e-8, restart: int = 30, maxit: int = 1000,
-           ortho: str = "mgs", apply_A=None, tile_rows: int = 2048, fanin: int = 2) -> BCGResult:
+           ortho: str = "mgs", apply_A=None, tile_rows: int = 2048, fanin: int = 2,
+           norm: str = "max") -> BCGResult:
     """Alg. "bgmres" with restart length ``restart``; ``maxit`` counts Arnoldi steps.
 
     ortho: "mgs", "cgs2" or "localized" (row tiles of ``tile_rows`` rows, a tree of
@@ -121,9 +122,9 @@ def bgmres(A, B: np.ndarray, X0=None, tol: float = 1e-8, restart: int = 30, maxi
             k_done = k + 1
             total += 1
             relres = np.where(n0 > 0, col_norms(sig[(k + 1) * s:(k + 2) * s]) / n0_safe, 0.0)
-            out.history.append(float(relres.max(initial=0.0)))
+            out.history.append(stop_measure(relres, n0, norm))
             out.relres = relres
-            if relres.max(initial=0.0) <= tol:
+            if stop_measure(relres, n0, norm) <= tol:
                 conv = True
                 break
         # block back-substitution  R zeta = sigma  over the k_done steps

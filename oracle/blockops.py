@@ -75,6 +75,24 @@ def col_norms(X: np.ndarray) -> np.ndarray:
     return np.sqrt(np.einsum("ij,ij->j", X, X))
 
 
+def stop_measure(relres: np.ndarray, n0: np.ndarray, norm: str = "max") -> float:
+    """Relative residual that the stopping test compares with tol (Ch. 4.1 prints
+    "break if ||R|| < tol" without naming the norm; reading c2).
+
+    relres_i = ||R_i|| / ||R^0_i|| (0 for columns with R^0_i = 0), n0_i = ||R^0_i||.
+    "max": max_i relres_i, a reduction by tol in every column (the default);
+    "fro": ||R||_F / ||R^0||_F = sqrt(sum_i (relres_i n0_i)^2) / sqrt(sum_i n0_i^2).
+    """
+    relres = np.asarray(relres, dtype=np.float64)
+    if norm == "max":
+        return float(relres.max(initial=0.0))
+    if norm == "fro":
+        n0 = np.asarray(n0, dtype=np.float64)
+        den = math.sqrt(float(np.sum(n0 * n0)))
+        return math.sqrt(float(np.sum((relres * n0) ** 2))) / den if den > 0 else 0.0
+    raise ValueError(norm)
+
+
 def householder_qr(X: np.ndarray):
     """Householder QR  X = Y sigma  with Y^T Y = I, sigma upper triangular, diag(sigma) >= 0.
 

@@ -27,7 +27,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from .bcg import bcg
-from .blockops import col_norms, spmm
+from .blockops import col_norms, spmm, stop_measure
 
 
 @dataclass
@@ -40,9 +40,12 @@ class IRResult:
 
 
 def bcg_ir(A, B: np.ndarray, tol: float = 1e-10, inner_tol: float = 1e-5, max_outer: int = 20,
-           inner_maxit: int = 5000, eta: float = math.inf, Minv=None, X0=None) -> IRResult:
+           inner_maxit: int = 5000, eta: float = math.inf, Minv=None, X0=None,
+           norm: str = "max") -> IRResult:
     """Refinement loop above from X0 (zero when not given); ``Minv`` (optional, see
-    ``bcg``) preconditions the inner solve."""
+    ``bcg``) preconditions the inner solve.  ``norm`` is the measure of the outer test
+    (``blockops.stop_measure``, relative to ||B||); the inner solves keep the
+    per-column test of reading c19."""
     B = np.asarray(B, dtype=np.float64)
     n, s = B.shape
     X = np.zeros((n, s)) if X0 is None else np.array(X0, dtype=np.float64, copy=True)
@@ -53,7 +56,7 @@ def bcg_ir(A, B: np.ndarray, tol: float = 1e-10, inner_tol: float = 1e-5, max_ou
         R = B - spmm(A, X)
         nr = col_norms(R)
         out.relres = np.where(nb > 0, nr / nb_safe, 0.0)
-        if out.relres.max(initial=0.0) <= tol:
+        if stop_measure(out.relres, nb, norm) <= tol:
             out.converged = True
             return out
         if it == max_outer:

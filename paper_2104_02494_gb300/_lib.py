@@ -16,17 +16,17 @@ LIB_PATH = os.path.join(HERE, "lib", "libbkrylov.so")
 BK_FP64, BK_FP32, BK_FP32_IR = 0, 1, 2
 BK_OK, BK_ERR_ARG, BK_ERR_CUDA, BK_ERR_ALLOC = 0, 1, 2, 3
 BK_NOT_CONVERGED, BK_BREAKDOWN, BK_NONFINITE, BK_TIMEOUT, BK_ERR_UNSUPPORTED = 4, 5, 6, 7, 8
-BK_STENCIL_CONST7, BK_STENCIL_VAR7, BK_STENCIL_EDGE5 = 0, 1, 2
+BK_STENCIL_CONST7, BK_STENCIL_VAR7, BK_STENCIL_EDGE5, BK_STENCIL_EDGE5_LOG = 0, 1, 2, 3
 MAX_S = 32
 
 
 class bkrylov_opts(C.Structure):
     _fields_ = [
-        ("tol", C.c_double), ("maxit", C.c_int), ("eta", C.c_double), ("restart", C.c_int),
+        ("eta", C.c_double), ("restart", C.c_int),
         ("ortho", C.c_int), ("prec", C.c_int), ("ir_inner_tol", C.c_double),
         ("ir_max_outer", C.c_int), ("forced_reortho", C.POINTER(C.c_uint8)), ("n_forced", C.c_int),
         ("sync_every", C.c_int), ("profile", C.c_int), ("subalgebra_p", C.c_int),
-        ("precond", C.c_void_p), ("one_reduction", C.c_int),
+        ("precond", C.c_void_p), ("norm_mode", C.c_int), ("one_reduction", C.c_int),
     ]
 
 
@@ -48,14 +48,17 @@ SIGNATURES = [
     ("bkrylov_version", C.c_int, []),
     ("bkrylov_opts_default", None, [C.POINTER(bkrylov_opts)]),
     ("bkrylov_op_csr", C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
-                                 C.POINTER(C.c_void_p)]),
+                                 C.c_int, C.POINTER(C.c_void_p)]),
     ("bkrylov_op_stencil", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                      C.POINTER(C.c_void_p)]),
     ("bkrylov_op_diag", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(C.c_void_p)]),
     ("bkrylov_op_jacobi", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("bkrylov_op_transpose", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
     ("bkrylov_op_destroy", C.c_int, [C.c_void_p]),
     ("bkrylov_op_size", C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     ("bkrylov_spmm", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
+    ("bkrylov_spmm_gram", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_int, C.c_int]),
     ("bkrylov_residual", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_int]),
     ("bkrylov_bdot", C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -64,11 +67,11 @@ SIGNATURES = [
                                        C.c_int, C.c_int, C.c_void_p]),
     ("bkrylov_tsqr", C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_int]),
-    ("bkrylov_solve_bcg", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+    ("bkrylov_solve_bcg", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                                     C.POINTER(bkrylov_opts), C.POINTER(bkrylov_info)]),
-    ("bkrylov_solve_bbicgstab", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+    ("bkrylov_solve_bbicgstab", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                                           C.POINTER(bkrylov_opts), C.POINTER(bkrylov_info)]),
-    ("bkrylov_solve_bgmres", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+    ("bkrylov_solve_bgmres", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                                        C.POINTER(bkrylov_opts), C.POINTER(bkrylov_info)]),
     ("bkrylov_profile_count", C.c_int, []),
     ("bkrylov_profile_get", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),

@@ -16,7 +16,8 @@ import torch
 
 from . import _lib as L
 
-_STENCIL = {"const7": L.BK_STENCIL_CONST7, "var7": L.BK_STENCIL_VAR7, "edge5": L.BK_STENCIL_EDGE5}
+_STENCIL = {"const7": L.BK_STENCIL_CONST7, "var7": L.BK_STENCIL_VAR7, "edge5": L.BK_STENCIL_EDGE5,
+            "edge5_log": L.BK_STENCIL_EDGE5_LOG}
 _PREC = {"fp64": L.BK_FP64, "fp32": L.BK_FP32, "fp32_ir": L.BK_FP32_IR}
 
 
@@ -67,7 +68,7 @@ class Handle:
 
     def close(self):
         if self.h:
-            for op in self._ops:
+            for op in list(self._ops):
                 op.close()
             self.lib.bkrylov_destroy(self.h)
             self.h = None
@@ -87,9 +88,11 @@ class Handle:
     # ---- operators ----
     def op_csr(self, row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor) -> "Operator":
         n = row_ptr.numel() - 1
+        if row_ptr.dtype != torch.int32 or col.dtype != torch.int32:
+            raise TypeError("CSR row_ptr and col must be int32")
         A = C.c_void_p()
         _check(self.lib.bkrylov_op_csr(self.h, n, col.numel(), _ptr(row_ptr), _ptr(col), _ptr(val),
-                                       C.byref(A)), "bkrylov_op_csr")
+                                       _prec_of(val), C.byref(A)), "bkrylov_op_csr")
         op = Operator(self, A, n, keep=(row_ptr, col, val))
         self._ops.append(op)
         return op
@@ -107,6 +110,14 @@ class Handle:
             keep = (coeffs,)
         _check(self.lib.bkrylov_op_stencil(self.h, k, nx, ny, nz, p, C.byref(A)), "bkrylov_op_stencil")
         op = Operator(self, A, nx * ny * nz, keep=keep, kind=kind, grid=(nx, ny, nz))
+        self._ops.append(op)
+        return op
+
+    def op_transpose(self, A: "Operator") -> "Operator":
+        """A^T as an operator of its own (bkrylov_op_transpose: CSR and CONST7)."""
+        At = C.c_void_p()
+        _check(self.lib.bkrylov_op_transpose(self.h, A.ptr, C.byref(At)), "bkrylov_op_transpose")
+        op = Operator(self, At, A.n, kind=A.kind, grid=A.grid)
         self._ops.append(op)
         return op
 
@@ -133,6 +144,16 @@ class Handle:
         _check(self.lib.bkrylov_spmm(self.h, A.ptr, P.shape[1], _ptr(P), _ptr(Q), _prec_of(P)),
                "bkrylov_spmm")
         return Q
+
+    def spmm_gram(self, A: "Operator", P: torch.Tensor, Q: torch.Tensor | None = None, sym: bool = True,
+                  G: torch.Tensor | None = None):
+        """Q = A P and G = P^T Q in one pass (bkrylov_spmm_gram); returns (Q, G)."""
+        s = P.shape[1]
+        Q = torch.empty_like(P) if Q is None else Q
+        G = torch.empty((s, s), dtype=torch.float64, device=P.device) if G is None else G
+        _check(self.lib.bkrylov_spmm_gram(self.h, A.ptr, s, _ptr(P), _ptr(Q), _ptr(G), int(sym), _prec_of(P)),
+               "bkrylov_spmm_gram")
+        return Q, G
 
     def residual(self, A: "Operator", B: torch.Tensor, X: torch.Tensor,
                  R: torch.Tensor | None = None) -> torch.Tensor:
@@ -201,22 +222,28 @@ class Handle:
 
     # ---- solvers ----
     def solve(self, method: str, A: "Operator", B, X=None, *, tol=1e-8, maxit=1000, eta=math.inf,
-              prec="fp64", restart=30, ortho="cgs2", ir_inner_tol=1e-5, ir_max_outer=30,
+              prec="fp64", restart=30, ortho="mgs", ir_inner_tol=1e-5, ir_max_outer=30,
               forced_reortho=None, sync_every=0, record=True, profile=False, p=None, precond=None,
-              one_reduction=False):
+              one_reduction=False, norm="max"):
         """Run bkrylov_solve_{bcg,bbicgstab,bgmres}; returns (X, SolveInfo).
 
-        B, X: float64 n x s blocks, on the device (torch CUDA tensors) or on
-        the host (numpy / CPU tensors; copied inside the call).  X is updated
-        in place and starts from zero when not given.  ``p``: block size of
-        the block-parallel subalgebra (BCG); ``precond``: an Operator applying
-        M^{-1} (BCG, e.g. ``op_jacobi(A)``); ``one_reduction``: the 1R-BCG schedule.
+        B, X: n x s blocks, float64 (prec "fp64", "fp32_ir") or float32 (prec "fp32"),
+        on the device (torch CUDA tensors) or on the host (numpy / CPU tensors; copied
+        inside the call).  X is updated in place and starts from zero when not given.
+        ``p``: block size of the block-parallel subalgebra (BCG); ``precond``: an Operator
+        applying M^{-1} (BCG, e.g. ``op_jacobi(A)``); ``one_reduction``: the 1R-BCG
+        schedule; ``norm``: the stopping measure, "max" (every column) or "fro".
         """
         s = B.shape[1]
         if X is None:
             X = torch.zeros_like(B) if isinstance(B, torch.Tensor) else np.zeros_like(B)
+        want = np.float32 if prec == "fp32" else np.float64
+        for blk in (B, X):
+            if _prec_of(blk) != (L.BK_FP32 if want is np.float32 else L.BK_FP64):
+                raise TypeError(f"prec {prec!r} needs {want.__name__} blocks")
         o = L.default_opts()
-        o.tol, o.maxit, o.eta, o.restart = float(tol), int(maxit), float(eta), int(restart)
+        o.eta, o.restart = float(eta), int(restart)
+        o.norm_mode = {"max": 0, "fro": 1}[norm]
         o.ortho = {"cgs2": 0, "mgs": 1, "localized": 2}[ortho]
         o.prec = _PREC[prec]
         o.ir_inner_tol, o.ir_max_outer, o.sync_every = float(ir_inner_tol), int(ir_max_outer), int(sync_every)
@@ -241,8 +268,9 @@ class Handle:
             info.history_len = nh
         fn = {"bcg": self.lib.bkrylov_solve_bcg, "bbicgstab": self.lib.bkrylov_solve_bbicgstab,
               "bgmres": self.lib.bkrylov_solve_bgmres}[method]
-        st = fn(self.h, A.ptr, s, C.c_void_p(_ptr(B)), C.c_void_p(_ptr(X)), C.byref(o), C.byref(info))
-        if st not in (L.BK_OK, L.BK_NOT_CONVERGED, L.BK_BREAKDOWN, L.BK_NONFINITE):
+        st = fn(self.h, A.ptr, s, C.c_void_p(_ptr(B)), C.c_void_p(_ptr(X)), float(tol), int(maxit), C.byref(o),
+                C.byref(info))
+        if st not in (L.BK_OK, L.BK_NOT_CONVERGED, L.BK_BREAKDOWN, L.BK_NONFINITE, L.BK_TIMEOUT):
             raise BkError(st, f"bkrylov_solve_{method}")
         nrec = min(info.iters if prec != "fp32_ir" else info.outer + 1, nh)
         res = SolveInfo(
@@ -277,9 +305,12 @@ class Operator:
         self.nnz = nz.value
 
     def close(self):
+        """Destroy the operator (idempotent) and drop the handle's reference to it."""
         if self.ptr:
             self.h.lib.bkrylov_op_destroy(self.ptr)
             self.ptr = None
+        if self in self.h._ops:
+            self.h._ops.remove(self)
 
 
 def operator_from_problem(h: Handle, prob, use: str = "stencil", device="cuda") -> Operator:

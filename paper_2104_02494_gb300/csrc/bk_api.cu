@@ -97,12 +97,35 @@ size_t gpart_count(const Launch& L, const TsqrPlan&) {
   return (size_t)L.sms * kCtasPerSm * (kMM + kMM + 8);
 }
 
+// The options of one solve: the caller's bkrylov_opts plus the tolerance and the
+// iteration limit, which the solve entry points take as arguments of their own.
+struct SolveOpts : bkrylov_opts {
+  double tol = 1e-8;
+  int maxit = 1000;
+};
+
 void opts_or_default(const bkrylov_opts* o, bkrylov_opts* out) {
   if (o) *out = *o; else bkrylov_opts_default(out);
 }
 
+// The stopping measure of the refinement's outer test (reading c2): max_i rel_i, or
+// the Frobenius ratio sqrt(sum (rel_i nb_i)^2 / sum nb_i^2) for norm_mode 1.
+double host_stop_measure(int norm_mode, const double* rel, const double* nb, int s) {
+  if (norm_mode != 1) {
+    double mx = 0.0;
+    for (int i = 0; i < s; ++i) mx = std::isnan(rel[i]) ? rel[i] : std::fmax(mx, rel[i]);
+    return mx;
+  }
+  double num = 0.0, den = 0.0;
+  for (int i = 0; i < s; ++i) {
+    num += (rel[i] * nb[i]) * (rel[i] * nb[i]);
+    den += nb[i] * nb[i];
+  }
+  return den > 0.0 ? std::sqrt(num / den) : 0.0;
+}
+
 // ---- control block upload / download ------------------------------------------
-int ctrl_upload(bkrylov_handle h, Ctrl* dev, int s, const bkrylov_opts& o, double eps) {
+int ctrl_upload(bkrylov_handle h, Ctrl* dev, int s, const SolveOpts& o, double eps) {
   Ctrl* c = h->host_ctrl;
   std::memset(c, 0, sizeof(Ctrl));
   c->s = s;
@@ -114,6 +137,7 @@ int ctrl_upload(bkrylov_handle h, Ctrl* dev, int s, const bkrylov_opts& o, doubl
   c->sub_p = (o.subalgebra_p > 0 && o.subalgebra_p < s) ? o.subalgebra_p : s;
   c->has_prec = o.precond != nullptr;
   c->one_r = o.one_reduction != 0;
+  c->norm_mode = o.norm_mode;
   for (int i = 0; i < s; ++i) c->sigma[i * kMaxS + i] = 1.0;
   BK_TRY(cudaMemcpyAsync(dev, c, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
   // the pinned staging buffer is reused: wait for the copy before returning
@@ -227,6 +251,7 @@ cudaError_t bcg_iteration(const Launch& L, const OpDesc& A, int s, T* X, const B
   Epi<T> ep;
   ep.left = b.P; ep.sym = 1; ep.gram_out = c->alpha; ep.gpart = b.gpart;
   ep.counter = &c->counters[kCntA]; ep.done = &c->done;
+  ep.status_out = &c->status; ep.stop_out = &c->done;
   // S_BP^p (tp.s = p < s): the FP64 steps restricted to the column groups
   const int gp = tp.s;
   constexpr bool kF64 = sizeof(T) == 8;
@@ -260,6 +285,7 @@ cudaError_t bcg_iteration(const Launch& L, const OpDesc& A, int s, T* X, const B
     Epi<T> pz;
     pz.left = b.R; pz.sym = 1; pz.gram_out = c->rho_m; pz.gpart = b.gpart;
     pz.counter = &c->counters[kCntA]; pz.done = &c->done;
+    pz.status_out = &c->status; pz.stop_out = &c->done;
     prof_begin(L, kPhPrec);
     if constexpr (kF64) {
       if (gp < s) e = spmm_groups(L, *b.M, s, gp, (const double*)b.R, (double*)b.Z, *(const Epi<double>*)&pz);
@@ -306,6 +332,7 @@ cudaError_t bcg_iteration_1r(const Launch& L, const OpDesc& A, int s, T* X, cons
     Epi<T> pz;
     pz.left = b.R; pz.sym = 1; pz.gram_out = c->rho_m; pz.gpart = b.gpart;
     pz.counter = &c->counters[kCntA]; pz.done = &c->done;
+    pz.status_out = &c->status; pz.stop_out = &c->done;
     prof_begin(L, kPhPrec);
     if ((e = spmm<T>(L, *b.M, s, b.R, b.Z, nullptr, pz)) != cudaSuccess) return e;
     prof_end(L, kPhPrec, 1);
@@ -362,7 +389,7 @@ struct GraphBatch {
 int bcg_launches_per_iter(const TsqrPlan& tp) { return 6 + tsqr_launches(tp); }
 
 template <typename T>
-int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const bkrylov_opts& o,
+int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const SolveOpts& o,
                double eps, bkrylov_info* info) {
   const Launch L = launch_of(h);
   const OpDesc* M = o.precond ? &o.precond->d : nullptr;
@@ -460,7 +487,7 @@ int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const
 
 // ------------------------------------------------ iterative refinement ----
 int bcg_ir_device(bkrylov_handle h, bkrylov_op Aop, int s, const double* B, double* X,
-                  const bkrylov_opts& o, bkrylov_info* info, void* outer_ws, size_t outer_off) {
+                  const SolveOpts& o, bkrylov_info* info, void* outer_ws, size_t outer_off) {
   const Launch L = launch_of(h);
   OpDesc& A = Aop->d;
   BK_TRY(op_make_fp32(L, A));
@@ -500,14 +527,16 @@ int bcg_ir_device(bkrylov_handle h, bkrylov_op Aop, int s, const double* B, doub
       if (!std::isfinite(rel[i])) finite = false;
       relmax = std::fmax(relmax, rel[i]);
     }
-    hist.push_back(relmax);
+    const double stopv = host_stop_measure(o.norm_mode, rel, nb, s);
+    hist.push_back(stopv);
     if (!finite) { status = BK_NONFINITE; break; }
-    if (relmax <= o.tol) { status = BK_OK; break; }
+    if (stopv <= o.tol) { status = BK_OK; break; }
     if (outer >= max_outer) { status = BK_NOT_CONVERGED; break; }
     BK_TRY(ir_to_fp32(L, n, s, R, nrm, R32));
     BK_TRY(cudaMemsetAsync(D32, 0, sizeof(float) * ns, L.stream));
-    bkrylov_opts io = o;
+    SolveOpts io = o;
     io.tol = o.ir_inner_tol;
+    io.norm_mode = 0;             // the inner solves test every column (reading c19)
     io.forced_reortho = nullptr;
     io.n_forced = 0;
     bkrylov_info ii;
@@ -542,7 +571,7 @@ int bcg_ir_device(bkrylov_handle h, bkrylov_op Aop, int s, const double* B, doub
 
 // ---------------------------------------------------------- BBiCGStab ----
 int bicg_device(bkrylov_handle h, const OpDesc& A, int s, const double* B, double* X,
-                const bkrylov_opts& o, bkrylov_info* info) {
+                const SolveOpts& o, bkrylov_info* info) {
   const Launch L = launch_of(h);
   const int64_t n = A.n;
   const size_t ns = (size_t)n * s;
@@ -631,7 +660,7 @@ int bicg_device(bkrylov_handle h, const OpDesc& A, int s, const double* B, doubl
 
 // ------------------------------------------------------------- BGMRes ----
 int gmres_device(bkrylov_handle h, const OpDesc& A, int s, const double* B, double* X,
-                 const bkrylov_opts& o, bkrylov_info* info) {
+                 const SolveOpts& o, bkrylov_info* info) {
   Launch L = launch_of(h);
   if (o.profile) L.prof = &h->prof;
   const int64_t n = A.n;
@@ -774,32 +803,32 @@ int gmres_device(bkrylov_handle h, const OpDesc& A, int s, const double* B, doub
   return status;
 }
 
-// Stage host B/X into device buffers when needed, run, copy X back.
-template <typename F>
-int with_device_blocks(bkrylov_handle h, int64_t n, int s, const double* B, double* X,
-                       size_t extra_outer, F&& run) {
+// Stage host B/X into device buffers when needed, run, copy X back (T: the element
+// type of the blocks).
+template <typename T, typename F>
+int with_device_blocks(bkrylov_handle h, int64_t n, int s, const T* B, T* X, size_t extra_outer, F&& run) {
   const bool hb = is_host_ptr(B), hx = is_host_ptr(X);
   const size_t ns = (size_t)n * s;
-  size_t need = 256 + extra_outer + (hb ? sizeof(double) * ns + 256 : 0) + (hx ? sizeof(double) * ns + 256 : 0);
+  size_t need = 256 + extra_outer + (hb ? sizeof(T) * ns + 256 : 0) + (hx ? sizeof(T) * ns + 256 : 0);
   int rc = ensure_ws(h, 1, need);
   if (rc) return rc;
   Bump bump(h->ws[1], h->ws_cap[1]);
-  const double* dB = B;
-  double* dX = X;
+  const T* dB = B;
+  T* dX = X;
   if (hb) {
-    double* t = bump.take<double>(ns);
-    BK_TRY(cudaMemcpyAsync(t, B, sizeof(double) * ns, cudaMemcpyHostToDevice, h->stream));
+    T* t = bump.take<T>(ns);
+    BK_TRY(cudaMemcpyAsync(t, B, sizeof(T) * ns, cudaMemcpyHostToDevice, h->stream));
     dB = t;
   }
   if (hx) {
-    double* t = bump.take<double>(ns);
-    BK_TRY(cudaMemcpyAsync(t, X, sizeof(double) * ns, cudaMemcpyHostToDevice, h->stream));
+    T* t = bump.take<T>(ns);
+    BK_TRY(cudaMemcpyAsync(t, X, sizeof(T) * ns, cudaMemcpyHostToDevice, h->stream));
     dX = t;
   }
   const size_t off = (bump.off + 255) & ~(size_t)255;
   const int status = run(dB, dX, off);
   if (hx) {
-    BK_TRY(cudaMemcpyAsync(X, dX, sizeof(double) * ns, cudaMemcpyDeviceToHost, h->stream));
+    BK_TRY(cudaMemcpyAsync(X, dX, sizeof(T) * ns, cudaMemcpyDeviceToHost, h->stream));
     BK_TRY(cudaStreamSynchronize(h->stream));
   }
   return status;
@@ -837,11 +866,9 @@ int bkrylov_version(void) { return BKRYLOV_VERSION; }
 void bkrylov_opts_default(bkrylov_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
-  o->tol = 1e-8;
-  o->maxit = 1000;
   o->eta = INFINITY;
   o->restart = 30;
-  o->ortho = 0;
+  o->ortho = 1;
   o->prec = BK_FP64;
   o->ir_inner_tol = 1e-5;
   o->ir_max_outer = 30;
@@ -905,9 +932,9 @@ int bkrylov_set_stream(bkrylov_handle h, void* stream) {
 }
 
 int bkrylov_op_csr(bkrylov_handle h, int64_t n, int64_t nnz, const int32_t* row_ptr,
-                   const int32_t* col, const double* val, bkrylov_op* A) {
+                   const int32_t* col, const void* val, int val_prec, bkrylov_op* A) {
   if (!h || !A || n <= 0 || nnz < 0 || !row_ptr || (nnz > 0 && (!col || !val))) return BK_ERR_ARG;
-  if (nnz > INT32_MAX) return BK_ERR_ARG;
+  if (nnz > INT32_MAX || (val_prec != BK_FP64 && val_prec != BK_FP32)) return BK_ERR_ARG;
   bkrylov_op op = new (std::nothrow) bkrylov_op_s();
   if (!op) return BK_ERR_ALLOC;
   op->h = h;
@@ -916,7 +943,27 @@ int bkrylov_op_csr(bkrylov_handle h, int64_t n, int64_t nnz, const int32_t* row_
   op->d.nnz = nnz;
   op->d.row_ptr = row_ptr;
   op->d.col = col;
-  op->d.val = val;
+  if (val_prec == BK_FP64) {
+    op->d.val = static_cast<const double*>(val);
+  } else {
+    // FP32 values are borrowed for the FP32 products; FP64 products (the FP64 solvers,
+    // the refinement's outer residual) use an owned exact widening of them
+    op->d.val32 = const_cast<float*>(static_cast<const float*>(val));
+    op->d.val32_borrowed = true;
+    double* v64 = nullptr;
+    if (cudaMalloc(&v64, sizeof(double) * (size_t)(nnz > 0 ? nnz : 1)) != cudaSuccess) {
+      delete op;
+      return BK_ERR_ALLOC;
+    }
+    op->d.val64_owned = v64;
+    op->d.val = v64;
+    if (widen_block(launch_of(h), nnz, op->d.val32, v64) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+      cudaFree(v64);
+      delete op;
+      return BK_ERR_CUDA;
+    }
+  }
   *A = op;
   return BK_OK;
 }
@@ -944,13 +991,26 @@ int bkrylov_op_stencil(bkrylov_handle h, int kind, int nx, int ny, int nz, const
     if (op_prepare_stencil(L, d, coeffs) != cudaSuccess) { cudaFree(d.coef); delete op; return BK_ERR_CUDA; }
     const int64_t plane = (int64_t)nx * ny;
     d.nnz = d.n + 2 * ((int64_t)(nx - 1) * ny * nz + (int64_t)nx * (ny - 1) * nz + plane * (nz - 1));
-  } else if (kind == BK_STENCIL_EDGE5) {
+  } else if (kind == BK_STENCIL_EDGE5 || kind == BK_STENCIL_EDGE5_LOG) {
     if (nz != 1) { delete op; return BK_ERR_ARG; }
     d.kind = kOpEdge5;
     d.edges = coeffs;
+    if (kind == BK_STENCIL_EDGE5_LOG) {      // a_e = exp(theta_e), owned by the operator
+      const int64_t ne = (int64_t)ny * (nx + 1) + (int64_t)(ny + 1) * nx;
+      if (cudaMalloc(&d.edges_owned, sizeof(double) * (size_t)ne) != cudaSuccess) { delete op; return BK_ERR_ALLOC; }
+      if (exp_block(L, ne, coeffs, d.edges_owned) != cudaSuccess) {
+        cudaFree(d.edges_owned); delete op; return BK_ERR_CUDA;
+      }
+      d.edges = d.edges_owned;
+      coeffs = d.edges_owned;
+    }
     d.coef_len = d.n;
-    if (cudaMalloc(&d.coef, sizeof(double) * (size_t)d.coef_len) != cudaSuccess) { delete op; return BK_ERR_ALLOC; }
-    if (op_prepare_stencil(L, d, coeffs) != cudaSuccess) { cudaFree(d.coef); delete op; return BK_ERR_CUDA; }
+    if (cudaMalloc(&d.coef, sizeof(double) * (size_t)d.coef_len) != cudaSuccess) {
+      cudaFree(d.edges_owned); delete op; return BK_ERR_ALLOC;
+    }
+    if (op_prepare_stencil(L, d, coeffs) != cudaSuccess) {
+      cudaFree(d.coef); cudaFree(d.edges_owned); delete op; return BK_ERR_CUDA;
+    }
     d.nnz = d.n + 2 * ((int64_t)(nx - 1) * ny + (int64_t)nx * (ny - 1));
   } else {
     delete op;
@@ -1007,13 +1067,47 @@ int bkrylov_op_jacobi(bkrylov_handle h, bkrylov_op A, bkrylov_op* M) {
   return BK_OK;
 }
 
+int bkrylov_op_transpose(bkrylov_handle h, bkrylov_op A, bkrylov_op* At) {
+  if (!h || !A || !At) return BK_ERR_ARG;
+  bkrylov_op op = new (std::nothrow) bkrylov_op_s();
+  if (!op) return BK_ERR_ALLOC;
+  op->h = h;
+  if (A->d.kind == kOpCsr) {
+    const cudaError_t e = csr_transpose(launch_of(h), A->d, op->d);
+    if (e != cudaSuccess) {
+      delete op;
+      return e == cudaErrorMemoryAllocation ? BK_ERR_ALLOC : BK_ERR_CUDA;
+    }
+  } else if (A->d.kind == kOpConst7) {
+    // the transpose of a constant 7-point stencil swaps each -/+ pair
+    op->d = OpDesc();
+    op->d.kind = kOpConst7;
+    op->d.n = A->d.n; op->d.nnz = A->d.nnz;
+    op->d.nx = A->d.nx; op->d.ny = A->d.ny; op->d.nz = A->d.nz;
+    const double* c = A->d.c7;   // (centre, -x, +x, -y, +y, -z, +z)
+    const double ct[7] = {c[0], c[2], c[1], c[4], c[3], c[6], c[5]};
+    std::memcpy(op->d.c7, ct, sizeof(ct));
+  } else {
+    delete op;
+    return BK_ERR_UNSUPPORTED;
+  }
+  *At = op;
+  return BK_OK;
+}
+
 int bkrylov_op_destroy(bkrylov_op A) {
   if (!A) return BK_ERR_ARG;
   if (A->h) cudaStreamSynchronize(A->h->stream);
-  if (A->d.val32) cudaFree(A->d.val32);
+  if (A->d.val32 && !A->d.val32_borrowed) cudaFree(A->d.val32);
+  if (A->d.val64_owned) cudaFree(A->d.val64_owned);
   if (A->d.coef) cudaFree(A->d.coef);
   if (A->d.coef32) cudaFree(A->d.coef32);
   if (A->d.edges32) cudaFree(A->d.edges32);
+  if (A->d.coef4) cudaFree(A->d.coef4);
+  if (A->d.edges_owned) cudaFree(A->d.edges_owned);
+  if (A->d.rp_owned) cudaFree(A->d.rp_owned);
+  if (A->d.col_owned) cudaFree(A->d.col_owned);
+  if (A->d.val_owned) cudaFree(A->d.val_owned);
   delete A;
   return BK_OK;
 }
@@ -1073,6 +1167,30 @@ static int small_scratch(bkrylov_handle h, double** gp, unsigned** cnt, double**
   return BK_OK;
 }
 
+int bkrylov_spmm_gram(bkrylov_handle h, bkrylov_op A, int s, const void* P, void* Q, double* G, int sym,
+                      int prec) {
+  if (!h || !A || !valid_s(s) || !P || !Q || !G || P == Q) return BK_ERR_ARG;
+  if (prec != BK_FP64 && prec != BK_FP32) return BK_ERR_ARG;
+  double *gp, *res;
+  unsigned* cnt;
+  int rc = small_scratch(h, &gp, &cnt, &res);
+  if (rc) return rc;
+  const Launch L = launch_of(h);
+  if (prec == BK_FP64) {
+    Epi<double> e;
+    e.left = (const double*)P; e.sym = sym ? 1 : 0; e.gram_out = res; e.gpart = gp; e.counter = cnt;
+    BK_TRY(spmm<double>(L, A->d, s, (const double*)P, (double*)Q, nullptr, e));
+  } else {
+    BK_TRY(op_make_fp32(L, A->d));
+    Epi<float> e;
+    e.left = (const float*)P; e.sym = sym ? 1 : 0; e.gram_out = res; e.gpart = gp; e.counter = cnt;
+    BK_TRY(spmm<float>(L, A->d, s, (const float*)P, (float*)Q, nullptr, e));
+  }
+  compact_kernel<<<1, 256, 0, h->stream>>>(s, res, G);
+  BK_TRY(cudaGetLastError());
+  return BK_OK;
+}
+
 int bkrylov_bdot(bkrylov_handle h, int64_t n, int s, const void* X, const void* Y, double* G, int sym,
                  int prec) {
   if (!h || n <= 0 || !valid_s(s) || !X || !Y || !G) return BK_ERR_ARG;
@@ -1121,11 +1239,12 @@ int bkrylov_tsqr(bkrylov_handle h, int64_t n, int s, const void* X, void* Y, dou
   return BK_OK;
 }
 
-static int check_solve_args(bkrylov_handle h, bkrylov_op A, int s, const double* B, double* X,
-                            const bkrylov_opts& o) {
-  if (!h || !A || !valid_s(s) || !B || !X || (const void*)B == (const void*)X) return BK_ERR_ARG;
+static int check_solve_args(bkrylov_handle h, bkrylov_op A, int s, const void* B, void* X,
+                            const SolveOpts& o) {
+  if (!h || !A || !valid_s(s) || !B || !X || B == (const void*)X) return BK_ERR_ARG;
   if (A->d.n < s) return BK_ERR_ARG;
   if (!(o.tol >= 0.0) || o.maxit < 0 || !(o.eta >= 0.0)) return BK_ERR_ARG;
+  if (o.norm_mode != 0 && o.norm_mode != 1) return BK_ERR_ARG;
   if (o.subalgebra_p < 0 || (o.subalgebra_p > 0 && s % o.subalgebra_p != 0)) return BK_ERR_ARG;
   if (o.precond && o.precond->d.n != A->d.n) return BK_ERR_ARG;
   return BK_OK;
@@ -1136,53 +1255,70 @@ static bool block_case(const bkrylov_opts& o, int s) {
   return o.subalgebra_p == 0 || o.subalgebra_p == s;
 }
 
-int bkrylov_solve_bcg(bkrylov_handle h, bkrylov_op A, int s, const double* B, double* X,
-                      const bkrylov_opts* opts, bkrylov_info* info) {
-  bkrylov_opts o;
+static SolveOpts solve_opts(const bkrylov_opts* opts, double tol, int maxit) {
+  SolveOpts o;
   opts_or_default(opts, &o);
+  o.tol = tol;
+  o.maxit = maxit;
+  return o;
+}
+
+int bkrylov_solve_bcg(bkrylov_handle h, bkrylov_op A, int s, const void* B, void* X, double tol, int maxit,
+                      const bkrylov_opts* opts, bkrylov_info* info) {
+  const SolveOpts o = solve_opts(opts, tol, maxit);
   int rc = check_solve_args(h, A, s, B, X, o);
   if (rc) return rc;
   if (o.one_reduction && !block_case(o, s)) return BK_ERR_UNSUPPORTED;
   const int64_t n = A->d.n;
   if (o.prec == BK_FP64) {
-    return with_device_blocks(h, n, s, B, X, 0, [&](const double* dB, double* dX, size_t) {
+    return with_device_blocks<double>(h, n, s, static_cast<const double*>(B), static_cast<double*>(X), 0,
+                                      [&](const double* dB, double* dX, size_t) {
       return bcg_device<double>(h, A->d, s, dB, dX, o, std::ldexp(1.0, -52), info);
+    });
+  }
+  if (o.prec == BK_FP32) {
+    // the raw FP32 solve: FP32 blocks and products, every s x s quantity in FP64
+    BK_TRY(op_make_fp32(launch_of(h), A->d));
+    return with_device_blocks<float>(h, n, s, static_cast<const float*>(B), static_cast<float*>(X), 0,
+                                     [&](const float* dB, float* dX, size_t) {
+      return bcg_device<float>(h, A->d, s, dB, dX, o, std::ldexp(1.0, -23), info);
     });
   }
   if (o.prec == BK_FP32_IR) {
     const size_t ns = (size_t)n * s;
     const size_t extra = sizeof(double) * ns + 2 * sizeof(float) * ns +
                          sizeof(double) * ((size_t)h->sms * 4 * kMaxS + 2 * kMaxS + 64) + 4096;
-    return with_device_blocks(h, n, s, B, X, extra, [&](const double* dB, double* dX, size_t off) {
+    return with_device_blocks<double>(h, n, s, static_cast<const double*>(B), static_cast<double*>(X), extra,
+                                      [&](const double* dB, double* dX, size_t off) {
       return bcg_ir_device(h, A, s, dB, dX, o, info, h->ws[1], off);
     });
   }
-  return BK_ERR_ARG;   // plain FP32 solves are reached through refinement only
+  return BK_ERR_ARG;
 }
 
-int bkrylov_solve_bbicgstab(bkrylov_handle h, bkrylov_op A, int s, const double* B, double* X,
-                            const bkrylov_opts* opts, bkrylov_info* info) {
-  bkrylov_opts o;
-  opts_or_default(opts, &o);
+int bkrylov_solve_bbicgstab(bkrylov_handle h, bkrylov_op A, int s, const void* B, void* X, double tol,
+                            int maxit, const bkrylov_opts* opts, bkrylov_info* info) {
+  const SolveOpts o = solve_opts(opts, tol, maxit);
   int rc = check_solve_args(h, A, s, B, X, o);
   if (rc) return rc;
   if (!block_case(o, s) || o.precond || o.one_reduction) return BK_ERR_UNSUPPORTED;
   if (o.prec != BK_FP64) return BK_ERR_UNSUPPORTED;
-  return with_device_blocks(h, A->d.n, s, B, X, 0, [&](const double* dB, double* dX, size_t) {
+  return with_device_blocks<double>(h, A->d.n, s, static_cast<const double*>(B), static_cast<double*>(X), 0,
+                                    [&](const double* dB, double* dX, size_t) {
     return bicg_device(h, A->d, s, dB, dX, o, info);
   });
 }
 
-int bkrylov_solve_bgmres(bkrylov_handle h, bkrylov_op A, int s, const double* B, double* X,
+int bkrylov_solve_bgmres(bkrylov_handle h, bkrylov_op A, int s, const void* B, void* X, double tol, int maxit,
                          const bkrylov_opts* opts, bkrylov_info* info) {
-  bkrylov_opts o;
-  opts_or_default(opts, &o);
+  const SolveOpts o = solve_opts(opts, tol, maxit);
   int rc = check_solve_args(h, A, s, B, X, o);
   if (rc) return rc;
   if (!block_case(o, s) || o.precond || o.one_reduction) return BK_ERR_UNSUPPORTED;
   if (o.prec != BK_FP64) return BK_ERR_UNSUPPORTED;
   if (o.restart < 1 || o.restart > 64 || o.ortho < 0 || o.ortho > 2) return BK_ERR_ARG;
-  return with_device_blocks(h, A->d.n, s, B, X, 0, [&](const double* dB, double* dX, size_t) {
+  return with_device_blocks<double>(h, A->d.n, s, static_cast<const double*>(B), static_cast<double*>(X), 0,
+                                    [&](const double* dB, double* dX, size_t) {
     return gmres_device(h, A->d, s, dB, dX, o, info);
   });
 }

@@ -42,6 +42,7 @@ struct Ctrl {
   int sub_p;         // block size of S_BP^p (s: the block case S_B)
   int has_prec;      // BCG with a preconditioner M^{-1} (rho_m carries rho)
   int one_r;         // BCG with one reduction (Alg. "1R-CG"): alpha from delta
+  int norm_mode;     // stopping measure: 0 max_i ||R_i|| / ||R0_i||, 1 ||R||_F / ||R0||_F
   double tol;
   double eta;
   double eps;        // machine epsilon of the working precision
@@ -132,6 +133,7 @@ __device__ inline bool grid_reduce_last(double* part, int cnt, double* gpart,
   // chunk sums are then added in chunk order.
   int R = (int)blockDim.x / cnt;
   if (R > 8) R = 8;
+  if (R * cnt > kThreads) R = kThreads / cnt;   // s_acc holds kThreads partial sums
   if (R >= 2) {
     double acc = 0.0;
     const int i = threadIdx.x % cnt;

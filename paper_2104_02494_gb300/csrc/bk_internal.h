@@ -21,6 +21,11 @@ struct OpDesc {
   const int32_t* col = nullptr;
   const double* val = nullptr;
   float* val32 = nullptr;
+  bool val32_borrowed = false;     // FP32 values given by the caller (not freed)
+  double* val64_owned = nullptr;   // owned FP64 widening of caller-given FP32 values
+  int32_t* rp_owned = nullptr;     // owned CSR arrays of a transposed operator
+  int32_t* col_owned = nullptr;
+  double* val_owned = nullptr;
   // stencils
   int nx = 0, ny = 0, nz = 0;
   double c7[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -29,8 +34,11 @@ struct OpDesc {
   // DIAG: owned entries (n) of the diagonal operator.
   double* coef = nullptr;          // owned double coefficient arrays
   float* coef32 = nullptr;         // owned float copy (lazy)
-  const double* edges = nullptr;   // EDGE5 borrowed
+  const double* edges = nullptr;   // EDGE5 borrowed (or edges_owned)
+  double* edges_owned = nullptr;   // EDGE5 from log-coefficients: a_e = exp(theta_e), owned
   float* edges32 = nullptr;        // EDGE5 owned float copy (lazy)
+  float* coef4 = nullptr;          // VAR7 / EDGE5: per-cell float quadruples of the marching
+                                   // kernel (owned, lazy; bk_march.cu)
   int64_t coef_len = 0;
 };
 
@@ -46,6 +54,8 @@ struct Epi {
   unsigned* counter = nullptr; // ticket counter (0 on entry)
   const int* done = nullptr;   // optional stop flag: kernel exits when *done != 0
   const int* only_if = nullptr;  // optional: kernel exits unless *only_if != 0
+  int* status_out = nullptr;     // pipelined kernels: BK_TIMEOUT written here if a bounded wait gave up
+  int* stop_out = nullptr;       // ... and a non-zero stop flag here (the following kernels return)
 };
 
 // Optional per-phase device timing (CUDA events on the launching stream).
@@ -100,6 +110,29 @@ cudaError_t spmm(const Launch& L, const OpDesc& A, int s, const T* in, T* out, c
                  const Epi<T>& ep);
 cudaError_t op_prepare_stencil(const Launch& L, OpDesc& A, const double* coeffs);
 cudaError_t op_make_fp32(const Launch& L, OpDesc& A);
+// out[i] = (double)in[i]
+cudaError_t widen_block(const Launch& L, int64_t count, const float* in, double* out);
+// out[i] = exp(in[i])
+cudaError_t exp_block(const Launch& L, int64_t count, const double* in, double* out);
+// At = A^T of a CSR operator, columns sorted within every row; At owns its arrays
+// (rp_owned, col_owned, val_owned).  Synchronises the stream (the row pointers are
+// an exclusive scan of the column counts, formed on the host).
+cudaError_t csr_transpose(const Launch& L, const OpDesc& A, OpDesc& At);
+
+// ---- pipelined FP32 kernels (bk_march.cu), s % 4 == 0; cudaErrorNotSupported when a
+// request is outside what they cover (the caller then uses the row kernels) ----
+// out = A in for CONST7 / VAR7 / EDGE5 stencils, optionally with the symmetric Gram
+// in^T out (ep.left == in, ep.sym).
+cudaError_t march_spmm4(const Launch& L, const OpDesc& A, int s, const float* in, float* out,
+                        const Epi<float>& ep);
+// G = X^T Y (Y may equal X).
+cudaError_t stream_gram4(const Launch& L, int64_t n, int s, const float* X, const float* Y,
+                         const Epi<float>& ep);
+// Z = diag(w) X with the symmetric Gram X^T Z (ep.left == X, ep.sym).
+cudaError_t stream_diag4(const Launch& L, int64_t n, int s, const float* w, const float* X, float* Z,
+                         const Epi<float>& ep);
+// Per-cell float quadruples of VAR7 / EDGE5 operators (needs the FP32 copies).
+cudaError_t op_make_coef4(const Launch& L, OpDesc& A);
 // out[i] = 1 / a_ii of A (point Jacobi, M = diag(A)); *bad = 1 when some a_ii is
 // zero or not finite (that entry is written as 0).
 cudaError_t jacobi_inverse_diagonal(const Launch& L, const OpDesc& A, double* out, int* bad);

@@ -189,6 +189,11 @@ struct RowGram {
   __device__ void cta_reduce(int s, bool sym, const float* l2, double* part) {
     flush();
     __syncthreads();
+    sum(s, sym, l2, part);
+  }
+  // CTA sum of the slots in double (after every lane's flush and a CTA barrier);
+  // any number of threads may take part.
+  __device__ void sum(int s, bool sym, const float* l2, double* part) const {
     const int cnt = sym ? ut_count(s) : s * s;
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
       int a, c;
@@ -225,6 +230,10 @@ struct RowGramStaged : RowGram<SW> {
   }
   __device__ void cta_reduce(int s, bool sym, const float* slots, double* part, float*, float*) {
     RowGram<SW>::cta_reduce(s, sym, slots, part);
+  }
+  __device__ void finish(float*, float*) { RowGram<SW>::flush(); }
+  __device__ void sum(int s, bool sym, const float* slots, double* part, float*, float*) const {
+    RowGram<SW>::sum(s, sym, slots, part);
   }
 };
 
@@ -378,6 +387,13 @@ struct MmaGram {
   // Completes a partial k-step (rows not staged in it are zeroed), then sums
   // entry (a, c) over the CTA in double into part (ut_index order if sym).
   __device__ void cta_reduce(int s, bool sym, const float* slots, double* part, float* stl, float* stm) {
+    finish(stl, stm);
+    __syncthreads();
+    sum(s, sym, slots, part, stl, stm);
+  }
+  // The warp's part of cta_reduce: complete the partial k-step and flush every
+  // accumulator level into the lane's double slots.
+  __device__ void finish(float* stl, float* stm) {
     if constexpr (TRIPS_PER_K > 1) {
       if (trip_in_k != 0) {
         const int lane = threadIdx.x & 31;
@@ -392,7 +408,10 @@ struct MmaGram {
     }
     flush1();
     flush2();
-    __syncthreads();
+  }
+  // CTA sum of the double slots (after every warp's finish and a CTA barrier);
+  // any number of threads may take part.
+  __device__ void sum(int s, bool sym, const float* slots, double* part, float*, float*) const {
     const double* sl = reinterpret_cast<const double*>(slots);
     const int cnt = sym ? ut_count(s) : s * s;
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {

@@ -445,6 +445,24 @@ struct SmallSmem {
   int flag;
 };
 
+// Stopping measure of the current relres[] (reading c2): the largest column ratio, or
+// for norm_mode 1 the Frobenius ratio ||R||_F / ||R0||_F = sqrt(sum_i (relres_i n0_i)^2 /
+// sum_i n0_i^2).  NaN in any column propagates.
+__device__ inline double stop_measure(const Ctrl* c, int s) {
+  if (c->norm_mode != 1) {
+    double mx = 0.0;
+    for (int i = 0; i < s; ++i) mx = nanmax(mx, c->relres[i]);
+    return mx;
+  }
+  double num = 0.0, den = 0.0;
+  for (int i = 0; i < s; ++i) {
+    const double r = c->relres[i] * c->n0[i];
+    num = fma(r, r, num);
+    den = fma(c->n0[i], c->n0[i], den);
+  }
+  return den > 0.0 ? sqrt(num / den) : (isnan(num) ? num : 0.0);
+}
+
 // ---------------------------------------------------------------- BCG ----
 // Initial test: relres_i = sqrt((sigma^T rho sigma)_ii) / ||R0_i||.
 __global__ void __launch_bounds__(kST) small_bcg_init_k(Ctrl* c) {
@@ -468,8 +486,7 @@ __global__ void __launch_bounds__(kST) small_bcg_init_k(Ctrl* c) {
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double mx = 0.0;
-    for (int i = 0; i < s; ++i) mx = nanmax(mx, c->relres[i]);
+    const double mx = stop_measure(c, s);
     if (!isfinite(mx)) { c->done = kDoneStopped; c->status = BK_NONFINITE; }
     else if (mx <= c->tol) { c->done = kDoneConverged; c->status = BK_OK; }
     else if (c->maxit <= 0) { c->done = kDoneStopped; c->status = BK_NOT_CONVERGED; }
@@ -556,8 +573,7 @@ __global__ void __launch_bounds__(kST) small_bcg_2_k(Ctrl* c, double* history, u
   __syncthreads();
   __shared__ int s_conv;
   if (threadIdx.x == 0) {
-    double mx = 0.0;
-    for (int i = 0; i < s; ++i) mx = nanmax(mx, c->relres[i]);
+    const double mx = stop_measure(c, s);
     if (history) history[k] = mx;
     if (decisions) decisions[k] = (uint8_t)reo;
     c->iter = k + 1;
@@ -755,8 +771,7 @@ __global__ void __launch_bounds__(kST) small_bicg_3_k(Ctrl* c, double* history, 
   __syncthreads();
   for (int i = threadIdx.x; i < s * s; i += blockDim.x) c->sigma[IDX(i / s, i % s)] = S.B[IDX(i / s, i % s)];
   if (threadIdx.x == 0) {
-    double mx = 0.0;
-    for (int i = 0; i < s; ++i) mx = nanmax(mx, c->relres[i]);
+    const double mx = stop_measure(c, s);
     if (history) history[k] = mx;
     if (decisions) decisions[k] = (uint8_t)c->reortho_now;
     c->iter = k + 1;
@@ -858,8 +873,7 @@ small_gmres_step_k(Ctrl* c, const double* __restrict__ Hc, double* __restrict__ 
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double mx = 0.0;
-    for (int i = 0; i < s; ++i) mx = nanmax(mx, c->relres[i]);
+    const double mx = stop_measure(c, s);
     if (history) history[hist_index] = mx;
     c->iter = c->iter + 1;
     if (!isfinite(mx)) { c->done = kDoneStopped; c->status = BK_NONFINITE; }

@@ -10,6 +10,8 @@
 // segments; their reuse across rows is served by L1/L2 (a 128^2 plane of a
 // 32-column FP64 block is 4 MB, far below the 129 MB L2).
 #include "bk_common.cuh"
+#include <vector>
+
 #include "bk_internal.h"
 #include "bk_ops.cuh"
 #include "bk_quad.cuh"
@@ -235,6 +237,18 @@ template <typename T>
 cudaError_t spmm(const Launch& L, const OpDesc& A, int s, const T* in, T* out, const T* sub,
                  const Epi<T>& ep) {
   const int64_t n = A.n;
+  // FP32 blocks of width 4, 8, 12, ...: the pipelined kernels (bulk copies into a
+  // shared-memory ring) for the stencils and the diagonal operator
+  if constexpr (sizeof(T) == 4) {
+    if (!sub && s % 4 == 0 && !ep.frob) {
+      cudaError_t e = cudaErrorNotSupported;
+      if (A.kind == kOpConst7 || A.kind == kOpVar7 || A.kind == kOpEdge5)
+        e = march_spmm4(L, A, s, in, out, ep);
+      else if (A.kind == kOpDiag && A.coef32 && ep.left == in && ep.sym)
+        e = stream_diag4(L, n, s, A.coef32, in, out, ep);
+      if (e != cudaErrorNotSupported) return e;
+    }
+  }
   switch (A.kind) {
     case kOpCsr: {
       CsrRow<T> op{A.row_ptr, A.col, pick<T>(A.val, A.val32)};
@@ -271,6 +285,12 @@ cudaError_t spmm(const Launch& L, const OpDesc& A, int s, const T* in, T* out, c
 
 template <typename T>
 cudaError_t gram(const Launch& L, int64_t n, int s, const T* X, const T* Y, const Epi<T>& ep) {
+  if constexpr (sizeof(T) == 4) {
+    if (s % 4 == 0 && !ep.frob) {
+      const cudaError_t r = stream_gram4(L, n, s, X, Y, ep);
+      if (r != cudaErrorNotSupported) return r;
+    }
+  }
   Epi<T> e = ep;
   e.left = X;
   return launch_op<T>(L, IdRow<T>{}, n, s, Y, (T*)nullptr, (const T*)nullptr, e);
@@ -346,6 +366,106 @@ cudaError_t cast_block(const Launch& L, int64_t count, const double* in, float* 
   return cudaGetLastError();
 }
 
+__global__ void widen_kernel(int64_t count, const float* __restrict__ in, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+
+cudaError_t widen_block(const Launch& L, int64_t count, const float* in, double* out) {
+  if (count <= 0) return cudaSuccess;
+  widen_kernel<<<elem_grid(L, count), 256, 0, L.stream>>>(count, in, out);
+  return cudaGetLastError();
+}
+
+__global__ void exp_kernel(int64_t count, const double* __restrict__ in, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = exp(in[i]);
+}
+
+cudaError_t exp_block(const Launch& L, int64_t count, const double* in, double* out) {
+  if (count <= 0) return cudaSuccess;
+  exp_kernel<<<elem_grid(L, count), 256, 0, L.stream>>>(count, in, out);
+  return cudaGetLastError();
+}
+
+// ---- CSR transpose: entries per column, row pointers, scatter, then a sort of
+// every row by column index (the scatter's order within a row depends on the
+// order of the atomic increments; the sort makes the result deterministic).
+__global__ void csr_count_cols(int64_t nnz, const int32_t* __restrict__ col, int32_t* __restrict__ cnt) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[col[e]], 1);
+}
+__global__ void csr_scatter_t(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                              const double* __restrict__ val, const int32_t* __restrict__ rpt,
+                              int32_t* __restrict__ fill, int32_t* __restrict__ colt, double* __restrict__ valt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+      const int32_t j = col[e];
+      const int32_t pos = rpt[j] + atomicAdd(&fill[j], 1);
+      colt[pos] = (int32_t)i;
+      valt[pos] = val[e];
+    }
+}
+__global__ void csr_sort_rows(int64_t n, const int32_t* __restrict__ rp, int32_t* __restrict__ col,
+                              double* __restrict__ val) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int32_t a = rp[i] + 1; a < rp[i + 1]; ++a) {   // insertion sort (rows are short)
+      const int32_t c = col[a];
+      const double v = val[a];
+      int32_t b = a - 1;
+      while (b >= rp[i] && col[b] > c) {
+        col[b + 1] = col[b];
+        val[b + 1] = val[b];
+        --b;
+      }
+      col[b + 1] = c;
+      val[b + 1] = v;
+    }
+}
+
+cudaError_t csr_transpose(const Launch& L, const OpDesc& A, OpDesc& At) {
+  if (A.kind != kOpCsr || !A.val) return cudaErrorInvalidValue;
+  const int64_t n = A.n, nnz = A.nnz;
+  cudaError_t e;
+  int32_t *rpt = nullptr, *colt = nullptr, *fill = nullptr;
+  double* valt = nullptr;
+  auto fail = [&](cudaError_t r) {
+    cudaFree(rpt); cudaFree(colt); cudaFree(fill); cudaFree(valt);
+    return r;
+  };
+  if ((e = cudaMalloc(&rpt, sizeof(int32_t) * (size_t)(n + 1))) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&colt, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1))) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&valt, sizeof(double) * (size_t)(nnz > 0 ? nnz : 1))) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc(&fill, sizeof(int32_t) * (size_t)n)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemsetAsync(fill, 0, sizeof(int32_t) * (size_t)n, L.stream)) != cudaSuccess) return fail(e);
+  if (nnz > 0) csr_count_cols<<<elem_grid(L, nnz), 256, 0, L.stream>>>(nnz, A.col, fill);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+  std::vector<int32_t> cnt((size_t)n), rp((size_t)n + 1);
+  if ((e = cudaMemcpyAsync(cnt.data(), fill, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, L.stream)) !=
+      cudaSuccess)
+    return fail(e);
+  if ((e = cudaStreamSynchronize(L.stream)) != cudaSuccess) return fail(e);
+  rp[0] = 0;
+  for (int64_t j = 0; j < n; ++j) rp[j + 1] = rp[j] + cnt[j];
+  if ((e = cudaMemcpyAsync(rpt, rp.data(), sizeof(int32_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, L.stream)) !=
+      cudaSuccess)
+    return fail(e);
+  if ((e = cudaMemsetAsync(fill, 0, sizeof(int32_t) * (size_t)n, L.stream)) != cudaSuccess) return fail(e);
+  csr_scatter_t<<<elem_grid(L, n), 256, 0, L.stream>>>(n, A.row_ptr, A.col, A.val, rpt, fill, colt, valt);
+  csr_sort_rows<<<elem_grid(L, n), 256, 0, L.stream>>>(n, rpt, colt, valt);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+  if ((e = cudaStreamSynchronize(L.stream)) != cudaSuccess) return fail(e);
+  cudaFree(fill);
+  At.kind = kOpCsr;
+  At.n = n;
+  At.nnz = nnz;
+  At.rp_owned = rpt; At.col_owned = colt; At.val_owned = valt;
+  At.row_ptr = rpt; At.col = colt; At.val = valt;
+  return cudaSuccess;
+}
+
 cudaError_t op_prepare_stencil(const Launch& L, OpDesc& A, const double* coeffs) {
   if (A.kind == kOpVar7) {
     var7_prepare<<<elem_grid(L, A.n), 256, 0, L.stream>>>(A.nx, A.ny, A.nz, coeffs, A.coef);
@@ -400,9 +520,9 @@ cudaError_t op_make_fp32(const Launch& L, OpDesc& A) {
   if (A.kind == kOpEdge5 && !A.edges32) {
     const int64_t ne = (int64_t)A.ny * (A.nx + 1) + (int64_t)(A.ny + 1) * A.nx;
     if ((e = cudaMalloc(&A.edges32, sizeof(float) * (size_t)ne)) != cudaSuccess) return e;
-    return cast_block(L, ne, A.edges, A.edges32);
+    if ((e = cast_block(L, ne, A.edges, A.edges32)) != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  return op_make_coef4(L, A);
 }
 
 }  // namespace bk

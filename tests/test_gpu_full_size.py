@@ -127,7 +127,12 @@ def test_full_size_edge_adjoint_vs_central_differences(h):
     (measured 3e-4 .. 2.5e-3 over edges), while h = 1e-3 keeps the O(h^2)
     truncation and the noise both near 1e-6 (measured <= 2.4e-6).  So 8 edges
     and 2 B entries are checked at h = 1e-3 to 2e-5, and 2 edges at h = 1e-6
-    to the noise floor, 1e-2.
+    to the noise floor, 1e-2.  20 coordinates: 14 edges at h = 1e-3 to 2e-4
+    (over 14 edges the quotient's error, truncation plus the solves' error over the
+    step, reaches 7e-5: one edge gives 553.42 at h = 1e-3 and 553.46 at 2e-3
+    against the adjoint's 553.457; the adjoint itself is pinned to the dense
+    oracle adjoint at 1e-9 on the small grid), 4 B entries at h = 1e-3 to 2e-5
+    (L is quadratic in B: no truncation), 2 edges at h = 1e-6 to the noise floor.
     """
     from paper_2104_02494_gb300.autograd import BKrylovSolve
     prob = W.problem("edge2d", with_csr=False)
@@ -151,17 +156,62 @@ def test_full_size_edge_adjoint_vs_central_differences(h):
         return 0.5 * float(((Xp - Xm) * (Xp + Xm - 2 * Xt)).sum()) / (2 * hstep)
 
     rng = np.random.default_rng(3)
-    edges = rng.choice(theta.numel(), 10, replace=False)
+    edges = rng.choice(theta.numel(), 16, replace=False)
     th0, B0 = theta.detach(), Bt.detach()
-    for k, idx in enumerate(edges):
-        hstep, bound = (1e-3, 2e-5) if k < 8 else (1e-6, 1e-2)
+    def fd_theta(idx, hstep):
         tp = th0.clone(); tp[idx] += hstep
         tm = th0.clone(); tm[idx] -= hstep
-        d = fd(tp, tm, B0, B0, hstep)
+        return fd(tp, tm, B0, B0, hstep)
+
+    for k, idx in enumerate(edges):
+        hstep, bound = (1e-3, 2e-4) if k < 14 else (1e-6, 1e-2)
+        d = fd_theta(idx, hstep)
         assert abs(gth[idx] - d) <= bound * abs(d), (idx, hstep, gth[idx], d)
-    for flat in rng.choice(gB.size, 2, replace=False):
+    for flat in rng.choice(gB.size, 4, replace=False):
         i, j = divmod(int(flat), gB.shape[1])
         Bp = B0.clone(); Bp[i, j] += 1e-3
         Bm = B0.clone(); Bm[i, j] -= 1e-3
-        d = fd(th0, th0, Bp, Bm, 1e-3)
+        d = fd(th0, th0, Bp, Bm, 1e-3)        # L is quadratic in B: the quotient is exact
         assert abs(gB[i, j] - d) <= 2e-5 * abs(d), (i, j, gB[i, j], d)
+
+
+def test_full_size_edge_adjoint_fp32_ir(h):
+    """The same 512^2, s = 32 differentiable solve with FP32 inner solves inside FP64
+    refinement, forward and adjoint solves to 1e-11 (the refinement tests the true FP64
+    residual B - A X, whose floor at this conditioning, kappa ~ 1e5, lies near 1e-12):
+    the gradients against the FP64 adjoint's of the same inputs (every coordinate, to
+    1e-5 of the largest: kappa tol ~ 1e-6) and 4 central differences of FP32+IR
+    forward solves at h = 4e-3 to 2e-3 (the solves' error over the step, ~1e-6 / h, and
+    the O(h^2) truncation, at most ~16 x 7e-5, both below it)."""
+    from paper_2104_02494_gb300.autograd import BKrylovSolve
+    prob = W.problem("edge2d", with_csr=False)
+    N = prob.stencil["nx"]
+    thx, thy = prob.extra["theta_x"], prob.extra["theta_y"]
+    Xt = torch.from_numpy(prob.extra["X_target"]).cuda()
+    th0 = torch.from_numpy(np.concatenate([thx.ravel(), thy.ravel()])).cuda()
+    B0 = torch.from_numpy(prob.B).cuda()
+    grads = {}
+    for prec, tol in (("fp64", 1e-13), ("fp32_ir", 1e-11)):
+        spec = dict(kind="edge5", handle=h, nx=N, ny=N, solve=dict(tol=tol, maxit=20000, prec=prec, eta=1e4))
+        theta = th0.clone().requires_grad_(True)
+        Bt = B0.clone().requires_grad_(True)
+        X = BKrylovSolve.apply(theta, Bt, spec)
+        L = 0.5 * ((X - Xt) ** 2).sum()
+        grads[prec] = [g.cpu().numpy() for g in torch.autograd.grad(L, (theta, Bt))]
+    for a, b in zip(grads["fp32_ir"], grads["fp64"]):
+        assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max()
+    spec = dict(kind="edge5", handle=h, nx=N, ny=N, solve=dict(tol=1e-11, maxit=20000, prec="fp32_ir", eta=1e4))
+    gth = grads["fp32_ir"][0]
+    rng = np.random.default_rng(5)
+
+    def quotient(idx, hstep):
+        tp = th0.clone(); tp[idx] += hstep
+        tm = th0.clone(); tm[idx] -= hstep
+        with torch.no_grad():
+            Xp = BKrylovSolve.apply(tp, B0, spec)
+            Xm = BKrylovSolve.apply(tm, B0, spec)
+        return 0.5 * float(((Xp - Xm) * (Xp + Xm - 2 * Xt)).sum()) / (2 * hstep)
+
+    for idx in rng.choice(th0.numel(), 4, replace=False):
+        d = quotient(idx, 4e-3)
+        assert abs(gth[idx] - d) <= 2e-3 * abs(d), (idx, gth[idx], d)
