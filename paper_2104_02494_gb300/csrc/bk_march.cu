@@ -169,7 +169,9 @@ struct MarchPlanEntry {
 // are resident at once (one per SM), and the largest item bounds the time.
 // Cost of an item: its cells times its planes, weighted lightly by the halo
 // share of the copied boxes (read again from L2 by the neighbouring tiles),
-// plus a fixed cost per plane.  Odd segments march downwards, so the two
+// plus a fixed cost per plane (the consumer warps' barrier waits and ring
+// bookkeeping, about the work of 160 cells: small tiles with a few steps per
+// warp and plane ran well below their bandwidth).  Odd segments march downwards, so the two
 // segments on either side of a segment boundary copy the planes next to it at
 // the same time (both at their start or both at their end): the two halo
 // planes of a segment are L2 hits too and cost little.
@@ -226,7 +228,7 @@ static bool plan_march(int gx, int gy, int gz, int s, int cf, int sms, size_t gr
         if ((int64_t)(nseg - 1) * zlen >= gz) continue;
         const double cells = (double)Tx * Ty;
         const double halo = (double)bx * by / cells - 1.0;
-        double cost = cells * zlen * (1.0 + 0.15 * halo) + cells * (nseg > 1 ? 0.6 : 0.0) + 24.0 * (zlen + 2);
+        double cost = cells * zlen * (1.0 + 0.15 * halo) + cells * (nseg > 1 ? 0.6 : 0.0) + 160.0 * (zlen + 2);
         if (ns < 6) cost *= 1.0 + 0.1 * (6 - ns);
         if (cost < best) {
           best = cost;
@@ -287,7 +289,7 @@ __device__ __forceinline__ void gram_epilogue(QuadGram<SW, kPair>& g, double* pa
 
 // One stencil quad (columns 4 qi .. 4 qi + 3) of the cell at box index cidx,
 // summed in the ascending column order of a column-sorted CSR row.
-template <int kOp>
+template <int kOp, bool kHY>
 __device__ __forceinline__ float4 stencil_quad(const MarchArgs& a, int s, const float* sm, const float* sc,
                                                const float* spp, int cidx, int qi) {
   const int o = cidx * s + 4 * qi;
@@ -295,11 +297,11 @@ __device__ __forceinline__ float4 stencil_quad(const MarchArgs& a, int s, const 
   float4 q = zero4();
   if constexpr (kOp == kMConst7) {
     q = fma4(a.c[0], ld4(sm + o), q);
-    if (a.hy) q = fma4(a.c[1], ld4(sc + o - dy), q);
+    if constexpr (kHY) q = fma4(a.c[1], ld4(sc + o - dy), q);
     q = fma4(a.c[2], ld4(sc + o - s), q);
     q = fma4(a.c[3], ld4(sc + o), q);
     q = fma4(a.c[4], ld4(sc + o + s), q);
-    if (a.hy) q = fma4(a.c[5], ld4(sc + o + dy), q);
+    if constexpr (kHY) q = fma4(a.c[5], ld4(sc + o + dy), q);
     q = fma4(a.c[6], ld4(spp + o), q);
   } else if constexpr (kOp == kMVar7) {
     // per cell (diag, fx, fy, fz): faces to the +x, +y, +z neighbour
@@ -308,11 +310,11 @@ __device__ __forceinline__ float4 stencil_quad(const MarchArgs& a, int s, const 
     const int oc = cidx * 4;
     const float4 own = ld4(cc + oc);
     q = fma4(-cm[oc + 3], ld4(sm + o), q);
-    if (a.hy) q = fma4(-cc[oc - a.bx * 4 + 2], ld4(sc + o - dy), q);
+    if constexpr (kHY) q = fma4(-cc[oc - a.bx * 4 + 2], ld4(sc + o - dy), q);
     q = fma4(-cc[oc - 4 + 1], ld4(sc + o - s), q);
     q = fma4(own.x, ld4(sc + o), q);
     q = fma4(-own.y, ld4(sc + o + s), q);
-    if (a.hy) q = fma4(-own.z, ld4(sc + o + dy), q);
+    if constexpr (kHY) q = fma4(-own.z, ld4(sc + o + dy), q);
     q = fma4(-own.w, ld4(spp + o), q);
   } else {
     // 2D per-edge operator, grid (nx, 1, ny): per cell (diag, a of the -x edge,
@@ -330,7 +332,7 @@ __device__ __forceinline__ float4 stencil_quad(const MarchArgs& a, int s, const 
   return q;
 }
 
-template <int SW, int kOp, int kEpi>
+template <int SW, int kOp, int kEpi, bool kHY>
 __global__ void __launch_bounds__(kPipeThreads, 1)
 march4_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmC,
               const MarchArgs a, int s, float* __restrict__ Q, const Epi<float> ep) {
@@ -412,15 +414,19 @@ march4_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ C
     const int nsteps = (cells + 2 * RS - 1) / (2 * RS);
     const int64_t plane = (int64_t)a.gx * a.gy;
     bool alive = mbar_wait(&full[0], 0, &s_abort) && mbar_wait(&full[1], 0, &s_abort);
+    // slots of ring indices i - 1, i, i + 1 and the phase parity of index i + 1,
+    // advanced without divisions
+    int sl_prev = 0, sl_cur = 1, sl_next = 2 % ns;
+    uint32_t ph_next = 0;
     for (int i = 1; i <= nplanes && alive; ++i) {   // ring index of the computed plane
       const int z = down ? z_hi - i : z_lo - 1 + i;
-      if (!mbar_wait(&full[(i + 1) % ns], (uint32_t)((i + 1) / ns) & 1u, &s_abort)) {
+      if (!mbar_wait(&full[sl_next], ph_next, &s_abort)) {
         alive = false;
         break;
       }
-      const float* prev = ring + (size_t)((i - 1) % ns) * a.stage_floats;
-      const float* sc = ring + (size_t)(i % ns) * a.stage_floats;
-      const float* next = ring + (size_t)((i + 1) % ns) * a.stage_floats;
+      const float* prev = ring + (size_t)sl_prev * a.stage_floats;
+      const float* sc = ring + (size_t)sl_cur * a.stage_floats;
+      const float* next = ring + (size_t)sl_next * a.stage_floats;
       const float* sm = down ? next : prev;    // plane z - 1
       const float* spp = down ? prev : next;   // plane z + 1
       float* Qz = Q + (int64_t)z * plane * s;
@@ -434,14 +440,20 @@ march4_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ C
         const int b0 = in0 ? (ty0c + a.hy) * a.bx + tx0c + 1 : a.hy * a.bx + 1;
         const int b1 = in1 ? (ty1c + a.hy) * a.bx + tx1c + 1 : a.hy * a.bx + 1;
         float4 v0 = zero4(), v1 = zero4();
-        if (in0 && qok0) v0 = stencil_quad<kOp>(a, s, sm, sc, spp, b0, q);
-        if (in1 && qok1) v1 = stencil_quad<kOp>(a, s, sm, sc, spp, b1, qb);
+        if (in0 && qok0) v0 = stencil_quad<kOp, kHY>(a, s, sm, sc, spp, b0, q);
+        if (in1 && qok1) v1 = stencil_quad<kOp, kHY>(a, s, sm, sc, spp, b1, qb);
         if (in0 && qok0) st4(Qz + ((int64_t)(ty0 + ty0c) * a.gx + tx0 + tx0c) * s + 4 * q, v0);
         if (in1 && qok1) st4(Qz + ((int64_t)(ty0 + ty1c) * a.gx + tx0 + tx1c) * s + 4 * qb, v1);
         if constexpr (kGram) g.add(sc + b0 * s, sc + b1 * s, v0, v1, s);
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[(i - 1) % ns]);   // ring index i - 1 is no longer read
+      if (lane == 0) mbar_arrive(&empty[sl_prev]);   // ring index i - 1 is no longer read
+      sl_prev = sl_cur;
+      sl_cur = sl_next;
+      if (++sl_next == ns) {
+        sl_next = 0;
+        ph_next ^= 1u;
+      }
     }
     if (!alive) {
       report_timeout(ep.status_out, ep.stop_out);
@@ -593,8 +605,11 @@ stream4_kernel(const float* __restrict__ X, const float* __restrict__ Y, const f
 // s = 4, 8, 16.  A stage is R = 192 nbox rows of each operand, copied as nbox
 // swizzled boxes of 192 rows (rows past n arrive as zeros); six consumer warps
 // take the stage's 32-row groups, warp w computing Gram class w % NCLS.
-constexpr int kRConsumers = 6;
-constexpr int kRThreads = (kRConsumers + 1) * 32;
+// Consumer warps: 9 (three warps of each of three Gram classes at s = 16, or one
+// class), 6 for the full 16-column Gram, whose larger classes need the registers
+// of fewer warps.
+template <int SW, bool kSym>
+__host__ __device__ constexpr int rconsumers() { return (SW == 16 && !kSym) ? 6 : 9; }
 constexpr int kBoxRows = 192;
 
 struct RStreamArgs {
@@ -617,11 +632,15 @@ __device__ __forceinline__ bool rstream_consume(const RStreamArgs& a, const floa
   using C = GramClasses<SW, kSym>;
   constexpr int LPR = SW / 4;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int wpc = kRConsumers / C::NCLS, wic = warp / C::NCLS;
+  constexpr int kNC = rconsumers<SW, kSym>();
+  const int wpc = kNC / C::NCLS, wic = warp / C::NCLS;
   RowGram2<SW, kSym, CLS> g;
   g.init(wslots + (size_t)warp * C::MB * 16);
   bool alive = true;
   const int ngroups = a.R / 32;
+  int off[LPR];
+#pragma unroll
+  for (int q = 0; q < LPR; ++q) off[q] = Swz<SW>::lane_off(lane, q);
   for (int64_t i = 0; i < my_chunks; ++i) {
     const int slot = (int)(i % a.ns);
     if (!mbar_wait(&full[slot], (uint32_t)(i / a.ns) & 1u, abort)) {
@@ -635,10 +654,10 @@ __device__ __forceinline__ bool rstream_consume(const RStreamArgs& a, const floa
       const int r = grp * 32 + lane;
       float4 l[LPR], m[LPR];
 #pragma unroll
-      for (int q = 0; q < LPR; ++q) l[q] = ld4(Swz<SW>::at(sx, r, q));
+      for (int q = 0; q < LPR; ++q) l[q] = ld4(sx + r * SW + off[q]);
       if constexpr (kMode == 0) {
 #pragma unroll
-        for (int q = 0; q < LPR; ++q) m[q] = a.two ? ld4(Swz<SW>::at(sy, r, q)) : l[q];
+        for (int q = 0; q < LPR; ++q) m[q] = a.two ? ld4(sy + r * SW + off[q]) : l[q];
       } else {
         const int64_t row = base + r;
         const float d = row < a.n ? w[row] : 0.f;
@@ -658,16 +677,17 @@ __device__ __forceinline__ bool rstream_consume(const RStreamArgs& a, const floa
 }
 
 template <int SW, int kMode, bool kSym>
-__global__ void __launch_bounds__(kRThreads, 1)
+__global__ void __launch_bounds__((rconsumers<SW, kSym>() + 1) * 32, 1)
 rstream_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
                const float* __restrict__ w, float* __restrict__ Z, const RStreamArgs a, const Epi<float> ep) {
   if (ep.done && *ep.done) return;
   if (ep.only_if && !*ep.only_if) return;
   using C = GramClasses<SW, kSym>;
+  constexpr int kNC = rconsumers<SW, kSym>();
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ int s_abort;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool consumer = warp < kRConsumers;
+  const bool consumer = warp < kNC;
   const int cnt = kSym ? ut_count(SW) : SW * SW;
   double* part = reinterpret_cast<double*>(smem);
   double* wslots = part + ((cnt + 1) & ~1);
@@ -678,7 +698,7 @@ rstream_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
   if (threadIdx.x == 0) {
     for (int k = 0; k < ns; ++k) {
       mbar_init(&full[k], 1);
-      mbar_init(&empty[k], kRConsumers);
+      mbar_init(&empty[k], kNC);
     }
     s_abort = 0;
     mbar_fence_init();
@@ -733,7 +753,7 @@ rstream_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
   }
   __syncthreads();
   const bool aborted = s_abort != 0;
-  row_gram_sum<SW, kSym>(SW, wslots, kRConsumers, part);
+  row_gram_sum<SW, kSym>(SW, wslots, kNC, part);
   if (aborted)
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) part[i] = __longlong_as_double(0x7ff8000000000000ll);
   __syncthreads();
@@ -784,7 +804,7 @@ cudaError_t march_launch(const Launch& L, const OpDesc& A, int s, const float* i
   } else {
     tmC = tmP;
   }
-  auto k = march4_kernel<SW, kOp, kEpi>;
+  auto k = a.hy ? march4_kernel<SW, kOp, kEpi, true> : march4_kernel<SW, kOp, kEpi, false>;
   if ((e = smem_attr(k, smem)) != cudaSuccess) return e;
   k<<<grid, kPipeThreads, smem, L.stream>>>(tmP, tmC, a, s, out, ep);
   return cudaGetLastError();
@@ -867,13 +887,16 @@ cudaError_t rstream_launch(const Launch& L, int64_t n, const float* X, const flo
   RStreamArgs a;
   a.n = n;
   a.s = SW;
-  a.nbox = 32 / SW;                   // 24 KB of each operand per stage
+  // 18-24 KB of each operand per stage, its 6 nbox 32-row groups a multiple of the
+  // warps of a class (3 with three classes, 9 with one, 2 for the full 16-column Gram)
+  a.nbox = SW == 4 ? 6 : (SW == 8 ? 3 : 2);
   a.R = kBoxRows * a.nbox;
   a.nchunks = (n + a.R - 1) / a.R;
   a.two = (kMode == 0 && X != Y) ? 1 : 0;
   a.op_floats = a.R * SW;
   a.stage_floats = a.op_floats * (a.two ? 2 : 1);
-  a.gram_bytes = (int)align_up(sizeof(double) * ((size_t)((cnt + 1) & ~1) + (size_t)kRConsumers * C::MB * 16), 16);
+  constexpr int kNC = rconsumers<SW, kSym>();
+  a.gram_bytes = (int)align_up(sizeof(double) * ((size_t)((cnt + 1) & ~1) + (size_t)kNC * C::MB * 16), 16);
   const size_t fixed = a.gram_bytes + 2 * kMaxStages * sizeof(uint64_t) + kRingAlign;
   int nsg = (int)((kDynSmemMax - fixed) / ((size_t)a.stage_floats * 4));
   a.ns = nsg > 8 ? 8 : nsg;
@@ -892,7 +915,7 @@ cudaError_t rstream_launch(const Launch& L, int64_t n, const float* X, const flo
   const int64_t grid = a.nchunks < L.sms ? a.nchunks : L.sms;
   auto k = rstream_kernel<SW, kMode, kSym>;
   if ((e = smem_attr(k, smem)) != cudaSuccess) return e;
-  k<<<(int)grid, kRThreads, smem, L.stream>>>(tx, ty, w, Z, a, ep);
+  k<<<(int)grid, (kNC + 1) * 32, smem, L.stream>>>(tx, ty, w, Z, a, ep);
   return cudaGetLastError();
 }
 

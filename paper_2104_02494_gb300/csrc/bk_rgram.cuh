@@ -35,6 +35,9 @@ struct Swz {
     return base + r * SW + 4 * chunk(r, q);
   }
   __device__ __forceinline__ static float* at(float* base, int r, int q) { return base + r * SW + 4 * chunk(r, q); }
+  // For rows r = 32 g + lane the swizzle bits of r are those of the lane: the
+  // float offset of chunk q within the row is a per-lane constant.
+  __device__ __forceinline__ static int lane_off(int lane, int q) { return 4 * chunk(lane, q); }
 };
 
 // A class's blocks packed 4 bits each (aq in bits 0-1, cq in bits 2-3), block 0 lowest.
@@ -61,11 +64,12 @@ template <> struct GramClasses<8, false> {
   }
 };
 template <> struct GramClasses<16, true> {
-  static constexpr int NCLS = 2, MB = 5;
-  __host__ __device__ static constexpr int nb(int) { return 5; }
+  static constexpr int NCLS = 3, MB = 4;
+  __host__ __device__ static constexpr int nb(int c) { return c == 0 ? 4 : 3; }
   __host__ __device__ static constexpr uint64_t code(int c) {
-    return c == 0 ? blk4(0, 0, 0) | blk4(0, 1, 1) | blk4(1, 1, 2) | blk4(0, 3, 3) | blk4(1, 3, 4)
-                  : blk4(0, 2, 0) | blk4(1, 2, 1) | blk4(2, 2, 2) | blk4(2, 3, 3) | blk4(3, 3, 4);
+    return c == 0 ? blk4(0, 0, 0) | blk4(0, 1, 1) | blk4(1, 1, 2) | blk4(0, 2, 3)
+           : c == 1 ? blk4(1, 2, 0) | blk4(2, 2, 1) | blk4(0, 3, 2)
+                    : blk4(1, 3, 0) | blk4(2, 3, 1) | blk4(3, 3, 2);
   }
 };
 template <> struct GramClasses<16, false> {
