@@ -29,7 +29,7 @@ rank-deficient right-hand sides, finite differences for the adjoint, and
 planted one-token mistakes that every battery must reject.  Functions without such a pin
 are marked "parity unpinned" in their docstring (none at present).
 """
-from .blockops import (spmm, gram, householder_qr, normalizer, kappa_d, chol_solve,
+from .blockops import (spmm, gram, householder_qr, cholesky_qr2, normalizer, kappa_d, chol_solve,
                        lu_solve, col_norms, reortho_decision, project_subalgebra)
 from .bcg import bcg, bcg_1r, scalar_cg, BCGResult
 from .bbicgstab import bbicgstab
@@ -41,7 +41,7 @@ from .localized import LocalizedArnoldi
 from .adjoint import dense_adjoint, adjoint_scatter, edge_theta_grad
 
 __all__ = [
-    "spmm", "gram", "householder_qr", "normalizer", "kappa_d", "chol_solve", "lu_solve",
+    "spmm", "gram", "householder_qr", "cholesky_qr2", "normalizer", "kappa_d", "chol_solve", "lu_solve",
     "col_norms", "reortho_decision", "project_subalgebra", "bcg", "bcg_1r", "scalar_cg",
     "BCGResult", "bbicgstab", "bgmres", "tsqr", "bcg_ir", "dense_adjoint",
     "adjoint_scatter", "edge_theta_grad", "jacobi_inverse_diagonal", "apply_diagonal", "LocalizedArnoldi",

@@ -144,6 +144,55 @@ def householder_qr(X: np.ndarray):
     return Y * d[None, :], R * d[:, None]
 
 
+def cholesky_qr2(X: np.ndarray, min_sine2: float = 1e-10):
+    """X = Y sigma by CholeskyQR2 (Fukaya, Nakatsukasa, Yanagisawa, Yamamoto,
+    "CholeskyQR2: a simple and communication-avoiding algorithm for computing a
+    tall-skinny QR factorization", 2014), or None when X is too close to rank
+    deficient for it.
+
+    The normalizer (Def. "normalizer") of a full-rank block is unique once
+    diag(sigma) > 0, so any QR method gives it up to rounding; this one runs in
+    two Gram-and-triangular passes:
+        G1 = X^T X,  R1 = chol(G1) (upper, R1^T R1 = G1),  Y1 = X R1^{-1},
+        G2 = Y1^T Y1, R2 = chol(G2),                       Y  = Y1 R2^{-1},
+        sigma = R2 R1.
+    One pass leaves Y1 with an orthogonality error of order eps kappa(X)^2; the
+    second brings it to O(eps) when kappa(X) is well below eps^{-1/2}.  The
+    block is declined (None) unless every pivot of the first Cholesky keeps
+    R1_jj^2 > min_sine2 G1_jj: R1_jj^2 / G1_jj is the squared sine between
+    column j and the span of the columns before it, so rank-deficient and
+    nearly dependent blocks go to the Householder normaliser instead.  The
+    second Cholesky must keep R2_jj^2 > G2_jj / 2 (G2 is then close to I).
+    """
+    X = np.asarray(X, dtype=np.float64)
+    n, s = X.shape
+    if n < s:
+        raise ValueError("cholesky_qr2 needs n >= s")
+
+    def chol_upper(G, floor):
+        R = np.zeros_like(G)
+        for j in range(s):
+            d = G[j, j] - float(np.dot(R[:j, j], R[:j, j]))
+            if not (d > floor * G[j, j]) or not (G[j, j] > 0):
+                return None
+            R[j, j] = math.sqrt(d)
+            for c in range(j + 1, s):
+                R[j, c] = (G[j, c] - float(np.dot(R[:j, j], R[:j, c]))) / R[j, j]
+        return R
+
+    G1 = X.T @ X
+    R1 = chol_upper(G1, min_sine2)
+    if R1 is None:
+        return None
+    Y1 = np.linalg.solve(R1.T, X.T).T          # X R1^{-1}
+    G2 = Y1.T @ Y1
+    R2 = chol_upper(G2, 0.5)
+    if R2 is None:
+        return None
+    Y = np.linalg.solve(R2.T, Y1.T).T
+    return Y, R2 @ R1
+
+
 def normalizer(X: np.ndarray, p: int | None = None):
     """Y, sigma = Norm_S(X) (Def. "normalizer"): Householder QR of every p-column group.
 

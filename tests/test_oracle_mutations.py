@@ -584,3 +584,55 @@ def test_scatter_mutation_is_caught(old, new):
 @pytest.mark.parametrize("old,new", DENSE_ADJOINT_MUTATIONS)
 def test_dense_adjoint_mutation_is_caught(old, new):
     assert not _dense_adjoint_nonsym_passes(_mutant("oracle.adjoint", "dense_adjoint", old, new))
+
+
+# ---- CholeskyQR2 (the fast normaliser) ----------------------------------------------
+def _cholqr_battery_passes(fn):
+    """Householder agreement, orthogonality and the decline test for a CholeskyQR2."""
+    try:
+        g = np.random.default_rng(11)
+        for n, s, cond in ((300, 4, 1e2), (2000, 8, 1e4), (500, 1, 1.0)):
+            U, _ = np.linalg.qr(g.standard_normal((n, s)))
+            V, _ = np.linalg.qr(g.standard_normal((s, s)))
+            X = (U * np.geomspace(1.0, 1.0 / cond, s)) @ V.T
+            out = fn(X)
+            if out is None:
+                return False
+            Y, R = out
+            Yh, Rh = oracle.householder_qr(X)
+            if np.abs(Y.T @ Y - np.eye(s)).max() > 1e-13 or np.abs(Y @ R - X).max() > 1e-13:
+                return False
+            if np.abs(R - Rh).max() > 1e-9 * np.abs(Rh).max():
+                return False
+        Xd = g.standard_normal((100, 4))
+        Xd[:, 2] = Xd[:, 0] + Xd[:, 1]
+        if fn(Xd) is not None:
+            return False
+        # a column at sine ~3e-6 from the span of the others: below the 1e-5 threshold,
+        # declined although CholeskyQR2 would still factor it (kappa ~ 3e5)
+        Xe = g.standard_normal((400, 4))
+        Xe[:, 3] = Xe[:, 1] + 3e-6 * np.linalg.norm(Xe[:, 1]) * g.standard_normal(400) / 20.0
+        if fn(Xe) is not None:
+            return False
+        return True
+    except Exception:
+        return False
+
+
+CHOLQR_MUTATIONS = [
+    ("return Y, R2 @ R1", "return Y, R1 @ R2"),                          # factors in the wrong order
+    ("Y1 = np.linalg.solve(R1.T, X.T).T", "Y1 = np.linalg.solve(R1, X.T).T"),   # dropped transpose
+    ("Y = np.linalg.solve(R2.T, Y1.T).T", "Y = Y1"),                     # second pass dropped
+    ("if not (d > floor * G[j, j])", "if not (d > -1.0)"),             # decline test dropped
+    ("R[j, c] = (G[j, c] - float(np.dot(R[:j, j], R[:j, c]))) / R[j, j]",
+     "R[j, c] = (G[j, c] + float(np.dot(R[:j, j], R[:j, c]))) / R[j, j]"),   # sign of the update
+]
+
+
+def test_unmutated_cholqr_passes_battery():
+    assert _cholqr_battery_passes(oracle.cholesky_qr2)
+
+
+@pytest.mark.parametrize("old,new", CHOLQR_MUTATIONS)
+def test_cholqr_mutation_is_caught(old, new):
+    assert not _cholqr_battery_passes(_mutant("oracle.blockops", "cholesky_qr2", old, new))
