@@ -28,7 +28,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .blockops import (Breakdown, chol_solve, col_norms, gram, kappa_d, normalizer,
+from .blockops import (Breakdown, chol_solve, cholesky_qr2, col_norms, gram, kappa_d, normalizer,
                        project_subalgebra, reortho_decision, spmm, stop_measure)
 from .precond import apply_diagonal
 
@@ -46,12 +46,13 @@ class BCGResult:
     kappas: list = field(default_factory=list)     # kappa_D(alpha^k) when 0 < eta < inf, else None
     alphas: list = field(default_factory=list)     # alpha^k (projected), when record_alpha
     iterates: list = field(default_factory=list)   # X^{k+1} for the first record_iterates steps
+    reorths_cholqr: int = 0          # re-orthonormalisations done by CholeskyQR2 (qr="cholqr2")
 
 
 def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit: int = 1000,
         eta: float = math.inf, p: int | None = None, forced=None, record_iterates: int = 0,
         dtype=np.float64, eps: float | None = None, apply_A=None, Minv=None,
-        record_alpha: bool = False, norm: str = "max") -> BCGResult:
+        record_alpha: bool = False, norm: str = "max", qr: str = "householder") -> BCGResult:
     """Alg. "bcgaro" (2R grouping, Alg. "2R-CG") for A X = B.
 
     A: CSR (attributes n, row_ptr, col, val) or None when ``apply_A`` is given.
@@ -65,9 +66,15 @@ def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit
         V -> M^{-1} V.  M must be symmetric positive definite (Ch. 4).
     norm: the stopping measure, "max" (max-column) or "fro" (Frobenius), see
         ``blockops.stop_measure``; the history records the same measure.
+    qr: the normaliser of the re-orthonormalising iterations (Def. "normalizer"):
+        "householder", or "cholqr2" (``blockops.cholesky_qr2``; the Householder QR for
+        the blocks it declines; block case only).  Both give the unique normalizer of
+        a full-rank block, so they differ by rounding only.
     """
     B = np.asarray(B)
     n, s = B.shape
+    if qr not in ("householder", "cholqr2"):
+        raise ValueError(f"unknown normaliser {qr!r}")
     if eps is None:
         eps = float(np.finfo(dtype).eps)
     op = apply_A if apply_A is not None else (lambda V: spmm(A, V, dtype=dtype))
@@ -118,7 +125,9 @@ def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit
         X += P @ (lam @ sigma).astype(dtype)
         Rt = Rb - Q @ lam.astype(dtype)
         if reo:
-            Rb, gamma = normalizer(Rt, p)
+            fast = cholesky_qr2(Rt) if qr == "cholqr2" and (p is None or p == s) else None
+            Rb, gamma = fast if fast is not None else normalizer(Rt, p)
+            out.reorths_cholqr += fast is not None
             Rb = Rb.astype(dtype)
             sigma = gamma @ sigma
             out.reorths += 1

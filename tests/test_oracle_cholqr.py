@@ -66,3 +66,52 @@ def test_cholqr2_one_pass_is_not_enough():
     assert np.abs(Y1.T @ Y1 - np.eye(6)).max() > 1e-8
     Y, R = oracle.cholesky_qr2(X)
     assert np.abs(Y.T @ Y - np.eye(6)).max() <= 100 * EPS
+
+
+@pytest.mark.parametrize("s", [1, 4, 8])
+def test_bcg_with_cholqr2_normaliser_matches_householder(s):
+    """The normalizer of a full-rank block is unique (Def. "normalizer"), so BCG with the
+    CholeskyQR2 normaliser follows the Householder one iterate for iterate up to
+    rounding, re-orthonormalising in every iteration (eta = inf)."""
+    import workloads as W
+    prob = W.problem("poisson2d", s=s, grid=20)
+    r1 = oracle.bcg(prob.A, prob.B, tol=1e-10, maxit=400, record_iterates=30)
+    r2 = oracle.bcg(prob.A, prob.B, tol=1e-10, maxit=400, record_iterates=30, qr="cholqr2")
+    assert r1.status == r2.status == "ok" and abs(r1.iters - r2.iters) <= 1
+    for a, b in zip(r1.iterates, r2.iterates):
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+    assert r1.decisions == r2.decisions[:len(r1.decisions)]
+
+
+def test_bcg_cholqr2_declines_nearly_dependent_residual_blocks():
+    """Columns 1 and 3 of B differ by 1e-7 relative and the first two iterations keep R
+    as it is (eta = 0 with forced decisions): R-tilde of iteration 2 is then nearly
+    dependent (squared sine ~1e-14), CholeskyQR2 declines it and the Householder QR
+    normalises; every later block is taken by CholeskyQR2.  A block that the normaliser
+    made orthonormal stays far from dependent (its near-dependence moved into sigma)."""
+    import workloads as W
+    prob = W.problem("poisson2d", s=4, grid=16)
+    B = prob.B.copy()
+    B[:, 3] = B[:, 1] + 1e-7 * np.linalg.norm(B[:, 1]) * prob.B[:, 3] / np.linalg.norm(prob.B[:, 3])
+    forced = [False, False] + [True] * 400
+    r1 = oracle.bcg(prob.A, B, tol=1e-9, maxit=400, eta=0.0, forced=forced)
+    r2 = oracle.bcg(prob.A, B, tol=1e-9, maxit=400, eta=0.0, forced=forced, qr="cholqr2")
+    assert r1.status == r2.status == "ok"
+    assert r2.reorths == r1.reorths and r2.reorths_cholqr == r2.reorths - 1
+    X = np.linalg.solve(prob.A.toarray() if hasattr(prob.A, "toarray") else _dense(prob.A), B)
+    for r in (r1, r2):
+        assert np.abs(r.X - X).max() <= 1e-6 * np.abs(X).max()
+    # the well-separated default case: CholeskyQR2 takes every block
+    r3 = oracle.bcg(prob.A, prob.B, tol=1e-9, maxit=400, qr="cholqr2")
+    assert r3.reorths_cholqr == r3.reorths == r3.iters
+    assert oracle.cholesky_qr2(B) is None
+    with pytest.raises(ValueError):
+        oracle.bcg(prob.A, B, qr="gram-schmidt")
+
+
+def _dense(A):
+    D = np.zeros((A.n, A.n))
+    for i in range(A.n):
+        for e in range(A.row_ptr[i], A.row_ptr[i + 1]):
+            D[i, A.col[e]] = A.val[e]
+    return D
