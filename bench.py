@@ -5,8 +5,9 @@ Laplacian on a 128^3 grid (n = 2,097,152), matrix-free stencil, FP64,
 s = 8 right-hand sides drawn N(0,1) (seed 0), block CG with residual-block
 QR stabilisation in every iteration (eta = inf, Alg. "bcgaro" scheduled as
 Alg. "2R-CG").  One step = one BCG iteration: SpMM with the fused alpha Gram,
-s x s solve, fused X/R update, TSQR normaliser (leaf factor, tree, leaf apply,
-rho Gram), s x s step, direction update.
+s x s solve, fused X/R update with the Gram of R-tilde, the normaliser
+(CholeskyQR2: two row passes with their Grams and two s x s factors; the
+Householder TSQR for blocks it declines), s x s step, direction update.
 
   value      RHS*iterations/s = s * K / (device time of K steady-state iterations);
              the K iterations are timed as the difference of two solves with
@@ -14,9 +15,11 @@ rho Gram), s x s step, direction update.
              CUDA events on the library's stream;
   e2e        the same metric through the C ABI with HOST buffers (B and X0 copied
              in, X copied out inside the call), host wall clock around the call;
-  roofline   the dominant kernel phase, timed live with CUDA events (profiled
-             solve), against the FP64 FMA rate of this GPU (the path is bound by
-             FP64 arithmetic at s = 8: the FP64 ridge point is ~0.19 flop/byte);
+  roofline   the dominant single-kernel phase, timed live with CUDA events (profiled
+             solve), against the measured HBM bandwidth or the FP64 FMA rate of this
+             GPU, whichever it comes closer to (the FP64 ridge point is ~0.19
+             flop/byte; the operator and update passes sit near it at s = 8);
+  iteration  the whole iteration's algorithmic FP64 flops and HBM bytes per second;
   cpu_baseline  the FP64 oracle (numpy/scipy) on the host cores, a bounded
              number of iterations of the same workload.
 
@@ -190,21 +193,31 @@ def spmm_alpha_ms(h, op, B, prec, iters=6):
     return float("nan")
 
 
-def iteration_flops(n, s, tp_levels=None):
+def iteration_flops(n, s, cholqr=True):
     """Algorithmic FP64 flops of one BCG iteration (stencil, eta = inf); FMA = 2 flops.
 
     SpMM 7-point 14ns; the Grams alpha and rho (upper triangles) 2 n s(s+1);
     the block updates X += P lx, R -= Q lam, P = R + P beta: 6ns^2; the
-    normaliser, Householder factor 2ns^2 and Q [sigma~; 0] 2ns^2.  The s x s
-    work, the WY factors and the TSQR tree are O(n s^2 / tile) and not counted.
+    normaliser: CholeskyQR2's two passes Y <- Y U^-1 with the Gram Y^T Y, 4 n s(s+1)
+    (its first Gram is rho's), or the Householder factor 2ns^2 and Q [sigma~; 0] 2ns^2.
+    The s x s work, the WY factors and the TSQR tree are O(n s^2 / tile) and not counted.
     """
-    return 14 * n * s + 2 * n * s * (s + 1) + 10 * n * s * s
+    norm = 4 * n * s * (s + 1) if cholqr else 4 * n * s * s
+    return 14 * n * s + 2 * n * s * (s + 1) + 6 * n * s * s + norm
+
+
+def iteration_bytes(n, s, cholqr=True, elem=8):
+    """Algorithmic HBM bytes of one BCG iteration (stencil, eta = inf): the SpMM reads P
+    and writes Q, the update reads P, Q, X, R and writes X, R, the P update reads R, P and
+    writes P, and the normaliser reads and writes the block twice (CholeskyQR2's passes;
+    the Householder TSQR's factor and apply)."""
+    return elem * n * s * (2 + 6 + 3 + 4)
 
 
 PHASE_FLOPS = {
-    # algorithmic flops per launch of each phase, as functions of (n, s)
+    # algorithmic flops per launch of each single-kernel phase, as functions of (n, s)
     "spmm_alpha": lambda n, s: 14 * n * s + n * s * (s + 1),
-    "update_rho": lambda n, s: 4 * n * s * s,
+    "update_rho": lambda n, s: 4 * n * s * s + n * s * (s + 1),
     # Householder QR of the tiles (2 n s^2) and the strict upper triangle of
     # V^T V that defines their compact WY factors (n s (s - 1))
     "tsqr_leaf_factor": lambda n, s: 2 * n * s * s + n * s * (s - 1),
@@ -219,6 +232,10 @@ PHASE_BYTES = {
     "tsqr_leaf_apply": lambda n, s: 2 * 8 * n * s,
     "p_update": lambda n, s: 3 * 8 * n * s,
 }
+# The CholeskyQR2 phase per iteration: two row passes (read + write of the block, the
+# triangular product and the Gram, 2 n s(s+1) flops each) and two one-CTA s x s kernels.
+PHASE_ITER_FLOPS = {"cholqr": lambda n, s: 4 * n * s * (s + 1)}
+PHASE_ITER_BYTES = {"cholqr": lambda n, s: 4 * 8 * n * s}
 
 
 class Clocks:
@@ -680,9 +697,11 @@ def run_sweep(h, args, prob, torch):
             kk = 10
             m2 = time_iters(h, op, B2, ss, 3, kk, torch)
             fl = iteration_flops(n, ss)
+            by_it = iteration_bytes(n, ss) + (prob.A.nnz * 12 + 4 * (n + 1) if use == "csr" else 0)
             e = {"rhs_iter_per_s": ss * kk / (m2 / 1000.0), "ms_per_iter": m2 / kk,
                  "fp64_tflops": fl / (m2 / kk / 1000.0) / 1e12}
             e["fp64_frac"] = e["fp64_tflops"] / FP64_PEAK_TFLOPS
+            e["hbm_frac"] = by_it / (m2 / kk / 1000.0) / 1e9 / HBM_PEAK_GBS
             P32 = B2.float()
             Q32 = torch.empty_like(P32)
             G = torch.empty(ss, ss, dtype=torch.float64, device="cuda")
@@ -787,16 +806,33 @@ def main():
     tot = sum(t for _, t, _ in prof)
     phases = {nm: {"ms_per_launch": t / max(nl, 1) * (1 if nm != "tsqr_tree" else 1), "share": t / tot,
                    "launches": nl} for nm, t, nl in prof}
+    # the dominant single-kernel phase (one launch per iteration), against whichever of the
+    # FP64 pipe and HBM it comes closer to
     dom = max((p for p in prof if p[0] in PHASE_FLOPS), key=lambda p: p[1])
     dom_ms = dom[1] / max(dom[2], 1)
-    flops = PHASE_FLOPS[dom[0]](n, s)
-    achieved = flops / (dom_ms / 1000.0) / 1e12
+    tfl = PHASE_FLOPS[dom[0]](n, s) / (dom_ms / 1000.0) / 1e12
+    gbs = PHASE_BYTES[dom[0]](n, s) / (dom_ms / 1000.0) / 1e9
     traffic = NCU_TRAFFIC.get((dom[0], args.grid, s, args.op))
-    roofline = {"bound": "alu", "kernel": dom[0], "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "traffic_unit": "bytes per launch (ncu dram read + write)" if traffic else None,
-                "peak_source": "derived: 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop",
-                "hbm_achieved_gbs": PHASE_BYTES[dom[0]](n, s) / (dom_ms / 1000.0) / 1e9}
+    if gbs / HBM_PEAK_GBS >= tfl / FP64_PEAK_TFLOPS:
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                    "frac": gbs / HBM_PEAK_GBS, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                    "fp64_tflops": tfl, "fp64_frac": tfl / FP64_PEAK_TFLOPS}
+    else:
+        roofline = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tfl / FP64_PEAK_TFLOPS,
+                    "peak_source": "derived: 152 SMs x 2.07 GHz x 2 DFMA/clk/SM x 2 flop",
+                    "hbm_achieved_gbs": gbs, "hbm_frac": gbs / HBM_PEAK_GBS}
+    roofline.update({"kernel": dom[0], "ms_per_launch": dom_ms, "traffic": traffic,
+                     "traffic_unit": "bytes per launch (ncu dram read + write)" if traffic else None})
+    for nm, t_ms, nl in prof:
+        if nm in PHASE_ITER_BYTES and nm in phases:
+            per_it = t_ms / K
+            phases[nm]["ms_per_iter"] = per_it
+            phases[nm]["hbm_frac"] = PHASE_ITER_BYTES[nm](n, s) / (per_it / 1000.0) / 1e9 / HBM_PEAK_GBS
+    iteration = {"ms": ms / K, "fp64_tflops": iteration_flops(n, s) / (ms / K / 1000.0) / 1e12,
+                 "hbm_gbs": iteration_bytes(n, s) / (ms / K / 1000.0) / 1e9}
+    iteration["fp64_frac"] = iteration["fp64_tflops"] / FP64_PEAK_TFLOPS
+    iteration["hbm_frac"] = iteration["hbm_gbs"] / HBM_PEAK_GBS
 
     # end to end through the C ABI with host buffers
     Bh = np.ascontiguousarray(prob.B)
@@ -818,7 +854,7 @@ def main():
         cpu = cpu_baseline(prob, s, iters=3)
         cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
-    launches = _lib.load().bkrylov_bcg_launches_per_iteration(n, s) * K
+    launches = _lib.load().bkrylov_bcg_launches_per_iteration(n, s, None) * K
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
                 "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
@@ -826,8 +862,8 @@ def main():
                 "config": {"workload": f"laplace3d {args.grid}^3 7-point, {args.op}, s={s}, BCG eta=inf",
                            "n": n, "s": s, "l2": "inputs larger than L2 (each n x s block 134 MB)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
-                           "fp64_tflops_per_iter": iteration_flops(n, s) / (ms / K / 1000.0) / 1e12},
-                "roofline": roofline, "phases": phases, "cpu_baseline": cpu, "e2e": e2e,
+                           "normaliser": "CholeskyQR2 (Householder TSQR for declined blocks)"},
+                "iteration": iteration, "roofline": roofline, "phases": phases, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk.summary(), "gpu_launches": launches}
         if sweep:
             line["sweep"] = sweep

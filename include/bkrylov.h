@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define BKRYLOV_VERSION 200
+#define BKRYLOV_VERSION 201
 #define BKRYLOV_MAX_S 32
 
 typedef struct bkrylov_ctx* bkrylov_handle;   /* owns workspace + stream binding */
@@ -132,6 +132,15 @@ typedef struct {
                           default two-reduction schedule (Alg. "2R-CG") at two more block
                           vectors and one more block update per iteration.  Needs the
                           block case (BK_ERR_UNSUPPORTED with subalgebra_p < s)     (0) */
+  int qr_mode;         /* normaliser of the re-orthonormalising BCG iterations (Def.
+                          "normalizer", Ch. 3.1): 0 = CholeskyQR2 (Fukaya et al. 2014: two
+                          passes Y <- Y U^-1 with U the Cholesky factor of the Gram, the first
+                          Gram fused into the block update) wherever the first Gram's pivots
+                          all keep U_kk^2 > 1e-10 G_kk, the Householder TSQR (Ch. 7.3) for the
+                          other blocks (nearly dependent or rank deficient) and when the
+                          second factor fails; used by FP64 two-reduction BCG in the block
+                          case, the other solves always take the TSQR.  1 = the Householder
+                          TSQR in every iteration.  Other values: BK_ERR_ARG       (0)    */
 } bkrylov_opts;
 
 /* Solver report.  Pointer members are HOST arrays supplied by the caller (or NULL). */
@@ -148,6 +157,8 @@ typedef struct {
   uint8_t* decisions;  /* [maxit]  re-orthonormalised in iteration k?, or NULL          */
   int history_len;     /* capacity of history/decisions (entries written <= this)      */
   double elapsed_ms;   /* device time of the solve (CUDA events)                      */
+  int reorths_cholqr;  /* of reorths, those normalised by CholeskyQR2 (qr_mode 0; the
+                          others by the Householder TSQR)                             */
 } bkrylov_info;
 
 /* ---- handle ------------------------------------------------------------------ */
@@ -293,8 +304,11 @@ int bkrylov_kappa_d(bkrylov_handle h, int s, const double* A, double* kappa);
    than 1 % off the threshold that decides, otherwise the FP64 kappa_D of bkrylov_kappa_d does.
    A: DEVICE s x s symmetric, row-major; decision: DEVICE int.  Enqueued on the stream. */
 int bkrylov_reortho_decision(bkrylov_handle h, int s, const double* A, double eta, double eps, int* decision);
-/* Kernel launches of one BCG iteration for an n x s block (host-only, no GPU). */
-int bkrylov_bcg_launches_per_iteration(int64_t n, int s);
+/* Kernel launches of one BCG iteration for an n x s block with the options opts (NULL:
+   the defaults); host-only, no GPU.  Kernels whose device-side condition is not met
+   (the TSQR when the CholeskyQR2 normaliser was taken) are launched and return at once,
+   and are counted. */
+int bkrylov_bcg_launches_per_iteration(int64_t n, int s, const bkrylov_opts* opts);
 
 /* ---- adjoint (reverse-mode derivative of X = A^{-1} B) ----------------------------- */
 /* For a CSR operator: g[e] = -sum_k Lam[i,k] X[j,k] for every stored entry e = (i, j),

@@ -27,6 +27,7 @@ class bkrylov_opts(C.Structure):
         ("ir_max_outer", C.c_int), ("forced_reortho", C.POINTER(C.c_uint8)), ("n_forced", C.c_int),
         ("sync_every", C.c_int), ("profile", C.c_int), ("subalgebra_p", C.c_int),
         ("precond", C.c_void_p), ("norm_mode", C.c_int), ("one_reduction", C.c_int),
+        ("qr_mode", C.c_int),
     ]
 
 
@@ -35,7 +36,7 @@ class bkrylov_info(C.Structure):
         ("iters", C.c_int), ("reorths", C.c_int), ("converged", C.c_int), ("status", C.c_int),
         ("outer", C.c_int), ("relres_max", C.c_double), ("relres", C.POINTER(C.c_double)),
         ("history", C.POINTER(C.c_double)), ("decisions", C.POINTER(C.c_uint8)),
-        ("history_len", C.c_int), ("elapsed_ms", C.c_double),
+        ("history_len", C.c_int), ("elapsed_ms", C.c_double), ("reorths_cholqr", C.c_int),
     ]
 
 
@@ -80,7 +81,7 @@ SIGNATURES = [
     ("bkrylov_kappa_d", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     ("bkrylov_reortho_decision", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_double, C.c_double,
                                            C.c_void_p]),
-    ("bkrylov_bcg_launches_per_iteration", C.c_int, [C.c_int64, C.c_int]),
+    ("bkrylov_bcg_launches_per_iteration", C.c_int, [C.c_int64, C.c_int, C.c_void_p]),
     ("bkrylov_adjoint_scatter", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                           C.c_void_p]),
     ("bkrylov_edge_theta_grad", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,

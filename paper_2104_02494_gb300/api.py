@@ -224,7 +224,7 @@ class Handle:
     def solve(self, method: str, A: "Operator", B, X=None, *, tol=1e-8, maxit=1000, eta=math.inf,
               prec="fp64", restart=30, ortho="mgs", ir_inner_tol=1e-5, ir_max_outer=30,
               forced_reortho=None, sync_every=0, record=True, profile=False, p=None, precond=None,
-              one_reduction=False, norm="max"):
+              one_reduction=False, norm="max", qr="cholqr2"):
         """Run bkrylov_solve_{bcg,bbicgstab,bgmres}; returns (X, SolveInfo).
 
         B, X: n x s blocks, float64 (prec "fp64", "fp32_ir") or float32 (prec "fp32"),
@@ -232,7 +232,9 @@ class Handle:
         inside the call).  X is updated in place and starts from zero when not given.
         ``p``: block size of the block-parallel subalgebra (BCG); ``precond``: an Operator
         applying M^{-1} (BCG, e.g. ``op_jacobi(A)``); ``one_reduction``: the 1R-BCG
-        schedule; ``norm``: the stopping measure, "max" (every column) or "fro".
+        schedule; ``norm``: the stopping measure, "max" (every column) or "fro"; ``qr``:
+        the normaliser of FP64 BCG, "cholqr2" (CholeskyQR2, Householder TSQR for the
+        blocks it declines) or "householder" (TSQR every time).
         """
         s = B.shape[1]
         if X is None:
@@ -251,6 +253,7 @@ class Handle:
         o.subalgebra_p = 0 if p is None else int(p)
         o.precond = None if precond is None else precond.ptr.value
         o.one_reduction = 1 if one_reduction else 0
+        o.qr_mode = {"cholqr2": 0, "householder": 1}[qr]
         forced_arr = None
         if forced_reortho is not None:
             forced_arr = (C.c_uint8 * max(1, len(forced_reortho)))(*[1 if f else 0 for f in forced_reortho])
@@ -278,7 +281,7 @@ class Handle:
             converged=bool(info.converged), outer=info.outer, relres_max=info.relres_max,
             relres=np.array(relres[:s]), history=list(hist[:nrec]) if record else [],
             decisions=[bool(d) for d in dec[:nrec]] if record and prec != "fp32_ir" else [],
-            elapsed_ms=info.elapsed_ms)
+            elapsed_ms=info.elapsed_ms, reorths_cholqr=info.reorths_cholqr)
         return X, res
 
 
@@ -295,6 +298,7 @@ class SolveInfo:
     history: list = field(default_factory=list)
     decisions: list = field(default_factory=list)
     elapsed_ms: float = 0.0
+    reorths_cholqr: int = 0          # re-orthonormalisations done by CholeskyQR2
 
 
 class Operator:

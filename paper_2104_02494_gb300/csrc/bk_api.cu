@@ -33,7 +33,7 @@ struct bkrylov_ctx {
 const char* const bk::kPhaseNames[kNumPhases] = {
     "spmm_alpha", "small_1", "update_rho", "tsqr_leaf_factor", "tsqr_tree", "tsqr_leaf_apply",
     "tsqr_rho_gram", "small_2", "p_update", "precond_rho", "gmres_orthogonalise", "localized_tree",
-    "localized_assemble"};
+    "localized_assemble", "cholqr"};
 
 struct bkrylov_op_s {
   bkrylov_handle h = nullptr;
@@ -179,6 +179,7 @@ int finish_info(bkrylov_handle h, const Ctrl* dev, int s, const double* hist_dev
     if (info->decisions && dec_dev && nh > 0)
       BK_TRY(cudaMemcpy(info->decisions, dec_dev, nh, cudaMemcpyDeviceToHost));
     info->elapsed_ms = ms;
+    info->reorths_cholqr = c->cholqr_count;
     (void)nrec;
   }
   return status;
@@ -197,6 +198,7 @@ struct BcgBufs {
   double* hist;
   uint8_t* dec;
   uint8_t* forced;
+  bool cholqr = false;         // FP64 block case: CholeskyQR2 normaliser, TSQR the fallback
 };
 
 template <typename T, typename Alloc>
@@ -271,15 +273,30 @@ cudaError_t bcg_iteration(const Launch& L, const OpDesc& A, int s, T* X, const B
   if constexpr (kF64) {
     if (gp < s) e = bcg_update_groups(L, A.n, s, gp, (const double*)b.P, (const double*)b.Q, (double*)X,
                                       (double*)b.R, c, b.gpart, 1);
-    else e = bcg_update<T>(L, A.n, s, b.P, b.Q, X, b.R, c, b.gpart, 1);
+    else e = bcg_update<T>(L, A.n, s, b.P, b.Q, X, b.R, c, b.gpart, b.cholqr ? 2 : 1);
   } else {
     e = bcg_update<T>(L, A.n, s, b.P, b.Q, X, b.R, c, b.gpart, 1);
   }
   if (e != cudaSuccess) return e;
-  prof_end(L, kPhUpdate, 2);
+  prof_end(L, kPhUpdate, b.cholqr ? 1 : 2);
+  if constexpr (kF64) {
+    if (b.cholqr) {
+      // CholeskyQR2 of R-tilde from the update's Gram; the device declines nearly
+      // dependent blocks (then tsqr_now is set and the TSQR below normalises).  Without
+      // a preconditioner the second row pass is folded into the direction update.
+      prof_begin(L, kPhCholqr);
+      if ((e = small_cholqr(L, c, 1)) != cudaSuccess) return e;
+      if ((e = cholqr_pass(L, A.n, s, (double*)b.R, c, b.gpart, true)) != cudaSuccess) return e;
+      if ((e = small_cholqr(L, c, 2)) != cudaSuccess) return e;
+      if (b.M && (e = cholqr_pass(L, A.n, s, (double*)b.R, c, b.gpart, false)) != cudaSuccess) return e;
+      prof_end(L, kPhCholqr, b.M ? 4 : 3);
+    }
+  }
   // preconditioned: after a re-orthonormalisation only rho = <Z, R-bar> is needed
   if ((e = tsqr_groups<T>(L, tp, s, b.R, c->gamma, b.M ? nullptr : c->rho_new, b.tsqr, b.gpart,
-                          &c->counters[kCntC], &c->done, &c->reortho_now)) != cudaSuccess) return e;
+                          &c->counters[kCntC], &c->done, b.cholqr ? &c->tsqr_now : &c->reortho_now)) !=
+      cudaSuccess)
+    return e;
   if (b.M) {
     // Z = M^{-1} R-bar and rho_m = R-bar^T Z in one fused operator pass
     Epi<T> pz;
@@ -303,6 +320,7 @@ cudaError_t bcg_iteration(const Launch& L, const OpDesc& A, int s, T* X, const B
   prof_begin(L, kPhPupdate);
   if constexpr (kF64) {
     if (gp < s) e = bcg_pupdate_groups(L, A.n, s, gp, (const double*)Zn, (double*)b.P, c);
+    else if (b.cholqr && !b.M) e = cholqr_pupdate(L, A.n, s, (double*)b.R, (double*)b.P, c);
     else e = bcg_pupdate<T>(L, A.n, s, Zn, b.P, c);
   } else {
     e = bcg_pupdate<T>(L, A.n, s, Zn, b.P, c);
@@ -385,8 +403,18 @@ struct GraphBatch {
   }
 };
 
-// launches of one iteration (the TSQR tree has 2 * levels + 1 launches)
-int bcg_launches_per_iter(const TsqrPlan& tp) { return 6 + tsqr_launches(tp); }
+// launches of one two-reduction iteration (the TSQR has 2 * levels + 3 launches): the
+// SpMM, two s x s kernels, the update (lean and Gram-carrying, or the Gram-carrying one
+// alone with CholeskyQR2, which adds two s x s kernels and one row pass, two with M) and
+// the direction update, plus the preconditioner pass
+int bcg_launches_per_iter(const TsqrPlan& tp, bool cholqr, bool prec) {
+  return (cholqr ? (prec ? 9 : 8) : 6) + (prec ? 1 : 0) + tsqr_launches(tp);
+}
+
+// The CholeskyQR2 normaliser serves FP64 two-reduction BCG in the block case
+bool use_cholqr(const bkrylov_opts& o, int s, bool f64) {
+  return f64 && o.qr_mode == 0 && (o.subalgebra_p == 0 || o.subalgebra_p == s) && !o.one_reduction;
+}
 
 template <typename T>
 int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const SolveOpts& o,
@@ -408,6 +436,7 @@ int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const
   Bump bump(h->ws[0], h->ws_cap[0]);
   bcg_layout<T>(bump, n, s, maxit, tp, L, &b, M != nullptr, one_r);
   b.M = M;
+  b.cholqr = use_cholqr(o, s, sizeof(T) == 8);
   if ((rc = ctrl_upload(h, b.ctrl, s, o, eps))) return rc;
   if (o.forced_reortho && o.n_forced > 0) {
     const int nf = o.n_forced < maxit + 1 ? o.n_forced : maxit + 1;
@@ -1245,6 +1274,7 @@ static int check_solve_args(bkrylov_handle h, bkrylov_op A, int s, const void* B
   if (A->d.n < s) return BK_ERR_ARG;
   if (!(o.tol >= 0.0) || o.maxit < 0 || !(o.eta >= 0.0)) return BK_ERR_ARG;
   if (o.norm_mode != 0 && o.norm_mode != 1) return BK_ERR_ARG;
+  if (o.qr_mode != 0 && o.qr_mode != 1) return BK_ERR_ARG;
   if (o.subalgebra_p < 0 || (o.subalgebra_p > 0 && s % o.subalgebra_p != 0)) return BK_ERR_ARG;
   if (o.precond && o.precond->d.n != A->d.n) return BK_ERR_ARG;
   return BK_OK;
@@ -1352,9 +1382,11 @@ int bkrylov_reortho_decision(bkrylov_handle h, int s, const double* A, double et
   return BK_OK;
 }
 
-int bkrylov_bcg_launches_per_iteration(int64_t n, int s) {
+int bkrylov_bcg_launches_per_iteration(int64_t n, int s, const bkrylov_opts* opts) {
   if (n < 1 || s < 1 || s > kMaxS) return -1;
-  return bcg_launches_per_iter(tsqr_plan(n, s));
+  bkrylov_opts o;
+  opts_or_default(opts, &o);
+  return bcg_launches_per_iter(tsqr_plan(n, s), use_cholqr(o, s, o.prec == BK_FP64), o.precond != nullptr);
 }
 
 int bkrylov_adjoint_scatter(bkrylov_handle h, bkrylov_op A, int s, const double* Lam,

@@ -43,6 +43,10 @@ struct Ctrl {
   int has_prec;      // BCG with a preconditioner M^{-1} (rho_m carries rho)
   int one_r;         // BCG with one reduction (Alg. "1R-CG"): alpha from delta
   int norm_mode;     // stopping measure: 0 max_i ||R_i|| / ||R0_i||, 1 ||R||_F / ||R0||_F
+  int qr_fast;       // CholeskyQR2 normaliser of this iteration: 0 not taken (declined or no
+                     // re-orthonormalisation), 1 taken, 2 second factor failed (TSQR of Y1)
+  int tsqr_now;      // the Householder TSQR runs in this iteration
+  int cholqr_count;  // re-orthonormalisations normalised by CholeskyQR2
   double tol;
   double eta;
   double eps;        // machine epsilon of the working precision
@@ -65,6 +69,8 @@ struct Ctrl {
   double g3[kMM];        // BBiCGStab R0s^T U
   double lu[kMM];        // BBiCGStab LU factors of R0s^T Q
   double sigma_new[kMM]; // BBiCGStab sigma^{k+1}
+  double cq_u1[kMM];     // CholeskyQR2: first upper Cholesky factor U1 (G1 = U1^T U1)
+  double cq_inv[kMM];    // CholeskyQR2: inverse of the factor of the current pass
   int piv[kMaxS];
   double nb[kMaxS];      // refinement: ||B_i||
 };

@@ -61,7 +61,7 @@ struct Epi {
 // Optional per-phase device timing (CUDA events on the launching stream).
 enum Phase : int {
   kPhSpmm = 0, kPhSmall1, kPhUpdate, kPhTsqrLeaf, kPhTsqrTree, kPhTsqrApply, kPhTsqrGram,
-  kPhSmall2, kPhPupdate, kPhPrec, kPhOrtho, kPhLaTree, kPhLaAssemble, kNumPhases
+  kPhSmall2, kPhPupdate, kPhPrec, kPhOrtho, kPhLaTree, kPhLaAssemble, kPhCholqr, kNumPhases
 };
 struct Prof {
   static constexpr int kMax = 16;
@@ -231,6 +231,13 @@ cudaError_t tsqr(const Launch& L, const TsqrPlan& plan, const T* X, T* Y, double
 cudaError_t small_bcg_init(const Launch& L, Ctrl* ctrl, int eta_positive);
 cudaError_t small_bcg_1(const Launch& L, Ctrl* ctrl, const uint8_t* forced);
 cudaError_t small_bcg_2(const Launch& L, Ctrl* ctrl, double* history, uint8_t* decisions);
+// CholeskyQR2 normaliser of BCG (FP64 block case): the s x s factor of pass 1 or 2
+// (pass 1 declines nearly dependent blocks, pass 2 falls back to the TSQR on failure),
+// the row pass Y <- Y U^{-1} (with rho_new = Y^T Y when gram), and the direction update
+// P <- R-bar + P beta with the second pass R-bar = Y1 U2^{-1} folded in.
+cudaError_t small_cholqr(const Launch& L, Ctrl* ctrl, int pass);
+cudaError_t cholqr_pass(const Launch& L, int64_t n, int s, double* Y, Ctrl* ctrl, double* gpart, bool gram);
+cudaError_t cholqr_pupdate(const Launch& L, int64_t n, int s, double* R, double* P, Ctrl* ctrl);
 cudaError_t small_bicg_1(const Launch& L, Ctrl* ctrl, const uint8_t* forced);
 cudaError_t small_bicg_2(const Launch& L, Ctrl* ctrl);
 cudaError_t small_bicg_3(const Launch& L, Ctrl* ctrl, double* history, uint8_t* decisions);

@@ -35,14 +35,14 @@ __global__ void __launch_bounds__(kThreads, min_ctas<T>())
 bcg_update_kernel(int64_t n, int s, const T* __restrict__ P, const T* __restrict__ Q,
                   T* __restrict__ X, T* __restrict__ R, Ctrl* ctrl, double* gpart, int rho_mode) {
   if (ctrl->done) return;
-  if (ctrl->reortho_now) return;        // then the lean kernel updates, TSQR gives rho
+  if (ctrl->reortho_now && rho_mode != 2) return;   // then the lean kernel updates, TSQR gives rho
   extern __shared__ double smem[];
   T* lx = reinterpret_cast<T*>(smem);
   T* lam = lx + kMM;
   double* red = reinterpret_cast<double*>(lam + kMM);   // after the two staged matrices
   stage_matrix(lx, ctrl->lx, s);
   stage_matrix(lam, ctrl->lam, s);
-  const bool want_rho = rho_mode != 0 && ctrl->reortho_now == 0;
+  const bool want_rho = rho_mode == 2 || (rho_mode != 0 && ctrl->reortho_now == 0);
   __syncthreads();
   constexpr int RPW = 32 / SW;
   const int lane = threadIdx.x & 31, c = lane & (SW - 1), rs = lane / SW;
@@ -227,6 +227,8 @@ static cudaError_t launch_update(const Launch& L, int64_t n, int s, const T* P, 
 // rho_mode 1 (BCG): the lean kernel runs when the iteration re-orthonormalises,
 // the Gram-carrying kernel otherwise (the device flag picks; the other returns).
 // rho_mode 0 (BBiCGStab): the lean kernel always.
+// rho_mode 2 (FP64 BCG with the CholeskyQR2 normaliser): the Gram-carrying kernel
+// always, its rho_new = R-tilde^T R-tilde being the normaliser's first Gram.
 template <typename T>
 cudaError_t bcg_update(const Launch& L, int64_t n, int s, const T* P, const T* Q, T* X, T* R,
                        Ctrl* ctrl, double* gpart, int rho_mode) {
@@ -234,6 +236,7 @@ cudaError_t bcg_update(const Launch& L, int64_t n, int s, const T* P, const T* Q
     if (s % 4 == 0) return bcg_update4(L, n, s, P, Q, X, R, ctrl, gpart, rho_mode);
   }
   const int grid = row_grid(L, n, s);
+  if (rho_mode == 2) BK_SW_DISPATCH(s, return launch_update<T, SW>(L, n, s, P, Q, X, R, ctrl, gpart, rho_mode));
   BK_SW_DISPATCH(s, {
     bcg_update_lean_kernel<T, SW><<<grid, kThreads, 0, L.stream>>>(n, s, P, Q, X, R, ctrl, rho_mode);
     cudaError_t e = cudaGetLastError();
@@ -249,6 +252,147 @@ cudaError_t bcg_pupdate(const Launch& L, int64_t n, int s, const T* R, T* P, Ctr
   }
   const int grid = row_grid(L, n, s);
   BK_SW_DISPATCH(s, bcg_pupdate_kernel<T, SW><<<grid, kThreads, 0, L.stream>>>(n, s, R, P, ctrl);
+                 return cudaGetLastError());
+}
+
+// Upper-triangular product of TWO rows per sub-warp without idle lanes (FP64):
+// y_c = sum_{a <= c} x_a U_ac (U s x s, row stride s, upper triangular).  Lane c takes
+// column c of row A (c + 1 terms) and column SW - 1 - c of row B (SW - c terms), SW + 1
+// FMAs per lane whatever c is; the terms of every entry are added in the order a = 0, 1,
+// ...  On exit lane c holds y_A[c] and y_B[c] (row B's values moved back by a shuffle).
+template <int SW>
+__device__ __forceinline__ void tri_pair(double xA, double xB, const double* U, int s, double& yA,
+                                         double& yB) {
+  const int c = threadIdx.x & (SW - 1);
+  const int cB = SW - 1 - c;
+  double accA = 0.0, accB = 0.0;
+#pragma unroll
+  for (int t = 0; t <= SW; ++t) {
+    const bool first = t <= c;
+    const int a = first ? t : t - c - 1;
+    const double va = __shfl_sync(0xffffffffu, xA, a, SW);
+    const double vb = __shfl_sync(0xffffffffu, xB, a, SW);
+    const int col = first ? c : cB;
+    const double u = (a < s && col < s) ? U[a * s + col] : 0.0;
+    const double r = fma(first ? va : vb, u, first ? accA : accB);
+    if (first) accA = r; else accB = r;
+  }
+  yA = accA;
+  yB = __shfl_sync(0xffffffffu, accB, cB, SW);
+}
+
+// CholeskyQR2 row pass (FP64): Y <- Y U^{-1} in place with U^{-1} = ctrl->cq_inv (upper
+// triangular), and with kGram rho_new = Y^T Y (upper, mirrored) through the last-CTA grid
+// reduction.  Runs only while ctrl->qr_fast == 1.
+template <int SW, bool kGram>
+__global__ void __launch_bounds__(kThreads, 1)
+cholqr_pass_kernel(int64_t n, int s, double* __restrict__ Y, Ctrl* ctrl, double* gpart) {
+  if (ctrl->done || ctrl->qr_fast != 1) return;
+  extern __shared__ double smem[];
+  double* ui = smem;
+  double* red = smem + kMM;
+  stage_matrix(ui, ctrl->cq_inv, s);
+  __syncthreads();
+  constexpr int RPW = 32 / SW;
+  const int lane = threadIdx.x & 31, c = lane & (SW - 1), rs = lane / SW;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t nw = (int64_t)gridDim.x * kWarps;
+  constexpr bool kPair = SW >= 2;
+  double acc[SW];
+#pragma unroll
+  for (int a = 0; a < SW; ++a) acc[a] = 0.0;
+  SymGramPair<kPair ? SW : 2> pg;
+  pg.zero();
+  for (int64_t base = gw * RPW; base < n; base += 2 * nw * RPW) {
+    const int64_t rA = base + rs, rB = base + nw * RPW + rs;
+    const bool okA = (rA < n) && (c < s), okB = (rB < n) && (c < s);
+    const double xA = okA ? Y[rA * s + c] : 0.0, xB = okB ? Y[rB * s + c] : 0.0;
+    double yA, yB;
+    tri_pair<SW>(xA, xB, ui, s, yA, yB);
+    if (okA) Y[rA * s + c] = yA;
+    if (okB) Y[rB * s + c] = yB;
+    if constexpr (kGram) {
+      if constexpr (kPair) {
+        pg.add(yA, yA, yB, yB);
+      } else {
+        acc[0] = fma(yA, yA, acc[0]);
+        acc[0] = fma(yB, yB, acc[0]);
+      }
+    }
+  }
+  if constexpr (!kGram) return;
+  const int cnt = ut_count(s);
+  double* part = red;
+  double* scratch = red + cnt + 1;
+  if constexpr (kPair) pg.cta_reduce(s, scratch, part);
+  else cta_reduce_gram<SW>(acc, s, true, scratch, part);
+  if (!grid_reduce_last(part, cnt, gpart, &ctrl->counters[kCntC])) return;
+  unpack_gram(part, s, true, ctrl->rho_new);
+}
+
+cudaError_t cholqr_pass(const Launch& L, int64_t n, int s, double* Y, Ctrl* ctrl, double* gpart, bool gram) {
+  const int grid = row_grid(L, n, s);
+  const size_t sm = sizeof(double) * (kMM + ut_count(s) + 2 + kWarps * ut_count(s));
+  BK_SW_DISPATCH(s, {
+    auto k = gram ? cholqr_pass_kernel<SW, true> : cholqr_pass_kernel<SW, false>;
+    if (sm > 44 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    k<<<grid, kThreads, sm, L.stream>>>(n, s, Y, ctrl, gpart);
+    return cudaGetLastError();
+  });
+}
+
+// BCG direction update with the second CholeskyQR2 pass folded in (FP64, M = I): where
+// the iteration's normaliser was CholeskyQR2 (ctrl->qr_fast == 1), R-bar = Y1 U2^{-1} is
+// formed here (written back) and P <- R-bar + P beta uses it from registers; otherwise
+// this is P <- R + P beta.
+template <int SW>
+__global__ void __launch_bounds__(kThreads, 2)
+cholqr_pupdate_kernel(int64_t n, int s, double* __restrict__ R, double* __restrict__ P, Ctrl* ctrl) {
+  if (ctrl->done) return;
+  __shared__ double beta[kMM];
+  __shared__ double ui[kMM];
+  const bool fq = ctrl->qr_fast == 1;
+  stage_matrix(beta, ctrl->beta, s);
+  if (fq) stage_matrix(ui, ctrl->cq_inv, s);
+  __syncthreads();
+  constexpr int RPW = 32 / SW;
+  const int lane = threadIdx.x & 31, c = lane & (SW - 1), rs = lane / SW;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t nw = (int64_t)gridDim.x * kWarps;
+  for (int64_t base = gw * RPW; base < n; base += 2 * nw * RPW) {
+    const int64_t rA = base + rs, rB = base + nw * RPW + rs;
+    const bool okA = (rA < n) && (c < s), okB = (rB < n) && (c < s);
+    const double pA = okA ? P[rA * s + c] : 0.0, pB = okB ? P[rB * s + c] : 0.0;
+    double xA = okA ? R[rA * s + c] : 0.0, xB = okB ? R[rB * s + c] : 0.0;
+    if (fq) {
+      double yA, yB;
+      tri_pair<SW>(xA, xB, ui, s, yA, yB);
+      xA = yA;
+      xB = yB;
+      if (okA) R[rA * s + c] = xA;
+      if (okB) R[rB * s + c] = xB;
+    }
+    double accA = 0.0, accB = 0.0;
+#pragma unroll
+    for (int a = 0; a < SW; ++a) {
+      const double paA = sw_bcast<SW>(pA, a), paB = sw_bcast<SW>(pB, a);
+      if (a < s && c < s) {
+        const double b = beta[a * s + c];
+        accA = fma(paA, b, accA);
+        accB = fma(paB, b, accB);
+      }
+    }
+    if (okA) P[rA * s + c] = xA + accA;
+    if (okB) P[rB * s + c] = xB + accB;
+  }
+}
+
+cudaError_t cholqr_pupdate(const Launch& L, int64_t n, int s, double* R, double* P, Ctrl* ctrl) {
+  const int grid = row_grid(L, n, s);
+  BK_SW_DISPATCH(s, cholqr_pupdate_kernel<SW><<<grid, kThreads, 0, L.stream>>>(n, s, R, P, ctrl);
                  return cudaGetLastError());
 }
 

@@ -15,6 +15,7 @@
 namespace bk {
 
 constexpr int kST = 256;   // threads of the small-solve CTA
+constexpr double kCholQrMinSine2 = 1e-10;   // CholeskyQR2 decline threshold (squared sine)
 #define IDX(i, j) ((i) * kMaxS + (j))
 
 __device__ void sm_copy(double* dst, const double* src, int s) {
@@ -95,6 +96,53 @@ __device__ bool sm_cholesky(double* A, int s, int* flag) {
     __syncthreads();
   }
   return true;
+}
+
+// In-place Cholesky A = L L^T with a relative pivot floor: fails unless every pivot
+// d_k (the Schur complement's diagonal entry, d_k = L_kk^2) keeps d_k > floor G_kk
+// with G the matrix on entry (G_kk > 0).  d_k / G_kk is the squared sine between
+// column k of a block whose Gram is G and the span of the columns before it, so a
+// floor rejects nearly dependent blocks.  gd: kMaxS doubles of scratch.
+__device__ bool sm_cholesky_floor(double* A, int s, double floor, double* gd, int* flag) {
+  for (int i = threadIdx.x; i < s; i += blockDim.x) gd[i] = A[IDX(i, i)];
+  if (threadIdx.x == 0) *flag = 1;
+  __syncthreads();
+  for (int k = 0; k < s; ++k) {
+    const double d = A[IDX(k, k)], g = gd[k];
+    if (!(g > 0.0) || !(d > floor * g) || !isfinite(d)) return false;   // uniform
+    const double lkk = sqrt(d);
+    for (int i = k + 1 + threadIdx.x; i < s; i += blockDim.x) A[IDX(i, k)] /= lkk;
+    __syncthreads();
+    if (threadIdx.x == 0) A[IDX(k, k)] = lkk;
+    const int r = s - k - 1;
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+      const int i = k + 1 + e / r, j = k + 1 + e % r;
+      if (j <= i) A[IDX(i, j)] = fma(-A[IDX(i, k)], A[IDX(j, k)], A[IDX(i, j)]);
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// U = L^T and Uinv = L^{-T} (both upper triangular, zeros below the diagonal) from the
+// lower factor L of sm_cholesky (its strict upper triangle is ignored).  One warp per
+// column c of L^{-1}: forward substitution L z = e_c with lane i holding z_i.
+__device__ void sm_upper_and_inverse(const double* L, double* U, double* Uinv, int s) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double dinv = (lane < s) ? 1.0 / L[IDX(lane, lane)] : 0.0;
+  for (int c = warp; c < s; c += nw) {
+    double v = (lane == c) ? 1.0 : 0.0;
+    for (int i = c; i < s; ++i) {
+      const double zi = __shfl_sync(0xffffffffu, v * dinv, i);
+      if (lane > i && lane < s) v = fma(-L[IDX(lane, i)], zi, v);
+      if (lane == i) v = zi;
+    }
+    if (lane < s) {
+      Uinv[IDX(c, lane)] = v;                           // (L^{-1})_{lane c}, zero for lane < c
+      U[IDX(c, lane)] = (lane >= c) ? L[IDX(lane, c)] : 0.0;
+    }
+  }
+  __syncthreads();
 }
 
 // X = (L L^T)^{-1} B (X may alias B).  One warp per right-hand-side column,
@@ -546,6 +594,17 @@ __global__ void __launch_bounds__(kST) small_bcg_2_k(Ctrl* c, double* history, u
   sm_copy(S.B, c->sigma, s);
   if (reo) sm_copy(S.C, c->gamma, s); else sm_identity(S.C, s);
   __syncthreads();
+  if (reo && c->qr_fast == 2) {
+    // CholeskyQR2 whose second factor failed: the TSQR factored Y1 = R-tilde U1^{-1},
+    // so R-tilde = Y gamma' U1 and gamma = gamma' U1
+    sm_copy(S.E, c->cq_u1, s);
+    __syncthreads();
+    sm_matmul(S.F, S.C, false, S.E, s);
+    __syncthreads();
+    sm_copy(S.C, S.F, s);
+    for (int i = threadIdx.x; i < s * s; i += blockDim.x) c->gamma[IDX(i / s, i % s)] = S.F[IDX(i / s, i % s)];
+    __syncthreads();
+  }
   sm_project(S.A, s, c->sub_p);            // S_BP^p: rho block diagonal
   __syncthreads();
   if (!sm_all_finite(S.A, s, &S.flag)) { stop(c, BK_NONFINITE); return; }
@@ -578,6 +637,7 @@ __global__ void __launch_bounds__(kST) small_bcg_2_k(Ctrl* c, double* history, u
     if (decisions) decisions[k] = (uint8_t)reo;
     c->iter = k + 1;
     c->reorths += reo;
+    c->cholqr_count += (reo && c->qr_fast == 1) ? 1 : 0;
     s_conv = !isfinite(mx) ? -1 : (mx <= c->tol ? 1 : 0);
   }
   __syncthreads();
@@ -621,6 +681,77 @@ __global__ void __launch_bounds__(kST) small_bcg_2_k(Ctrl* c, double* history, u
     }
   }
   if (threadIdx.x == 0 && c->iter >= c->maxit) { c->done = kDoneStopped; c->status = BK_NOT_CONVERGED; }
+}
+
+// CholeskyQR2 normaliser of the re-orthonormalising iterations (Fukaya, Nakatsukasa,
+// Yanagisawa, Yamamoto 2014), the s x s steps; the row passes Y <- Y U^{-1} with the
+// Gram Y^T Y fused run between them.
+// Pass 1: G1 = rho_new = R-tilde^T R-tilde from the update kernel.  G1 = U1^T U1 is taken
+// only when every pivot keeps U1_kk^2 > 1e-10 G1_kk (every column's squared sine to
+// the span of the columns before it); otherwise the Householder TSQR normalises.
+__global__ void __launch_bounds__(kST) small_cholqr_1_k(Ctrl* c) {
+  if (c->done) return;
+  extern __shared__ double smraw[];
+  SmallSmem& S = *reinterpret_cast<SmallSmem*>(smraw);
+  const int s = c->s;
+  if (!c->reortho_now) {
+    if (threadIdx.x == 0) { c->qr_fast = 0; c->tsqr_now = 0; }
+    return;
+  }
+  sm_copy(S.A, c->rho_new, s);
+  __syncthreads();
+  const bool ok = sm_all_finite(S.A, s, &S.flag) && sm_cholesky_floor(S.A, s, kCholQrMinSine2, S.w, &S.flag);
+  __syncthreads();
+  if (!ok) {
+    if (threadIdx.x == 0) { c->qr_fast = 0; c->tsqr_now = 1; }
+    return;
+  }
+  sm_upper_and_inverse(S.A, S.B, S.C, s);
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
+    const int a = i / s, b = i % s;
+    c->cq_u1[IDX(a, b)] = S.B[IDX(a, b)];
+    c->cq_inv[IDX(a, b)] = S.C[IDX(a, b)];
+  }
+  if (threadIdx.x == 0) { c->qr_fast = 1; c->tsqr_now = 0; }
+}
+
+// Pass 2: G2 = Y1^T Y1 (close to I) = U2^T U2 with every pivot above G2_kk / 2, then
+// gamma = U2 U1 and the inverse U2^{-1} for the second row pass, and rho_new = I: the
+// normalised block R-bar = Y1 U2^{-1} has orthonormal columns (Def. "normalizer"), so
+// its Gram is not formed.  A failure leaves Y1 to the TSQR (qr_fast = 2; the small BCG
+// kernel multiplies its factor by U1).
+__global__ void __launch_bounds__(kST) small_cholqr_2_k(Ctrl* c) {
+  if (c->done || c->qr_fast != 1) return;
+  extern __shared__ double smraw[];
+  SmallSmem& S = *reinterpret_cast<SmallSmem*>(smraw);
+  const int s = c->s;
+  sm_copy(S.A, c->rho_new, s);
+  sm_copy(S.D, c->cq_u1, s);
+  __syncthreads();
+  const bool ok = sm_all_finite(S.A, s, &S.flag) && sm_cholesky_floor(S.A, s, 0.5, S.w, &S.flag);
+  __syncthreads();
+  if (!ok) {
+    if (threadIdx.x == 0) { c->qr_fast = 2; c->tsqr_now = 1; }
+    return;
+  }
+  sm_upper_and_inverse(S.A, S.B, S.C, s);
+  sm_matmul(S.E, S.B, false, S.D, s);          // gamma = U2 U1
+  __syncthreads();
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
+    const int a = i / s, b = i % s;
+    c->gamma[IDX(a, b)] = S.E[IDX(a, b)];
+    c->cq_inv[IDX(a, b)] = S.C[IDX(a, b)];
+    c->rho_new[IDX(a, b)] = (a == b) ? 1.0 : 0.0;
+  }
+}
+
+cudaError_t small_cholqr(const Launch& L, Ctrl* c, int pass) {
+  auto k = pass == 1 ? small_cholqr_1_k : small_cholqr_2_k;
+  const size_t sm = sizeof(SmallSmem);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k<<<1, kST, sm, L.stream>>>(c);
+  return cudaGetLastError();
 }
 
 static cudaError_t launch_small(void (*k)(Ctrl*), const Launch& L, Ctrl* c) {

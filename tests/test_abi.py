@@ -38,7 +38,7 @@ def test_binding_covers_header():
 def test_host_only_entry_points(lib):
     from paper_2104_02494_gb300 import _lib
     L = _lib.load()
-    assert L.bkrylov_version() == 200
+    assert L.bkrylov_version() == 201
     assert L.bkrylov_status_string(_lib.BK_BREAKDOWN) == b"breakdown"
     o = _lib.default_opts()
     assert o.restart == 30 and o.eta == float("inf") and o.ortho == 1 and o.norm_mode == 0
