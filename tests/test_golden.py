@@ -6,8 +6,11 @@ gmres_cyclic_shift.json is the thesis's own worked example (Ch. 2, Ex. "nonconve
 GMRes on the cyclic shift with b = e_1 cannot improve on x = 0 before n steps and is exact at n.
 
 Residual histories are compared relatively (1e-9 on the CPU, where only the BLAS build may
-differ; 1e-8 on the GPU, whose Gram summation order differs), decisions and iteration
-counts exactly.
+differ; 1e-8 on the GPU, whose Gram summation order differs and whose FP64 BCG normalises
+by CholeskyQR2), decisions and iteration counts exactly.  On the GPU each entry may also be
+off by 1e-15 absolutely: the history is max_i ||R-bar sigma e_i|| / ||R0_i||, and the
+normaliser's rounding in sigma is relative to ||sigma|| (about 1 in these units), not to a
+converged column's own small norm (near 1e-11 at the end).
 """
 import json
 import math
@@ -36,12 +39,12 @@ CASES = [("bcg_eta_inf", "bcg", math.inf, False, False), ("bcg_eta_0", "bcg", 0.
          ("bcg_jacobi_vardiff_eta_inf", "bcg", math.inf, True, True)]
 
 
-def _check(got_hist, got_dec, got_iters, ref, tol):
+def _check(got_hist, got_dec, got_iters, ref, tol, floor=0.0):
     assert got_iters == ref["iters"]
     assert list(got_dec) == ref["decisions"]
     h = np.array(got_hist[:len(ref["history"])])
     r = np.array(ref["history"])
-    assert np.all(np.abs(h - r) <= tol * np.abs(r)), np.abs(h / r - 1).max()
+    assert np.all(np.abs(h - r) <= tol * np.abs(r) + floor), np.abs(h / r - 1).max()
 
 
 @pytest.mark.parametrize("key,fn,eta,jacobi,var", CASES)
@@ -68,7 +71,7 @@ def test_gpu_matches_golden(key, fn, eta, jacobi, var):
         P = h.op_jacobi(op) if jacobi else None
         X, info = h.solve("bcg", op, dv(R), tol=1e-10, maxit=500, eta=eta, precond=P,
                           one_reduction=(fn == "bcg_1r"))
-        _check(info.history, info.decisions, info.iters, GOLD[key], 1e-8)
+        _check(info.history, info.decisions, info.iters, GOLD[key], 1e-8, floor=1e-15)
         ref_row = np.array(GOLD[key]["X_first_row"])
         assert np.abs(X.cpu().numpy()[0] - ref_row).max() <= 1e-9 * np.abs(ref_row).max()
         if P is not None:
