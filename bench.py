@@ -198,20 +198,22 @@ def iteration_flops(n, s, cholqr=True):
 
     SpMM 7-point 14ns; the Grams alpha and rho (upper triangles) 2 n s(s+1);
     the block updates X += P lx, R -= Q lam, P = R + P beta: 6ns^2; the
-    normaliser: CholeskyQR2's two passes Y <- Y U^-1 with the Gram Y^T Y, 4 n s(s+1)
-    (its first Gram is rho's), or the Householder factor 2ns^2 and Q [sigma~; 0] 2ns^2.
-    The s x s work, the WY factors and the TSQR tree are O(n s^2 / tile) and not counted.
+    normaliser: CholeskyQR2's two triangular products Y <- Y U^-1, 2 n s(s+1), and the
+    Gram of the first, n s(s+1) (its first Gram is rho's; the second pass's Gram is I
+    by construction and not formed), or the Householder factor 2ns^2 and
+    Q [sigma~; 0] 2ns^2.  The s x s work, the WY factors and the TSQR tree are
+    O(n s^2 / tile) and not counted.
     """
-    norm = 4 * n * s * (s + 1) if cholqr else 4 * n * s * s
+    norm = 3 * n * s * (s + 1) if cholqr else 4 * n * s * s
     return 14 * n * s + 2 * n * s * (s + 1) + 6 * n * s * s + norm
 
 
 def iteration_bytes(n, s, cholqr=True, elem=8):
     """Algorithmic HBM bytes of one BCG iteration (stencil, eta = inf): the SpMM reads P
-    and writes Q, the update reads P, Q, X, R and writes X, R, the P update reads R, P and
-    writes P, and the normaliser reads and writes the block twice (CholeskyQR2's passes;
-    the Householder TSQR's factor and apply)."""
-    return elem * n * s * (2 + 6 + 3 + 4)
+    and writes Q, the update reads P, Q, X, R and writes X, R, the normaliser reads and
+    writes the block (CholeskyQR2's first pass; the TSQR's factor and apply: twice), and
+    the P update reads R, P and writes P (and R-bar with CholeskyQR2)."""
+    return elem * n * s * ((2 + 6 + 2 + 4) if cholqr else (2 + 6 + 4 + 3))
 
 
 PHASE_FLOPS = {
@@ -222,7 +224,8 @@ PHASE_FLOPS = {
     # V^T V that defines their compact WY factors (n s (s - 1))
     "tsqr_leaf_factor": lambda n, s: 2 * n * s * s + n * s * (s - 1),
     "tsqr_leaf_apply": lambda n, s: 2 * n * s * s + n * s * (s + 1),
-    "p_update": lambda n, s: 2 * n * s * s,
+    # P = R-bar + P beta with R-bar = Y1 U2^-1 formed on the way (CholeskyQR2 iterations)
+    "p_update": lambda n, s: 2 * n * s * s + n * s * (s + 1),
 }
 PHASE_BYTES = {
     # algorithmic bytes per launch (FP64): blocks read + written
@@ -230,12 +233,13 @@ PHASE_BYTES = {
     "update_rho": lambda n, s: 6 * 8 * n * s,
     "tsqr_leaf_factor": lambda n, s: 2 * 8 * n * s,
     "tsqr_leaf_apply": lambda n, s: 2 * 8 * n * s,
-    "p_update": lambda n, s: 3 * 8 * n * s,
+    "p_update": lambda n, s: 4 * 8 * n * s,
 }
-# The CholeskyQR2 phase per iteration: two row passes (read + write of the block, the
-# triangular product and the Gram, 2 n s(s+1) flops each) and two one-CTA s x s kernels.
-PHASE_ITER_FLOPS = {"cholqr": lambda n, s: 4 * n * s * (s + 1)}
-PHASE_ITER_BYTES = {"cholqr": lambda n, s: 4 * 8 * n * s}
+# The CholeskyQR2 phase per iteration (M = I): one row pass (read + write of the block,
+# the triangular product and the Gram, 2 n s(s+1) flops) and two one-CTA s x s kernels;
+# the second triangular product runs inside p_update.
+PHASE_ITER_FLOPS = {"cholqr": lambda n, s: 2 * n * s * (s + 1)}
+PHASE_ITER_BYTES = {"cholqr": lambda n, s: 2 * 8 * n * s}
 
 
 class Clocks:
@@ -418,8 +422,11 @@ def run_micro(args):
             fn()
         tot = 0.0
         for _ in range(reps):
-            flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            # two 512 MB writes: the L2 flush, and ~80 us more device work so that the host
+            # has enqueued fn's kernels before e0 is reached (no host time in the window)
+            flush.zero_()
+            flush.zero_()
             e0.record()
             fn()
             e1.record()
@@ -661,7 +668,8 @@ def run_one_reduction(args):
 
 
 def _flush_timer(torch):
-    """Device time (ms) of one call after an L2 flush (a 512 MB write), CUDA events."""
+    """Device time (ms) of one call after an L2 flush (512 MB written twice, so that the
+    host has enqueued the call before the start event is reached), CUDA events."""
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
     def timeit(fn, reps=10, warm=3):
@@ -669,8 +677,9 @@ def _flush_timer(torch):
             fn()
         tot = 0.0
         for _ in range(reps):
-            flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            flush.zero_()          # keeps the device busy while the host enqueues fn
             e0.record(); fn(); e1.record()
             torch.cuda.synchronize()
             tot += e0.elapsed_time(e1)

@@ -24,6 +24,20 @@ constexpr int kWarps = kThreads / 32;
 // so that enough loads are in flight to cover HBM latency.
 constexpr int kCtasPerSm = 8;
 
+// CTAs of a kThreads-thread kernel with `smem` dynamic bytes that stay resident on one SM
+// (its registers and shared memory decide), at most kCtasPerSm.  A grid-stride kernel
+// launched with sms x this many CTAs runs as one full wave: a compute-bound kernel
+// loses no partial last wave.
+template <class K>
+inline int resident_ctas(K kern, size_t smem) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    occ = 0;
+  }
+  return occ < 1 ? 1 : (occ > kCtasPerSm ? kCtasPerSm : occ);
+}
+
 // ---- per-solve device control block --------------------------------------------
 // s x s matrices are stored with row stride kMaxS: M[i][j] at i * kMaxS + j.
 enum : int { kDoneRunning = 0, kDoneConverged = 1, kDoneStopped = 2 };

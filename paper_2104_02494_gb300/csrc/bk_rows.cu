@@ -202,13 +202,13 @@ bcg_pupdate_kernel(int64_t n, int s, const T* __restrict__ R, T* __restrict__ P,
 template <typename T, int SW>
 static cudaError_t launch_update(const Launch& L, int64_t n, int s, const T* P, const T* Q, T* X,
                                  T* R, Ctrl* ctrl, double* gpart, int rho_mode) {
-  const int grid = row_grid(L, n, s);
   const size_t sm = 2 * kMM * sizeof(T) + sizeof(double) * (ut_count(s) + 2 + kWarps * ut_count(s));
   auto k = bcg_update_kernel<T, SW>;
   if (sm > 44 * 1024) {   // 48 KB default includes the static reduction buffers
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
+  const int grid = row_grid(L, n, s, resident_ctas(k, sm));
   k<<<grid, kThreads, sm, L.stream>>>(n, s, P, Q, X, R, ctrl, gpart, rho_mode);
   return cudaGetLastError();
 }
@@ -235,9 +235,9 @@ cudaError_t bcg_update(const Launch& L, int64_t n, int s, const T* P, const T* Q
   if constexpr (sizeof(T) == 4) {
     if (s % 4 == 0) return bcg_update4(L, n, s, P, Q, X, R, ctrl, gpart, rho_mode);
   }
-  const int grid = row_grid(L, n, s);
   if (rho_mode == 2) BK_SW_DISPATCH(s, return launch_update<T, SW>(L, n, s, P, Q, X, R, ctrl, gpart, rho_mode));
   BK_SW_DISPATCH(s, {
+    const int grid = row_grid(L, n, s, resident_ctas(bcg_update_lean_kernel<T, SW>, 0));
     bcg_update_lean_kernel<T, SW><<<grid, kThreads, 0, L.stream>>>(n, s, P, Q, X, R, ctrl, rho_mode);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || rho_mode == 0) return e;
@@ -250,8 +250,8 @@ cudaError_t bcg_pupdate(const Launch& L, int64_t n, int s, const T* R, T* P, Ctr
   if constexpr (sizeof(T) == 4) {
     if (s % 4 == 0) return bcg_pupdate4(L, n, s, R, P, ctrl);
   }
-  const int grid = row_grid(L, n, s);
-  BK_SW_DISPATCH(s, bcg_pupdate_kernel<T, SW><<<grid, kThreads, 0, L.stream>>>(n, s, R, P, ctrl);
+  BK_SW_DISPATCH(s, bcg_pupdate_kernel<T, SW><<<row_grid(L, n, s, resident_ctas(bcg_pupdate_kernel<T, SW>, 0)),
+                                                 kThreads, 0, L.stream>>>(n, s, R, P, ctrl);
                  return cudaGetLastError());
 }
 
@@ -331,7 +331,6 @@ cholqr_pass_kernel(int64_t n, int s, double* __restrict__ Y, Ctrl* ctrl, double*
 }
 
 cudaError_t cholqr_pass(const Launch& L, int64_t n, int s, double* Y, Ctrl* ctrl, double* gpart, bool gram) {
-  const int grid = row_grid(L, n, s);
   const size_t sm = sizeof(double) * (kMM + ut_count(s) + 2 + kWarps * ut_count(s));
   BK_SW_DISPATCH(s, {
     auto k = gram ? cholqr_pass_kernel<SW, true> : cholqr_pass_kernel<SW, false>;
@@ -339,7 +338,7 @@ cudaError_t cholqr_pass(const Launch& L, int64_t n, int s, double* Y, Ctrl* ctrl
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return e;
     }
-    k<<<grid, kThreads, sm, L.stream>>>(n, s, Y, ctrl, gpart);
+    k<<<row_grid(L, n, s, resident_ctas(k, sm)), kThreads, sm, L.stream>>>(n, s, Y, ctrl, gpart);
     return cudaGetLastError();
   });
 }
@@ -391,8 +390,8 @@ cholqr_pupdate_kernel(int64_t n, int s, double* __restrict__ R, double* __restri
 }
 
 cudaError_t cholqr_pupdate(const Launch& L, int64_t n, int s, double* R, double* P, Ctrl* ctrl) {
-  const int grid = row_grid(L, n, s);
-  BK_SW_DISPATCH(s, cholqr_pupdate_kernel<SW><<<grid, kThreads, 0, L.stream>>>(n, s, R, P, ctrl);
+  BK_SW_DISPATCH(s, cholqr_pupdate_kernel<SW><<<row_grid(L, n, s, resident_ctas(cholqr_pupdate_kernel<SW>, 0)),
+                                                kThreads, 0, L.stream>>>(n, s, R, P, ctrl);
                  return cudaGetLastError());
 }
 

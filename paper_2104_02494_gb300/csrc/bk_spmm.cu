@@ -196,13 +196,16 @@ template <typename T, int SW, class RowOp>
 static cudaError_t launch_sw(const Launch& L, const RowOp& op, int64_t n, int s, const T* in,
                              T* out, const T* sub, const Epi<T>& ep) {
   const bool g = ep.left != nullptr, f = ep.frob != nullptr;
-  int grid = spmm_grid(L, n, s);
+  const int grid_max = spmm_grid(L, n, s);
   size_t sm = (g || f) ? epi_smem(s, g, ep.sym != 0, f, sizeof(T) == 4) : 0;
   auto launch = [&](auto kern) -> cudaError_t {
     if (sm > 44 * 1024) {   // 48 KB default includes the static reduction buffers
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return e;
     }
+    // one resident wave (FP64 rows are bound by the FP64 pipe: no partial last wave)
+    const int wave = L.sms * resident_ctas(kern, sm);
+    const int grid = grid_max < wave ? grid_max : wave;
     kern<<<grid, kThreads, sm, L.stream>>>(op, n, s, in, out, sub, ep);
     return cudaGetLastError();
   };

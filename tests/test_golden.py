@@ -7,10 +7,11 @@ GMRes on the cyclic shift with b = e_1 cannot improve on x = 0 before n steps an
 
 Residual histories are compared relatively (1e-9 on the CPU, where only the BLAS build may
 differ; 1e-8 on the GPU, whose Gram summation order differs and whose FP64 BCG normalises
-by CholeskyQR2), decisions and iteration counts exactly.  On the GPU each entry may also be
-off by 1e-15 absolutely: the history is max_i ||R-bar sigma e_i|| / ||R0_i||, and the
-normaliser's rounding in sigma is relative to ||sigma|| (about 1 in these units), not to a
-converged column's own small norm (near 1e-11 at the end).
+by CholeskyQR2), decisions and iteration counts exactly.  Each entry may also be off by
+1e-15 absolutely: the history is max_i ||R-bar sigma e_i|| / ||R0_i||, and the normaliser's
+rounding in sigma is relative to ||sigma|| (about 1 in these units), not to a converged
+column's own small norm (near 1e-11 at the end; another BLAS build on an Arm host moved
+the preconditioned case's tail by 3e-8 relative).
 """
 import json
 import math
@@ -53,7 +54,7 @@ def test_oracle_reproduces_golden(key, fn, eta, jacobi, var):
     M, R = (Av, Bv) if var else (A, B)
     w = oracle.jacobi_inverse_diagonal(M) if jacobi else None
     r = getattr(oracle, fn)(M, R, tol=1e-10, maxit=500, eta=eta, Minv=w)
-    _check(r.history, r.decisions, r.iters, GOLD[key], 1e-9)
+    _check(r.history, r.decisions, r.iters, GOLD[key], 1e-9, floor=1e-15)
 
 
 @pytest.mark.gpu
