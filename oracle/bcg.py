@@ -47,6 +47,7 @@ class BCGResult:
     alphas: list = field(default_factory=list)     # alpha^k (projected), when record_alpha
     iterates: list = field(default_factory=list)   # X^{k+1} for the first record_iterates steps
     reorths_cholqr: int = 0          # re-orthonormalisations done by CholeskyQR2 (qr="cholqr2")
+    replacements: int = 0            # 1R-BCG: direct recomputations of Q and alpha
 
 
 def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit: int = 1000,
@@ -164,7 +165,7 @@ def bcg(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit
 
 def bcg_1r(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, maxit: int = 1000,
            eta: float = math.inf, forced=None, record_iterates: int = 0, dtype=np.float64,
-           eps: float | None = None, Minv=None, norm: str = "max") -> BCGResult:
+           eps: float | None = None, Minv=None, norm: str = "max", replace: int = 0) -> BCGResult:
     """BCG with one reduction per iteration, Alg. "1R-CG" (Ch. 8.1), block case S_B.
 
     Arithmetically equal to Alg. "bcgaro": with U = A Z, delta = <Z, U>, the
@@ -172,6 +173,13 @@ def bcg_1r(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, ma
     (Eq. "alpha_k+1" simplified with <Z^{k+1}, Q^k> = -beta^T alpha), and Q is
     updated as Q = U + Q beta instead of being recomputed as A P.  The norms,
     the re-orthonormalisation test and the readings are those of ``bcg``.
+
+    replace: replacement of the recursive quantities (the residual-replacement idea
+    of van der Vorst and Ye, 2000, applied to the recursion of Ch. 8.1): with replace
+    = m > 0, after every m-th iteration, and after any iteration whose recursive
+    alpha^{k+1} has a non-positive Cholesky pivot, Q = A P and alpha = <P, Q> are
+    formed directly as in the two-reduction schedule (one more operator application);
+    ``replacements`` counts them.  0: the plain recursion.
     """
     B = np.asarray(B)
     n, s = B.shape
@@ -250,8 +258,21 @@ def bcg_1r(A, B: np.ndarray, X0: np.ndarray | None = None, tol: float = 1e-8, ma
         alpha = delta - beta.T @ alpha @ beta           # alpha^{k+1} = delta^{k+1} - beta^T alpha^k beta
         alpha = np.triu(alpha) + np.triu(alpha, 1).T
         rho = rho_new
+        if replace > 0 and ((k + 1) % replace == 0 or not _chol_ok(alpha)):
+            Q = op(P)                                   # Q^{k+1} = A P^{k+1}
+            alpha = gram(P, Q)                          # alpha^{k+1} = <P^{k+1}, Q^{k+1}>
+            out.replacements += 1
     out.status = "not_converged"
     return out
+
+
+def _chol_ok(A) -> bool:
+    """Whether the Cholesky factorisation of the symmetric A has positive pivots only."""
+    try:
+        chol_solve(A, np.eye(A.shape[0]))
+        return True
+    except Breakdown:
+        return False
 
 
 def _resid_from(sigma, G, p, reortho):

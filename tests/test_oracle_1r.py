@@ -81,3 +81,46 @@ def test_1r_dense_solve_finite_termination():
     assert r.converged and r.iters <= 6 + 2
     Xs = np.linalg.solve(M, B)
     assert _rel(r.X, Xs) <= 1e-10
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_1r_replacing_every_iteration_is_the_2r_schedule(dtype):
+    """With Q = A P and alpha = <P, Q> formed after every iteration (replace = 1) the
+    recursion never feeds alpha or Q, so the iterates are those of Alg. "bcgaro" up to
+    the rounding of the Grams (rho = <Z, R-bar> with Z a copy of R-bar here), in FP64
+    and in FP32: 30 iterates on the 2D Laplacian (8 on a log-normal field, whose block
+    CG amplifies rounding tenfold per iteration, as in ``test_1r_equals_2r``)."""
+    for A, K in ((W.lap2d5(16, 15), 30), (_var7(6, sd=1.0), 8)):
+        B = W.normal_block(A.n, 6, 3).astype(dtype)
+        tol = 1e-9 if dtype == np.float64 else 1e-5
+        r1 = oracle.bcg_1r(A, B, tol=tol, maxit=400, eta=math.inf, dtype=dtype, replace=1, record_iterates=K)
+        r2 = oracle.bcg(A, B, tol=tol, maxit=400, eta=math.inf, dtype=dtype, record_iterates=K)
+        assert r1.status == r2.status == "ok" and abs(r1.iters - r2.iters) <= max(2, r2.iters // 10)
+        assert r1.replacements == r1.iters - 1
+        bound = 1e-10 if dtype == np.float64 else 1e-4
+        for a, b in zip(r1.iterates, r2.iterates):
+            assert _rel(a, b) <= bound
+
+
+def test_1r_replacement_schedule_and_fp32_breakdown():
+    """replace = m forms Q and alpha directly after iterations m, 2m, ... (FP64, where the
+    recursive alpha stays definite), without changing the FP64 iterates beyond rounding.
+    In FP32 on the log-normal diffusion workload the plain recursion breaks down
+    (alpha loses definiteness) and only replacement after every iteration converges:
+    one recursive step between replacements already loses the iterates (cancellation
+    in delta - beta^T alpha beta, not slow drift)."""
+    A = W.lap2d5(16, 15)
+    B = W.normal_block(A.n, 8, 4)
+    ref = oracle.bcg(A, B, tol=1e-8, maxit=800, eta=math.inf, record_iterates=30)
+    for m in (3, 7):
+        r = oracle.bcg_1r(A, B, tol=1e-8, maxit=800, eta=math.inf, replace=m, record_iterates=30)
+        assert r.converged and abs(r.iters - ref.iters) <= 2
+        assert r.replacements == (r.iters - 1) // m
+        for a, b in zip(r.iterates, ref.iterates):
+            assert _rel(a, b) <= 1e-10
+    prob = W.problem("vardiff3d", grid=16, s=16)
+    Rs = (prob.B / oracle.col_norms(prob.B)).astype(np.float32)
+    plain = oracle.bcg_1r(prob.A, Rs, tol=1e-5, maxit=300, eta=math.inf, dtype=np.float32)
+    every = oracle.bcg_1r(prob.A, Rs, tol=1e-5, maxit=300, eta=math.inf, dtype=np.float32, replace=1)
+    second = oracle.bcg_1r(prob.A, Rs, tol=1e-5, maxit=300, eta=math.inf, dtype=np.float32, replace=2)
+    assert plain.status == "breakdown" and every.converged and not second.converged
