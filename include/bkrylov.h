@@ -132,6 +132,14 @@ typedef struct {
                           default two-reduction schedule (Alg. "2R-CG") at two more block
                           vectors and one more block update per iteration.  Needs the
                           block case (BK_ERR_UNSUPPORTED with subalgebra_p < s)     (0) */
+  int replace_every;   /* one_reduction only: m > 0 forms Q = A P and alpha = <P, Q> directly
+                          (one more operator pass, the two-reduction formulas) after every
+                          m-th iteration and after any iteration whose recursive alpha has
+                          a non-positive Cholesky pivot (residual replacement applied to the
+                          recursion of Ch. 8.1); m = 1 gives the iterates of Alg. "2R-CG".
+                          In FP32 the recursion's cancellation can lose alpha within one
+                          step (the log-normal diffusion workloads: only m = 1 converges).
+                          0: never.  Negative: BK_ERR_ARG                        (0)    */
   int qr_mode;         /* normaliser of the re-orthonormalising BCG iterations (Def.
                           "normalizer", Ch. 3.1): 0 = CholeskyQR2 (Fukaya et al. 2014: two
                           passes Y <- Y U^-1 with U the Cholesky factor of the Gram, the first
@@ -159,6 +167,7 @@ typedef struct {
   double elapsed_ms;   /* device time of the solve (CUDA events)                      */
   int reorths_cholqr;  /* of reorths, those normalised by CholeskyQR2 (qr_mode 0; the
                           others by the Householder TSQR)                             */
+  int replacements;    /* 1R-BCG: iterations after which Q and alpha were formed directly */
 } bkrylov_info;
 
 /* ---- handle ------------------------------------------------------------------ */

@@ -27,7 +27,7 @@ class bkrylov_opts(C.Structure):
         ("ir_max_outer", C.c_int), ("forced_reortho", C.POINTER(C.c_uint8)), ("n_forced", C.c_int),
         ("sync_every", C.c_int), ("profile", C.c_int), ("subalgebra_p", C.c_int),
         ("precond", C.c_void_p), ("norm_mode", C.c_int), ("one_reduction", C.c_int),
-        ("qr_mode", C.c_int),
+        ("replace_every", C.c_int), ("qr_mode", C.c_int),
     ]
 
 
@@ -37,6 +37,7 @@ class bkrylov_info(C.Structure):
         ("outer", C.c_int), ("relres_max", C.c_double), ("relres", C.POINTER(C.c_double)),
         ("history", C.POINTER(C.c_double)), ("decisions", C.POINTER(C.c_uint8)),
         ("history_len", C.c_int), ("elapsed_ms", C.c_double), ("reorths_cholqr", C.c_int),
+        ("replacements", C.c_int),
     ]
 
 

@@ -224,7 +224,7 @@ class Handle:
     def solve(self, method: str, A: "Operator", B, X=None, *, tol=1e-8, maxit=1000, eta=math.inf,
               prec="fp64", restart=30, ortho="mgs", ir_inner_tol=1e-5, ir_max_outer=30,
               forced_reortho=None, sync_every=0, record=True, profile=False, p=None, precond=None,
-              one_reduction=False, norm="max", qr="cholqr2"):
+              one_reduction=False, norm="max", qr="cholqr2", replace_every=0):
         """Run bkrylov_solve_{bcg,bbicgstab,bgmres}; returns (X, SolveInfo).
 
         B, X: n x s blocks, float64 (prec "fp64", "fp32_ir") or float32 (prec "fp32"),
@@ -234,7 +234,9 @@ class Handle:
         applying M^{-1} (BCG, e.g. ``op_jacobi(A)``); ``one_reduction``: the 1R-BCG
         schedule; ``norm``: the stopping measure, "max" (every column) or "fro"; ``qr``:
         the normaliser of FP64 BCG, "cholqr2" (CholeskyQR2, Householder TSQR for the
-        blocks it declines) or "householder" (TSQR every time).
+        blocks it declines) or "householder" (TSQR every time); ``replace_every``: with
+        ``one_reduction``, form Q = A P and alpha = P^T Q directly after every m-th
+        iteration (and after a non-positive pivot of the recursive alpha).
         """
         s = B.shape[1]
         if X is None:
@@ -254,6 +256,7 @@ class Handle:
         o.precond = None if precond is None else precond.ptr.value
         o.one_reduction = 1 if one_reduction else 0
         o.qr_mode = {"cholqr2": 0, "householder": 1}[qr]
+        o.replace_every = int(replace_every)
         forced_arr = None
         if forced_reortho is not None:
             forced_arr = (C.c_uint8 * max(1, len(forced_reortho)))(*[1 if f else 0 for f in forced_reortho])
@@ -281,7 +284,7 @@ class Handle:
             converged=bool(info.converged), outer=info.outer, relres_max=info.relres_max,
             relres=np.array(relres[:s]), history=list(hist[:nrec]) if record else [],
             decisions=[bool(d) for d in dec[:nrec]] if record and prec != "fp32_ir" else [],
-            elapsed_ms=info.elapsed_ms, reorths_cholqr=info.reorths_cholqr)
+            elapsed_ms=info.elapsed_ms, reorths_cholqr=info.reorths_cholqr, replacements=info.replacements)
         return X, res
 
 
@@ -299,6 +302,7 @@ class SolveInfo:
     decisions: list = field(default_factory=list)
     elapsed_ms: float = 0.0
     reorths_cholqr: int = 0          # re-orthonormalisations done by CholeskyQR2
+    replacements: int = 0            # 1R-BCG: direct recomputations of Q and alpha
 
 
 class Operator:

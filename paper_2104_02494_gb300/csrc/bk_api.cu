@@ -138,6 +138,7 @@ int ctrl_upload(bkrylov_handle h, Ctrl* dev, int s, const SolveOpts& o, double e
   c->has_prec = o.precond != nullptr;
   c->one_r = o.one_reduction != 0;
   c->norm_mode = o.norm_mode;
+  c->replace_every = o.one_reduction ? o.replace_every : 0;
   for (int i = 0; i < s; ++i) c->sigma[i * kMaxS + i] = 1.0;
   BK_TRY(cudaMemcpyAsync(dev, c, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
   // the pinned staging buffer is reused: wait for the copy before returning
@@ -180,6 +181,7 @@ int finish_info(bkrylov_handle h, const Ctrl* dev, int s, const double* hist_dev
       BK_TRY(cudaMemcpy(info->decisions, dec_dev, nh, cudaMemcpyDeviceToHost));
     info->elapsed_ms = ms;
     info->reorths_cholqr = c->cholqr_count;
+    info->replacements = c->replacements;
     (void)nrec;
   }
   return status;
@@ -199,6 +201,7 @@ struct BcgBufs {
   uint8_t* dec;
   uint8_t* forced;
   bool cholqr = false;         // FP64 block case: CholeskyQR2 normaliser, TSQR the fallback
+  bool replace = false;        // 1R-BCG with the replacement of Q and alpha
 };
 
 template <typename T, typename Alloc>
@@ -369,6 +372,15 @@ cudaError_t bcg_iteration_1r(const Launch& L, const OpDesc& A, int s, T* X, cons
   if ((e = bcg_pupdate<T>(L, A.n, s, Zn, b.P, c)) != cudaSuccess) return e;    // P = Z + P beta
   e = bcg_pupdate<T>(L, A.n, s, b.U, b.Q, c);                                  // Q = U + Q beta
   prof_end(L, kPhPupdate, 2);
+  if (e != cudaSuccess || !b.replace) return e;
+  // replacement (the small kernel decided): Q = A P and alpha = P^T Q as in Alg. "2R-CG"
+  Epi<T> er;
+  er.left = b.P; er.sym = 1; er.gram_out = c->alpha; er.gpart = b.gpart;
+  er.counter = &c->counters[kCntA]; er.done = &c->done; er.only_if = &c->replace_now;
+  er.status_out = &c->status; er.stop_out = &c->done;
+  prof_begin(L, kPhSpmm);
+  e = spmm<T>(L, A, s, b.P, b.Q, nullptr, er);
+  prof_end(L, kPhSpmm, 1);
   return e;
 }
 
@@ -437,6 +449,7 @@ int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const
   bcg_layout<T>(bump, n, s, maxit, tp, L, &b, M != nullptr, one_r);
   b.M = M;
   b.cholqr = use_cholqr(o, s, sizeof(T) == 8);
+  b.replace = one_r && o.replace_every > 0;
   if ((rc = ctrl_upload(h, b.ctrl, s, o, eps))) return rc;
   if (o.forced_reortho && o.n_forced > 0) {
     const int nf = o.n_forced < maxit + 1 ? o.n_forced : maxit + 1;
@@ -539,7 +552,7 @@ int bcg_ir_device(bkrylov_handle h, bkrylov_op Aop, int s, const double* B, doub
   BK_TRY(cudaMemcpyAsync(nb, nrm + kMaxS, sizeof(double) * s, cudaMemcpyDeviceToHost, L.stream));
   BK_TRY(cudaStreamSynchronize(L.stream));
   for (int i = 0; i < s; ++i) nb[i] = std::sqrt(nb[i]);
-  int outer = 0, inner_total = 0, reorth_total = 0, status = BK_NOT_CONVERGED;
+  int outer = 0, inner_total = 0, reorth_total = 0, repl_total = 0, status = BK_NOT_CONVERGED;
   double relmax = 0.0, rel[kMaxS];
   const int max_outer = o.ir_max_outer > 0 ? o.ir_max_outer : 30;
   std::vector<double> hist;
@@ -573,6 +586,7 @@ int bcg_ir_device(bkrylov_handle h, bkrylov_op Aop, int s, const double* B, doub
     const int irc = bcg_device<float>(h, A, s, R32, D32, io, std::ldexp(1.0, -23), &ii);
     inner_total += ii.iters;
     reorth_total += ii.reorths;
+    repl_total += ii.replacements;
     if (irc != BK_OK && irc != BK_NOT_CONVERGED) { status = irc; break; }
     BK_TRY(ir_accumulate(L, n, s, D32, nrm, X));
     ++outer;
@@ -586,6 +600,8 @@ int bcg_ir_device(bkrylov_handle h, bkrylov_op Aop, int s, const double* B, doub
   if (info) {
     info->iters = inner_total;
     info->reorths = reorth_total;
+    info->replacements = repl_total;
+    info->reorths_cholqr = 0;
     info->outer = outer;
     info->converged = status == BK_OK;
     info->status = status;
@@ -1275,6 +1291,7 @@ static int check_solve_args(bkrylov_handle h, bkrylov_op A, int s, const void* B
   if (!(o.tol >= 0.0) || o.maxit < 0 || !(o.eta >= 0.0)) return BK_ERR_ARG;
   if (o.norm_mode != 0 && o.norm_mode != 1) return BK_ERR_ARG;
   if (o.qr_mode != 0 && o.qr_mode != 1) return BK_ERR_ARG;
+  if (o.replace_every < 0) return BK_ERR_ARG;
   if (o.subalgebra_p < 0 || (o.subalgebra_p > 0 && s % o.subalgebra_p != 0)) return BK_ERR_ARG;
   if (o.precond && o.precond->d.n != A->d.n) return BK_ERR_ARG;
   return BK_OK;
@@ -1386,7 +1403,10 @@ int bkrylov_bcg_launches_per_iteration(int64_t n, int s, const bkrylov_opts* opt
   if (n < 1 || s < 1 || s > kMaxS) return -1;
   bkrylov_opts o;
   opts_or_default(opts, &o);
-  return bcg_launches_per_iter(tsqr_plan(n, s), use_cholqr(o, s, o.prec == BK_FP64), o.precond != nullptr);
+  const TsqrPlan tp = tsqr_plan(n, s);
+  if (o.one_reduction)   // small 1, update (2), TSQR, preconditioner, U = A Z, small 2, two updates, replacement
+    return 7 + tsqr_launches(tp) + (o.precond ? 1 : 0) + (o.replace_every > 0 ? 1 : 0);
+  return bcg_launches_per_iter(tp, use_cholqr(o, s, o.prec == BK_FP64), o.precond != nullptr);
 }
 
 int bkrylov_adjoint_scatter(bkrylov_handle h, bkrylov_op A, int s, const double* Lam,

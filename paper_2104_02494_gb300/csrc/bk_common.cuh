@@ -61,6 +61,9 @@ struct Ctrl {
                      // re-orthonormalisation), 1 taken, 2 second factor failed (TSQR of Y1)
   int tsqr_now;      // the Householder TSQR runs in this iteration
   int cholqr_count;  // re-orthonormalisations normalised by CholeskyQR2
+  int replace_every; // 1R-BCG: form Q = A P and alpha = <P, Q> after every m-th iteration
+  int replace_now;   // ... after this iteration (set by the small kernel)
+  int replacements;
   double tol;
   double eta;
   double eps;        // machine epsilon of the working precision

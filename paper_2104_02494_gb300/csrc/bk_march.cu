@@ -45,8 +45,8 @@ namespace bk {
 
 namespace {
 
-// 7 consumer warps and one producer warp: 256 threads, so that a thread may hold
-// up to 255 registers (the FP32 Gram accumulators of 32-column blocks)
+// Streaming kernels: 7 consumer warps and one producer warp, 256 threads, so that a
+// thread may hold up to 255 registers (the FP32 Gram accumulators of 32-column blocks).
 constexpr int kConsumers = 7;
 constexpr int kPipeThreads = (kConsumers + 1) * 32;
 // Producer lanes of the producer warp.  The copies one thread issues do not
@@ -64,6 +64,15 @@ constexpr size_t kOneCtaSmem = 120 * 1024;
 // every shared-memory size below reserves that much for the alignment.
 constexpr size_t kRingAlign = 1024;
 enum : int { kQEpiNone = 0, kQEpiSym = 1, kQEpiFull = 2 };
+
+// Marching operator kernels (s <= 16): without a Gram, 11 consumer warps and the
+// producer warp (384 threads of at most 168 registers: more warps hide the latency of
+// the stencil's shared-memory loads; measured 0.55 -> 0.74 of HBM at s = 16); with
+// the Gram, whose two FP32 accumulator levels need up to 255 registers, 7.
+template <int kEpi>
+__host__ __device__ constexpr int march_consumers() { return kEpi == kQEpiNone ? 11 : 7; }
+template <int kEpi>
+__host__ __device__ constexpr int march_threads() { return (march_consumers<kEpi>() + 1) * 32; }
 enum : int { kMConst7 = 0, kMVar7 = 1, kMEdge5 = 2 };
 
 // ------------------------------------------------------------ host helpers ----
@@ -266,20 +275,20 @@ __device__ __forceinline__ float* ring_base(unsigned char* smem, int bar_off) {
   return reinterpret_cast<float*>((p + kRingAlign - 1) & ~(uintptr_t)(kRingAlign - 1));
 }
 template <int SW, bool kPair>
-__host__ __device__ constexpr size_t qgram_bytes(int cnt) {
-  return sizeof(double) * ((size_t)((cnt + 1) & ~1) + (size_t)kConsumers * QuadGram<SW, kPair>::kWarpDoubles);
+__host__ __device__ constexpr size_t qgram_bytes(int cnt, int nconsumers) {
+  return sizeof(double) * ((size_t)((cnt + 1) & ~1) + (size_t)nconsumers * QuadGram<SW, kPair>::kWarpDoubles);
 }
 
 // Grid-wide end of a fused Gram: every thread of the CTA takes part.  A CTA
 // whose pipeline gave up contributes NaN, so the result shows it.
-template <int SW, bool kPair>
+template <int SW, bool kPair, int NC>
 __device__ __forceinline__ void gram_epilogue(QuadGram<SW, kPair>& g, double* part, const double* wslots,
                                               int s, bool sym, bool consumer, bool aborted,
                                               const Epi<float>& ep) {
   const int cnt = sym ? ut_count(s) : s * s;
   if (consumer) g.finish();
   __syncthreads();
-  QuadGram<SW, kPair>::sum(s, sym, wslots, kConsumers, part);
+  QuadGram<SW, kPair>::sum(s, sym, wslots, NC, part);
   if (aborted)
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) part[i] = __longlong_as_double(0x7ff8000000000000ll);
   __syncthreads();
@@ -333,7 +342,7 @@ __device__ __forceinline__ float4 stencil_quad(const MarchArgs& a, int s, const 
 }
 
 template <int SW, int kOp, int kEpi, bool kHY>
-__global__ void __launch_bounds__(kPipeThreads, 1)
+__global__ void __launch_bounds__(march_threads<kEpi>(), 1)
 march4_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmC,
               const MarchArgs a, int s, float* __restrict__ Q, const Epi<float> ep) {
   if (ep.done && *ep.done) return;
@@ -344,7 +353,8 @@ march4_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ C
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_abort;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool consumer = warp < kConsumers;
+  constexpr int kNC = march_consumers<kEpi>();
+  const bool consumer = warp < kNC;
   const int cnt = kGram ? ut_count(s) : 0;
   double* part = reinterpret_cast<double*>(smem);
   double* wslots = part + ((cnt + 1) & ~1);
@@ -355,7 +365,7 @@ march4_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ C
   if (threadIdx.x == 0) {
     for (int k = 0; k < ns; ++k) {
       mbar_init(&full[k], 1);
-      mbar_init(&empty[k], kConsumers);
+      mbar_init(&empty[k], kNC);
     }
     s_abort = 0;
     mbar_fence_init();
@@ -430,7 +440,7 @@ march4_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ C
       const float* sm = down ? next : prev;    // plane z - 1
       const float* spp = down ? prev : next;   // plane z + 1
       float* Qz = Q + (int64_t)z * plane * s;
-      for (int st = warp; st < nsteps; st += kConsumers) {
+      for (int st = warp; st < nsteps; st += kNC) {
         const int c0 = st * 2 * RS + ps, c1 = c0 + RS;
         const int ty0c = (int)a.fdx.div((uint32_t)c0), ty1c = (int)a.fdx.div((uint32_t)c1);
         const int tx0c = c0 - ty0c * a.Tx, tx1c = c1 - ty1c * a.Tx;
@@ -463,7 +473,7 @@ march4_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ C
   if constexpr (kGram) {
     __syncthreads();
     aborted = s_abort != 0;
-    gram_epilogue<SW, true>(g, part, wslots, s, true, consumer, aborted, ep);
+    gram_epilogue<SW, true, kNC>(g, part, wslots, s, true, consumer, aborted, ep);
   }
 }
 
@@ -597,7 +607,7 @@ stream4_kernel(const float* __restrict__ X, const float* __restrict__ Y, const f
   }
   __syncthreads();
   aborted = s_abort != 0;
-  gram_epilogue<SW, kSym>(g, part, wslots, s, kSym, consumer, aborted, ep);
+  gram_epilogue<SW, kSym, kConsumers>(g, part, wslots, s, kSym, consumer, aborted, ep);
 }
 
 // ------------------------------------------------- row-per-lane streaming ----
@@ -779,7 +789,7 @@ cudaError_t march_launch(const Launch& L, const OpDesc& A, int s, const float* i
   int gx, gy, gz;
   march_grid(A, &gx, &gy, &gz);
   const int cf = kOp == kMConst7 ? 0 : 4;
-  const size_t gb = kEpi == kQEpiNone ? 0 : qgram_bytes<SW, true>(ut_count(s));
+  const size_t gb = kEpi == kQEpiNone ? 0 : qgram_bytes<SW, true>(ut_count(s), march_consumers<kEpi>());
   MarchArgs a;
   int grid = 0;
   size_t smem = 0;
@@ -806,7 +816,7 @@ cudaError_t march_launch(const Launch& L, const OpDesc& A, int s, const float* i
   }
   auto k = a.hy ? march4_kernel<SW, kOp, kEpi, true> : march4_kernel<SW, kOp, kEpi, false>;
   if ((e = smem_attr(k, smem)) != cudaSuccess) return e;
-  k<<<grid, kPipeThreads, smem, L.stream>>>(tmP, tmC, a, s, out, ep);
+  k<<<grid, march_threads<kEpi>(), smem, L.stream>>>(tmP, tmC, a, s, out, ep);
   return cudaGetLastError();
 }
 
@@ -841,7 +851,7 @@ template <int SW, int kMode, int kEpi>
 cudaError_t stream_launch(const Launch& L, int64_t n, int s, const float* X, const float* Y, const float* w,
                           float* Z, const Epi<float>& ep) {
   const int cnt = kEpi == kQEpiSym ? ut_count(s) : s * s;
-  const size_t gb = align_up(qgram_bytes<SW, kEpi == kQEpiSym>(cnt), 16);
+  const size_t gb = align_up(qgram_bytes<SW, kEpi == kQEpiSym>(cnt, kConsumers), 16);
   StreamArgs a;
   a.n = n;
   a.s = s;

@@ -26,8 +26,14 @@ __device__ __forceinline__ void l2_prefetch_rows(const float* base, int64_t n, i
 }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 __device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+// Packed FP32 FMAs (two lanes of a register pair per instruction on sm_100 and later),
+// rounded per component exactly as fmaf.
+__device__ __forceinline__ float2 fma2(float2 a, float2 x, float2 y) { return __ffma2_rn(a, x, y); }
 __device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
-  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+  const float2 aa = make_float2(a, a);
+  const float2 lo = fma2(aa, make_float2(x.x, x.y), make_float2(y.x, y.y));
+  const float2 hi = fma2(aa, make_float2(x.z, x.w), make_float2(y.z, y.w));
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 __device__ __forceinline__ float4 add4(float4 a, float4 b) {
   return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);

@@ -123,12 +123,14 @@ struct QuadGram {
 
   __device__ __forceinline__ static void outer(float (&acc)[16], const float4& l, const float4& m) {
     const float lv[4] = {l.x, l.y, l.z, l.w};
+    const float2 mlo = make_float2(m.x, m.y), mhi = make_float2(m.z, m.w);
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      acc[4 * t + 0] = fmaf(lv[t], m.x, acc[4 * t + 0]);
-      acc[4 * t + 1] = fmaf(lv[t], m.y, acc[4 * t + 1]);
-      acc[4 * t + 2] = fmaf(lv[t], m.z, acc[4 * t + 2]);
-      acc[4 * t + 3] = fmaf(lv[t], m.w, acc[4 * t + 3]);
+      const float2 aa = make_float2(lv[t], lv[t]);
+      const float2 lo = fma2(aa, mlo, make_float2(acc[4 * t + 0], acc[4 * t + 1]));
+      const float2 hi = fma2(aa, mhi, make_float2(acc[4 * t + 2], acc[4 * t + 3]));
+      acc[4 * t + 0] = lo.x; acc[4 * t + 1] = lo.y;
+      acc[4 * t + 2] = hi.x; acc[4 * t + 3] = hi.y;
     }
   }
 

@@ -677,7 +677,21 @@ __global__ void __launch_bounds__(kST) small_bcg_2_k(Ctrl* c, double* history, u
     for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
       const int a = i / s, b = i % s;
       const int u = a < b ? a : b, v = a < b ? b : a;
-      c->alpha[IDX(a, b)] = c->delta[IDX(u, v)] - S.C[IDX(u, v)];
+      const double al = c->delta[IDX(u, v)] - S.C[IDX(u, v)];
+      c->alpha[IDX(a, b)] = al;
+      S.D[IDX(a, b)] = al;
+    }
+    if (c->replace_every > 0) {
+      // replacement after every m-th iteration and whenever the recursive alpha has a
+      // non-positive Cholesky pivot (the next lambda needs its Cholesky factor)
+      __syncthreads();
+      const bool due = (k + 1) % c->replace_every == 0;
+      const bool ok = due || sm_cholesky(S.D, s, &S.flag);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        c->replace_now = ok && !due ? 0 : 1;
+        c->replacements += c->replace_now;
+      }
     }
   }
   if (threadIdx.x == 0 && c->iter >= c->maxit) { c->done = kDoneStopped; c->status = BK_NOT_CONVERGED; }

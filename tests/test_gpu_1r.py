@@ -130,3 +130,54 @@ def test_1r_unsupported(h):
         with pytest.raises(BkError):
             h.solve(method, op, _dev(prob.B), tol=1e-8, maxit=10, one_reduction=True)
     op.close()
+
+
+def test_1r_replacement_iterates_and_count(h):
+    """replace_every = m: Q = A P and alpha = P^T Q formed after every m-th iteration, the
+    iterates of the oracle's bcg_1r(replace=m) at 1e-12 (FP64), the same count, and with
+    m = 1 the two-reduction schedule's iterates."""
+    prob = W.problem("poisson2d")
+    op = _op(h, prob, "csr")
+    ref2 = oracle.bcg(prob.A, prob.B, tol=1e-8, maxit=1000, eta=math.inf, record_iterates=30)
+    for m in (1, 3):
+        ref = oracle.bcg_1r(prob.A, prob.B, tol=1e-8, maxit=1000, eta=math.inf, replace=m, record_iterates=30)
+        for k in (1, 5, 30):
+            X, info = h.solve("bcg", op, _dev(prob.B), tol=0.0, maxit=k, eta=math.inf, one_reduction=True,
+                              replace_every=m)
+            assert _rel(X.cpu().numpy(), ref.iterates[k - 1]) <= 1e-12, (m, k)
+            assert info.replacements == k // m
+            if m == 1:
+                assert _rel(X.cpu().numpy(), ref2.iterates[k - 1]) <= 1e-11
+        X, info = h.solve("bcg", op, _dev(prob.B), tol=1e-8, maxit=1000, eta=math.inf, one_reduction=True,
+                          replace_every=m)
+        assert info.converged and abs(info.iters - ref.iters) <= 2
+        assert info.replacements == (info.iters - 1) // m == ref.replacements
+    from paper_2104_02494_gb300.api import BkError
+    with pytest.raises(BkError):
+        h.solve("bcg", op, _dev(prob.B), tol=1e-8, maxit=10, one_reduction=True, replace_every=-1)
+    op.close()
+
+
+def test_1r_fp32_inner_converges_with_replacement_every_iteration(h):
+    """The FP32 inner solves on the log-normal workload, where the plain recursion breaks
+    down: with replacement after every iteration (the two-reduction formulas for alpha and
+    Q) they follow the oracle's float32 bcg_1r(replace=1) and refinement reaches 1e-10."""
+    prob = W.problem("vardiff3d", grid=16, s=16)
+    op = _op(h, prob, "stencil")
+    Rs = (prob.B / oracle.col_norms(prob.B)).astype(np.float32)
+    ref = oracle.bcg_1r(prob.A, Rs, tol=1e-5, maxit=2000, eta=math.inf, dtype=np.float32, replace=1,
+                        record_iterates=4)
+    assert ref.converged
+    # FP32 block CG on this workload amplifies rounding about tenfold per iteration: the
+    # iterates of two FP32 implementations are comparable for the first few only
+    for k in (1, 2, 4):
+        X, info = h.solve("bcg", op, _dev(prob.B), tol=0.0, maxit=k, eta=math.inf, prec="fp32_ir",
+                          ir_max_outer=1, one_reduction=True, replace_every=1)
+        refk = ref.iterates[k - 1].astype(np.float64) * oracle.col_norms(prob.B)
+        assert _rel(X.cpu().numpy(), refk) <= 2e-4, k
+    X, info = h.solve("bcg", op, _dev(prob.B), tol=1e-10, maxit=5000, prec="fp32_ir", one_reduction=True,
+                      replace_every=1)
+    assert info.converged and info.replacements > 0
+    true = oracle.col_norms(prob.B - oracle.spmm(prob.A, X.cpu().numpy())) / oracle.col_norms(prob.B)
+    assert true.max() <= 1.5e-10
+    op.close()
