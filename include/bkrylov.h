@@ -251,7 +251,13 @@ int bkrylov_bdot(bkrylov_handle h, int64_t n, int s, const void* X, const void* 
    Errors: BK_ERR_ARG for n < 1, s outside 1..32, null pointers or another prec, before
    any work; BK_ERR_CUDA if a CUDA call fails.
    The first call on a device looks up the array's device address (cudaGetSymbolAddress
-   on the current device); make that first call before any stream capture.
+   on the current device); make that first call before any stream capture.  With lazy
+   module loading the first call of each precision on a device may also make the driver
+   load the library's kernels and the array itself: make one call per device and
+   precision before reserving the device-memory budget; later calls allocate nothing.
+   The sums run in a fixed order, so results are reproducible from call to call, but the
+   512-CTA grid orders the partial sums differently from bkrylov_bdot: the two agree to
+   rounding, not bit for bit.
    All calls share the one array: calls that overlap on the GPU (other streams, other
    host threads) race and must be serialised by the caller. */
 int bkrylov_bdot_noalloc(int64_t n, int s, const void* X, const void* Y, double* G, int sym,

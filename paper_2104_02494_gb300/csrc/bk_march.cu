@@ -69,10 +69,33 @@ enum : int { kQEpiNone = 0, kQEpiSym = 1, kQEpiFull = 2 };
 // producer warp (384 threads of at most 168 registers: more warps hide the latency of
 // the stencil's shared-memory loads; measured 0.55 -> 0.74 of HBM at s = 16); with
 // the Gram, whose two FP32 accumulator levels need up to 255 registers, 7.
-template <int kEpi>
-__host__ __device__ constexpr int march_consumers() { return kEpi == kQEpiNone ? 11 : 7; }
-template <int kEpi>
-__host__ __device__ constexpr int march_threads() { return (march_consumers<kEpi>() + 1) * 32; }
+template <int kEpi, int SW>
+__host__ __device__ constexpr int march_consumers() { return (kEpi == kQEpiNone || SW >= 16) ? 11 : 7; }
+template <int kEpi, int SW>
+__host__ __device__ constexpr int march_threads() { return (march_consumers<kEpi, SW>() + 1) * 32; }
+// The fused Gram of the marching kernel: for s = 16 the tensor-core MmaGram (TF32
+// products with the three-term split, 16 x 8 tiles of mma.sync; a few accumulator
+// registers per lane, so 11 consumer warps fit), for s = 4 and 8 the CUDA-core pair
+// scheme QuadGram (at s = 8 half of every 16-row tensor-core tile would be empty;
+// measured: 0.372 of HBM with QuadGram against 0.338 on the 192^3 VAR7 operator).
+// MmaGram keeps its double slots in registers while streaming and dumps them into the
+// ring's memory (free once the pipeline has drained) for the CTA sum.
+template <int SW, int kEpi>
+using MarchGram =
+    typename std::conditional<(SW >= 16), MmaGram<SW, march_threads<kEpi, SW>(), true>, QuadGram<SW, true>>::type;
+// Bytes of the Gram region at the start of the dynamic shared memory: the packed sums,
+// then the Gram's slots (QuadGram) or the per-warp staging buffers (MmaGram).
+template <int SW, int kEpi>
+__host__ __device__ constexpr size_t march_gram_bytes(int cnt) {
+  if constexpr (SW >= 16) {
+    using G = MarchGram<SW, kEpi>;
+    return sizeof(double) * (size_t)((cnt + 1) & ~1) +
+           sizeof(float) * ((size_t)(march_threads<kEpi, SW>() / 32) * G::stage_floats());
+  } else {
+    return sizeof(double) * ((size_t)((cnt + 1) & ~1) +
+                             (size_t)march_consumers<kEpi, SW>() * QuadGram<SW, true>::kWarpDoubles);
+  }
+}
 enum : int { kMConst7 = 0, kMVar7 = 1, kMEdge5 = 2 };
 
 // ------------------------------------------------------------ host helpers ----
@@ -342,22 +365,31 @@ __device__ __forceinline__ float4 stencil_quad(const MarchArgs& a, int s, const 
 }
 
 template <int SW, int kOp, int kEpi, bool kHY>
-__global__ void __launch_bounds__(march_threads<kEpi>(), 1)
+__global__ void __launch_bounds__(march_threads<kEpi, SW>(), 1)
 march4_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmC,
               const MarchArgs a, int s, float* __restrict__ Q, const Epi<float> ep) {
   if (ep.done && *ep.done) return;
   if (ep.only_if && !*ep.only_if) return;
   constexpr int LPR = SW / 4, RS = 32 / LPR;
-  using Gram = QuadGram<SW, true>;
+  using Gram = MarchGram<SW, kEpi>;
   constexpr bool kGram = kEpi != kQEpiNone;
+  constexpr bool kMma = SW >= 16;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_abort;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int kNC = march_consumers<kEpi>();
+  constexpr int kNC = march_consumers<kEpi, SW>();
   const bool consumer = warp < kNC;
   const int cnt = kGram ? ut_count(s) : 0;
   double* part = reinterpret_cast<double*>(smem);
   double* wslots = part + ((cnt + 1) & ~1);
+  // MmaGram: two staging buffers per warp (its double slots are registers, dumped at
+  // the end into the ring's memory)
+  float* stl = nullptr;
+  float* stm = nullptr;
+  if constexpr (kMma) {
+    stl = reinterpret_cast<float*>(wslots) + (size_t)warp * Gram::stage_floats();
+    stm = stl + Gram::stage_floats() / 2;
+  }
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.gram_bytes);
   uint64_t* empty = full + kMaxStages;
   float* ring = ring_base(smem, a.gram_bytes);
@@ -371,7 +403,10 @@ march4_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ C
     mbar_fence_init();
   }
   Gram g;
-  if (kGram && consumer) g.init(wslots + (size_t)warp * Gram::kWarpDoubles);
+  if constexpr (kGram) {
+    if constexpr (kMma) g.init(nullptr);   // every thread zeroes its register slots
+    else if (consumer) g.init(wslots + (size_t)warp * Gram::kWarpDoubles);
+  }
   __syncthreads();
 
   const int tile = blockIdx.x % a.ntiles, seg = blockIdx.x / a.ntiles;
@@ -416,9 +451,10 @@ march4_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ C
     __syncwarp();
   } else {
     // ---- consumers: per step a warp takes 2 RS cells of the tile; the lane of row
-    // slot ps and quad q computes quad q of cell c0 = base + ps and quad LPR - 1 - q of
-    // cell c1 = c0 + RS (two independent chains), and adds the pair to the Gram ----
-    const int ps = lane / LPR, q = lane % LPR, qb = LPR - 1 - q;
+    // slot ps and quad q computes quad q of cell c0 = base + ps and quad q1 of cell
+    // c1 = c0 + RS (two independent chains): q1 = q for the tensor-core Gram, which
+    // stages both cells' rows; q1 = LPR - 1 - q for the pair scheme of QuadGram ----
+    const int ps = lane / LPR, q = lane % LPR, qb = kMma ? q : LPR - 1 - q;
     const bool qok0 = 4 * q < s, qok1 = 4 * qb < s;
     const int cells = a.Tx * a.Ty;
     const int nsteps = (cells + 2 * RS - 1) / (2 * RS);
@@ -454,7 +490,16 @@ march4_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ C
         if (in1 && qok1) v1 = stencil_quad<kOp, kHY>(a, s, sm, sc, spp, b1, qb);
         if (in0 && qok0) st4(Qz + ((int64_t)(ty0 + ty0c) * a.gx + tx0 + tx0c) * s + 4 * q, v0);
         if (in1 && qok1) st4(Qz + ((int64_t)(ty0 + ty1c) * a.gx + tx0 + tx1c) * s + 4 * qb, v1);
-        if constexpr (kGram) g.add(sc + b0 * s, sc + b1 * s, v0, v1, s);
+        if constexpr (kGram) {
+          if constexpr (kMma) {
+            const float4 l0 = (in0 && qok0) ? ld4(sc + b0 * s + 4 * q) : zero4();
+            const float4 l1 = (in1 && qok1) ? ld4(sc + b1 * s + 4 * qb) : zero4();
+            g.row(l0, v0, stl, stm);
+            g.row(l1, v1, stl, stm);
+          } else {
+            g.add(sc + b0 * s, sc + b1 * s, v0, v1, s);
+          }
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[sl_prev]);   // ring index i - 1 is no longer read
@@ -473,7 +518,21 @@ march4_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ C
   if constexpr (kGram) {
     __syncthreads();
     aborted = s_abort != 0;
-    gram_epilogue<SW, true, kNC>(g, part, wslots, s, true, consumer, aborted, ep);
+    if constexpr (kMma) {
+      // the ring is idle here: every consumer has passed its last stage and the
+      // producer lanes have waited for their last copies
+      if (consumer) g.finish(stl, stm);
+      g.dump(ring);
+      __syncthreads();
+      g.sum(s, true, ring, part, stl, stm);
+      if (aborted)
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) part[i] = __longlong_as_double(0x7ff8000000000000ll);
+      __syncthreads();
+      if (!grid_reduce_last(part, cnt, ep.gpart, ep.counter)) return;
+      unpack_gram(part, s, true, ep.gram_out);
+    } else {
+      gram_epilogue<SW, true, kNC>(g, part, wslots, s, true, consumer, aborted, ep);
+    }
   }
 }
 
@@ -789,11 +848,15 @@ cudaError_t march_launch(const Launch& L, const OpDesc& A, int s, const float* i
   int gx, gy, gz;
   march_grid(A, &gx, &gy, &gz);
   const int cf = kOp == kMConst7 ? 0 : 4;
-  const size_t gb = kEpi == kQEpiNone ? 0 : qgram_bytes<SW, true>(ut_count(s), march_consumers<kEpi>());
+  const size_t gb = kEpi == kQEpiNone ? 0 : march_gram_bytes<SW, kEpi>(ut_count(s));
   MarchArgs a;
   int grid = 0;
   size_t smem = 0;
   if (!plan_march(gx, gy, gz, s, cf, L.sms, gb, &a, &grid, &smem)) return cudaErrorNotSupported;
+  if constexpr (SW >= 16 && kEpi != kQEpiNone) {
+    // the Gram's slots are dumped into the ring at the end
+    if ((size_t)a.ns * a.stage_floats < MarchGram<SW, kEpi>::slot_floats()) return cudaErrorNotSupported;
+  }
   a.fdx = FastDiv((uint32_t)a.Tx);
   if (kOp == kMConst7) {
     const double* c = A.c7;   // (centre, -x, +x, -y, +y, -z, +z)
@@ -816,7 +879,7 @@ cudaError_t march_launch(const Launch& L, const OpDesc& A, int s, const float* i
   }
   auto k = a.hy ? march4_kernel<SW, kOp, kEpi, true> : march4_kernel<SW, kOp, kEpi, false>;
   if ((e = smem_attr(k, smem)) != cudaSuccess) return e;
-  k<<<grid, march_threads<kEpi>(), smem, L.stream>>>(tmP, tmC, a, s, out, ep);
+  k<<<grid, march_threads<kEpi, SW>(), smem, L.stream>>>(tmP, tmC, a, s, out, ep);
   return cudaGetLastError();
 }
 

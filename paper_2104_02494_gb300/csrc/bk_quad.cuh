@@ -290,7 +290,10 @@ __device__ __forceinline__ void mma_tf32(float* d, const uint32_t (&a)[4], const
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-template <int SW>
+// NTH: threads of the CTA (every thread owns 4 NTILE double slots; the CTA sum runs
+// over NTH / 32 warps).  kRegSlots: the double slots live in registers until dump()
+// writes them to a slot array for the CTA sum (no shared memory while streaming).
+template <int SW, int NTH = kThreads, bool kRegSlots = false>
 struct MmaGram {
   using S = QuadShape<SW>;
   static_assert(SW >= 8, "MmaGram needs at least 8 columns");
@@ -305,26 +308,46 @@ struct MmaGram {
   static constexpr int WIN2 = 32;                      // windows per float register level
   float c[NTILE][4];
   float c2[NTILE][4];
+  double sreg[kRegSlots ? NTILE : 1][4];
   int ks, wins, trip_in_k;
-  double* slot;                                        // slot[e * kThreads], e < 4 NTILE
+  double* slot;                                        // slot[e * NTH], e < 4 NTILE
 
-  __host__ __device__ static constexpr size_t slot_floats() { return (size_t)2 * 4 * NTILE * kThreads; }
+  __host__ __device__ static constexpr size_t slot_floats() { return (size_t)2 * 4 * NTILE * NTH; }
   __host__ __device__ static constexpr size_t stage_floats() { return (size_t)2 * BUFROWS * STR; }   // per warp
 
   __device__ __forceinline__ void init(float* slots) {
-    slot = reinterpret_cast<double*>(slots) + threadIdx.x;
+    slot = kRegSlots ? nullptr : reinterpret_cast<double*>(slots) + threadIdx.x;
 #pragma unroll
     for (int i = 0; i < NTILE; ++i)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) { c[i][e] = 0.f; c2[i][e] = 0.f; slot[(4 * i + e) * kThreads] = 0.0; }
+      for (int e = 0; e < 4; ++e) {
+        c[i][e] = 0.f;
+        c2[i][e] = 0.f;
+        if constexpr (kRegSlots) sreg[i][e] = 0.0;
+        else slot[(4 * i + e) * NTH] = 0.0;
+      }
     ks = 0; wins = 0; trip_in_k = 0;
   }
   __device__ __forceinline__ void flush2() {
 #pragma unroll
     for (int i = 0; i < NTILE; ++i)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) { slot[(4 * i + e) * kThreads] += (double)c2[i][e]; c2[i][e] = 0.f; }
+      for (int e = 0; e < 4; ++e) {
+        if constexpr (kRegSlots) sreg[i][e] += (double)c2[i][e];
+        else slot[(4 * i + e) * NTH] += (double)c2[i][e];
+        c2[i][e] = 0.f;
+      }
     wins = 0;
+  }
+  // kRegSlots: the thread's double slots into the slot array (slot_floats() floats)
+  __device__ __forceinline__ void dump(float* slots) const {
+    if constexpr (kRegSlots) {
+      double* d = reinterpret_cast<double*>(slots) + threadIdx.x;
+#pragma unroll
+      for (int i = 0; i < NTILE; ++i)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) d[(4 * i + e) * NTH] = sreg[i][e];
+    }
   }
   __device__ __forceinline__ void flush1() {
 #pragma unroll
@@ -429,7 +452,7 @@ struct MmaGram {
       const int ln = (r % 8) * 4 + q / 2;
       const int e = 4 * tile + (r / 8) * 2 + (q % 2);
       double sum = 0.0;
-      for (int w = 0; w < kWarps; ++w) sum += sl[e * kThreads + w * 32 + ln];
+      for (int w = 0; w < NTH / 32; ++w) sum += sl[e * NTH + w * 32 + ln];
       part[i] = sum;
     }
     __syncthreads();
