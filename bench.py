@@ -52,10 +52,12 @@ UNIT = "RHS*iter/s"
 # (the part's nominal 1.25 TFLOP/s FP64 rate at its maximum SM clock)
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
 
-# DRAM bytes (read + write) per launch of a kernel phase, from one ncu --set full capture
-# of the current kernel on the same workload (the level-0 TSQR leaf factor at 128^3, s = 8:
-# 134.349 MB read + 79.423 MB written); keyed by (phase, grid, s, operator).
-NCU_TRAFFIC = {("tsqr_leaf_factor", 128, 8, "stencil"): 134.349056e6 + 79.423488e6}
+# DRAM bytes (read + write) per launch of a kernel phase, from one ncu capture of the current
+# kernel on the same workload (the level-0 TSQR leaf factor at 128^3, s = 8: 134.349 MB read +
+# 79.423 MB written; the FP64 update with the Gram of R-tilde: 536.946 MB read + 226.509 MB
+# written); keyed by (phase, grid, s, operator).
+NCU_TRAFFIC = {("tsqr_leaf_factor", 128, 8, "stencil"): 134.349056e6 + 79.423488e6,
+               ("update_rho", 128, 8, "stencil"): 536.946432e6 + 226.508544e6}
 
 
 def _hbm_peak():
