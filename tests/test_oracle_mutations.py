@@ -172,6 +172,45 @@ def test_bcg1r_mutation_is_caught(old, new):
     assert not _bcg1r_battery_passes(_mutant("oracle.bcg", "bcg_1r", old, new))
 
 
+def _replace_battery_passes(fn):
+    """1R-BCG with the replacement of Q and alpha: after every iteration (replace = 1) the
+    iterates are the 2R oracle's and every iteration counts; replace = 5 replaces after
+    iterations 5 and 10 of 12 without moving the (well-conditioned, FP64) iterates."""
+    try:
+        bmod = sys.modules["oracle.bcg"]
+        A = W.lap2d5(12, 11)
+        B = W.normal_block(A.n, 4, 2)
+        a = bmod.bcg(A, B, tol=0.0, maxit=12, eta=math.inf, record_iterates=12)
+        for m, count in ((1, 12), (5, 2)):
+            b = fn(A, B, tol=0.0, maxit=12, eta=math.inf, record_iterates=12, replace=m)
+            if b.replacements != count:
+                return False
+            for k in range(12):
+                if np.abs(b.iterates[k] - a.iterates[k]).max() > 1e-10 * np.abs(a.iterates[k]).max():
+                    return False
+        return True
+    except Exception:
+        return False
+
+
+REPLACE_MUTATIONS = [
+    ("Q = op(P)                                   # Q^{k+1} = A P^{k+1}",
+     "Q = op(Z)                                   # Q^{k+1} = A P^{k+1}"),          # wrong operand
+    ("alpha = gram(P, Q)                          # alpha^{k+1}", "alpha = gram(Q, Q)                          # alpha^{k+1}"),
+    ("(k + 1) % replace == 0", "k % replace == 0"),                                  # off by one
+    ("or not _chol_ok(alpha)", "and not _chol_ok(alpha)"),                           # trigger inverted
+]
+
+
+def test_unmutated_replacement_passes_battery():
+    assert _replace_battery_passes(sys.modules["oracle.bcg"].bcg_1r)
+
+
+@pytest.mark.parametrize("old,new", REPLACE_MUTATIONS)
+def test_replacement_mutation_is_caught(old, new):
+    assert not _replace_battery_passes(_mutant("oracle.bcg", "bcg_1r", old, new))
+
+
 def _localized_battery_passes(cls):
     """Distributed S-QR = LAPACK QR of the concatenated blocks (signs fixed), 1, 5 and 8 tiles."""
     try:
