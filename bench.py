@@ -631,33 +631,42 @@ def run_one_reduction(args):
     from paper_2104_02494_gb300.api import Handle, operator_from_problem
     build()
     h = Handle(0)
+    # variants: (name, one_reduction, replace_every)
+    std = (("two_reductions", False, 0), ("one_reduction", True, 0), ("one_reduction_replace10", True, 10))
+    ir = (("two_reductions", False, 0), ("one_reduction", True, 0), ("one_reduction_replace1", True, 1))
     cases = [
         ("poisson2d 64^2 5-point CSR, s=4, FP64 BCG eta=inf, 1e-8", "poisson2d", "csr", None, 4, False,
-         dict(tol=1e-8, eta=math.inf)),
+         dict(tol=1e-8, eta=math.inf), std),
         ("laplace3d 128^3 stencil, s=8, FP64 BCG eta=inf, 1e-8", "laplace3d", "stencil", None, 8, False,
-         dict(tol=1e-8, eta=math.inf)),
+         dict(tol=1e-8, eta=math.inf), std),
         ("vardiff3d 128^3 var7 stencil, s=8, FP64 BCG eta=1e4, Jacobi, 1e-8", "vardiff3d", "stencil", 128, 8,
-         True, dict(tol=1e-8, eta=1e4)),
+         True, dict(tol=1e-8, eta=1e4), std),
+        ("vardiff3d 128^3 var7 stencil, s=16, FP32 BCG + FP64 refinement, Jacobi, eta=1, 1e-10", "vardiff3d",
+         "stencil", 128, 16, True, dict(tol=1e-10, eta=1.0, prec="fp32_ir"), ir),
     ]
     out = []
-    for label, wl, use, grid, s, jac, kw in cases:
+    for label, wl, use, grid, s, jac, kw, variants in cases:
         prob = W.problem(wl, s=s, grid=grid, with_csr=(use == "csr"))
         op = operator_from_problem(h, prob, use)
         M = h.op_jacobi(op) if jac else None
         B = torch.from_numpy(prob.B).cuda()
         row = {"case": label}
-        for name, one in (("two_reductions", False), ("one_reduction", True)):
-            h.solve("bcg", op, B, maxit=3, record=False, precond=M, one_reduction=one, **kw)
+        for name, one, rep in variants:
+            h.solve("bcg", op, B, maxit=3, record=False, precond=M, one_reduction=one, replace_every=rep, **kw)
             times = []
             for _ in range(2):
-                _, info = h.solve("bcg", op, B, maxit=20000, record=False, precond=M, one_reduction=one, **kw)
+                _, info = h.solve("bcg", op, B, maxit=20000, record=False, precond=M, one_reduction=one,
+                                  replace_every=rep, **kw)
                 times.append(info.elapsed_ms)
             pk = dict(kw, tol=0.0)
             if kw.get("prec") == "fp32_ir":
                 pk["ir_max_outer"] = 1
-            _, i23 = h.solve("bcg", op, B, maxit=23, record=False, precond=M, one_reduction=one, **pk)
-            _, i3 = h.solve("bcg", op, B, maxit=3, record=False, precond=M, one_reduction=one, **pk)
+            _, i23 = h.solve("bcg", op, B, maxit=23, record=False, precond=M, one_reduction=one, replace_every=rep,
+                             **pk)
+            _, i3 = h.solve("bcg", op, B, maxit=3, record=False, precond=M, one_reduction=one, replace_every=rep,
+                            **pk)
             row[name] = {"time_ms": min(times), "iters": info.iters, "converged": info.converged,
+                         "status": info.status_name, "replacements": info.replacements,
                          "relres_max": info.relres_max, "ms_per_iter": (i23.elapsed_ms - i3.elapsed_ms) / 20}
         out.append(row)
         if M is not None:
