@@ -65,19 +65,21 @@ constexpr size_t kOneCtaSmem = 120 * 1024;
 constexpr size_t kRingAlign = 1024;
 enum : int { kQEpiNone = 0, kQEpiSym = 1, kQEpiFull = 2 };
 
-// Marching operator kernels (s <= 16): without a Gram, 11 consumer warps and the
+// Marching operator kernels (s <= 32): without a Gram, 11 consumer warps and the
 // producer warp (384 threads of at most 168 registers: more warps hide the latency of
 // the stencil's shared-memory loads; measured 0.55 -> 0.74 of HBM at s = 16); with
 // the Gram, whose two FP32 accumulator levels need up to 255 registers, 7.
 template <int kEpi, int SW>
-__host__ __device__ constexpr int march_consumers() { return (kEpi == kQEpiNone || SW >= 16) ? 11 : 7; }
+__host__ __device__ constexpr int march_consumers() { return (kEpi == kQEpiNone || SW == 16) ? 11 : 7; }
 template <int kEpi, int SW>
 __host__ __device__ constexpr int march_threads() { return (march_consumers<kEpi, SW>() + 1) * 32; }
-// The fused Gram of the marching kernel: for s = 16 the tensor-core MmaGram (TF32
-// products with the three-term split, 16 x 8 tiles of mma.sync; a few accumulator
-// registers per lane, so 11 consumer warps fit), for s = 4 and 8 the CUDA-core pair
-// scheme QuadGram (at s = 8 half of every 16-row tensor-core tile would be empty;
-// measured: 0.372 of HBM with QuadGram against 0.338 on the 192^3 VAR7 operator).
+// The fused Gram of the marching kernel: for s = 16 and 32 the tensor-core MmaGram
+// (TF32 products with the three-term split, 16 x 8 tiles of mma.sync; at s = 16 few
+// accumulator registers per lane, so 11 consumer warps fit; at s = 32 its 8 tiles take
+// 128 registers per lane and 7 consumers keep the 255-register budget), for s = 4 and
+// 8 the CUDA-core pair scheme QuadGram (at s = 8 half of every 16-row tensor-core tile
+// would be empty; measured: 0.372 of HBM with QuadGram against 0.338 on the 192^3 VAR7
+// operator).
 // MmaGram keeps its double slots in registers while streaming and dumps them into the
 // ring's memory (free once the pipeline has drained) for the CTA sum.
 template <int SW, int kEpi>
@@ -890,15 +892,13 @@ cudaError_t march_epi(const Launch& L, const OpDesc& A, int s, const float* in, 
   return cudaErrorNotSupported;
 }
 
-// Widths above 16 stay with the row kernels: the 32-column Gram accumulators of
-// this kernel do not fit the registers of a thread next to the stencil (measured:
-// slower than the row kernel at s = 32).
 template <int kOp>
 cudaError_t march_sw(const Launch& L, const OpDesc& A, int s, const float* in, float* out, const Epi<float>& ep) {
   switch (next_pow2_s(s)) {
     case 4: return march_epi<4, kOp>(L, A, s, in, out, ep);
     case 8: return march_epi<8, kOp>(L, A, s, in, out, ep);
     case 16: return march_epi<16, kOp>(L, A, s, in, out, ep);
+    case 32: return march_epi<32, kOp>(L, A, s, in, out, ep);
     default: return cudaErrorNotSupported;
   }
 }
