@@ -747,6 +747,43 @@ __device__ __forceinline__ bool rstream_consume(const RStreamArgs& a, const floa
   return alive;
 }
 
+// The producer warp of the streaming kernels: lane i (< kProducers) issues the stages
+// i, i + kProducers, ... of this CTA's chunks (nbox boxes of kBoxRows rows of each
+// operand), each after its slot was released, then waits (bounded) for its last copies.
+template <int SW>
+__device__ __forceinline__ void rstream_produce(const CUtensorMap& tmX, const CUtensorMap& tmY, const RStreamArgs& a,
+                                                float* ring, uint64_t* full, uint64_t* empty, int64_t my_chunks,
+                                                volatile int* s_abort, const Epi<float>& ep) {
+  const int lane = threadIdx.x & 31;
+  const int ns = a.ns;
+  if (lane < kProducers) {
+    int64_t last[kMaxStages];
+    for (int k = 0; k < kMaxStages; ++k) last[k] = -1;
+    const uint32_t box_bytes = (uint32_t)kBoxRows * SW * 4;
+    const uint32_t bytes = box_bytes * a.nbox * (a.two ? 2 : 1);
+    for (int64_t i = lane; i < my_chunks; i += kProducers) {
+      const int slot = (int)(i % ns);
+      if (i >= ns && !mbar_wait(&empty[slot], (uint32_t)((i / ns) - 1) & 1u, s_abort)) {
+        report_timeout(ep.status_out, ep.stop_out);
+        *s_abort = 1;
+        break;
+      }
+      const int64_t r0 = (blockIdx.x + i * gridDim.x) * (int64_t)a.R;
+      float* st = ring + (size_t)slot * a.stage_floats;
+      mbar_arrive_expect_tx(&full[slot], bytes);
+      for (int b = 0; b < a.nbox; ++b) {
+        tma_load_2d(st + b * kBoxRows * SW, &tmX, 0, (int)(r0 + b * kBoxRows), &full[slot]);
+        if (a.two) tma_load_2d(st + a.op_floats + b * kBoxRows * SW, &tmY, 0, (int)(r0 + b * kBoxRows), &full[slot]);
+      }
+      last[slot] = i;
+    }
+    volatile int never = 0;
+    for (int k = lane; k < ns; k += kProducers)
+      if (last[k] >= 0) mbar_wait(&full[k], (uint32_t)(last[k] / ns) & 1u, &never);
+  }
+  __syncwarp();
+}
+
 template <int SW, int kMode, bool kSym>
 __global__ void __launch_bounds__((rconsumers<SW, kSym>() + 1) * 32, 1)
 rstream_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
@@ -778,32 +815,7 @@ rstream_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
   const int64_t my_chunks =
       (int64_t)blockIdx.x < a.nchunks ? (a.nchunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   if (!consumer) {
-    if (lane < kProducers) {
-      int64_t last[kMaxStages];
-      for (int k = 0; k < kMaxStages; ++k) last[k] = -1;
-      const uint32_t box_bytes = (uint32_t)kBoxRows * SW * 4;
-      const uint32_t bytes = box_bytes * a.nbox * (a.two ? 2 : 1);
-      for (int64_t i = lane; i < my_chunks; i += kProducers) {
-        const int slot = (int)(i % ns);
-        if (i >= ns && !mbar_wait(&empty[slot], (uint32_t)((i / ns) - 1) & 1u, &s_abort)) {
-          report_timeout(ep.status_out, ep.stop_out);
-          s_abort = 1;
-          break;
-        }
-        const int64_t r0 = (blockIdx.x + i * gridDim.x) * (int64_t)a.R;
-        float* st = ring + (size_t)slot * a.stage_floats;
-        mbar_arrive_expect_tx(&full[slot], bytes);
-        for (int b = 0; b < a.nbox; ++b) {
-          tma_load_2d(st + b * kBoxRows * SW, &tmX, 0, (int)(r0 + b * kBoxRows), &full[slot]);
-          if (a.two) tma_load_2d(st + a.op_floats + b * kBoxRows * SW, &tmY, 0, (int)(r0 + b * kBoxRows), &full[slot]);
-        }
-        last[slot] = i;
-      }
-      volatile int never = 0;
-      for (int k = lane; k < ns; k += kProducers)
-        if (last[k] >= 0) mbar_wait(&full[k], (uint32_t)(last[k] / ns) & 1u, &never);
-    }
-    __syncwarp();
+    rstream_produce<SW>(tmX, tmY, a, ring, full, empty, my_chunks, &s_abort, ep);
   } else {
     bool alive = true;
     switch (warp % C::NCLS) {
@@ -825,6 +837,100 @@ rstream_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
   __syncthreads();
   const bool aborted = s_abort != 0;
   row_gram_sum<SW, kSym>(SW, wslots, kNC, part);
+  if (aborted)
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) part[i] = __longlong_as_double(0x7ff8000000000000ll);
+  __syncthreads();
+  if (!grid_reduce_last(part, cnt, ep.gpart, ep.counter)) return;
+  unpack_gram(part, SW, kSym, ep.gram_out);
+}
+
+// Streaming G = X^T Y (Y = X when !two) for s = 16, 32 with the products on the tensor
+// cores: the consumer warps take the stage's 8-row k-steps w, w + NC, ... and read them
+// as mma.m16n8k8 TF32 fragments straight from the swizzled ring (MmaGram::kstep_ring:
+// three-term split, FP32 over 32-row windows and 32 windows, FP64 in registers); the
+// slots are dumped into the idle ring for the CTA sum.  12 consumers at s = 16 (48
+// k-steps per stage of 384 rows); 7 at s = 32 (256 threads, so that the 8 accumulator
+// tiles fit the 255-register budget), the k-steps dealt round-robin across stages.
+template <int SW>
+__host__ __device__ constexpr int mconsumers() { return SW == 16 ? 12 : 7; }
+template <int SW>
+using StreamMma = MmaGram<SW, (mconsumers<SW>() + 1) * 32, true>;
+
+template <int SW, bool kSym>
+__global__ void __launch_bounds__((mconsumers<SW>() + 1) * 32, 1)
+mstream_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
+               const RStreamArgs a, const Epi<float> ep) {
+  if (ep.done && *ep.done) return;
+  if (ep.only_if && !*ep.only_if) return;
+  constexpr int kNC = mconsumers<SW>();
+  using G = StreamMma<SW>;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ int s_abort;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool consumer = warp < kNC;
+  const int cnt = kSym ? ut_count(SW) : SW * SW;
+  double* part = reinterpret_cast<double*>(smem);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.gram_bytes);
+  uint64_t* empty = full + kMaxStages;
+  float* ring = ring_base(smem, a.gram_bytes);
+  const int ns = a.ns;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < ns; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], kNC);
+    }
+    s_abort = 0;
+    mbar_fence_init();
+  }
+  G g;
+  g.init(nullptr);
+  g.template init_ring<Swz<SW>>();
+  __syncthreads();
+  const int64_t my_chunks =
+      (int64_t)blockIdx.x < a.nchunks ? (a.nchunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  if (!consumer) {
+    rstream_produce<SW>(tmX, tmY, a, ring, full, empty, my_chunks, &s_abort, ep);
+  } else {
+    bool alive = true;
+    const int nk = a.R / 8;
+    const bool same = !a.two;
+    int slot = 0;
+    uint32_t ph = 0;
+    for (int64_t i = 0; i < my_chunks; ++i) {
+      if (!mbar_wait(&full[slot], ph, &s_abort)) {
+        alive = false;
+        break;
+      }
+      const float* sx = ring + (size_t)slot * a.stage_floats;
+      const float* sy = a.two ? sx + a.op_floats : sx;
+      // k-steps dealt round-robin over the chunk's stages: warp w takes the global k-step
+      // indices w, w + NC, ...
+      const int k0 = (warp - (int)((i * nk) % kNC) + kNC) % kNC;
+      if (same) {
+        for (int k = k0; k < nk; k += kNC) g.template kstep_ring<true>(sx, sx, 8 * k);
+      } else {
+        for (int k = k0; k < nk; k += kNC) g.template kstep_ring<false>(sx, sy, 8 * k);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[slot]);
+      if (++slot == ns) {
+        slot = 0;
+        ph ^= 1u;
+      }
+    }
+    g.finish_ring();
+    if (!alive) {
+      report_timeout(ep.status_out, ep.stop_out);
+      s_abort = 1;
+    }
+  }
+  // the ring is idle: every consumer has released its last stage and the producer lanes
+  // have waited for their last copies
+  __syncthreads();
+  const bool aborted = s_abort != 0;
+  g.dump(ring);
+  __syncthreads();
+  g.sum(SW, kSym, ring, part, nullptr, nullptr);
   if (aborted)
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) part[i] = __longlong_as_double(0x7ff8000000000000ll);
   __syncthreads();
@@ -992,6 +1098,43 @@ cudaError_t rstream_launch(const Launch& L, int64_t n, const float* X, const flo
   return cudaGetLastError();
 }
 
+template <int SW, bool kSym>
+cudaError_t mstream_launch(const Launch& L, int64_t n, const float* X, const float* Y, const Epi<float>& ep) {
+  const int cnt = kSym ? ut_count(SW) : SW * SW;
+  RStreamArgs a;
+  a.n = n;
+  a.s = SW;
+  a.nbox = SW == 16 ? 2 : 1;               // 384 or 192 rows (24 KB of each operand) per stage
+  a.R = kBoxRows * a.nbox;
+  a.nchunks = (n + a.R - 1) / a.R;
+  a.two = X != Y ? 1 : 0;
+  a.op_floats = a.R * SW;
+  a.stage_floats = a.op_floats * (a.two ? 2 : 1);
+  a.gram_bytes = (int)align_up(sizeof(double) * (size_t)((cnt + 1) & ~1), 16);
+  const size_t fixed = a.gram_bytes + 2 * kMaxStages * sizeof(uint64_t) + kRingAlign;
+  int nsg = (int)((kDynSmemMax - fixed) / ((size_t)a.stage_floats * 4));
+  a.ns = nsg > 8 ? 8 : nsg;
+  a.ns -= a.ns % kProducers;
+  if (a.ns < kProducers) return cudaErrorNotSupported;
+  // the Gram's double slots are dumped into the ring at the end
+  if ((size_t)a.ns * a.stage_floats < StreamMma<SW>::slot_floats()) return cudaErrorNotSupported;
+  size_t smem = fixed + (size_t)a.ns * a.stage_floats * 4;
+  if (smem < kOneCtaSmem) smem = kOneCtaSmem;
+  CUtensorMap tx, ty;
+  cudaError_t e = make_map_rows(&tx, X, SW, n, kBoxRows);
+  if (e != cudaSuccess) return e;
+  if (a.two) {
+    if ((e = make_map_rows(&ty, Y, SW, n, kBoxRows)) != cudaSuccess) return e;
+  } else {
+    ty = tx;
+  }
+  const int64_t grid = a.nchunks < L.sms ? a.nchunks : L.sms;
+  auto k = mstream_kernel<SW, kSym>;
+  if ((e = smem_attr(k, smem)) != cudaSuccess) return e;
+  k<<<(int)grid, (mconsumers<SW>() + 1) * 32, smem, L.stream>>>(tx, ty, a, ep);
+  return cudaGetLastError();
+}
+
 template <int kMode, bool kSym>
 cudaError_t rstream_sw(const Launch& L, int64_t n, int s, const float* X, const float* Y, const float* w, float* Z,
                        const Epi<float>& ep) {
@@ -1020,6 +1163,12 @@ cudaError_t march_spmm4(const Launch& L, const OpDesc& A, int s, const float* in
 cudaError_t stream_gram4(const Launch& L, int64_t n, int s, const float* X, const float* Y,
                          const Epi<float>& ep) {
   if (s % 4 != 0 || n < 1 || !aligned16(X) || !aligned16(Y)) return cudaErrorNotSupported;
+  if (s == 16 || s == 32) {
+    cudaError_t e;
+    if (s == 16) e = ep.sym ? mstream_launch<16, true>(L, n, X, Y, ep) : mstream_launch<16, false>(L, n, X, Y, ep);
+    else e = ep.sym ? mstream_launch<32, true>(L, n, X, Y, ep) : mstream_launch<32, false>(L, n, X, Y, ep);
+    if (e != cudaErrorNotSupported) return e;
+  }
   if (s == 4 || s == 8 || s == 16) {
     if (ep.sym) return rstream_sw<0, true>(L, n, s, X, Y, nullptr, nullptr, ep);
     return rstream_sw<0, false>(L, n, s, X, Y, nullptr, nullptr, ep);

@@ -390,6 +390,72 @@ struct MmaGram {
     }
     if (++ks == WIN1) flush1();
   }
+  // Ring-fed k-steps: a ring stage holds rows of SW floats stored with the swizzle SWZ
+  // (chunk q of row r at SWZ::chunk(r, q)) and the k-steps start at multiples of 8 rows,
+  // where the swizzle term depends on the row within the k-step only: every fragment
+  // element of a k-step is at a per-lane constant offset from the k-step's first row.
+  // The B fragments read the same (row, column) pairs as the A fragments (B[nj][h] =
+  // A[nj / 2][2 h + nj % 2]), so they share the offsets, and the values when the two
+  // operands are one block.
+  int ring_off[MT][4];
+  template <class SWZ>
+  __device__ __forceinline__ void init_ring() {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < MT; ++mi)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = t + ((e & 2) ? 4 : 0);
+        const int col = 16 * mi + g + ((e & 1) ? 8 : 0);
+        ring_off[mi][e] = r * SW + 4 * SWZ::chunk(r, col >> 2) + (col & 3);
+      }
+  }
+  // One k-step over rows r0 .. r0 + 7 (r0 a multiple of 8) of the left operand (the
+  // Gram's rows, sx) and the right one (sy; kSame: the same block).
+  template <bool kSame>
+  __device__ __forceinline__ void kstep_ring(const float* sx, const float* sy, int r0) {
+    static_assert(NT == 2 * MT, "ring-fed k-steps need SW = 16 or 32");
+    const float* bx = sx + r0 * SW;
+    const float* by = sy + r0 * SW;
+    uint32_t ab[MT][4], as[MT][4];
+#pragma unroll
+    for (int mi = 0; mi < MT; ++mi)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float x = bx[ring_off[mi][e]];
+        ab[mi][e] = tf32_of(x);
+        as[mi][e] = tf32_of(x - __uint_as_float(ab[mi][e]));
+      }
+    uint32_t bb[NT][2], bs[NT][2];
+#pragma unroll
+    for (int nj = 0; nj < NT; ++nj)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int mi = nj >> 1, e = 2 * h + (nj & 1);
+        if constexpr (kSame) {
+          bb[nj][h] = ab[mi][e];
+          bs[nj][h] = as[mi][e];
+        } else {
+          const float y = by[ring_off[mi][e]];
+          bb[nj][h] = tf32_of(y);
+          bs[nj][h] = tf32_of(y - __uint_as_float(bb[nj][h]));
+        }
+      }
+#pragma unroll
+    for (int mi = 0; mi < MT; ++mi)
+#pragma unroll
+      for (int nj = 0; nj < NT; ++nj) {
+        mma_tf32(c[mi * NT + nj], ab[mi], bb[nj]);
+        mma_tf32(c[mi * NT + nj], ab[mi], bs[nj]);
+        mma_tf32(c[mi * NT + nj], as[mi], bb[nj]);
+      }
+    if (++ks == WIN1) flush1();
+  }
+  // Flush every level (the ring-fed use: no partial k-step).
+  __device__ __forceinline__ void finish_ring() {
+    flush1();
+    flush2();
+  }
   // Stage the lane's quads of this trip's rows (zero for rows past n) into the
   // warp's buffers stl / stm (BUFROWS x STR floats each; stm may equal stl)
   // and run the k-steps that became complete.
