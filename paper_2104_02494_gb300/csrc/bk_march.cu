@@ -856,10 +856,11 @@ __host__ __device__ constexpr int mconsumers() { return SW == 16 ? 12 : 7; }
 template <int SW>
 using StreamMma = MmaGram<SW, (mconsumers<SW>() + 1) * 32, true>;
 
-template <int SW, bool kSym>
+// kDiag: the diagonal preconditioner pass, Z = diag(w) X written out and G = X^T Z.
+template <int SW, bool kSym, bool kDiag>
 __global__ void __launch_bounds__((mconsumers<SW>() + 1) * 32, 1)
 mstream_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
-               const RStreamArgs a, const Epi<float> ep) {
+               const RStreamArgs a, const float* __restrict__ w, float* __restrict__ Z, const Epi<float> ep) {
   if (ep.done && *ep.done) return;
   if (ep.only_if && !*ep.only_if) return;
   constexpr int kNC = mconsumers<SW>();
@@ -896,17 +897,38 @@ mstream_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
     const bool same = !a.two;
     int slot = 0;
     uint32_t ph = 0;
+    // kDiag: a warp takes at most kMaxK k-steps of a stage (48 / 12 at s = 16, 24 / 7 at 32)
+    constexpr int kMaxK = 4;
     for (int64_t i = 0; i < my_chunks; ++i) {
+      // k-steps dealt round-robin over the chunk's stages: warp w takes the global k-step
+      // indices w, w + NC, ...
+      const int k0 = (warp - (int)((i * nk) % kNC) + kNC) % kNC;
+      float wv[kMaxK][2];
+      const int64_t base = (blockIdx.x + i * gridDim.x) * (int64_t)a.R;
+      if constexpr (kDiag) {
+        // the scaling of the warp's rows, loaded before the stage wait (it does not come
+        // through the ring)
+#pragma unroll
+        for (int j = 0; j < kMaxK; ++j) {
+          const int64_t r = base + 8 * (k0 + j * kNC) + (lane & 3);
+          const bool ok = k0 + j * kNC < nk;
+          wv[j][0] = ok && r < a.n ? w[r] : 0.f;
+          wv[j][1] = ok && r + 4 < a.n ? w[r + 4] : 0.f;
+        }
+      }
       if (!mbar_wait(&full[slot], ph, &s_abort)) {
         alive = false;
         break;
       }
       const float* sx = ring + (size_t)slot * a.stage_floats;
       const float* sy = a.two ? sx + a.op_floats : sx;
-      // k-steps dealt round-robin over the chunk's stages: warp w takes the global k-step
-      // indices w, w + NC, ...
-      const int k0 = (warp - (int)((i * nk) % kNC) + kNC) % kNC;
-      if (same) {
+      if constexpr (kDiag) {
+#pragma unroll
+        for (int j = 0; j < kMaxK; ++j) {
+          const int k = k0 + j * kNC;
+          if (k < nk) g.kstep_ring_diag(sx, 8 * k, wv[j][0], wv[j][1], Z, base + 8 * k, a.n);
+        }
+      } else if (same) {
         for (int k = k0; k < nk; k += kNC) g.template kstep_ring<true>(sx, sx, 8 * k);
       } else {
         for (int k = k0; k < nk; k += kNC) g.template kstep_ring<false>(sx, sy, 8 * k);
@@ -1098,8 +1120,9 @@ cudaError_t rstream_launch(const Launch& L, int64_t n, const float* X, const flo
   return cudaGetLastError();
 }
 
-template <int SW, bool kSym>
-cudaError_t mstream_launch(const Launch& L, int64_t n, const float* X, const float* Y, const Epi<float>& ep) {
+template <int SW, bool kSym, bool kDiag>
+cudaError_t mstream_launch(const Launch& L, int64_t n, const float* X, const float* Y, const float* w, float* Z,
+                           const Epi<float>& ep) {
   const int cnt = kSym ? ut_count(SW) : SW * SW;
   RStreamArgs a;
   a.n = n;
@@ -1107,7 +1130,7 @@ cudaError_t mstream_launch(const Launch& L, int64_t n, const float* X, const flo
   a.nbox = SW == 16 ? 2 : 1;               // 384 or 192 rows (24 KB of each operand) per stage
   a.R = kBoxRows * a.nbox;
   a.nchunks = (n + a.R - 1) / a.R;
-  a.two = X != Y ? 1 : 0;
+  a.two = (!kDiag && X != Y) ? 1 : 0;
   a.op_floats = a.R * SW;
   a.stage_floats = a.op_floats * (a.two ? 2 : 1);
   a.gram_bytes = (int)align_up(sizeof(double) * (size_t)((cnt + 1) & ~1), 16);
@@ -1118,6 +1141,8 @@ cudaError_t mstream_launch(const Launch& L, int64_t n, const float* X, const flo
   if (a.ns < kProducers) return cudaErrorNotSupported;
   // the Gram's double slots are dumped into the ring at the end
   if ((size_t)a.ns * a.stage_floats < StreamMma<SW>::slot_floats()) return cudaErrorNotSupported;
+  // the diagonal pass preloads at most 4 k-steps' scalings per warp and stage
+  if (kDiag && (a.R / 8 + mconsumers<SW>() - 1) / mconsumers<SW>() > 4) return cudaErrorNotSupported;
   size_t smem = fixed + (size_t)a.ns * a.stage_floats * 4;
   if (smem < kOneCtaSmem) smem = kOneCtaSmem;
   CUtensorMap tx, ty;
@@ -1129,9 +1154,9 @@ cudaError_t mstream_launch(const Launch& L, int64_t n, const float* X, const flo
     ty = tx;
   }
   const int64_t grid = a.nchunks < L.sms ? a.nchunks : L.sms;
-  auto k = mstream_kernel<SW, kSym>;
+  auto k = mstream_kernel<SW, kSym, kDiag>;
   if ((e = smem_attr(k, smem)) != cudaSuccess) return e;
-  k<<<(int)grid, (mconsumers<SW>() + 1) * 32, smem, L.stream>>>(tx, ty, a, ep);
+  k<<<(int)grid, (mconsumers<SW>() + 1) * 32, smem, L.stream>>>(tx, ty, a, w, Z, ep);
   return cudaGetLastError();
 }
 
@@ -1165,8 +1190,12 @@ cudaError_t stream_gram4(const Launch& L, int64_t n, int s, const float* X, cons
   if (s % 4 != 0 || n < 1 || !aligned16(X) || !aligned16(Y)) return cudaErrorNotSupported;
   if (s == 16 || s == 32) {
     cudaError_t e;
-    if (s == 16) e = ep.sym ? mstream_launch<16, true>(L, n, X, Y, ep) : mstream_launch<16, false>(L, n, X, Y, ep);
-    else e = ep.sym ? mstream_launch<32, true>(L, n, X, Y, ep) : mstream_launch<32, false>(L, n, X, Y, ep);
+    if (s == 16)
+      e = ep.sym ? mstream_launch<16, true, false>(L, n, X, Y, nullptr, nullptr, ep)
+                 : mstream_launch<16, false, false>(L, n, X, Y, nullptr, nullptr, ep);
+    else
+      e = ep.sym ? mstream_launch<32, true, false>(L, n, X, Y, nullptr, nullptr, ep)
+                 : mstream_launch<32, false, false>(L, n, X, Y, nullptr, nullptr, ep);
     if (e != cudaErrorNotSupported) return e;
   }
   if (s == 4 || s == 8 || s == 16) {
@@ -1181,6 +1210,11 @@ cudaError_t stream_diag4(const Launch& L, int64_t n, int s, const float* w, cons
                          const Epi<float>& ep) {
   if (s % 4 != 0 || n < 1 || !ep.sym || ep.left != X || !aligned16(X) || !aligned16(Z))
     return cudaErrorNotSupported;
+  if (s == 16 || s == 32) {
+    const cudaError_t e = s == 16 ? mstream_launch<16, true, true>(L, n, X, X, w, Z, ep)
+                                  : mstream_launch<32, true, true>(L, n, X, X, w, Z, ep);
+    if (e != cudaErrorNotSupported) return e;
+  }
   if (s == 4 || s == 8 || s == 16) return rstream_sw<1, true>(L, n, s, X, nullptr, w, Z, ep);
   return stream_sw<1, kQEpiSym>(L, n, s, X, nullptr, w, Z, ep);
 }

@@ -451,6 +451,53 @@ struct MmaGram {
       }
     if (++ks == WIN1) flush1();
   }
+  // The preconditioner pass on a ring k-step: Z = diag(w) X for rows r0 .. r0 + 7 of the
+  // stage (w0, w1: w of the lane's rows r0 + t and r0 + t + 4; rows zr0 + ... of Z, stored
+  // only below n) and the Gram X^T Z.  The A fragments cover each element of the k-step
+  // once, so each lane stores its 4 MT elements of Z; the B values are those elements.
+  __device__ __forceinline__ void kstep_ring_diag(const float* sx, int r0, float w0, float w1, float* z,
+                                                  int64_t zr0, int64_t n) {
+    static_assert(NT == 2 * MT, "ring-fed k-steps need SW = 16 or 32");
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const float* bx = sx + r0 * SW;
+    uint32_t ab[MT][4], as[MT][4];
+    float zv[MT][4];
+#pragma unroll
+    for (int mi = 0; mi < MT; ++mi)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float x = bx[ring_off[mi][e]];
+        ab[mi][e] = tf32_of(x);
+        as[mi][e] = tf32_of(x - __uint_as_float(ab[mi][e]));
+        zv[mi][e] = ((e & 2) ? w1 : w0) * x;
+      }
+#pragma unroll
+    for (int mi = 0; mi < MT; ++mi)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int64_t row = zr0 + t + ((e & 2) ? 4 : 0);
+        const int col = 16 * mi + g + ((e & 1) ? 8 : 0);
+        if (row < n) z[row * SW + col] = zv[mi][e];
+      }
+    uint32_t bb[NT][2], bs[NT][2];
+#pragma unroll
+    for (int nj = 0; nj < NT; ++nj)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float y = zv[nj >> 1][2 * h + (nj & 1)];
+        bb[nj][h] = tf32_of(y);
+        bs[nj][h] = tf32_of(y - __uint_as_float(bb[nj][h]));
+      }
+#pragma unroll
+    for (int mi = 0; mi < MT; ++mi)
+#pragma unroll
+      for (int nj = 0; nj < NT; ++nj) {
+        mma_tf32(c[mi * NT + nj], ab[mi], bb[nj]);
+        mma_tf32(c[mi * NT + nj], ab[mi], bs[nj]);
+        mma_tf32(c[mi * NT + nj], as[mi], bb[nj]);
+      }
+    if (++ks == WIN1) flush1();
+  }
   // Flush every level (the ring-fed use: no partial k-step).
   __device__ __forceinline__ void finish_ring() {
     flush1();
