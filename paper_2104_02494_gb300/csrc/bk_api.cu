@@ -415,7 +415,7 @@ struct GraphBatch {
   }
 };
 
-// launches of one two-reduction iteration (the TSQR has 2 * levels + 3 launches): the
+// launches of one two-reduction iteration (the TSQR has 3 * levels + 4 launches): the
 // SpMM, two s x s kernels, the update (lean and Gram-carrying, or the Gram-carrying one
 // alone with CholeskyQR2, which adds two s x s kernels and one row pass, two with M) and
 // the direction update, plus the preconditioner pass

@@ -662,7 +662,9 @@ static cudaError_t leaves(const Launch& L, int64_t rows, int s, int ld, int64_t 
 #undef BK_LEAVES
 }
 
-int tsqr_launches(const TsqrPlan& p) { return 2 * (p.levels + 1) + 1; }
+// Launches of one TSQR: a factor launch per level, the root's sign fix, and per level an
+// apply of two launches (the WY product W = T (V1^T sigma~), then the rows).
+int tsqr_launches(const TsqrPlan& p) { return 3 * (p.levels + 1) + 1; }
 
 // X = Y gamma (Y may alias X).  Level 0 tiles the n x s block; level l + 1
 // tiles the stacked R factors of level l (stored in FP64, factored in the
@@ -693,11 +695,11 @@ cudaError_t tsqr(const Launch& L, const TsqrPlan& p, const T* X, T* Y, double* g
   for (int l = p.levels; l >= 1; --l)
     if ((e = leaves<double, T>(L, p.rows[l], s, s, p.nodes[l], nullptr, q.R[l - 1], q.R[l], q.Tf[l],
                                nullptr, nullptr, nullptr, done, flag, false, false)) != cudaSuccess) return e;
-  prof_end(L, kPhTsqrTree, 2 * p.levels + 1);
+  prof_end(L, kPhTsqrTree, 3 * p.levels + 1);
   prof_begin(L, kPhTsqrApply);
   e = leaves<T, T>(L, p.n, s, ld, p.nodes[0], nullptr, Y, q.R[0], q.Tf[0], rho_out, gpart, counter,
                    done, flag, false, true);
-  prof_end(L, kPhTsqrApply, 1);
+  prof_end(L, kPhTsqrApply, 2);
   return e;
 }
 

@@ -67,3 +67,21 @@ def test_no_gpu_create_fails_cleanly():
     L = _lib.load()
     h = ctypes.c_void_p()
     assert L.bkrylov_create(ctypes.byref(h), 0, None) == _lib.BK_ERR_ARG
+
+
+def test_launches_per_iteration_counts():
+    """Launches of one BCG iteration as the library enqueues them (host-only): at 128^3, s = 8
+    the TSQR has a leaf level and two tree levels, so 3 factor launches, the root's sign fix
+    and 3 two-launch applies = 10; the CholeskyQR2 iteration adds the SpMM, two s x s
+    kernels, the update, two CholeskyQR2 s x s kernels, one row pass and the P update = 18
+    (the count of the ncu launch list of the benchmark); the Householder iteration 6 + 10."""
+    from paper_2104_02494_gb300 import _lib as L
+    lib = L.load()
+    assert lib.bkrylov_bcg_launches_per_iteration(2097152, 8, None) == 18
+    o = L.default_opts()
+    o.qr_mode = 1
+    assert lib.bkrylov_bcg_launches_per_iteration(2097152, 8, ctypes.byref(o)) == 16
+    o = L.default_opts()
+    o.one_reduction = 1
+    assert lib.bkrylov_bcg_launches_per_iteration(2097152, 8, ctypes.byref(o)) == 17
+    assert lib.bkrylov_bcg_launches_per_iteration(0, 8, None) == -1

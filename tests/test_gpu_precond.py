@@ -186,3 +186,23 @@ def test_pcg_graph_replay_equals_direct_launches(h):
     launches = {p[0]: p[2] for p in h.profile()}
     assert launches["precond_rho"] >= idr.iters
     M.close(); op.close()
+
+
+@pytest.mark.parametrize("n,s", [(100003, 16), (65537, 32), (777, 16), (3, 32)])
+def test_diag_pass_fp32_stream(h, n, s):
+    """The FP32 diagonal pass (Z = diag(w) X with rho = X^T Z, the preconditioner step of the
+    inner solves) on ragged row counts: Z bit-exact (one IEEE product per entry), rho within
+    the FP32 Gram bound of the other Gram tests."""
+    g = np.random.default_rng(n + s)
+    w = np.exp(g.standard_normal(n))
+    M = h.op_diag(torch.from_numpy(w).cuda())
+    P = g.standard_normal((n, s)).astype(np.float32)
+    Z, G = h.spmm_gram(M, _dev(P), sym=True)
+    w32 = w.astype(np.float32)
+    assert np.array_equal(Z.cpu().numpy(), w32[:, None] * P)
+    P64 = P.astype(np.float64)
+    Z64 = (w32[:, None] * P).astype(np.float64)
+    Gref = P64.T @ Z64
+    bound = np.abs(P64).T @ np.abs(Z64)
+    assert np.all(np.abs(G.cpu().numpy() - Gref) <= (2.0 ** -21 + 64 * 2.0 ** -24) * bound + 1e-30)
+    M.close()
