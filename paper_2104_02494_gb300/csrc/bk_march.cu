@@ -1,13 +1,11 @@
 // Pipelined FP32 operator and block-inner-product kernels (BOP and BDOT of
 // Ch. 3.3, Table "kernels"), for blocks whose width s is a multiple of 4.
 //
-// Both kernels separate data movement from arithmetic: one producer thread
-// keeps a ring of shared-memory stages filled with asynchronous bulk copies
-// (completion counted in bytes on mbarriers), and seven consumer warps compute
-// from shared memory in the quad layout (one float4 of a row per lane), with
-// the fused Gram on FP32 FMAs reading its left operand from the ring
-// (bk_qgram.cuh).  A CTA therefore keeps tens of KB of HBM reads in flight
-// without holding them in registers.
+// The kernels separate data movement from arithmetic: the lanes of one producer
+// warp keep a ring of shared-memory stages filled with asynchronous tensor or bulk
+// copies (completion counted in bytes on mbarriers; every wait bounded), and the
+// consumer warps compute from shared memory.  A CTA therefore keeps tens of KB of
+// HBM reads in flight without holding them in registers.
 //
 // march4_kernel: Q = A P for the matrix-free stencils, optionally with the
 // symmetric Gram P^T Q fused (the alpha of Eq. "cg_alpha").  The grid is seen
@@ -19,10 +17,15 @@
 // coefficients, the same box of per-cell coefficients.  Planes z - 1, z and
 // z + 1 stay in the ring while plane z is computed, so every P value is read
 // from HBM once per tile; the halos of neighbouring tiles are read by CTAs
-// that run at the same time and come from L2.
+// that run at the same time and come from L2.  Consumers work in the quad
+// layout (one float4 of a row per lane); the Gram is the tensor-core MmaGram at
+// s = 16, 32 and the CUDA-core QuadGram at s = 4, 8.
 //
-// stream4_kernel: G = X^T Y (or X^T X), or Z = diag(w) X with X^T Z, over
-// chunks of consecutive rows brought in by 1D bulk copies.
+// mstream_kernel (s = 16, 32): G = X^T Y (or X^T X), or Z = diag(w) X with X^T Z,
+// over stages of 192-row tensor-copy boxes in a swizzled ring, the products on
+// the tensor cores read straight from the ring.  rstream_kernel (s = 4, 8, 16)
+// and stream4_kernel (other widths): the same on CUDA cores, row per lane or in
+// the quad layout.
 //
 // Results: the row outputs are the same sums, term by term in the same
 // order, as the scalar and quad kernels (the ascending column order of a
