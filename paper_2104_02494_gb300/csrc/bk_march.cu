@@ -68,14 +68,21 @@ constexpr size_t kOneCtaSmem = 120 * 1024;
 constexpr size_t kRingAlign = 1024;
 enum : int { kQEpiNone = 0, kQEpiSym = 1, kQEpiFull = 2 };
 
+enum : int { kMConst7 = 0, kMVar7 = 1, kMEdge5 = 2 };
+
 // Marching operator kernels (s <= 32): without a Gram, 11 consumer warps and the
 // producer warp (384 threads of at most 168 registers: more warps hide the latency of
-// the stencil's shared-memory loads; measured 0.55 -> 0.74 of HBM at s = 16); with
-// the Gram, whose two FP32 accumulator levels need up to 255 registers, 7.
-template <int kEpi, int SW>
-__host__ __device__ constexpr int march_consumers() { return (kEpi == kQEpiNone || SW == 16) ? 11 : 7; }
-template <int kEpi, int SW>
-__host__ __device__ constexpr int march_threads() { return (march_consumers<kEpi, SW>() + 1) * 32; }
+// the stencil's shared-memory loads; measured 0.55 -> 0.74 of HBM at s = 16).  With the
+// Gram: 11 at s = 16 (tensor-core Gram), 7 at s = 32 (its 8 tiles need the 255-register
+// budget) and at s = 4; at s = 8 11 for the constant stencil (0.274 -> 0.301 of HBM on the
+// 128^3 Laplacian) and 7 for the coefficient stencils, whose extra registers spill at 168
+// (VAR7: 0.372 with 7 against 0.361 with 11).
+template <int kEpi, int SW, int kOp>
+__host__ __device__ constexpr int march_consumers() {
+  return (kEpi == kQEpiNone || SW == 16 || (SW == 8 && kOp == kMConst7)) ? 11 : 7;
+}
+template <int kEpi, int SW, int kOp>
+__host__ __device__ constexpr int march_threads() { return (march_consumers<kEpi, SW, kOp>() + 1) * 32; }
 // The fused Gram of the marching kernel: for s = 16 and 32 the tensor-core MmaGram
 // (TF32 products with the three-term split, 16 x 8 tiles of mma.sync; at s = 16 few
 // accumulator registers per lane, so 11 consumer warps fit; at s = 32 its 8 tiles take
@@ -85,23 +92,22 @@ __host__ __device__ constexpr int march_threads() { return (march_consumers<kEpi
 // operator).
 // MmaGram keeps its double slots in registers while streaming and dumps them into the
 // ring's memory (free once the pipeline has drained) for the CTA sum.
-template <int SW, int kEpi>
-using MarchGram =
-    typename std::conditional<(SW >= 16), MmaGram<SW, march_threads<kEpi, SW>(), true>, QuadGram<SW, true>>::type;
+template <int SW, int kEpi, int kOp>
+using MarchGram = typename std::conditional<(SW >= 16), MmaGram<SW, march_threads<kEpi, SW, kOp>(), true>,
+                                            QuadGram<SW, true>>::type;
 // Bytes of the Gram region at the start of the dynamic shared memory: the packed sums,
 // then the Gram's slots (QuadGram) or the per-warp staging buffers (MmaGram).
-template <int SW, int kEpi>
+template <int SW, int kEpi, int kOp>
 __host__ __device__ constexpr size_t march_gram_bytes(int cnt) {
   if constexpr (SW >= 16) {
-    using G = MarchGram<SW, kEpi>;
+    using G = MarchGram<SW, kEpi, kOp>;
     return sizeof(double) * (size_t)((cnt + 1) & ~1) +
-           sizeof(float) * ((size_t)(march_threads<kEpi, SW>() / 32) * G::stage_floats());
+           sizeof(float) * ((size_t)(march_threads<kEpi, SW, kOp>() / 32) * G::stage_floats());
   } else {
     return sizeof(double) * ((size_t)((cnt + 1) & ~1) +
-                             (size_t)march_consumers<kEpi, SW>() * QuadGram<SW, true>::kWarpDoubles);
+                             (size_t)march_consumers<kEpi, SW, kOp>() * QuadGram<SW, true>::kWarpDoubles);
   }
 }
-enum : int { kMConst7 = 0, kMVar7 = 1, kMEdge5 = 2 };
 
 // ------------------------------------------------------------ host helpers ----
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -370,19 +376,19 @@ __device__ __forceinline__ float4 stencil_quad(const MarchArgs& a, int s, const 
 }
 
 template <int SW, int kOp, int kEpi, bool kHY>
-__global__ void __launch_bounds__(march_threads<kEpi, SW>(), 1)
+__global__ void __launch_bounds__(march_threads<kEpi, SW, kOp>(), 1)
 march4_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmC,
               const MarchArgs a, int s, float* __restrict__ Q, const Epi<float> ep) {
   if (ep.done && *ep.done) return;
   if (ep.only_if && !*ep.only_if) return;
   constexpr int LPR = SW / 4, RS = 32 / LPR;
-  using Gram = MarchGram<SW, kEpi>;
+  using Gram = MarchGram<SW, kEpi, kOp>;
   constexpr bool kGram = kEpi != kQEpiNone;
   constexpr bool kMma = SW >= 16;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_abort;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int kNC = march_consumers<kEpi, SW>();
+  constexpr int kNC = march_consumers<kEpi, SW, kOp>();
   const bool consumer = warp < kNC;
   const int cnt = kGram ? ut_count(s) : 0;
   double* part = reinterpret_cast<double*>(smem);
@@ -981,14 +987,14 @@ cudaError_t march_launch(const Launch& L, const OpDesc& A, int s, const float* i
   int gx, gy, gz;
   march_grid(A, &gx, &gy, &gz);
   const int cf = kOp == kMConst7 ? 0 : 4;
-  const size_t gb = kEpi == kQEpiNone ? 0 : march_gram_bytes<SW, kEpi>(ut_count(s));
+  const size_t gb = kEpi == kQEpiNone ? 0 : march_gram_bytes<SW, kEpi, kOp>(ut_count(s));
   MarchArgs a;
   int grid = 0;
   size_t smem = 0;
   if (!plan_march(gx, gy, gz, s, cf, L.sms, gb, &a, &grid, &smem)) return cudaErrorNotSupported;
   if constexpr (SW >= 16 && kEpi != kQEpiNone) {
     // the Gram's slots are dumped into the ring at the end
-    if ((size_t)a.ns * a.stage_floats < MarchGram<SW, kEpi>::slot_floats()) return cudaErrorNotSupported;
+    if ((size_t)a.ns * a.stage_floats < MarchGram<SW, kEpi, kOp>::slot_floats()) return cudaErrorNotSupported;
   }
   a.fdx = FastDiv((uint32_t)a.Tx);
   if (kOp == kMConst7) {
@@ -1012,7 +1018,7 @@ cudaError_t march_launch(const Launch& L, const OpDesc& A, int s, const float* i
   }
   auto k = a.hy ? march4_kernel<SW, kOp, kEpi, true> : march4_kernel<SW, kOp, kEpi, false>;
   if ((e = smem_attr(k, smem)) != cudaSuccess) return e;
-  k<<<grid, march_threads<kEpi, SW>(), smem, L.stream>>>(tmP, tmC, a, s, out, ep);
+  k<<<grid, march_threads<kEpi, SW, kOp>(), smem, L.stream>>>(tmP, tmC, a, s, out, ep);
   return cudaGetLastError();
 }
 
