@@ -378,7 +378,11 @@ __device__ __forceinline__ float4 stencil_quad(const MarchArgs& a, int s, const 
 template <int SW, int kOp, int kEpi, bool kHY>
 __global__ void __launch_bounds__(march_threads<kEpi, SW, kOp>(), 1)
 march4_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmC,
-              const MarchArgs a, int s, float* __restrict__ Q, const Epi<float> ep) {
+              const MarchArgs a, int s_in, float* __restrict__ Q, const Epi<float> ep) {
+  // the block width is the compile-time SW (the launcher takes s == SW only): row offsets,
+  // the Gram's width and the quad tests fold into constants
+  constexpr int s = SW;
+  (void)s_in;
   if (ep.done && *ep.done) return;
   if (ep.only_if && !*ep.only_if) return;
   constexpr int LPR = SW / 4, RS = 32 / LPR;
@@ -1029,8 +1033,11 @@ cudaError_t march_epi(const Launch& L, const OpDesc& A, int s, const float* in, 
   return cudaErrorNotSupported;
 }
 
+// Widths that are powers of two only (the kernel takes s as the compile-time SW); s = 12,
+// 20, 24, 28 use the quad kernels.
 template <int kOp>
 cudaError_t march_sw(const Launch& L, const OpDesc& A, int s, const float* in, float* out, const Epi<float>& ep) {
+  if (s != next_pow2_s(s)) return cudaErrorNotSupported;
   switch (next_pow2_s(s)) {
     case 4: return march_epi<4, kOp>(L, A, s, in, out, ep);
     case 8: return march_epi<8, kOp>(L, A, s, in, out, ep);
