@@ -21,7 +21,12 @@ Householder TSQR for blocks it declines), s x s step, direction update.
              flop/byte; the operator and update passes sit near it at s = 8);
   iteration  the whole iteration's algorithmic FP64 flops and HBM bytes per second;
   cpu_baseline  the FP64 oracle (numpy/scipy) on the host cores, a bounded
-             number of iterations of the same workload.
+             number of iterations of the same workload;
+  sweep      s in {1, 4, 8, 16, 32}, stencil and CSR: RHS*iter/s, the FP64 and HBM
+             fractions of the iteration, the FP32 fused operator + Gram against HBM;
+  scalar_cg  time to 1e-8 of block CG against s independent scalar CG solves (one
+             after another, and side by side in the subalgebra with p = 1);
+  ir         FP32 + FP64 refinement against FP64 BCG, time to 1e-10 at 192^3.
 
 --impl reference times the oracle alone as the reference arm: W warm-up and
 exactly K timed BCG iterations of the same workload on the host cores (the K
@@ -82,7 +87,8 @@ def parse():
     p.add_argument("--grid", type=int, default=128)
     p.add_argument("--op", default="stencil", choices=["stencil", "csr"])
     p.add_argument("--no-extra", action="store_true",
-                   help="skip the rest of the metric (the s sweep and the FP32+IR vs FP64 time to 1e-10)")
+                   help="skip the rest of the metric (the s sweep, block vs scalar CG, and the FP32+IR vs FP64 "
+                        "time to 1e-10)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--probe", choices=["bcg_fp64", "bcg_fp32_ir"],
                    help="run one short solve (a target for ncu) on --workload/--grid/--s and exit")
@@ -296,7 +302,7 @@ class Clocks:
                 sm.append(clk)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": total, "samples_under_load": len(sm),
-                "covers": "timed region, then the sweep and refinement runs"}
+                "covers": "timed region, then the sweep, scalar CG and refinement runs"}
 
 
 def cpu_baseline(prob, s, iters=3):
@@ -736,6 +742,50 @@ def run_sweep(h, args, prob, torch):
     return out
 
 
+def run_scalar_cg(h, args, prob, torch):
+    """Block CG against s independent scalar CG solves on the 128^3 Laplacian stencil (FP64,
+    max-column relative residual 1e-8), s in {1, 4, 8, 16, 32}: the block solve with QR
+    stabilisation (eta = inf); the s columns solved one after another by CG (s = 1, eta = 0:
+    no normaliser after the first); and the s scalar CGs run side by side as one block in the
+    block-parallel subalgebra with p = 1 (every s x s quantity diagonal, eta = 0).  Device time
+    of each solve call, one untimed 3-iteration solve of each shape first.  The columns are the
+    first s of one seeded N(0, 1) draw, so the sequential time of s columns is a prefix sum."""
+    import workloads as W
+    from paper_2104_02494_gb300.api import operator_from_problem
+    n = prob.B.shape[0]
+    B32 = W.normal_block(n, 32, 0)
+    op = operator_from_problem(h, prob, "stencil")
+    widths = (1, 4, 8, 16, 32)
+    col_ms, col_it = [], []
+    for j in range(max(widths)):
+        b = torch.from_numpy(np.ascontiguousarray(B32[:, j:j + 1])).cuda()
+        if j == 0:
+            h.solve("bcg", op, b, tol=1e-8, maxit=3, eta=0.0, record=False)
+        _, info = h.solve("bcg", op, b, tol=1e-8, maxit=20000, eta=0.0, record=False)
+        col_ms.append(info.elapsed_ms)
+        col_it.append(info.iters)
+    out = {"workload": "laplace3d 128^3 7-point stencil, FP64, to 1e-8"}
+    for ss in widths:
+        Bs = torch.from_numpy(np.ascontiguousarray(B32[:, :ss])).cuda()
+        e = {}
+        for name, kw in (("block", dict(eta=math.inf)), ("batched_scalar", dict(eta=0.0, p=1))):
+            if name == "batched_scalar" and ss == 1:
+                continue
+            h.solve("bcg", op, Bs, tol=1e-8, maxit=3, record=False, **kw)
+            _, info = h.solve("bcg", op, Bs, tol=1e-8, maxit=20000, record=False, **kw)
+            e[name] = {"ms": info.elapsed_ms, "iters": info.iters, "converged": bool(info.converged)}
+        e["sequential_scalar"] = {"ms": float(sum(col_ms[:ss])), "iters_max": int(max(col_it[:ss])),
+                                  "iters_sum": int(sum(col_it[:ss]))}
+        e["block_speedup_vs_sequential"] = e["sequential_scalar"]["ms"] / e["block"]["ms"]
+        if "batched_scalar" in e:
+            e["block_speedup_vs_batched"] = e["batched_scalar"]["ms"] / e["block"]["ms"]
+        out[f"s{ss}"] = e
+        del Bs
+    op.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ir_pair(h, args, torch):
     """The FP32+IR vs FP64 half of the metric: time to a max-column relative residual of 1e-10
     on the 192^3 log-normal diffusion workload (s = 16), both with point Jacobi: FP64 BCG with
@@ -864,9 +914,10 @@ def main():
     e2e = {"value": s * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * Bh.nbytes / K,
            "d2h_bytes_per_step": Xh.nbytes / K, "note": "setup (residual, first QR) included"}
 
-    sweep = ir = None
+    sweep = ir = scalar = None
     if rank == 0 and not args.no_extra:
         sweep = run_sweep(h, args, prob, torch)
+        scalar = run_scalar_cg(h, args, prob, torch)
         ir = run_ir_pair(h, args, torch)
     clk.__exit__(None, None, None)
 
@@ -888,6 +939,8 @@ def main():
                 "clocks": clk.summary(), "gpu_launches": launches}
         if sweep:
             line["sweep"] = sweep
+        if scalar:
+            line["scalar_cg"] = scalar
         if ir:
             line["ir"] = ir
         print(json.dumps(line))

@@ -255,7 +255,7 @@ cudaError_t bcg_iteration(const Launch& L, const OpDesc& A, int s, T* X, const B
   cudaError_t e;
   Epi<T> ep;
   ep.left = b.P; ep.sym = 1; ep.gram_out = c->alpha; ep.gpart = b.gpart;
-  ep.counter = &c->counters[kCntA]; ep.done = &c->done;
+  ep.counter = c->counters[kCntA]; ep.done = &c->done;
   ep.status_out = &c->status; ep.stop_out = &c->done;
   // S_BP^p (tp.s = p < s): the FP64 steps restricted to the column groups
   const int gp = tp.s;
@@ -297,14 +297,14 @@ cudaError_t bcg_iteration(const Launch& L, const OpDesc& A, int s, T* X, const B
   }
   // preconditioned: after a re-orthonormalisation only rho = <Z, R-bar> is needed
   if ((e = tsqr_groups<T>(L, tp, s, b.R, c->gamma, b.M ? nullptr : c->rho_new, b.tsqr, b.gpart,
-                          &c->counters[kCntC], &c->done, b.cholqr ? &c->tsqr_now : &c->reortho_now)) !=
+                          c->counters[kCntC], &c->done, b.cholqr ? &c->tsqr_now : &c->reortho_now)) !=
       cudaSuccess)
     return e;
   if (b.M) {
     // Z = M^{-1} R-bar and rho_m = R-bar^T Z in one fused operator pass
     Epi<T> pz;
     pz.left = b.R; pz.sym = 1; pz.gram_out = c->rho_m; pz.gpart = b.gpart;
-    pz.counter = &c->counters[kCntA]; pz.done = &c->done;
+    pz.counter = c->counters[kCntA]; pz.done = &c->done;
     pz.status_out = &c->status; pz.stop_out = &c->done;
     prof_begin(L, kPhPrec);
     if constexpr (kF64) {
@@ -348,11 +348,11 @@ cudaError_t bcg_iteration_1r(const Launch& L, const OpDesc& A, int s, T* X, cons
   if ((e = bcg_update<T>(L, A.n, s, b.P, b.Q, X, b.R, c, b.gpart, 1)) != cudaSuccess) return e;
   prof_end(L, kPhUpdate, 2);
   if ((e = tsqr_groups<T>(L, tp, s, b.R, c->gamma, b.M ? nullptr : c->rho_new, b.tsqr, b.gpart,
-                          &c->counters[kCntC], &c->done, &c->reortho_now)) != cudaSuccess) return e;
+                          c->counters[kCntC], &c->done, &c->reortho_now)) != cudaSuccess) return e;
   if (b.M) {
     Epi<T> pz;
     pz.left = b.R; pz.sym = 1; pz.gram_out = c->rho_m; pz.gpart = b.gpart;
-    pz.counter = &c->counters[kCntA]; pz.done = &c->done;
+    pz.counter = c->counters[kCntA]; pz.done = &c->done;
     pz.status_out = &c->status; pz.stop_out = &c->done;
     prof_begin(L, kPhPrec);
     if ((e = spmm<T>(L, *b.M, s, b.R, b.Z, nullptr, pz)) != cudaSuccess) return e;
@@ -361,7 +361,7 @@ cudaError_t bcg_iteration_1r(const Launch& L, const OpDesc& A, int s, T* X, cons
   const T* Zn = b.M ? b.Z : b.R;
   Epi<T> ed;                                      // U = A Z, delta = Z^T U
   ed.left = Zn; ed.sym = 1; ed.gram_out = c->delta; ed.gpart = b.gpart;
-  ed.counter = &c->counters[kCntA]; ed.done = &c->done;
+  ed.counter = c->counters[kCntA]; ed.done = &c->done;
   prof_begin(L, kPhSpmm);
   if ((e = spmm<T>(L, A, s, Zn, b.U, nullptr, ed)) != cudaSuccess) return e;
   prof_end(L, kPhSpmm, 1);
@@ -376,7 +376,7 @@ cudaError_t bcg_iteration_1r(const Launch& L, const OpDesc& A, int s, T* X, cons
   // replacement (the small kernel decided): Q = A P and alpha = P^T Q as in Alg. "2R-CG"
   Epi<T> er;
   er.left = b.P; er.sym = 1; er.gram_out = c->alpha; er.gpart = b.gpart;
-  er.counter = &c->counters[kCntA]; er.done = &c->done; er.only_if = &c->replace_now;
+  er.counter = c->counters[kCntA]; er.done = &c->done; er.only_if = &c->replace_now;
   er.status_out = &c->status; er.stop_out = &c->done;
   prof_begin(L, kPhSpmm);
   e = spmm<T>(L, A, s, b.P, b.Q, nullptr, er);
@@ -464,7 +464,7 @@ int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const
   Epi<T> none;
   BK_TRY(spmm<T>(L, A, s, X, b.R, B, none));
   Epi<T> g;
-  g.sym = 1; g.gram_out = c->rho_new; g.gpart = b.gpart; g.counter = &c->counters[kCntA];
+  g.sym = 1; g.gram_out = c->rho_new; g.gpart = b.gpart; g.counter = c->counters[kCntA];
   BK_TRY(gram<T>(L, n, s, b.R, b.R, g));
   BK_TRY(diag_sqrt(L, s, c->rho_new, c->n0));
   if (o.eta > 0) {
@@ -476,7 +476,7 @@ int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const
     // P^0 = M^{-1} R-bar^0 and rho_m = R-bar^T P^0 (the init kernel takes rho from it
     // after the norms test, which uses the Euclidean Gram above)
     Epi<T> pz;
-    pz.left = b.R; pz.sym = 1; pz.gram_out = c->rho_m; pz.gpart = b.gpart; pz.counter = &c->counters[kCntA];
+    pz.left = b.R; pz.sym = 1; pz.gram_out = c->rho_m; pz.gpart = b.gpart; pz.counter = c->counters[kCntA];
     BK_TRY(spmm<T>(L, *M, s, b.R, b.P, nullptr, pz));
   } else {
     BK_TRY(cudaMemcpyAsync(b.P, b.R, sizeof(T) * (size_t)n * s, cudaMemcpyDeviceToDevice, L.stream));
@@ -484,7 +484,7 @@ int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const
   if (one_r) {
     // Alg. "1R-CG": Q^0 = A P^0 and alpha^0 = <P^0, Q^0> before the loop
     Epi<T> pa;
-    pa.left = b.P; pa.sym = 1; pa.gram_out = c->alpha; pa.gpart = b.gpart; pa.counter = &c->counters[kCntA];
+    pa.left = b.P; pa.sym = 1; pa.gram_out = c->alpha; pa.gpart = b.gpart; pa.counter = c->counters[kCntA];
     BK_TRY(spmm<T>(L, A, s, b.P, b.Q, nullptr, pa));
   }
   BK_TRY(small_bcg_init(L, c, o.eta > 0));
@@ -541,8 +541,8 @@ int bcg_ir_device(bkrylov_handle h, bkrylov_op Aop, int s, const double* B, doub
   float* D32 = bump.take<float>(ns);
   double* nrm = bump.take<double>(2 * kMaxS);
   double* gp = bump.take<double>((size_t)L.sms * 4 * kMaxS + 64);
-  unsigned* cnt = bump.take<unsigned>(4);
-  BK_TRY(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned), L.stream));
+  unsigned* cnt = bump.take<unsigned>(kTicketWords);
+  BK_TRY(cudaMemsetAsync(cnt, 0, kTicketWords * sizeof(unsigned), L.stream));
   cudaEvent_t e0, e1;
   BK_TRY(cudaEventCreate(&e0));
   BK_TRY(cudaEventCreate(&e1));
@@ -656,7 +656,7 @@ int bicg_device(bkrylov_handle h, const OpDesc& A, int s, const double* B, doubl
   Epi<double> none;
   BK_TRY(spmm<double>(L, A, s, X, R, B, none));
   Epi<double> g;
-  g.sym = 1; g.gram_out = c->rho_new; g.gpart = gp; g.counter = &c->counters[kCntA];
+  g.sym = 1; g.gram_out = c->rho_new; g.gpart = gp; g.counter = c->counters[kCntA];
   BK_TRY(gram<double>(L, n, s, R, R, g));
   BK_TRY(diag_sqrt(L, s, c->rho_new, c->n0));
   if (o.eta != 0) BK_TRY(tsqr<double>(L, tp, R, R, c->sigma, nullptr, ts, gp, nullptr, nullptr, nullptr));
@@ -665,7 +665,7 @@ int bicg_device(bkrylov_handle h, const OpDesc& A, int s, const double* B, doubl
   g.gram_out = c->rho;
   BK_TRY(gram<double>(L, n, s, R, R, g));
   Epi<double> g2;
-  g2.sym = 0; g2.gram_out = c->g2; g2.gpart = gp; g2.counter = &c->counters[kCntA];
+  g2.sym = 0; g2.gram_out = c->g2; g2.gpart = gp; g2.counter = c->counters[kCntA];
   BK_TRY(gram<double>(L, n, s, R0, R, g2));
   if (maxit <= 0) {
     // nothing to iterate: report the initial state as not converged
@@ -679,14 +679,14 @@ int bicg_device(bkrylov_handle h, const OpDesc& A, int s, const double* B, doubl
     for (int i = 0; i < todo; ++i) {
       Epi<double> e1p;
       e1p.left = R0; e1p.sym = 0; e1p.gram_out = c->alpha; e1p.gpart = gp;
-      e1p.counter = &c->counters[kCntA]; e1p.done = &c->done;
+      e1p.counter = c->counters[kCntA]; e1p.done = &c->done;
       BK_TRY(spmm<double>(L, A, s, P, Q, nullptr, e1p));                 // Q = A P, R0^T Q
       BK_TRY(small_bicg_1(L, c, fc));
       BK_TRY(bcg_update<double>(L, n, s, P, Q, X, R, c, gp, 0));         // X += P lx ; S = R - Q lam
       BK_TRY(tsqr<double>(L, tp, R, R, c->gamma, nullptr, ts, gp, nullptr, &c->done, &c->reortho_now));
       Epi<double> e3;
       e3.left = R0; e3.sym = 0; e3.gram_out = c->g3; e3.frob = R; e3.frob_out = c->frob;
-      e3.gpart = gp; e3.counter = &c->counters[kCntB]; e3.done = &c->done;
+      e3.gpart = gp; e3.counter = c->counters[kCntB]; e3.done = &c->done;
       BK_TRY(spmm<double>(L, A, s, R, U, nullptr, e3));                  // U = A S, R0^T U, <U,S>, <U,U>
       BK_TRY(small_bicg_2(L, c));
       BK_TRY(bicg_final(L, n, s, R, U, X, P, Q, R0, c, gp));
@@ -777,7 +777,7 @@ int gmres_device(bkrylov_handle h, const OpDesc& A, int s, const double* B, doub
   Epi<double> none;
   BK_TRY(spmm<double>(L, A, s, X, V, B, none));
   Epi<double> g;
-  g.sym = 1; g.gram_out = c->rho_new; g.gpart = gp; g.counter = &c->counters[kCntA];
+  g.sym = 1; g.gram_out = c->rho_new; g.gpart = gp; g.counter = c->counters[kCntA];
   BK_TRY(gram<double>(L, n, s, V, V, g));
   BK_TRY(diag_sqrt(L, s, c->rho_new, c->n0));
   int total = 0;
@@ -806,7 +806,7 @@ int gmres_device(bkrylov_handle h, const OpDesc& A, int s, const double* B, doub
         prof_begin(L, kPhOrtho);
         for (int j = 0; j <= k; ++j) {
           Epi<double> gj;
-          gj.sym = 0; gj.gram_out = Hc + (size_t)j * kMM; gj.gpart = gp; gj.counter = &c->counters[kCntA];
+          gj.sym = 0; gj.gram_out = Hc + (size_t)j * kMM; gj.gpart = gp; gj.counter = c->counters[kCntA];
           BK_TRY(gram<double>(L, n, s, vp[j], W, gj));
           BK_TRY(block_axpy<double>(L, n, s, vp[j], Hc + (size_t)j * kMM, -1.0, W, 1.0, nullptr));
         }
@@ -1202,13 +1202,13 @@ int bkrylov_residual(bkrylov_handle h, bkrylov_op A, int s, const void* B, const
 static int small_scratch(bkrylov_handle h, double** gp, unsigned** cnt, double** res) {
   const Launch L = launch_of(h);
   const size_t gpn = (size_t)L.sms * kCtasPerSm * (kMM + kMM + 8);
-  int rc = ensure_ws(h, 1, sizeof(double) * (gpn + kMM) + 1024);
+  int rc = ensure_ws(h, 1, sizeof(double) * (gpn + kMM) + sizeof(unsigned) * kTicketWords + 1024);
   if (rc) return rc;
   Bump b(h->ws[1], h->ws_cap[1]);
   *gp = b.take<double>(gpn);
   *res = b.take<double>(kMM);
-  *cnt = b.take<unsigned>(8);
-  BK_TRY(cudaMemsetAsync(*cnt, 0, 8 * sizeof(unsigned), h->stream));
+  *cnt = b.take<unsigned>(kTicketWords);
+  BK_TRY(cudaMemsetAsync(*cnt, 0, kTicketWords * sizeof(unsigned), h->stream));
   return BK_OK;
 }
 
@@ -1334,7 +1334,8 @@ int bkrylov_solve_bcg(bkrylov_handle h, bkrylov_op A, int s, const void* B, void
   if (o.prec == BK_FP32_IR) {
     const size_t ns = (size_t)n * s;
     const size_t extra = sizeof(double) * ns + 2 * sizeof(float) * ns +
-                         sizeof(double) * ((size_t)h->sms * 4 * kMaxS + 2 * kMaxS + 64) + 4096;
+                         sizeof(double) * ((size_t)h->sms * 4 * kMaxS + 2 * kMaxS + 64) +
+                         sizeof(unsigned) * kTicketWords + 4096;
     return with_device_blocks<double>(h, n, s, static_cast<const double*>(B), static_cast<double*>(X), extra,
                                       [&](const double* dB, double* dX, size_t off) {
       return bcg_ir_device(h, A, s, dB, dX, o, info, h->ws[1], off);

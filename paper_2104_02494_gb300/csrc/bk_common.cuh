@@ -42,6 +42,10 @@ inline int resident_ctas(K kern, size_t smem) {
 // s x s matrices are stored with row stride kMaxS: M[i][j] at i * kMaxS + j.
 enum : int { kDoneRunning = 0, kDoneConverged = 1, kDoneStopped = 2 };
 enum : int { kCntA = 0, kCntB = 1, kCntC = 2, kCntD = 3, kNumCounters = 8 };
+// Ticket words behind every grid-reduction counter (zero on entry, zero again on exit):
+// word 0 the final ticket, word 1 + g the ticket of CTA group g.
+constexpr int kTicketWords = 128;
+constexpr int kGroupCtas = 16;
 constexpr int kMM = kMaxS * kMaxS;
 
 struct Ctrl {
@@ -69,7 +73,7 @@ struct Ctrl {
   double eps;        // machine epsilon of the working precision
   double omega;      // BBiCGStab scalar
   double frob[4];    // Frobenius sums (BBiCGStab: <U,S>, <U,U>)
-  unsigned counters[kNumCounters];
+  unsigned counters[kNumCounters][kTicketWords];   // grid-reduction tickets
   double n0[kMaxS];      // ||R0_i||
   double relres[kMaxS];
   double alpha[kMM];     // BCG alpha = P^T Q        | BBiCGStab R0s^T Q
@@ -134,39 +138,25 @@ __host__ __device__ inline int ut_index(int a, int c) { return c * (c + 1) / 2 +
 __host__ __device__ inline int ut_count(int s) { return s * (s + 1) / 2; }
 
 // ---- deterministic grid reduction ----------------------------------------------
-// Every CTA stores its `cnt` partial sums (already reduced inside the CTA, in
-// shared memory `part`) to gpart[blockIdx.x * cnt + i].  The last CTA to
-// arrive (atomic ticket) sums the partials of CTA 0, 1, 2, ... in this fixed
-// order, so the result is bitwise reproducible for a given grid.  No thread
-// ever waits for another CTA.  Returns true in the last CTA only; the
-// reduced values are then in `part`.  The ticket counter is reset to 0 by
-// the last CTA for the next use.
-__device__ inline bool grid_reduce_last(double* part, int cnt, double* gpart,
-                                        unsigned* counter) {
-  __shared__ unsigned s_ticket;
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) gpart[(size_t)blockIdx.x * cnt + i] = part[i];
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_ticket = atomicAdd(counter, 1u);
-  __syncthreads();
-  if (s_ticket != gridDim.x - 1) return false;
-  __threadfence();
-  const int G = gridDim.x;
-  // R fixed chunks of CTAs per output (R = blockDim / cnt, at most 8); the
-  // chunk sums are then added in chunk order.
+// Sums gpart[(first + k * step) * cnt + j] over k < count into part[j] (shared memory)
+// in a fixed order: R chunks of k per output (R = blockDim / cnt, at most 8, R * cnt at
+// most kThreads), the chunk sums then added in chunk order.  Ends with a CTA barrier.
+__device__ inline void sum_slots(double* part, int cnt, const double* gpart, int first, int step,
+                                 int count) {
+  __shared__ double s_acc[kThreads];
   int R = (int)blockDim.x / cnt;
   if (R > 8) R = 8;
-  if (R * cnt > kThreads) R = kThreads / cnt;   // s_acc holds kThreads partial sums
+  if (R * cnt > kThreads) R = kThreads / cnt;
   if (R >= 2) {
     double acc = 0.0;
     const int i = threadIdx.x % cnt;
     const int q = threadIdx.x / cnt;
     if (q < R) {
-      int b0 = (int)((long long)G * q / R), b1 = (int)((long long)G * (q + 1) / R);
-      for (int b = b0; b < b1; ++b) acc += ldcg(gpart + (size_t)b * cnt + i);
+      const int k0 = (int)((long long)count * q / R), k1 = (int)((long long)count * (q + 1) / R);
+#pragma unroll 4
+      for (int k = k0; k < k1; ++k) acc += ldcg(gpart + (size_t)(first + k * step) * cnt + i);
+      s_acc[threadIdx.x] = acc;
     }
-    __shared__ double s_acc[kThreads];
-    if (q < R) s_acc[threadIdx.x] = acc;
     __syncthreads();
     if (threadIdx.x < cnt) {
       double t = 0.0;
@@ -176,11 +166,65 @@ __device__ inline bool grid_reduce_last(double* part, int cnt, double* gpart,
   } else {
     for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
       double t = 0.0;
-      for (int b = 0; b < G; ++b) t += ldcg(gpart + (size_t)b * cnt + j);
+#pragma unroll 4
+      for (int k = 0; k < count; ++k) t += ldcg(gpart + (size_t)(first + k * step) * cnt + j);
       part[j] = t;
     }
   }
-  if (threadIdx.x == 0) *counter = 0u;
+  __syncthreads();
+}
+
+// Below this many partial values one level is faster: the second level adds a fence
+// and an atomic round trip (measured on GB300: 152 CTAs x 36 values 8.2 us per launch
+// with one level, 9.2 with two; 152 x 136: 15.4 / 10.2; 152 x 528: 41.0 / 16.4).
+constexpr long long kTreeMinValues = 8192;
+
+// Every CTA stores its `cnt` partial sums (already reduced inside the CTA, in
+// shared memory `part`) to gpart[blockIdx.x * cnt + i].  One level: the last CTA
+// to arrive (atomic ticket) sums the partials of CTA 0, 1, 2, ... in fixed chunks.
+// Two levels, for large grids x cnt: the last CTA of each group of kGroupCtas
+// consecutive CTAs sums its group's partials (in CTA order) into the slot of the
+// group's first CTA, and the last group to finish sums the group sums in group
+// order.  The last CTA's additions run on one SM's FP64 pipe (two per clock on
+// GB300), so a single level of G x cnt additions is the cost the tree splits.
+// Either way the order depends on the grid only: the result is bitwise
+// reproducible for a given grid.  No thread ever waits for another CTA.
+// Returns true in the last CTA only; the reduced values are then in `part`.
+// `counter` points to kTicketWords words, zero on entry; the CTAs that use a
+// word reset it for the next use.  kTree = false keeps one level (for kernels
+// whose registers are at their cap, where the second level's state spills).
+template <bool kTree = true>
+__device__ inline bool grid_reduce_last(double* part, int cnt, double* gpart,
+                                        unsigned* counter) {
+  __shared__ unsigned s_ticket;
+  const int G = gridDim.x;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) gpart[(size_t)blockIdx.x * cnt + i] = part[i];
+  __threadfence();
+  __syncthreads();
+  const int ng = (G + kGroupCtas - 1) / kGroupCtas;
+  const bool tree = kTree && ng >= 2 && ng < kTicketWords && (long long)G * cnt >= kTreeMinValues;
+  // level 1 of the tree: this CTA's group; otherwise the whole grid
+  const int g = tree ? (int)blockIdx.x / kGroupCtas : -1;
+  int first = tree ? g * kGroupCtas : 0, step = 1;
+  int count = tree ? ((G - first < kGroupCtas) ? G - first : kGroupCtas) : G;
+  unsigned* ticket = counter + 1 + g;
+  for (;;) {
+    if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
+    __syncthreads();
+    if (s_ticket != (unsigned)count - 1) return false;
+    __threadfence();
+    sum_slots(part, cnt, gpart, first, step, count);
+    if (threadIdx.x == 0) *ticket = 0u;
+    if (ticket == counter) break;
+    // the group's sum replaces its first CTA's partial; then the ticket of the groups
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) gpart[(size_t)first * cnt + i] = part[i];
+    __threadfence();
+    __syncthreads();
+    ticket = counter;
+    first = 0;
+    step = kGroupCtas;
+    count = ng;
+  }
   __syncthreads();
   return true;
 }

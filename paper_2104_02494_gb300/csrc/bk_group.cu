@@ -150,7 +150,7 @@ update_grp_kernel(int64_t n, int s, int p, const double* __restrict__ P, const d
     double* scratch = part + ((cnt + 1) & ~1);
     __syncthreads();
     cta_reduce_group<SW>(acc, s, p, scratch, part);
-    if (!grid_reduce_last(part, cnt, gpart, &ctrl->counters[kCntB])) return;
+    if (!grid_reduce_last(part, cnt, gpart, ctrl->counters[kCntB])) return;
     unpack_gram(part, s, true, ctrl->rho_new);
   }
 }

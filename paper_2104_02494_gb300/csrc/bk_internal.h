@@ -51,7 +51,7 @@ struct Epi {
   double* gram_out = nullptr;  // s x s result, row stride 32 (device)
   double* frob_out = nullptr;  // [2]: <out,frob>, <out,out> (device)
   double* gpart = nullptr;     // grid partials scratch
-  unsigned* counter = nullptr; // ticket counter (0 on entry)
+  unsigned* counter = nullptr; // kTicketWords ticket words (0 on entry)
   const int* done = nullptr;   // optional stop flag: kernel exits when *done != 0
   const int* only_if = nullptr;  // optional: kernel exits unless *only_if != 0
   int* status_out = nullptr;     // pipelined kernels: BK_TIMEOUT written here if a bounded wait gave up

@@ -315,7 +315,7 @@ __host__ __device__ constexpr size_t qgram_bytes(int cnt, int nconsumers) {
 
 // Grid-wide end of a fused Gram: every thread of the CTA takes part.  A CTA
 // whose pipeline gave up contributes NaN, so the result shows it.
-template <int SW, bool kPair, int NC>
+template <int SW, bool kPair, int NC, bool kTree = true>
 __device__ __forceinline__ void gram_epilogue(QuadGram<SW, kPair>& g, double* part, const double* wslots,
                                               int s, bool sym, bool consumer, bool aborted,
                                               const Epi<float>& ep) {
@@ -326,7 +326,7 @@ __device__ __forceinline__ void gram_epilogue(QuadGram<SW, kPair>& g, double* pa
   if (aborted)
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) part[i] = __longlong_as_double(0x7ff8000000000000ll);
   __syncthreads();
-  if (!grid_reduce_last(part, cnt, ep.gpart, ep.counter)) return;
+  if (!grid_reduce_last<kTree>(part, cnt, ep.gpart, ep.counter)) return;
   unpack_gram(part, s, sym, ep.gram_out);
 }
 
@@ -546,7 +546,8 @@ march4_kernel(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ C
       if (!grid_reduce_last(part, cnt, ep.gpart, ep.counter)) return;
       unpack_gram(part, s, true, ep.gram_out);
     } else {
-      gram_epilogue<SW, true, kNC>(g, part, wslots, s, true, consumer, aborted, ep);
+      // s <= 8: at most 36 values per CTA, where one level is as fast
+      gram_epilogue<SW, true, kNC, false>(g, part, wslots, s, true, consumer, aborted, ep);
     }
   }
 }

@@ -22,8 +22,8 @@ using namespace bk;
 constexpr int kNaMaxCtas = 512;                               // reduction grid limit
 constexpr size_t kNaPartials = (size_t)kNaMaxCtas * kMM;      // partial Grams (<= s*s each)
 constexpr size_t kNaResult = kNaPartials;                     // reduced Gram, row stride 32
-constexpr size_t kNaCounter = kNaPartials + kMM;              // ticket counter slot
-constexpr size_t kNaDoubles = kNaPartials + kMM + 32;
+constexpr size_t kNaCounter = kNaPartials + kMM;              // ticket words (kTicketWords)
+constexpr size_t kNaDoubles = kNaPartials + kMM + kTicketWords / 2;
 
 static __device__ __align__(256) double g_bdot_scratch[kNaDoubles];
 
@@ -65,9 +65,9 @@ extern "C" int bkrylov_bdot_noalloc(int64_t n, int s, const void* X, const void*
   L.stream = static_cast<cudaStream_t>(cuda_stream);
   L.sms = kNaMaxCtas / kCtasPerSm;   // the row kernels launch at most kCtasPerSm * sms CTAs
   unsigned* counter = reinterpret_cast<unsigned*>(scratch + kNaCounter);
-  // the ticket counter must start at zero; the previous call's last CTA reset
-  // it, but a call that failed mid-way might not have
-  if (cudaMemsetAsync(counter, 0, sizeof(unsigned), L.stream) != cudaSuccess) return BK_ERR_CUDA;
+  // the ticket words must start at zero; the previous call's CTAs reset them,
+  // but a call that failed mid-way might not have
+  if (cudaMemsetAsync(counter, 0, sizeof(unsigned) * kTicketWords, L.stream) != cudaSuccess) return BK_ERR_CUDA;
   cudaError_t e;
   if (prec == BK_FP64) {
     Epi<double> ep;

@@ -205,7 +205,7 @@ update4_kernel(int64_t n, int s, const float* __restrict__ P, const float* __res
   }
   if constexpr (kRho) {
     g.cta_reduce(s, true, sp.slots, sp.part, sp.stl, sp.stl);
-    if (!grid_reduce_last(sp.part, cnt, gpart, &ctrl->counters[kCntB])) return;
+    if (!grid_reduce_last(sp.part, cnt, gpart, ctrl->counters[kCntB])) return;
     unpack_gram(sp.part, s, true, ctrl->rho_new);
   }
 }
@@ -285,7 +285,7 @@ update4r_kernel(int64_t n, int s, const float* __restrict__ P, const float* __re
   }
   if constexpr (kRho) {
     g.cta_reduce(s, true, sp.slots, sp.part, sp.stl, sp.stl);
-    if (!grid_reduce_last(sp.part, cnt, gpart, &ctrl->counters[kCntB])) return;
+    if (!grid_reduce_last(sp.part, cnt, gpart, ctrl->counters[kCntB])) return;
     unpack_gram(sp.part, s, true, ctrl->rho_new);
   }
 }

@@ -118,7 +118,7 @@ bcg_update_kernel(int64_t n, int s, const T* __restrict__ P, const T* __restrict
   double* scratch = red + cnt + 1;
   if constexpr (kPair) pg.cta_reduce(s, scratch, part);
   else cta_reduce_gram<SW>(acc, s, true, scratch, part);
-  if (!grid_reduce_last(part, cnt, gpart, &ctrl->counters[kCntB])) return;
+  if (!grid_reduce_last(part, cnt, gpart, ctrl->counters[kCntB])) return;
   unpack_gram(part, s, true, ctrl->rho_new);
 }
 
@@ -326,7 +326,7 @@ cholqr_pass_kernel(int64_t n, int s, double* __restrict__ Y, Ctrl* ctrl, double*
   double* scratch = red + cnt + 1;
   if constexpr (kPair) pg.cta_reduce(s, scratch, part);
   else cta_reduce_gram<SW>(acc, s, true, scratch, part);
-  if (!grid_reduce_last(part, cnt, gpart, &ctrl->counters[kCntC])) return;
+  if (!grid_reduce_last(part, cnt, gpart, ctrl->counters[kCntC])) return;
   unpack_gram(part, s, true, ctrl->rho_new);
 }
 
@@ -783,7 +783,7 @@ bicg_final_kernel(int64_t n, int s, double* __restrict__ S, const double* __rest
   double* scratch = red + c1 + c2 + 1;      // kWarps * c2
   cta_reduce_gram<SW>(a1, s, true, scratch, part);
   cta_reduce_gram<SW>(a2, s, false, scratch, part + c1);
-  if (!grid_reduce_last(part, c1 + c2, gpart, &ctrl->counters[kCntD])) return;
+  if (!grid_reduce_last(part, c1 + c2, gpart, ctrl->counters[kCntD])) return;
   unpack_gram(part, s, true, ctrl->rho);
   unpack_gram(part + c1, s, false, ctrl->g2);
 }
