@@ -62,7 +62,7 @@ FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
 # 79.423 MB written; the FP64 update with the Gram of R-tilde: 536.946 MB read + 226.509 MB
 # written); keyed by (phase, grid, s, operator).
 NCU_TRAFFIC = {("tsqr_leaf_factor", 128, 8, "stencil"): 134.349056e6 + 79.423488e6,
-               ("update_rho", 128, 8, "stencil"): 536.946432e6 + 226.508544e6}
+               ("update_rho", 128, 8, "stencil"): 536.935936e6 + 225.641472e6}
 
 
 def _hbm_peak():

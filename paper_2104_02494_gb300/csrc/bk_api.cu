@@ -491,23 +491,20 @@ int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const
   Launch Lp = L;
   if (o.profile) Lp.prof = &h->prof;
   int batch = o.sync_every > 0 ? o.sync_every : (n >= (1 << 20) ? 4 : 16);
-  // Small problems are bound by kernel launches: after the first batch (which
-  // also settles every kernel's launch attributes), a batch of iterations is
-  // captured once as a CUDA graph on a private stream and replayed on the
-  // handle's stream.  The iteration has no host-side branch (every decision is
-  // in the control block), so the replay is the same kernel sequence.
-  const bool use_graph = !o.profile && (size_t)n * s <= ((size_t)1 << 20) && maxit > 2 * batch;
+  // After the first batch (which also settles every kernel's launch attributes),
+  // a batch of iterations is captured once as a CUDA graph on a private stream
+  // and replayed on the handle's stream: small problems are bound by kernel
+  // launches, and at every size the kernels that a device flag turns into
+  // no-ops (the gated TSQR) cost a launch each.  The iteration has no host-side
+  // branch (every decision is in the control block), so the replay is the same
+  // kernel sequence.  Profiled solves launch directly (per-phase events).
+  const bool use_graph = !o.profile && maxit > 2 * batch;
   GraphBatch gb;
   int enq = 0;
   while (true) {
     if ((rc = ctrl_peek(h, c))) return rc;
     if (h->host_ctrl->done != kDoneRunning || enq >= maxit) break;
     const int todo = (maxit - enq) < batch ? (maxit - enq) : batch;
-    if (use_graph && !gb.failed && enq > 0 && todo == batch && !gb.exec) {
-      // a capture that the runtime refuses leaves the direct launches below in charge
-      if (gb.capture(h, batch, [&](const Launch& Lc) { return (one_r ? bcg_iteration_1r<T>(Lc, A, s, X, b, tp) : bcg_iteration<T>(Lc, A, s, X, b, tp)); }))
-        gb.failed = true;
-    }
     if (gb.exec && todo == batch) {
       BK_TRY(cudaGraphLaunch(gb.exec, L.stream));
     } else {
@@ -517,6 +514,13 @@ int bcg_device(bkrylov_handle h, const OpDesc& A, int s, const T* B, T* X, const
       }
     }
     enq += todo;
+    // capture the graph while the device runs the first batch (the capture only
+    // records launches); a capture that the runtime refuses leaves the direct
+    // launches in charge
+    if (use_graph && !gb.failed && !gb.exec && maxit - enq >= batch) {
+      if (gb.capture(h, batch, [&](const Launch& Lc) { return (one_r ? bcg_iteration_1r<T>(Lc, A, s, X, b, tp) : bcg_iteration<T>(Lc, A, s, X, b, tp)); }))
+        gb.failed = true;
+    }
   }
   BK_TRY(cudaEventRecord(e1, L.stream));
   BK_TRY(cudaEventSynchronize(e1));
