@@ -243,7 +243,7 @@ int bkrylov_bdot(bkrylov_handle h, int64_t n, int s, const void* X, const void* 
    device memory up front, or a loop where an allocation could block or fail).  The thesis
    has no counterpart: this is a deployment variant of the block inner product above.
    No handle: the call allocates nothing (no cudaMalloc/cudaFree, no allocating library
-   routine).  Its scratch (per-CTA partial sums, the reduced matrix, the ticket counter)
+   routine).  Its scratch (per-CTA partial sums, the reduced matrix, the ticket words)
    is one file-scope device array of 4.2 MB that every GPU loading the library keeps
    until the process exits; the reduction grid is limited to 512 CTAs (any n works).
    X, Y: n x s device blocks (prec BK_FP64 or BK_FP32); G: s x s device doubles.

@@ -1201,7 +1201,7 @@ int bkrylov_residual(bkrylov_handle h, bkrylov_op A, int s, const void* B, const
   return BK_OK;
 }
 
-// Scratch of the single-kernel entry points: grid partials + ticket counter +
+// Scratch of the single-kernel entry points: grid partials + ticket words +
 // a ctrl-layout result matrix, in workspace 1.
 static int small_scratch(bkrylov_handle h, double** gp, unsigned** cnt, double** res) {
   const Launch L = launch_of(h);

@@ -7,7 +7,7 @@
 // only its own buffers), or a latency-critical loop in which an allocation
 // could block or fail.  This entry point serves them: the caller passes the
 // inputs, the output and a stream, and every piece of scratch (per-CTA
-// partial sums, the reduced s x s matrix, the ticket counter of the
+// partial sums, the reduced s x s matrix, the ticket words of the
 // last-CTA reduction) lives in the file-scope device array below, which every
 // GPU that loads the library keeps until the process exits (4.2 MB).
 #include <mutex>
