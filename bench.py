@@ -96,6 +96,8 @@ def parse():
                    help="per-phase device time of FP32+IR and FP64 BCG iterations on --workload")
     p.add_argument("--micro", action="store_true",
                    help="stand-alone FP32 operator product and block inner product timings")
+    p.add_argument("--micro-case", default=None,
+                   help="with --micro: one case only, as workload:s (e.g. laplace3d:8)")
     p.add_argument("--workload", default=None, help="workload of --probe / --phases")
     p.add_argument("--maxit", type=int, default=3)
     p.add_argument("--eta", type=float, default=math.inf,
@@ -445,6 +447,11 @@ def run_micro(args):
     out = {"hbm_peak_gbs": HBM_PEAK_GBS, "l2": "flushed before every timed launch"}
     cases = [("laplace3d", 8, 128), ("laplace3d", 16, 128), ("laplace3d", 32, 128), ("vardiff3d", 8, 192),
              ("vardiff3d", 16, 192)]
+    if args.micro_case:
+        kind, s = args.micro_case.split(":")
+        cases = [c for c in cases if c[0] == kind and c[1] == int(s)]
+        if not cases:
+            raise SystemExit(f"no micro case {args.micro_case!r}")
     for kind, s, grid in cases:
         prob = W.problem(kind, s=s, grid=grid if args.grid == 128 else args.grid, with_csr=False)
         op = operator_from_problem(h, prob, "stencil")
