@@ -688,19 +688,13 @@ stream4_kernel(const float* __restrict__ X, const float* __restrict__ Y, const f
 // ------------------------------------------------- row-per-lane streaming ----
 // G = X^T Y (Y = X when !two), or Z = diag(w) X with G = X^T Z (kMode 1), for
 // s = 4, 8, 16.  A stage is R = 192 nbox rows of each operand, copied as nbox
-// swizzled boxes of 192 rows (rows past n arrive as zeros); the consumer warps
+// swizzled boxes of 192 rows (rows past n arrive as zeros); six consumer warps
 // take the stage's 32-row groups, warp w computing Gram class w % NCLS.
 // Consumer warps: 9 (three warps of each of three Gram classes at s = 16, or one
-// class at s = 8 with the full Gram), 6 for the full 16-column Gram, whose larger
-// classes need the registers of fewer warps; 11 where one class fits the 168
-// registers of a 384-thread CTA (s = 4, and the symmetric Gram at s = 8): the
-// consumers are latency-bound on their own FMA chains and shared-memory loads, so
-// more warps hide more of it.  With one class the 32-row groups are dealt
-// round-robin across stages, so the count need not divide a stage's groups.
+// class), 6 for the full 16-column Gram, whose larger classes need the registers
+// of fewer warps.
 template <int SW, bool kSym>
-__host__ __device__ constexpr int rconsumers() {
-  return (SW == 16 && !kSym) ? 6 : ((SW == 4 || (SW == 8 && kSym)) ? 11 : 9);
-}
+__host__ __device__ constexpr int rconsumers() { return (SW == 16 && !kSym) ? 6 : 9; }
 constexpr int kBoxRows = 192;
 
 struct RStreamArgs {
@@ -741,10 +735,7 @@ __device__ __forceinline__ bool rstream_consume(const RStreamArgs& a, const floa
     const int64_t base = (blockIdx.x + i * gridDim.x) * (int64_t)a.R;
     const float* sx = ring + (size_t)slot * a.stage_floats;
     const float* sy = a.two ? sx + a.op_floats : sx;
-    // one class: warp w takes the CTA's global group indices w, w + NC, ... (the
-    // groups of chunk i start at i * ngroups); several classes: a static deal
-    const int g0 = C::NCLS == 1 ? (wic - (int)((i * ngroups) % wpc) + wpc) % wpc : wic;
-    for (int grp = g0; grp < ngroups; grp += wpc) {
+    for (int grp = wic; grp < ngroups; grp += wpc) {
       const int r = grp * 32 + lane;
       float4 l[LPR], m[LPR];
 #pragma unroll
@@ -1115,8 +1106,7 @@ cudaError_t rstream_launch(const Launch& L, int64_t n, const float* X, const flo
   a.n = n;
   a.s = SW;
   // 18-24 KB of each operand per stage, its 6 nbox 32-row groups a multiple of the
-  // warps of a class where several classes share a stage (3 with three classes, 2 for
-  // the full 16-column Gram); one class deals them round-robin
+  // warps of a class (3 with three classes, 9 with one, 2 for the full 16-column Gram)
   a.nbox = SW == 4 ? 6 : (SW == 8 ? 3 : 2);
   a.R = kBoxRows * a.nbox;
   a.nchunks = (n + a.R - 1) / a.R;
