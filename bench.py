@@ -380,9 +380,9 @@ def _diag_setup(args, workload, s_default):
     from paper_2104_02494_gb300.api import Handle, operator_from_problem
     build()
     s = args.s if args.s != 8 or workload == "laplace3d" else s_default
-    prob = W.problem(workload, s=s, grid=args.grid, with_csr=False)
+    prob = W.problem(workload, s=s, grid=args.grid, with_csr=(args.op == "csr"))
     h = Handle(0)
-    op = operator_from_problem(h, prob, "stencil")
+    op = operator_from_problem(h, prob, args.op)
     return h, op, prob, torch.from_numpy(prob.B).cuda(), torch
 
 
